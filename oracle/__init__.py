@@ -1,0 +1,226 @@
+"""FP64 CPU oracle for the S1xR2 StePS hot path (arXiv 2602.20787).
+
+TEST INFRASTRUCTURE ONLY. The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers. The product path (the
+CUDA library and its binding) never imports this package, and this package
+never imports the product: the two share no code. The only module both sides
+read is the seeded input generator ``paper_2602_20787_gb300.ics``, which holds
+no force, integrator or surrogate arithmetic.
+
+The C source ``steps_oracle.c`` is compiled with gcc into ``liboracle.so`` next
+to it (``build()``); this module wraps it with ctypes and adds numpy-facing
+helpers. Each wrapper names the equation of the paper it evaluates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "steps_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MLP_HIDDEN = 32
+MLP_NW = MLP_HIDDEN * 3 + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + 2 * MLP_HIDDEN + 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP). Returns the library path."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "steps_oracle.h")))
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True, cwd=_HERE)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cosmo(ctypes.Structure):
+    """Eqs. Friedmann / DEdensity / CPLw0wa parameters; comoving=0 is static space."""
+    _fields_ = [("H0", ctypes.c_double), ("Omega_m", ctypes.c_double), ("Omega_r", ctypes.c_double),
+                ("Omega_L", ctypes.c_double), ("w0", ctypes.c_double), ("wa", ctypes.c_double),
+                ("comoving", ctypes.c_int32)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        d, i32, i64, p = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        L.or_spline_F.argtypes = [d, d]; L.or_spline_F.restype = d
+        L.or_spline_F_over_r.argtypes = [d, d]; L.or_spline_F_over_r.restype = d
+        L.or_image_force.argtypes = [d, d, d, d, d, i32, p]; L.or_image_force.restype = ctypes.c_int
+        L.or_pair_field.argtypes = [i64, p, p, p, p, p, d, d, i32, i64, p, p, p, p]
+        L.or_pair_field.restype = None
+        L.or_cylinder_field.argtypes = [d, d, d, d, d]; L.or_cylinder_field.restype = d
+        L.or_background_field.argtypes = [i64, p, p, d, d, d, d, p, p]
+        L.or_background_field.restype = None
+        L.or_hubble.argtypes = [ctypes.POINTER(Cosmo), d]; L.or_hubble.restype = d
+        L.or_a_of_t_step.argtypes = [ctypes.POINTER(Cosmo), d, d]; L.or_a_of_t_step.restype = d
+        L.or_kdk_factors.argtypes = [ctypes.POINTER(Cosmo), d, d, p, p, p, p]
+        L.or_kdk_factors.restype = None
+        L.or_kdk.argtypes = [i64, p, p, p, p, p, p, p, p, d, d, i32, d, d, i32,
+                             ctypes.POINTER(Cosmo), p, p, d, i32]
+        L.or_kdk.restype = ctypes.c_int
+        L.or_tail_sums.argtypes = [d, d, d, d, i32, i32, p, p]; L.or_tail_sums.restype = None
+        L.or_mlp_forward.argtypes = [p, p, p]; L.or_mlp_forward.restype = None
+        L.or_mlp_loss_grad.argtypes = [p, i64, p, p, p]; L.or_mlp_loss_grad.restype = d
+        L.or_adam_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]; L.or_adam_step.restype = None
+        L.or_num_threads.argtypes = []; L.or_num_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def spline_F(r: float, h: float) -> float:
+    """Eq. Force_spline_kernel."""
+    return lib().or_spline_F(float(r), float(h))
+
+
+def spline_F_over_r(r: float, h: float) -> float:
+    """Eq. Force_spline_kernel divided by r (finite at r = 0)."""
+    return lib().or_spline_F_over_r(float(r), float(h))
+
+
+def image_force(r, h: float, L: float, n_cut: int):
+    """Eq. ForceCylindrical per unit G. Returns (force[3], images used)."""
+    out = np.zeros(3)
+    cnt = lib().or_image_force(float(r[0]), float(r[1]), float(r[2]), float(h), float(L), int(n_cut),
+                               _ptr(out))
+    return out, cnt
+
+
+def pair_field(pos, m, h, G: float, L: float, n_cut: int, idx=None):
+    """Pair term of eq. ComovingEquationsOfMotionCylindrical times a^3 (no 1/a^3).
+
+    pos: (N, 3) with z in [0, L). idx: optional subset of i. Returns (len(idx), 3).
+    """
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], _ptr(idx)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    lib().or_pair_field(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), int(n_cut),
+                        ni, ip, _ptr(gx), _ptr(gy), _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)
+
+
+def cylinder_field(varrho: float, R: float, Lw: float, G: float = 1.0, rho0: float = 1.0) -> float:
+    """Eq. F_horiz (re-derived reading): radial mid-plane field of a finite cylinder."""
+    return lib().or_cylinder_field(float(varrho), float(R), float(Lw), float(G), float(rho0))
+
+
+def background_field(pos, R: float, Lw: float, G: float, rho0: float, mode: int = 1):
+    """-F_h(rho) rho_hat (times a^3). mode 1: eq. F_horiz, 2: eq. F_horiz_infty, 0: off."""
+    n = pos.shape[0]
+    out = np.zeros((n, 3))
+    if mode == 0:
+        return out
+    x, y = _f64(pos[:, 0]), _f64(pos[:, 1])
+    if mode == 1:
+        gx, gy = np.zeros(n), np.zeros(n)
+        lib().or_background_field(n, _ptr(x), _ptr(y), float(R), float(Lw), float(G), float(rho0),
+                                  _ptr(gx), _ptr(gy))
+        out[:, 0], out[:, 1] = gx, gy
+        return out
+    rho = np.hypot(x, y)
+    F = np.where(rho <= R, -2 * np.pi * G * rho0 * rho, -2 * np.pi * G * rho0 * R * R / np.maximum(rho, 1e-300))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out[:, 0] = np.where(rho > 0, -F * x / rho, 0.0)
+        out[:, 1] = np.where(rho > 0, -F * y / rho, 0.0)
+    return out
+
+
+def make_cosmo(H0=1.0, Omega_m=0.3, Omega_L=0.7, Omega_r=0.0, w0=-1.0, wa=0.0, comoving=True):
+    return Cosmo(float(H0), float(Omega_m), float(Omega_r), float(Omega_L), float(w0), float(wa),
+                 1 if comoving else 0)
+
+
+def hubble(c: Cosmo, a: float) -> float:
+    """Eq. Friedmann: H(a)."""
+    return lib().or_hubble(ctypes.byref(c), float(a))
+
+
+def a_step(c: Cosmo, a: float, dt: float) -> float:
+    """One RK4 step of da/dt = a H(a) (Sect. 2.3)."""
+    return lib().or_a_of_t_step(ctypes.byref(c), float(a), float(dt))
+
+
+def kdk_factors(c: Cosmo, a: float, dt: float):
+    """(K1, D, K2, a_next): Int dt/a over each half step and Int dt/a^2 over the step."""
+    out = np.zeros(4)
+    lib().or_kdk_factors(ctypes.byref(c), float(a), float(dt), _ptr(out[0:]), _ptr(out[1:]),
+                         _ptr(out[2:]), _ptr(out[3:]))
+    return tuple(float(v) for v in out)
+
+
+def kdk(pos, vel_p, m, h, G, L, n_cut, R_bg, rho0, background, c: Cosmo, a, t, dt, nsteps):
+    """KDK leapfrog (Sect. 2.1) on canonical momenta p = a^2 dx/dt. Returns (pos, p, a, t)."""
+    x, y, z = (_f64(pos[:, k]).copy() for k in range(3))
+    px, py, pz = (_f64(vel_p[:, k]).copy() for k in range(3))
+    m = _f64(m); h = _f64(h)
+    a_ = ctypes.c_double(a); t_ = ctypes.c_double(t)
+    rc = lib().or_kdk(x.shape[0], _ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py), _ptr(pz), _ptr(m), _ptr(h),
+                      float(G), float(L), int(n_cut), float(R_bg), float(rho0), int(background),
+                      ctypes.byref(c), ctypes.byref(a_), ctypes.byref(t_), float(dt), int(nsteps))
+    if rc != 0:
+        raise MemoryError("oracle KDK allocation failed")
+    return np.stack([x, y, z], 1), np.stack([px, py, pz], 1), a_.value, t_.value
+
+
+def tail_sums(dR, dzw, h, L, n_cut, n0):
+    """Far-image tail (|k| > n0) of eq. ForceCylindrical in the wrapped frame: (SR, Sz)."""
+    SR, Sz = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_sums(float(dR), float(dzw), float(h), float(L), int(n_cut), int(n0),
+                       ctypes.byref(SR), ctypes.byref(Sz))
+    return SR.value, Sz.value
+
+
+def mlp_forward(w, u):
+    """3 -> 32 -> 32 -> 2 ReLU MLP in FP64. u: (3,) or (ns, 3)."""
+    w = _f64(w)
+    u = np.atleast_2d(_f64(u))
+    y = np.zeros((u.shape[0], 2))
+    for s in range(u.shape[0]):
+        us = np.ascontiguousarray(u[s]); ys = np.zeros(2)
+        lib().or_mlp_forward(_ptr(w), _ptr(us), _ptr(ys))
+        y[s] = ys
+    return y
+
+
+def mlp_loss_grad(w, u, t):
+    """Loss 1/(2ns) sum (y - t)^2 and its gradient by backpropagation (FP64)."""
+    w = _f64(w); u = _f64(u); t = _f64(t)
+    g = np.zeros(MLP_NW)
+    loss = lib().or_mlp_loss_grad(_ptr(w), u.shape[0], _ptr(u), _ptr(t), _ptr(g))
+    return loss, g
+
+
+def adam_step(w, g, m1, m2, lr, beta1, beta2, eps, step):
+    """In-place Adam update (FP64)."""
+    lib().or_adam_step(w.shape[0], _ptr(w), _ptr(_f64(g)), _ptr(m1), _ptr(m2), float(lr), float(beta1),
+                       float(beta2), float(eps), int(step))

@@ -1,0 +1,413 @@
+/*
+ * FP64 CPU oracle for the S1xR2 StePS hot path (arXiv 2602.20787).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path. It shares no code
+ * with the CUDA library. It is written to be read against the paper: plain
+ * loops, FP64, no blocking or reordering beyond what the definitions state.
+ * j-sums are Neumaier-compensated in double so that the result is the
+ * definition up to rounding (no long double: it is software quad on aarch64).
+ *
+ * Readings of the paper taken here (each is also listed in the design doc):
+ *  - Eq. Force_spline_kernel: the "-\\-" inside the middle branch is a LaTeX
+ *    line break, i.e. a single minus sign. h is the support radius (Newtonian
+ *    for r >= h) and the pair uses h_i + h_j (eq. ComovingEquationsOfMotion).
+ *  - Eq. ForceCylindrical: images n in [-Ncut, Ncut] with |r_z - n L| < Ncut L
+ *    (strict), r_z the raw difference of z in [0, L).
+ *  - Eq. F_horiz is garbled; it is re-derived as the mid-plane radial field of a
+ *    homogeneous cylinder of radius R, z in [-Lw, Lw], Lw = Ncut L:
+ *      F(rho) = 2 G rho0 Int_0^R [ 2 ln((sqrt(Lw^2+A)+Lw)/(sqrt(Lw^2+B)+Lw)) - ln(A/B) ] dY,
+ *      A,B = R^2 + rho^2 +- 2 rho sqrt(R^2 - Y^2).
+ *    It tends to eq. F_horiz_infty (-2 pi G rho0 rho) as Lw -> inf and is 0 at Lw = 0.
+ *  - Eq. ComovingEquationsOfMotionCylindrical: the background term carries the
+ *    same 1/a^3 as the pair term (rho0 is the comoving mean density), so that a
+ *    homogeneous load feels no force in comoving coordinates (Sect. 2.1).
+ *  - KDK in cosmic time (Sect. 2.1) with canonical momentum p = a^2 dx/dt:
+ *    dp/dt = g/a, dx/dt = p/a^2 with g = a^3 (pair + background), which is the
+ *    comoving EOM with the Hubble drag absorbed exactly. Kick factors are
+ *    Int dt/a over each half step, the drift factor Int dt/a^2 over the step,
+ *    all integrated together with a(t) by RK4 (Sect. 2.3) in two half steps.
+ */
+#include "steps_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+int32_t or_num_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. Force_spline_kernel: softened force magnitude F(r, h).
+ * ------------------------------------------------------------------------- */
+double or_spline_F(double r, double h) {
+  if (r >= h) return 1.0 / (r * r);
+  double h3 = h * h * h, h4 = h3 * h, h5 = h4 * h, h6 = h5 * h;
+  double r2 = r * r, r3 = r2 * r, r4 = r3 * r;
+  if (r < 0.5 * h) return 32.0 * r4 / h6 - 38.4 * r3 / h5 + 32.0 * r / (3.0 * h3);
+  return -32.0 * r4 / (3.0 * h6) + 38.4 * r3 / h5 - 48.0 * r2 / h4 + 64.0 * r / (3.0 * h3) -
+         1.0 / (15.0 * r2);
+}
+
+/* F(r, h) / r, written out so that it stays finite at r = 0 (value 32/(3h^3)). */
+double or_spline_F_over_r(double r, double h) {
+  if (r >= h) return 1.0 / (r * r * r);
+  double h3 = h * h * h, h4 = h3 * h, h5 = h4 * h, h6 = h5 * h;
+  double r2 = r * r, r3 = r2 * r;
+  if (r < 0.5 * h) return 32.0 * r3 / h6 - 38.4 * r2 / h5 + 32.0 / (3.0 * h3);
+  return -32.0 * r3 / (3.0 * h6) + 38.4 * r2 / h5 - 48.0 * r / h4 + 64.0 / (3.0 * h3) -
+         1.0 / (15.0 * r3);
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. ForceCylindrical per unit G: out = -sum_n F(|r_n|,h) r_n/|r_n|,
+ * r_n = r - n L e_z, n in [-Ncut, Ncut], |r_z - n L| < Ncut L.
+ * Returns the number of images used.
+ * ------------------------------------------------------------------------- */
+int or_image_force(double rx, double ry, double rz, double h, double L, int32_t n_cut,
+                   double out[3]) {
+  int count = 0;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int n = -n_cut; n <= n_cut; ++n) {
+    double dz = rz - (double)n * L;
+    if (!(fabs(dz) < (double)n_cut * L)) continue;
+    double r = sqrt(rx * rx + ry * ry + dz * dz);
+    double f = or_spline_F_over_r(r, h);
+    out[0] -= f * rx;
+    out[1] -= f * ry;
+    out[2] -= f * dz;
+    ++count;
+  }
+  return count;
+}
+
+/* Neumaier compensated accumulation. */
+typedef struct { double s, c; } or_sum;
+static inline void or_add(or_sum* a, double v) {
+  double t = a->s + v;
+  if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+  else a->c += (v - t) + a->s;
+  a->s = t;
+}
+
+/* ---------------------------------------------------------------------------
+ * Pair term of eq. ComovingEquationsOfMotionCylindrical times a^3:
+ *   g_i = G sum_{j != i} m_j F_S1R2(x_i - x_j, h_i + h_j).
+ * idx == NULL evaluates every i (ni must equal n); otherwise the listed i.
+ * ------------------------------------------------------------------------- */
+void or_pair_field(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                   const double* h, double G, double L, int32_t n_cut, int64_t ni,
+                   const int64_t* idx, double* gx, double* gy, double* gz) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t q = 0; q < ni; ++q) {
+    int64_t i = idx ? idx[q] : q;
+    or_sum sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double f[3];
+      or_image_force(x[i] - x[j], y[i] - y[j], z[i] - z[j], h[i] + h[j], L, n_cut, f);
+      or_add(&sx, G * m[j] * f[0]);
+      or_add(&sy, G * m[j] * f[1]);
+      or_add(&sz, G * m[j] * f[2]);
+    }
+    gx[q] = sx.s + sx.c;
+    gy[q] = sy.s + sy.c;
+    gz[q] = sz.s + sz.c;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Background field (eq. F_horiz, re-derived; see header). The Y integral is
+ * taken in theta with Y = R sin(theta), which removes the square-root endpoint
+ * behaviour at Y = R; what is left is a log singularity at theta = 0 when
+ * rho = R, which adaptive Gauss-Legendre handles (no endpoint evaluations).
+ * ------------------------------------------------------------------------- */
+static double or_cyl_integrand(double th, double rho, double R, double Lw) {
+  /* A, B = R^2 + rho^2 +- 2 rho R cos(theta), written as (R +- rho)^2 -+ 4 rho R sin^2(theta/2)
+   * so that B keeps full relative precision when rho is close to R. */
+  double s2 = sin(0.5 * th);
+  double q = 4.0 * rho * R * s2 * s2;
+  double A = (R + rho) * (R + rho) - q;
+  double B = (R - rho) * (R - rho) + q;
+  double finite = 2.0 * log((sqrt(Lw * Lw + A) + Lw) / (sqrt(Lw * Lw + B) + Lw));
+  double inf = log(A / B);
+  return (finite - inf) * R * cos(th); /* dY = R cos(theta) dtheta */
+}
+
+static const double or_gl_x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                                  -0.1834346424956498, 0.1834346424956498,  0.5255324099163290,
+                                  0.7966664774136267,  0.9602898564975363};
+static const double or_gl_w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                                  0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                                  0.2223810344533745, 0.1012285362903763};
+
+/* 8-point Gauss-Legendre on [a, b]; *absint receives the same rule applied to |f|. */
+static double or_gl8(double a, double b, double rho, double R, double Lw, double* absint) {
+  double mid = 0.5 * (a + b), half = 0.5 * (b - a), s = 0.0, sa = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    double f = or_cyl_integrand(mid + half * or_gl_x[k], rho, R, Lw);
+    s += or_gl_w[k] * f;
+    sa += or_gl_w[k] * fabs(f);
+  }
+  *absint = sa * half;
+  return s * half;
+}
+
+/* Adaptive bisection. Tolerance: 1e-14 R per unit length of theta (total error
+ * below 1e-14 R pi/2), floored at the rounding level of the rule itself so that
+ * the recursion always ends; only an interval that touches the log
+ * singularity at theta = 0 (rho = R) keeps splitting, so depth grows linearly. */
+static double or_adapt(double a, double b, double whole, double rho, double R, double Lw,
+                       int depth) {
+  double m = 0.5 * (a + b), al, ar;
+  double l = or_gl8(a, m, rho, R, Lw, &al), r = or_gl8(m, b, rho, R, Lw, &ar);
+  double tol = 1e-14 * R * (b - a);
+  double floor_ = 64.0 * 2.220446049250313e-16 * (al + ar);
+  if (tol < floor_) tol = floor_;
+  if (depth <= 0 || fabs(l + r - whole) <= tol) return l + r;
+  return or_adapt(a, m, l, rho, R, Lw, depth - 1) + or_adapt(m, b, r, rho, R, Lw, depth - 1);
+}
+
+double or_cylinder_field(double varrho, double R, double Lw, double G, double rho0) {
+  if (varrho <= 0.0) return 0.0;
+  double a = 0.0, b = 0.5 * OR_PI, ab;
+  double I = or_adapt(a, b, or_gl8(a, b, varrho, R, Lw, &ab), varrho, R, Lw, 60);
+  return 2.0 * G * rho0 * I;
+}
+
+/* Background acceleration of eq. ComovingEquationsOfMotionCylindrical (times a^3):
+ * -F_h(rho) along the radial unit vector (F_h < 0, so it points outward). */
+void or_background_field(int64_t ni, const double* x, const double* y, double R, double Lw,
+                         double G, double rho0, double* gx, double* gy) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < ni; ++q) {
+    double rho = sqrt(x[q] * x[q] + y[q] * y[q]);
+    if (rho <= 0.0) { gx[q] = gy[q] = 0.0; continue; }
+    double F = or_cylinder_field(rho, R, Lw, G, rho0);
+    gx[q] = -F * x[q] / rho;
+    gy[q] = -F * y[q] / rho;
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Eqs. Friedmann, DEdensity, CPLw0wa. The DEdensity integral of the CPL w(a)
+ * is elementary: Int_1^a (1 + w0 + wa (1 - a'))/a' da' = (1+w0+wa) ln a - wa (a-1).
+ * ------------------------------------------------------------------------- */
+double or_hubble(const or_cosmo* c, double a) {
+  double Ok = 1.0 - c->Omega_m - c->Omega_r - c->Omega_L;
+  double ode = c->Omega_L * exp(-3.0 * ((1.0 + c->w0 + c->wa) * log(a) - c->wa * (a - 1.0)));
+  double E2 = c->Omega_r / (a * a * a * a) + c->Omega_m / (a * a * a) + Ok / (a * a) + ode;
+  return c->H0 * sqrt(E2);
+}
+
+/* One RK4 step of the autonomous system y = (a, Int dt/a, Int dt/a^2). */
+static void or_rk4_aug(const or_cosmo* c, double y[3], double dt) {
+  double k[4][3], s[3];
+  for (int st = 0; st < 4; ++st) {
+    double f = (st == 0) ? 0.0 : (st == 3 ? 1.0 : 0.5);
+    for (int q = 0; q < 3; ++q) s[q] = y[q] + (st == 0 ? 0.0 : f * dt * k[st - 1][q]);
+    double a = s[0];
+    k[st][0] = a * or_hubble(c, a);
+    k[st][1] = 1.0 / a;
+    k[st][2] = 1.0 / (a * a);
+  }
+  for (int q = 0; q < 3; ++q) y[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
+}
+
+double or_a_of_t_step(const or_cosmo* c, double a, double dt) {
+  double y[3] = {a, 0.0, 0.0};
+  or_rk4_aug(c, y, dt);
+  return y[0];
+}
+
+void or_kdk_factors(const or_cosmo* c, double a, double dt, double* K1, double* D, double* K2,
+                    double* a_next) {
+  if (!c->comoving) {
+    *K1 = 0.5 * dt; *K2 = 0.5 * dt; *D = dt; *a_next = 1.0;
+    return;
+  }
+  double y1[3] = {a, 0.0, 0.0};
+  or_rk4_aug(c, y1, 0.5 * dt);
+  double y2[3] = {y1[0], 0.0, 0.0};
+  or_rk4_aug(c, y2, 0.5 * dt);
+  *K1 = y1[1];
+  *K2 = y2[1];
+  *D = y1[2] + y2[2];
+  *a_next = y2[0];
+}
+
+/* Total comoving field g = a^3 (pair + background) at the current positions. */
+static void or_total_field(int64_t n, const double* x, const double* y, const double* z,
+                           const double* m, const double* h, double G, double L, int32_t n_cut,
+                           double R_bg, double rho0, int32_t background, double* gx, double* gy,
+                           double* gz) {
+  or_pair_field(n, x, y, z, m, h, G, L, n_cut, n, NULL, gx, gy, gz);
+  if (background == 0) return;
+  double* bx = (double*)malloc(sizeof(double) * (size_t)n);
+  double* by = (double*)malloc(sizeof(double) * (size_t)n);
+  if (background == 1) {
+    or_background_field(n, x, y, R_bg, (double)n_cut * L, G, rho0, bx, by);
+  } else {
+    /* eq. F_horiz_infty inside the cylinder; the infinite cylinder's exterior field outside */
+    for (int64_t i = 0; i < n; ++i) {
+      double rho = sqrt(x[i] * x[i] + y[i] * y[i]);
+      double F = rho <= R_bg ? -2.0 * OR_PI * G * rho0 * rho
+                             : -2.0 * OR_PI * G * rho0 * R_bg * R_bg / rho;
+      bx[i] = rho > 0 ? -F * x[i] / rho : 0.0;
+      by[i] = rho > 0 ? -F * y[i] / rho : 0.0;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) { gx[i] += bx[i]; gy[i] += by[i]; }
+  free(bx);
+  free(by);
+}
+
+/* KDK leapfrog in cosmic time on (x, p), p = a^2 dx/dt. z is kept in [0, L). */
+int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
+           const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
+           double rho0, int32_t background, const or_cosmo* c, double* a, double* t, double dt,
+           int32_t nsteps) {
+  double* gx = (double*)malloc(sizeof(double) * (size_t)n);
+  double* gy = (double*)malloc(sizeof(double) * (size_t)n);
+  double* gz = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!gx || !gy || !gz) { free(gx); free(gy); free(gz); return -1; }
+  or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, gx, gy, gz);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    double K1, D, K2, an;
+    or_kdk_factors(c, *a, dt, &K1, &D, &K2, &an);
+    for (int64_t i = 0; i < n; ++i) {
+      px[i] += gx[i] * K1; py[i] += gy[i] * K1; pz[i] += gz[i] * K1;
+      x[i] += px[i] * D; y[i] += py[i] * D; z[i] += pz[i] * D;
+      z[i] -= L * floor(z[i] / L);
+      if (z[i] >= L) z[i] -= L; /* floor rounding can leave z == L */
+    }
+    or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, gx, gy, gz);
+    for (int64_t i = 0; i < n; ++i) { px[i] += gx[i] * K2; py[i] += gy[i] * K2; pz[i] += gz[i] * K2; }
+    *a = an;
+    *t += dt;
+  }
+  free(gx); free(gy); free(gz);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Far-image tail of eq. ForceCylindrical for the learned surrogate.
+ * In the wrapped frame dzw in [-L/2, L/2) the window of eq. ForceCylindrical
+ * is the set of offsets o_k = dzw + k L with |o_k| < Ncut L. The near set is
+ * |k| <= n0; the tail is the rest of the window. Returned per unit G:
+ *   SR = sum_tail F(r_k,h)/r_k,  Sz = sum_tail o_k F(r_k,h)/r_k,
+ * so that the tail force on i from j is -G m_j (dx SR, dy SR, Sz).
+ * ------------------------------------------------------------------------- */
+void or_tail_sums(double dR, double dzw, double h, double L, int32_t n_cut, int32_t n0, double* SR,
+                  double* Sz) {
+  double sr = 0.0, sz = 0.0;
+  for (int k = -n_cut - 1; k <= n_cut + 1; ++k) {
+    if (k >= -n0 && k <= n0) continue;
+    double o = dzw + (double)k * L;
+    if (!(fabs(o) < (double)n_cut * L)) continue;
+    double r = sqrt(dR * dR + o * o);
+    double f = or_spline_F_over_r(r, h);
+    sr += f;
+    sz += o * f;
+  }
+  *SR = sr;
+  *Sz = sz;
+}
+
+/* ---------------------------------------------------------------------------
+ * Surrogate MLP 3 -> 32 -> 32 -> 2, ReLU hidden activations, FP64.
+ * Flat parameter layout: W1[32][3], b1[32], W2[32][32], b2[32], W3[2][32], b3[2].
+ * ------------------------------------------------------------------------- */
+#define OR_H 32
+#define OR_NW (OR_H * 3 + OR_H + OR_H * OR_H + OR_H + 2 * OR_H + 2)
+
+static void or_mlp_fwd_full(const double* w, const double* u, double* z1, double* a1, double* z2,
+                            double* a2, double* y) {
+  const double *W1 = w, *b1 = W1 + OR_H * 3, *W2 = b1 + OR_H, *b2 = W2 + OR_H * OR_H,
+               *W3 = b2 + OR_H, *b3 = W3 + 2 * OR_H;
+  for (int o = 0; o < OR_H; ++o) {
+    double s = b1[o];
+    for (int q = 0; q < 3; ++q) s += W1[o * 3 + q] * u[q];
+    z1[o] = s;
+    a1[o] = s > 0.0 ? s : 0.0;
+  }
+  for (int o = 0; o < OR_H; ++o) {
+    double s = b2[o];
+    for (int q = 0; q < OR_H; ++q) s += W2[o * OR_H + q] * a1[q];
+    z2[o] = s;
+    a2[o] = s > 0.0 ? s : 0.0;
+  }
+  for (int o = 0; o < 2; ++o) {
+    double s = b3[o];
+    for (int q = 0; q < OR_H; ++q) s += W3[o * OR_H + q] * a2[q];
+    y[o] = s;
+  }
+}
+
+void or_mlp_forward(const double* w, const double* u, double* y) {
+  double z1[OR_H], a1[OR_H], z2[OR_H], a2[OR_H];
+  or_mlp_fwd_full(w, u, z1, a1, z2, a2, y);
+}
+
+/* Loss = 1/(2 ns) sum_s sum_o (y_o(u_s) - t_so)^2 ; grad has OR_NW entries. */
+double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t,
+                        double* grad) {
+  const double *W2 = w + OR_H * 3 + OR_H, *W3 = W2 + OR_H * OR_H + OR_H;
+  double *gW1 = grad, *gb1 = gW1 + OR_H * 3, *gW2 = gb1 + OR_H, *gb2 = gW2 + OR_H * OR_H,
+         *gW3 = gb2 + OR_H, *gb3 = gW3 + 2 * OR_H;
+  memset(grad, 0, sizeof(double) * OR_NW);
+  double loss = 0.0;
+  for (int64_t s = 0; s < ns; ++s) {
+    double z1[OR_H], a1[OR_H], z2[OR_H], a2[OR_H], y[2], dy[2], d2[OR_H], d1[OR_H];
+    const double* us = u + 3 * s;
+    or_mlp_fwd_full(w, us, z1, a1, z2, a2, y);
+    for (int o = 0; o < 2; ++o) {
+      double e = y[o] - t[2 * s + o];
+      loss += 0.5 * e * e;
+      dy[o] = e / (double)ns;
+    }
+    for (int o = 0; o < 2; ++o) {
+      gb3[o] += dy[o];
+      for (int q = 0; q < OR_H; ++q) gW3[o * OR_H + q] += dy[o] * a2[q];
+    }
+    for (int q = 0; q < OR_H; ++q) {
+      double g = dy[0] * W3[q] + dy[1] * W3[OR_H + q];
+      d2[q] = z2[q] > 0.0 ? g : 0.0;
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      gb2[o] += d2[o];
+      for (int q = 0; q < OR_H; ++q) gW2[o * OR_H + q] += d2[o] * a1[q];
+    }
+    for (int q = 0; q < OR_H; ++q) {
+      double g = 0.0;
+      for (int o = 0; o < OR_H; ++o) g += d2[o] * W2[o * OR_H + q];
+      d1[q] = z1[q] > 0.0 ? g : 0.0;
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      gb1[o] += d1[o];
+      for (int q = 0; q < 3; ++q) gW1[o * 3 + q] += d1[o] * us[q];
+    }
+  }
+  return loss / (double)ns;
+}
+
+/* Adam (Kingma & Ba 2015), bias-corrected, step counted from 1. */
+void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2, double lr,
+                  double beta1, double beta2, double eps, int64_t step) {
+  double c1 = 1.0 - pow(beta1, (double)step), c2 = 1.0 - pow(beta2, (double)step);
+  for (int64_t k = 0; k < nw; ++k) {
+    m1[k] = beta1 * m1[k] + (1.0 - beta1) * g[k];
+    m2[k] = beta2 * m2[k] + (1.0 - beta2) * g[k] * g[k];
+    w[k] -= lr * (m1[k] / c1) / (sqrt(m2[k] / c2) + eps);
+  }
+}

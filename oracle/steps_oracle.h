@@ -1,0 +1,63 @@
+/*
+ * FP64 CPU oracle for the S1xR2 (periodic-cylinder) StePS force and integrator.
+ *
+ * TEST INFRASTRUCTURE ONLY. This library exists to check the CUDA path. Only the
+ * test-suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Every routine is the plain definition from the paper (arXiv 2602.20787):
+ *   - Eq. Force_spline_kernel (Sect. 2.1): cubic-spline softened force F(r,h).
+ *   - Eq. ForceCylindrical (Sect. 2.1): windowed image sum along z.
+ *   - Eq. ComovingEquationsOfMotionCylindrical (Sect. 2.1): pair term, 1/a^3,
+ *     background term of eq. F_horiz, Hubble drag.
+ *   - Eq. F_horiz (Sect. 2.1), re-derived (the printed form is garbled), with the
+ *     limit eq. F_horiz_infty.
+ *   - Eqs. Friedmann, DEdensity, CPLw0wa (Sect. 2.3) with RK4 (Sect. 2.3).
+ *   - KDK leapfrog in cosmic time (end of Sect. 2.1).
+ * The far-image surrogate (a 3->32->32->2 ReLU MLP) has its FP64 forward and
+ * backward pass here too, for gradient checks.
+ */
+#ifndef STEPS_ORACLE_H
+#define STEPS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Cosmology of eqs. Friedmann / DEdensity / CPLw0wa. comoving == 0 means
+ * static space: a = 1, H = 0 at all times. */
+typedef struct {
+  double H0, Omega_m, Omega_r, Omega_L, w0, wa;
+  int32_t comoving;
+} or_cosmo;
+
+double or_spline_F(double r, double h);
+double or_spline_F_over_r(double r, double h);
+int or_image_force(double rx, double ry, double rz, double h, double L, int32_t n_cut, double out[3]);
+void or_pair_field(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                   const double* h, double G, double L, int32_t n_cut, int64_t ni, const int64_t* idx,
+                   double* gx, double* gy, double* gz);
+double or_cylinder_field(double varrho, double R, double Lw, double G, double rho0);
+void or_background_field(int64_t ni, const double* x, const double* y, double R, double Lw, double G,
+                         double rho0, double* gx, double* gy);
+double or_hubble(const or_cosmo* c, double a);
+double or_a_of_t_step(const or_cosmo* c, double a, double dt);
+void or_kdk_factors(const or_cosmo* c, double a, double dt, double* K1, double* D, double* K2,
+                    double* a_next);
+int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
+           const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
+           double rho0, int32_t background, const or_cosmo* c, double* a, double* t, double dt,
+           int32_t nsteps);
+void or_tail_sums(double dR, double dzw, double h, double L, int32_t n_cut, int32_t n0, double* SR,
+                  double* Sz);
+void or_mlp_forward(const double* w, const double* u, double* y);
+double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t, double* grad);
+void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2, double lr,
+                  double beta1, double beta2, double eps, int64_t step);
+int32_t or_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

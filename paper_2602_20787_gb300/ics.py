@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs for the S1xR2 hot path (shared by the CUDA path's
+callers and by the oracle's tests; holds no force, integrator or surrogate
+arithmetic).
+
+Particle load (Sect. 3.1, eqs. inversestereographic and omegatovarrho): the
+compact radial coordinate w is drawn uniformly in [0, 0.9 pi), the azimuth phi
+uniformly in [0, 2 pi) and z uniformly in [0, L). The radius is
+rho = D_s tan(w/2) with D_s = L/2, so R_sim = (L/2) tan(0.45 pi). A uniform draw
+in w carries the volume element rho d(rho) = (D_s^2/2) tan(w/2) sec^2(w/2) dw,
+so each particle's mass is proportional to J(w) = tan(w/2) sec^2(w/2) and the
+comoving density is uniform (m_i = rho_bar V_i, Sect. 3.1).
+
+Softening: eps_i = 0.01 L (m_i/m_min)^(1/3) (the literal law), or for the
+production-shaped run a 1:8 range eps_i = 0.01 L 8^(ln(m_i/m_min)/ln(m_max/m_min)).
+
+Units: L = 1, G = 1, H0 = 1 (time in 1/H0). Static runs use M_tot = 1; comoving
+runs use the comoving mean density rho_bar = 3 Omega_m H0^2 / (8 pi G) and
+M_tot = rho_bar pi R_sim^2 L.
+
+The five workloads (sizes, seeds, image cut-offs and integration spans) are
+those of the benchmark configurations of this project: the plain-method small
+case (N=2048), the comoving LCDM run (N=65,536), the precision study with a
+central filament (N=262,144), the learned-surrogate case (N=1,048,576) and the
+production-shaped run (N=524,288).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+L_BOX = 1.0
+G_NEWTON = 1.0
+D_S = 0.5 * L_BOX
+W_MAX = 0.9 * math.pi
+R_SIM = D_S * math.tan(0.5 * W_MAX)
+
+
+def comoving_rho_bar(Omega_m: float = 0.3, H0: float = 1.0, G: float = G_NEWTON) -> float:
+    return 3.0 * Omega_m * H0 * H0 / (8.0 * math.pi * G)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n: int
+    seed: int
+    n_cut: int
+    comoving: bool
+    displaced: bool = False
+    filament_frac: float = 0.0
+    eps_law: str = "literal"      # "literal" | "ratio8"
+    a_start: float = 1.0
+    a_end: float = 1.0
+    nsteps: int = 0
+    dt: float = 0.0               # static runs: fixed dt
+    n0: int = 4
+    Omega_m: float = 0.3
+    Omega_L: float = 0.7
+
+    @property
+    def M_tot(self) -> float:
+        if not self.comoving:
+            return 1.0
+        return comoving_rho_bar(self.Omega_m) * math.pi * R_SIM * R_SIM * L_BOX
+
+    @property
+    def rho_bar(self) -> float:
+        return self.M_tot / (math.pi * R_SIM * R_SIM * L_BOX)
+
+
+WORKLOADS = {
+    "plain_small_n2048": Workload("plain_small_n2048", 2048, 0, 64, comoving=False, nsteps=10, dt=1e-3),
+    "lcdm_n65536": Workload("lcdm_n65536", 65536, 1, 16, comoving=True, displaced=True,
+                            a_start=0.02, a_end=0.1, nsteps=200),
+    "precision_n262144": Workload("precision_n262144", 262144, 2, 64, comoving=True, displaced=True,
+                                  filament_frac=0.2, a_start=0.02, a_end=0.02),
+    "surrogate_n1048576": Workload("surrogate_n1048576", 1048576, 3, 64, comoving=True, displaced=True,
+                                   a_start=0.02, a_end=0.02),
+    "production_n524288": Workload("production_n524288", 524288, 4, 64, comoving=True, displaced=True,
+                                   eps_law="ratio8", a_start=0.02, a_end=1.0, nsteps=1000),
+}
+
+
+def lcdm_time_of_a(a: float, Omega_m: float = 0.3, Omega_L: float = 0.7, H0: float = 1.0) -> float:
+    """Cosmic time of flat LCDM (textbook closed form), used only to size the
+    constant time step of a run that must span [a_start, a_end]."""
+    return 2.0 / (3.0 * math.sqrt(Omega_L) * H0) * math.asinh(math.sqrt(Omega_L / Omega_m) * a ** 1.5)
+
+
+def run_schedule(w: Workload):
+    """(t_start, dt) for a workload: constant dt in cosmic time."""
+    if not w.comoving:
+        return 0.0, w.dt
+    t0 = lcdm_time_of_a(w.a_start, w.Omega_m, w.Omega_L)
+    if w.nsteps == 0:
+        return t0, 0.0
+    t1 = lcdm_time_of_a(w.a_end, w.Omega_m, w.Omega_L)
+    return t0, (t1 - t0) / w.nsteps
+
+
+def particle_load(n: int, seed: int, M_tot: float = 1.0, *, displaced: bool = False,
+                  rho_bar: float | None = None, filament_frac: float = 0.0, eps_law: str = "literal",
+                  L: float = L_BOX):
+    """Returns dict(pos (n,3), vel (n,3), m (n,), h (n,)) in FP64, z in [0, L)."""
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.0, W_MAX, n)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n)
+    z = rng.uniform(0.0, L, n)
+    rho = D_S * np.tan(0.5 * w)
+    x, y = rho * np.cos(phi), rho * np.sin(phi)
+    J = np.tan(0.5 * w) / np.cos(0.5 * w) ** 2
+    m = J / J.sum() * M_tot
+    if rho_bar is None:
+        rho_bar = M_tot / (math.pi * R_SIM * R_SIM * L)
+    if filament_frac > 0.0:
+        nf = int(round(filament_frac * n))
+        sel = rng.permutation(n)[:nf]
+        mmed = float(np.median(m))
+        x[sel] = rng.normal(0.0, 0.05 * L, nf)
+        y[sel] = rng.normal(0.0, 0.05 * L, nf)
+        z[sel] = rng.uniform(0.0, L, nf)
+        m[sel] = mmed
+        m *= M_tot / m.sum()
+    if displaced:
+        sig = 0.02 * (m / rho_bar) ** (1.0 / 3.0)
+        d = rng.normal(0.0, 1.0, (n, 3)) * sig[:, None]
+        x += d[:, 0]
+        y += d[:, 1]
+        z += d[:, 2]
+    z = np.mod(z, L)
+    z[z >= L] -= L
+    mmin, mmax = float(m.min()), float(m.max())
+    if eps_law == "literal":
+        h = 0.01 * L * (m / mmin) ** (1.0 / 3.0)
+    elif eps_law == "ratio8":
+        h = 0.01 * L * 8.0 ** (np.log(m / mmin) / math.log(mmax / mmin))
+    else:
+        raise ValueError(eps_law)
+    pos = np.stack([x, y, z], axis=1)
+    return {"pos": pos, "vel": np.zeros((n, 3)), "m": m, "h": h}
+
+
+def workload_ics(w: Workload | str, n: int | None = None):
+    """Particle load of a named workload (optionally with a smaller n, same law)."""
+    if isinstance(w, str):
+        w = WORKLOADS[w]
+    nn = w.n if n is None else n
+    return particle_load(nn, w.seed, w.M_tot, displaced=w.displaced, rho_bar=w.rho_bar,
+                         filament_frac=w.filament_frac, eps_law=w.eps_law)
+
+
+def subsample(n: int, k: int, seed: int = 12345) -> np.ndarray:
+    """Sorted random subset of k particle indices (the error-metric subsample)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
+
+
+def tail_training_inputs(ns: int, seed: int, dR_max: float, h_max: float, L: float = L_BOX):
+    """Surrogate training inputs (dR, |dz_w|, h): dR with a density that puts
+    more samples near the axis, |dz_w| uniform in [0, L/2], h uniform."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0.0, 1.0, ns)
+    dR = dR_max * u * u
+    dz = rng.uniform(0.0, 0.5 * L, ns)
+    h = rng.uniform(0.0, h_max, ns)
+    return np.stack([dR, dz, h], axis=1)

@@ -1,0 +1,110 @@
+"""Pins of the oracle's finite-cylinder background (eq. F_horiz, re-derived
+because the printed form is garbled) and of the homogeneous-load balance
+(Sect. 2.1: the net comoving force of a homogeneous load vanishes)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2602_20787_gb300 import ics
+
+
+def field_point_polar(rho, R, Lw, G=1.0, rho0=1.0):
+    """Independent derivation: integrate the field of finite line segments
+    z in [-Lw, Lw] over the disk in polar coordinates centred on the field
+    point. Each segment at transverse distance s pulls with 2 G rho0 Lw /
+    (s sqrt(s^2 + Lw^2)) per unit area, so with dA = s ds dpsi the s-integral
+    is asinh(s/Lw) between the ray's entry and exit points of the disk."""
+    def integrand(psi):
+        c, s = math.cos(psi), math.sin(psi)
+        disc = R * R - rho * rho * s * s
+        if disc <= 0.0:
+            return 0.0
+        sp = -rho * c + math.sqrt(disc)
+        sm = -rho * c - math.sqrt(disc)
+        if rho < R:
+            return c * math.asinh(sp / Lw)
+        if sp <= 0.0:
+            return 0.0
+        return c * (math.asinh(sp / Lw) - math.asinh(max(sm, 0.0) / Lw))
+    pts = None
+    if rho > R:
+        a = math.asin(R / rho)
+        pts = [math.pi - a, math.pi + a]
+    val, _ = integrate.quad(integrand, 0.0, 2 * math.pi, points=pts, epsabs=0, epsrel=1e-13, limit=400)
+    return 2.0 * G * rho0 * Lw * val
+
+
+@pytest.mark.parametrize("Lw", [0.7, 5.0, 16.0, 64.0])
+@pytest.mark.parametrize("rho", [0.05, 1.0, 2.5, 3.1, 3.3, 4.5])
+def test_cylinder_field_matches_independent_quadrature(orc, rho, Lw):
+    R = ics.R_SIM
+    ref = field_point_polar(rho, R, Lw)
+    assert orc.cylinder_field(rho, R, Lw) == pytest.approx(ref, rel=2e-11, abs=1e-13)
+
+
+def test_cylinder_field_at_the_edge(orc):
+    # rho = R: the log singularity of the integrand sits at theta = 0
+    R = ics.R_SIM
+    assert orc.cylinder_field(R, R, 16.0) == pytest.approx(field_point_polar(R * (1 - 1e-12), R, 16.0), rel=1e-9)
+
+
+def test_cylinder_field_limits(orc):
+    R = 3.0
+    # eq. F_horiz_infty: Lw -> infinity gives -2 pi G rho0 rho inside ...
+    for rho in (0.1, 0.5, 1.7, 2.99):
+        assert orc.cylinder_field(rho, R, 1e7) == pytest.approx(-2 * math.pi * rho, rel=1e-10)
+    # ... and the line-mass field -2 pi G rho0 R^2 / rho outside
+    for rho in (3.2, 6.0):
+        assert orc.cylinder_field(rho, R, 1e7) == pytest.approx(-2 * math.pi * R * R / rho, rel=1e-10)
+    # a cylinder of zero height has no field
+    assert orc.cylinder_field(1.3, R, 0.0) == pytest.approx(0.0, abs=1e-14)
+    # G rho0 scaling and the axis
+    assert orc.cylinder_field(1.0, R, 8.0, 2.0, 3.0) == pytest.approx(6.0 * orc.cylinder_field(1.0, R, 8.0), rel=1e-14)
+    assert orc.cylinder_field(0.0, R, 8.0) == 0.0
+    # the printed form of eq. F_horiz would give +pi G rho0 rho as Lw -> inf; ours has the paper's sign
+
+
+def test_background_points_outward(orc):
+    pos = np.array([[1.0, 0.0, 0.5], [0.0, -2.0, 0.1], [0.6, 0.8, 0.9]])
+    g = orc.background_field(pos, 3.0, 16.0, 1.0, 0.25, mode=1)
+    rhat = pos[:, :2] / np.linalg.norm(pos[:, :2], axis=1)[:, None]
+    assert np.all(np.sum(g[:, :2] * rhat, axis=1) > 0)
+    np.testing.assert_allclose(g[:, 2], 0.0)
+    # infinite mode: 2 pi G rho0 rho outward
+    gi = orc.background_field(pos, 3.0, 16.0, 1.0, 0.25, mode=2)
+    np.testing.assert_allclose(np.linalg.norm(gi[:, :2], axis=1), 2 * math.pi * 0.25 * np.linalg.norm(pos[:, :2], axis=1), rtol=1e-14)
+
+
+def lattice_load(nw, nphi, nz, L=1.0):
+    """Regular cell-centred lattice in (w, phi, z) with each particle's mass
+    equal to the exact volume of its cell (Sect. 3.1 tessellation)."""
+    wv = np.linspace(0, ics.W_MAX, nw + 1)
+    V_w = 0.5 * ics.D_S ** 2 * (np.tan(wv[1:] / 2) ** 2 - np.tan(wv[:-1] / 2) ** 2)  # Int rho drho
+    wc = 0.5 * (wv[1:] + wv[:-1])
+    phic = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    zc = (np.arange(nz) + 0.5) * L / nz
+    W, P, Z = np.meshgrid(wc, phic, zc, indexing="ij")
+    Vm = np.broadcast_to(V_w[:, None, None], W.shape) * (2 * math.pi / nphi) * (L / nz)
+    rho = ics.D_S * np.tan(W / 2)
+    pos = np.stack([rho * np.cos(P), rho * np.sin(P), Z], -1).reshape(-1, 3)
+    return pos, Vm.reshape(-1)
+
+
+def test_homogeneous_load_feels_no_net_force(orc):
+    # Sect. 2.1: the compensation makes the net force vanish for a homogeneous
+    # load. A finite lattice leaves discreteness noise; the test checks that
+    # the pair field and the background cancel to a few percent in the interior
+    # (a sign error gives 200 %, a missing factor 2 gives 50 %).
+    pos, m = lattice_load(40, 48, 4)
+    rho0 = m.sum() / (math.pi * ics.R_SIM ** 2 * 1.0)
+    h = np.full(m.shape, 0.12)
+    n_cut = 16
+    rho = np.hypot(pos[:, 0], pos[:, 1])
+    idx = np.nonzero((rho > 0.4) & (rho < 1.2))[0][::7]
+    gp = orc.pair_field(pos, m, h, 1.0, 1.0, n_cut, idx=idx)
+    gb = orc.background_field(pos[idx], ics.R_SIM, n_cut * 1.0, 1.0, rho0, mode=1)
+    ratio = np.linalg.norm(gp + gb, axis=1) / np.linalg.norm(gp, axis=1)
+    assert np.median(ratio) < 0.03
+    assert ratio.max() < 0.1

@@ -1,0 +1,347 @@
+"""Benchmark of the S1xR2 StePS hot path on GB300.
+
+One step = one comoving KDK step (kick, drift + z wrap + repack, pair-force
+kernel over every pair and 2 Ncut images, background, kick) of the LCDM
+workload: N = 65,536 particles, Ncut = 16, FP32 pair math with Kahan-compensated
+sums on FP64 positions/momenta, a from 0.02 upward (the configuration the
+pair-interactions/s metric is quoted on). The metric is pair-images per second
+(images counted, N (N-1) 2 Ncut per step) over the whole job.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank advances its own independent cylinder
+(weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the deliberately plain reference of
+this project) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "lcdm_n65536"
+METRIC = "pair-interactions/s (images counted)"
+UNIT = "pair-images/s"
+MUFU_RSQRT_PER_SM_CLK = 16  # measured on sm_103: one rsqrt per pair-image
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pair_fp32.cuh",):
+        with open(os.path.join(ROOT, "paper_2602_20787_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pair_fp32_kahan_lcdm_n65536.md")
+    if not os.path.exists(path):
+        return None
+    src_hash, traffic = None, None
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("kernel_source_sha256_16:"):
+                src_hash = ln.split(":", 1)[1].strip()
+            if ln.startswith("dram_bytes_per_launch:"):
+                try:
+                    traffic = float(ln.split(":", 1)[1].strip())
+                except ValueError:
+                    traffic = None
+    if src_hash != kernel_source_hash():
+        return None
+    return traffic
+
+
+def cpu_baseline(w, d, target_s: float = 12.0):
+    """FP64 oracle (as it stands) on a bounded i-sample of the same workload:
+    pair field of the sampled i against all N particles plus the background."""
+    import oracle
+    from paper_2602_20787_gb300 import ics
+    n = w.n
+    probe = ics.subsample(n, 8, seed=777)
+    t0 = time.perf_counter()
+    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=probe)
+    dt_probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(n, max(8, 8 * target_s / dt_probe)))
+    idx = ics.subsample(n, k, seed=778)
+    t0 = time.perf_counter()
+    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+    oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
+    el = time.perf_counter() - t0
+    images = k * (n - 1) * 2.0 * w.n_cut
+    return {"value": images / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} i-particles x all {n} j x {2 * w.n_cut} images (FP64 pair field + background), {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2602_20787_gb300 import ics
+    import oracle
+    oracle.build()
+    w = ics.WORKLOADS[WORKLOAD]
+    d = ics.workload_ics(w)
+    n = w.n
+    per_step_target = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    probe = ics.subsample(n, 4, seed=900)
+    t0 = time.perf_counter()
+    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=probe)
+    dt_probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(n, max(4, 4 * per_step_target / dt_probe)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = ics.subsample(n, k, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+        oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
+        el = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(el)
+    images = k * (n - 1) * 2.0 * w.n_cut
+    value = images * len(times) / sum(times)
+    sample = f"each step: {k} i-particles x all {n} j x {2 * w.n_cut} images (FP64 oracle pair field + background)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "n_cut": w.n_cut, "i_sample_per_step": k},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = ics.WORKLOADS[WORKLOAD]
+    # each rank an independent cylinder (different seed), same law and size
+    d = ics.particle_load(w.n, w.seed + 1000 * rank, w.M_tot, displaced=True, rho_bar=w.rho_bar,
+                          filament_frac=w.filament_frac, eps_law=w.eps_law)
+    t0, dt = ics.run_schedule(w)
+    stream = torch.cuda.current_stream(dev)
+    cfg = sc.Config(n_cut=w.n_cut, precision=sc.STEPS_FP32_KAHAN, background=sc.STEPS_BG_FINITE, comoving=True,
+                    a_start=w.a_start, t_start=t0, rho_bar=w.rho_bar, device=local, stream=stream.cuda_stream)
+    n = w.n
+    cols = [torch.tensor(np.ascontiguousarray(d["pos"][:, k]), device=dev) for k in range(3)]
+    vel = [torch.zeros(n, dtype=torch.float64, device=dev) for _ in range(3)]
+    m_t = torch.tensor(d["m"], device=dev)
+    h_t = torch.tensor(d["h"], device=dev)
+    ctx = sc.steps_cyl_init(cfg, n, *cols, *vel, m_t, h_t)
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        sc.steps_cyl_kdk_step(ctx, dt, 1)
+    barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_ms = []
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    barrier()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        sc.steps_cyl_kdk_step(ctx, dt, 1)  # synchronises to read the device error word
+        ev[s][1].record(stream)
+        pair_ms.append(sc.steps_cyl_last_timing(ctx)[1])
+    g1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    region_ms = g0.elapsed_time(g1)
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    if dist is not None:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    images_per_step = n * (n - 1) * 2.0 * w.n_cut
+    value = images_per_step * args.steps * world / t_max
+
+    # roofline of the dominant kernel (the pair kernel): one MUFU rsqrt per pair-image
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk["sm_max_mhz"] or 2070.0
+    peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_max * 1e6
+    pair_avg_s = statistics.mean(pair_ms) / 1e3
+    achieved = images_per_step / pair_avg_s
+
+    # end to end through the public API with pinned host buffers: per step the
+    # state goes host -> device (set_state), one KDK step runs, the state comes back
+    e2e = None
+    if args.e2e_steps > 0:
+        host = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(6)]
+        sc.steps_cyl_get_state(ctx, *host)
+        torch.cuda.synchronize(dev)
+        barrier()
+        te0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sc.steps_cyl_set_state(ctx, *host)
+            sc.steps_cyl_kdk_step(ctx, dt, 1)
+            sc.steps_cyl_get_state(ctx, *host)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - te0
+        if dist is not None:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": images_per_step * args.e2e_steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": 6 * 8 * n, "d2h_bytes_per_step": 6 * 8 * n, "steps": args.e2e_steps}
+
+    diag = sc.steps_cyl_diagnostics(ctx)
+    sc.steps_cyl_free(ctx)
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(w, d)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "n_cut": w.n_cut, "images_per_pair": 2 * w.n_cut,
+                       "precision": "fp32 pair math, Kahan j-sum, fp64 state", "background": "finite cylinder",
+                       "cosmology": "LCDM 0.3/0.7", "a_after": diag[5],
+                       "l2": "256 MiB buffer written between timed steps (inputs 4 MB < L2)",
+                       "per_rank": "independent cylinder per rank" if world > 1 else None,
+                       "timed_region_ms": region_ms},
+            "kdk_step_ms": 1e3 * t_max / args.steps,
+            "pair_kernel_ms": 1e3 * pair_avg_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
+                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_RSQRT_PER_SM_CLK} MUFU rsqrt/SM/clk "
+                                       f"x {sm_max:.0f} MHz (max SM clock); 1 rsqrt per pair-image"},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    sys.exit(run(args))
+
+
+if __name__ == "__main__":
+    main()

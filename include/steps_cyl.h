@@ -1,0 +1,150 @@
+/*
+ * steps_cyl.h - C ABI of the GB300 (sm_103a) S1xR2 StePS hot path.
+ *
+ * What it computes (arXiv 2602.20787, Sect. 2.1 and 2.3):
+ *   - the softened pair force of eq. Force_spline_kernel summed over the periodic
+ *     images of eq. ForceCylindrical (window |r_z - n L| < Ncut L, n in [-Ncut, Ncut]),
+ *     with pair softening h_i + h_j (eq. ComovingEquationsOfMotion);
+ *   - the finite-cylinder background of eq. F_horiz (re-derived: the printed formula
+ *     is garbled) or its infinite limit eq. F_horiz_infty;
+ *   - the comoving equations of motion eq. ComovingEquationsOfMotionCylindrical,
+ *     integrated with a kick-drift-kick leapfrog in cosmic time with a(t) from the
+ *     Friedmann equation (eqs. Friedmann, DEdensity, CPLw0wa) by RK4.
+ *
+ * Conventions shared by every entry point
+ *   - Units are the caller's; positions x, y are free, z must lie in [0, L).
+ *   - Arrays are structure-of-arrays, one double per particle, contiguous.
+ *   - A pointer argument may be host memory or device memory of the context's
+ *     device; the library finds out with cudaPointerGetAttributes. The library
+ *     copies what it needs and never keeps a caller pointer past the call.
+ *   - Work is ordered on the context's stream (steps_cyl_params.stream, or the
+ *     legacy default stream when NULL). A call that writes host memory returns
+ *     after the data is there; a call that writes device memory returns once the
+ *     work is enqueued, except steps_cyl_kdk_step which always synchronises to
+ *     read the device error word.
+ *   - Every call returns STEPS_OK (0) or a negative STEPS_E* code. The message of
+ *     the last failure on the calling thread is steps_cyl_last_error().
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef STEPS_CYL_H
+#define STEPS_CYL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define STEPS_OK 0
+#define STEPS_EINVAL (-1)               /* bad argument (N < 2, h <= 0, L <= 0, z outside [0,L), non-finite input) */
+#define STEPS_ECUDA (-2)                /* a CUDA runtime call failed */
+#define STEPS_ENOMEM (-3)               /* device allocation failed */
+#define STEPS_EDEVICE (-4)              /* the device error word was set (non-finite force, particle beyond the background table) */
+#define STEPS_ESURROGATE_REJECTED (-5)  /* surrogate error above its bound: the plain image sum was used instead */
+#define STEPS_ENOSURROGATE (-6)         /* surrogate tail requested but no accepted network is loaded */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define STEPS_FP64 0        /* pair geometry and sums in FP64 */
+#define STEPS_FP32_KAHAN 1  /* FP32 pair math on hi/lo split positions, Kahan-compensated j sum */
+#define STEPS_FP32_PLAIN 2  /* FP32 pair math on hi/lo split positions, plain j sum */
+
+#define STEPS_TAIL_FULL 0       /* every image of the window summed directly */
+#define STEPS_TAIL_SURROGATE 1  /* images |k| <= n0 direct, far tail from the learned surrogate */
+
+#define STEPS_BG_OFF 0       /* no background term */
+#define STEPS_BG_FINITE 1    /* eq. F_horiz: cylinder of radius R_sim and height 2 Ncut L */
+#define STEPS_BG_INFINITE 2  /* eq. F_horiz_infty inside R_sim, line-mass field outside */
+
+typedef struct steps_cyl_ctx steps_cyl_ctx; /* opaque; owned by the library until steps_cyl_free */
+
+typedef struct {
+  double G;         /* gravitational constant (> 0) */
+  double L;         /* period L_z of the compact axis (> 0) */
+  double R_sim;     /* radius of the simulated cylinder used by the background term (> 0) */
+  double rho_bar;   /* comoving mean density of the background term; 0 means sum(m) / (pi R_sim^2 L) */
+  int32_t n_cut;    /* image cut-off Ncut of eq. ForceCylindrical, 1 <= n_cut <= 4096 */
+  int32_t n0;       /* surrogate near range: images |k| <= n0 summed directly, 1 <= n0 < n_cut */
+  int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
+  int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE */
+  int32_t background; /* STEPS_BG_OFF | STEPS_BG_FINITE | STEPS_BG_INFINITE */
+  int32_t comoving;   /* 0: static space (a = 1, H = 0); 1: expanding background */
+  double H0, Omega_m, Omega_r, Omega_L, w0, wa; /* eqs. Friedmann, DEdensity, CPLw0wa; Omega_k = 1 - sum */
+  double a_start;   /* scale factor at t_start (1 in static space) */
+  double t_start;   /* cosmic time at the start */
+  int32_t device;   /* CUDA device ordinal */
+  int32_t reserved; /* must be 0 */
+  void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
+} steps_cyl_params;
+
+/* Fill *p with defaults: G = L = 1, R_sim = 0.5 tan(0.45 pi), rho_bar = 0, n_cut = 16,
+ * n0 = 4, FP32_KAHAN, TAIL_FULL, BG_FINITE, static space, H0 = 1, Omega_m = 0.3,
+ * Omega_L = 0.7, w0 = -1, wa = 0, a_start = 1, t_start = 0, device 0, default stream. */
+int steps_cyl_params_default(steps_cyl_params* p);
+
+/* Create a context holding n particles (eq. ComovingEquationsOfMotionCylindrical state).
+ * x, y, z: positions (z in [0, L)); vx, vy, vz: comoving velocities dx/dt; m: masses
+ * (> 0); h: softening support radii (> 0; a pair uses h_i + h_j). All length n,
+ * host or device. 2 <= n < 2^31. On success *out is a new context and the forces at
+ * the initial positions are computed (they feed the first kick). */
+int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, const double* x,
+                   const double* y, const double* z, const double* vx, const double* vy,
+                   const double* vz, const double* m, const double* h);
+
+/* Accelerations at the current positions: the pair term of eq.
+ * ComovingEquationsOfMotionCylindrical divided by a^3 plus the background term
+ * (also divided by a^3), without the Hubble drag. ax, ay, az: length n, host or
+ * device, written in full. */
+int steps_cyl_forces(steps_cyl_ctx* ctx, double* ax, double* ay, double* az);
+
+/* Same as steps_cyl_forces for the ni particles listed in idx (host or device
+ * int64 array, values in [0, n)), each against all n particles. Output length ni. */
+int steps_cyl_forces_subset(steps_cyl_ctx* ctx, int64_t ni, const int64_t* idx, double* ax,
+                            double* ay, double* az);
+
+/* Advance nsteps >= 0 KDK steps of constant cosmic-time length dt > 0: kick by
+ * Int dt/a over the first half, drift by Int dt/a^2, new forces, kick by Int dt/a
+ * over the second half (canonical momentum p = a^2 dx/dt; the Hubble drag is
+ * exact in this form). z is wrapped into [0, L) after each drift. */
+int steps_cyl_kdk_step(steps_cyl_ctx* ctx, double dt, int32_t nsteps);
+
+/* Copy the state out: positions, comoving velocities dx/dt, and the scale factor
+ * and time (any output pointer may be NULL to skip it). */
+int steps_cyl_get_state(steps_cyl_ctx* ctx, double* x, double* y, double* z, double* vx,
+                        double* vy, double* vz, double* a, double* t);
+
+/* Replace positions and velocities (same n; masses and softenings unchanged).
+ * The forces that feed the next kick are recomputed unless the new positions are
+ * bitwise equal to the current ones (then the cached forces are still exact).
+ * Pointers as in steps_cyl_init. Synchronises the context stream. */
+int steps_cyl_set_state(steps_cyl_ctx* ctx, const double* x, const double* y, const double* z,
+                        const double* vx, const double* vy, const double* vz);
+
+/* Switch the pair-kernel precision (STEPS_FP64 / FP32_KAHAN / FP32_PLAIN) of an
+ * existing context; the cached forces are recomputed. */
+int steps_cyl_set_precision(steps_cyl_ctx* ctx, int32_t precision);
+
+/* Conserved quantities and energies (Sect. 1: P_z and L_z are conserved in
+ * S1xR2). out[0..2] = sum m p (canonical momentum a^2 dx/dt), out[3] = L_z =
+ * sum m (x p_y - y p_x), out[4] = sum m |dx/dt|^2 / 2, out[5] = a, out[6] = t,
+ * out[7] = total mass. out: 8 doubles of host memory. */
+int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
+
+/* Pair-images evaluated by the last force evaluation, counted as the paper's
+ * window (2 Ncut per pair, 2 Ncut - 1 when r_z = 0 mod L), and the device time of
+ * its pair kernel in milliseconds (CUDA events on the context stream). */
+int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
+
+/* Release the context and its device memory. NULL is accepted. */
+int steps_cyl_free(steps_cyl_ctx* ctx);
+
+/* Static description of a status code; never NULL. */
+const char* steps_cyl_strerror(int code);
+
+/* Message of the last failure on the calling thread ("" when none). */
+const char* steps_cyl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,66 @@
+"""In-tree build of the CUDA library ``libsteps_cyl.so`` for sm_103a.
+
+``build()`` runs nvcc once per changed source (a stamp of the source contents
+and flags sits next to the library) and returns the library path.
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+import subprocess
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "libsteps_cyl.so")
+SOURCES = ["steps_cyl.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
+_lock = threading.Lock()
+
+
+def _nvcc() -> str:
+    env = os.environ.get("NVCC")
+    if env:
+        return env
+    if os.path.exists("/usr/local/cuda/bin/nvcc"):
+        return "/usr/local/cuda/bin/nvcc"
+    return "nvcc"
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    files = sorted(os.listdir(CSRC)) + ["../../include/steps_cyl.h"]
+    for f in files:
+        path = os.path.normpath(os.path.join(CSRC, f))
+        if os.path.isfile(path):
+            h.update(f.encode())
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    with _lock:
+        stamp = LIB + ".stamp"
+        dig = _digest()
+        if not force and os.path.exists(LIB) and os.path.exists(stamp):
+            with open(stamp) as fh:
+                if fh.read().strip() == dig:
+                    return LIB
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [_nvcc(), *ARCH, *FLAGS, "-I" + INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+        with open(stamp, "w") as fh:
+            fh.write(dig)
+        return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose=True))

@@ -1,0 +1,287 @@
+// O(N) kernels of the S1xR2 step and the FP64 pair kernel (arXiv 2602.20787,
+// eq. ComovingEquationsOfMotionCylindrical and the KDK leapfrog of Sect. 2.1).
+#pragma once
+#include <cstdint>
+
+#include "pair_fp32.cuh"
+
+namespace steps {
+
+constexpr int kErrNonFinite = 1;     // a force, position or momentum is not finite
+constexpr int kErrBgRange = 2;       // a particle lies beyond the background table
+constexpr int kErrZRange = 4;        // z left [0, L) by more than rounding
+
+// FP64 positions -> FP32 hi/lo words in units of L (see pair_fp32.cuh).
+__device__ __forceinline__ void pack_one(double x, double y, double z, double m, double h, int i, double invL,
+                                         float4* __restrict__ jA, float4* __restrict__ jB) {
+  const double xu = x * invL, yu = y * invL, zu = z * invL;
+  const float xh = (float)xu, yh = (float)yu, zh = (float)zu;
+  const float xl = (float)(xu - (double)xh), yl = (float)(yu - (double)yh), zl = (float)(zu - (double)zh);
+  jA[i] = make_float4(xh, yh, zh, (float)m);
+  jB[i] = make_float4(xl, yl, zl, (float)(h * invL));
+}
+
+__global__ void pack_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                            const double* __restrict__ z, const double* __restrict__ m,
+                            const double* __restrict__ h, int n, double invL, float4* __restrict__ jA,
+                            float4* __restrict__ jB) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    pack_one(x[i], y[i], z[i], m[i], h[i], i, invL, jA, jB);
+}
+
+// Background of eq. ComovingEquationsOfMotionCylindrical: returns F_h(rho) (< 0
+// inside a homogeneous cylinder; the acceleration is -F_h along rho_hat).
+// F_h = F_inf + dF, with F_inf the infinite cylinder (-2 pi G rho0 rho inside,
+// -2 pi G rho0 R^2 / rho outside) and dF the smooth finite-height remainder,
+// tabulated on a uniform grid (nodes -1 .. K+2) and read with 4-point Lagrange.
+struct BgParams {
+  int mode;            // STEPS_BG_*
+  double two_pi_G_rho0;
+  double R;
+  const double* tab;   // dF at rho_k = k * dr, k = -1 .. K+2 (tab[0] is k = -1)
+  int K;
+  double inv_dr;
+};
+
+__device__ __forceinline__ double background_F(const BgParams& bg, double rho, int* err) {
+  if (bg.mode == 0) return 0.0;
+  double F = rho <= bg.R ? -bg.two_pi_G_rho0 * rho : -bg.two_pi_G_rho0 * bg.R * bg.R / rho;
+  if (bg.mode == 1) {
+    const double s = rho * bg.inv_dr;
+    int k = (int)floor(s);
+    if (k >= bg.K || !(s >= 0.0)) {
+      atomicOr(err, kErrBgRange);
+      k = bg.K - 1;
+    }
+    const double t = s - (double)k;  // in [0, 1)
+    // Lagrange weights on nodes k-1, k, k+1, k+2 at offset t from node k
+    const double wm = -t * (t - 1.0) * (t - 2.0) / 6.0;
+    const double w0 = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+    const double w1 = -(t + 1.0) * t * (t - 2.0) / 2.0;
+    const double w2 = (t + 1.0) * t * (t - 1.0) / 6.0;
+    const double* q = bg.tab + k;  // q[0] is node k-1
+    F += wm * q[0] + w0 * q[1] + w1 * q[2] + w2 * q[3];
+  }
+  return F;
+}
+
+// Sum the stream-K partials of each i in CTA order (or read direct sums when
+// NT == 0), scale to the comoving field
+// g = a^3 (pair + background), store it, optionally kick p += g K and optionally
+// write a = g / a^3 to an output.
+__global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
+                                double pair_scale, BgParams bg, const double* __restrict__ x,
+                                const double* __restrict__ y, double* __restrict__ gx,
+                                double* __restrict__ gy, double* __restrict__ gz, double K,
+                                double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
+                                double inv_a3, double* __restrict__ ox, double* __restrict__ oy,
+                                double* __restrict__ oz, int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  if (NT == 0) {
+    // direct sums (FP64 pair kernel): part = [3][n]
+    sx = part[i];
+    sy = part[(long long)n + i];
+    sz = part[2 * (long long)n + i];
+  } else {
+    const int b = i / kBI, l = i % kBI;
+    const long long p_lo = (long long)b * NT, p_hi = p_lo + NT - 1;
+    const int c_lo = cta_of_unit(p_lo, U, C), c_hi = cta_of_unit(p_hi, U, C);
+    for (int c = c_lo; c <= c_hi; ++c) {
+      const double* q = part + ((long long)b + c) * 3 * kBI;
+      sx += q[l];
+      sy += q[kBI + l];
+      sz += q[2 * kBI + l];
+    }
+  }
+  double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
+  const double xi = x[i], yi = y[i];
+  const double rho = sqrt(xi * xi + yi * yi);
+  if (rho > 0.0 && bg.mode != 0) {
+    const double F = background_F(bg, rho, err);
+    g0 -= F * xi / rho;
+    g1 -= F * yi / rho;
+  }
+  if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
+  gx[i] = g0; gy[i] = g1; gz[i] = g2;
+  if (px) {
+    px[i] += g0 * K;
+    py[i] += g1 * K;
+    pz[i] += g2 * K;
+  }
+  if (ox) {
+    ox[i] = g0 * inv_a3;
+    oy[i] = g1 * inv_a3;
+    oz[i] = g2 * inv_a3;
+  }
+}
+
+// First half of a KDK step: p += g K1; x += p D; z wrapped into [0, L); repack.
+__global__ void kick_drift_pack_kernel(double* __restrict__ x, double* __restrict__ y,
+                                       double* __restrict__ z, double* __restrict__ px,
+                                       double* __restrict__ py, double* __restrict__ pz,
+                                       const double* __restrict__ gx, const double* __restrict__ gy,
+                                       const double* __restrict__ gz, const double* __restrict__ m,
+                                       const double* __restrict__ h, int n, double K1, double D, double L,
+                                       double invL, float4* __restrict__ jA, float4* __restrict__ jB,
+                                       int* __restrict__ err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double qx = px[i] + gx[i] * K1, qy = py[i] + gy[i] * K1, qz = pz[i] + gz[i] * K1;
+    px[i] = qx; py[i] = qy; pz[i] = qz;
+    const double nx = x[i] + qx * D, ny = y[i] + qy * D;
+    double nz = z[i] + qz * D;
+    nz -= L * floor(nz * invL);
+    if (nz >= L) nz -= L;
+    if (nz < 0.0) nz = 0.0;
+    if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(err, kErrNonFinite);
+    x[i] = nx; y[i] = ny; z[i] = nz;
+    pack_one(nx, ny, nz, m[i], h[i], i, invL, jA, jB);
+  }
+}
+
+// y = s x for three arrays (acceleration output = g / a^3).
+__global__ void scale3_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
+                              const double* __restrict__ az, int n, double s, double* __restrict__ ox,
+                              double* __restrict__ oy, double* __restrict__ oz) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    ox[i] = ax[i] * s; oy[i] = ay[i] * s; oz[i] = az[i] * s;
+  }
+}
+
+// p = a^2 v (and back) on three arrays.
+__global__ void axpy_scale3_kernel(double* __restrict__ a0, double* __restrict__ a1, double* __restrict__ a2,
+                                   int n, double s) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    a0[i] *= s; a1[i] *= s; a2[i] *= s;
+  }
+}
+
+// Deterministic reductions for the diagnostics: each block writes its partial
+// sums of (m px, m py, m pz, m (x py - y px), m |p|^2 / 2, m) into part[block][6].
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 256;
+
+__global__ void diag_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                    const double* __restrict__ px, const double* __restrict__ py,
+                                    const double* __restrict__ pz, const double* __restrict__ m, int n,
+                                    double* __restrict__ part) {
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double mi = m[i];
+    v[0] += mi * px[i];
+    v[1] += mi * py[i];
+    v[2] += mi * pz[i];
+    v[3] += mi * (x[i] * py[i] - y[i] * px[i]);
+    v[4] += 0.5 * mi * (px[i] * px[i] + py[i] * py[i] + pz[i] * pz[i]);
+    v[5] += mi;
+  }
+  __shared__ double sh[kRedThreads / 32][6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    double s = v[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w][threadIdx.x];
+    part[blockIdx.x * 6 + threadIdx.x] = s;
+  }
+}
+
+__global__ void diag_final_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[b * 6 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pair kernel (precision study and reference form): one thread per listed
+// i, every j, same window and softening as the FP32 kernel but evaluated
+// directly (branch on r < h) in FP64. idx == nullptr means i = q.
+// Output: out[q], out[ni + q], out[2 ni + q] = sum_j m_j (dx, dy, dz-part) in
+// units of G / L^2 (scaled by the caller), i.e. the same quantity as the FP32
+// partial sums.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double spline_over_r_fp64(double r, double hh) {
+  const double ih = 1.0 / hh, u = r * ih, ih3 = ih * ih * ih;
+  if (u < 0.5) return (32.0 / 3.0 + u * u * (32.0 * u - 38.4)) * ih3;
+  const double u3 = u * u * u;
+  return (64.0 / 3.0 - 48.0 * u + 38.4 * u * u - (32.0 / 3.0) * u3 - 1.0 / (15.0 * u3)) * ih3;
+}
+
+__device__ __forceinline__ void image_fp64(double dR2, double o, double hh, double hh2, double w, double& sr,
+                                           double& sz) {
+  const double r2 = fma(o, o, dR2);
+  double f;
+  if (r2 < hh2) {
+    f = spline_over_r_fp64(sqrt(r2), hh);
+  } else {
+    const double ri = rsqrt(r2);
+    f = ri * ri * ri;
+  }
+  f *= w;
+  sr += f;
+  sz = fma(o, f, sz);
+}
+
+__global__ void __launch_bounds__(128)
+pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+                 const double* __restrict__ m, const double* __restrict__ h, int n,
+                 const int64_t* __restrict__ idx, int ni, double invL, int n_cut, double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ni) return;
+  const int i = idx ? (int)idx[q] : q;
+  const double xi = x[i] * invL, yi = y[i] * invL, zi = z[i] * invL, hi = h[i] * invL;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const double dx = xi - x[j] * invL, dy = yi - y[j] * invL;
+    double dz = zi - z[j] * invL;
+    dz -= rint(dz);
+    const double dR2 = dx * dx + dy * dy;
+    const double hh = hi + h[j] * invL, hh2 = hh * hh;
+    double sr = 0.0, sz = 0.0;
+    image_fp64(dR2, dz, hh, hh2, 1.0, sr, sz);
+    image_fp64(dR2, dz - copysign((double)n_cut, dz), hh, hh2, dz != 0.0 ? 1.0 : 0.0, sr, sz);
+    for (int k = 1; k < n_cut; ++k) {
+      image_fp64(dR2, dz + (double)k, hh, hh2, 1.0, sr, sz);
+      image_fp64(dR2, dz - (double)k, hh, hh2, 1.0, sr, sz);
+    }
+    const double mj = m[j];
+    ax += mj * dx * sr;
+    ay += mj * dy * sr;
+    az += mj * sz;
+  }
+  out[q] = ax;
+  out[ni + q] = ay;
+  out[2 * ni + q] = az;
+}
+
+// out3 (SoA, ni each) = pair_scale * pair + background at the listed i, / a^3
+__global__ void subset_finalize_kernel(const double* __restrict__ pairsum, int ni, const int64_t* __restrict__ idx,
+                                       double pair_scale, BgParams bg, const double* __restrict__ x,
+                                       const double* __restrict__ y, double inv_a3, double* __restrict__ ox,
+                                       double* __restrict__ oy, double* __restrict__ oz, int* __restrict__ err) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ni) return;
+  const int i = idx ? (int)idx[q] : q;
+  double g0 = pair_scale * pairsum[q], g1 = pair_scale * pairsum[ni + q], g2 = pair_scale * pairsum[2 * ni + q];
+  const double xi = x[i], yi = y[i];
+  const double rho = sqrt(xi * xi + yi * yi);
+  if (rho > 0.0 && bg.mode != 0) {
+    const double F = background_F(bg, rho, err);
+    g0 -= F * xi / rho;
+    g1 -= F * yi / rho;
+  }
+  if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
+  ox[q] = g0 * inv_a3;
+  oy[q] = g1 * inv_a3;
+  oz[q] = g2 * inv_a3;
+}
+
+}  // namespace steps

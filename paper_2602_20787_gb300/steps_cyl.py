@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in ``include/steps_cyl.h`` (ctypes).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library
+``libsteps_cyl.so`` built in-tree by ``paper_2602_20787_gb300.build``. If that
+library is missing or cannot be loaded, every call raises: there is no CPU
+fallback. Arrays may be CUDA torch tensors (device pointers are passed straight
+through), CPU torch tensors or numpy arrays (host pointers; the library copies).
+All arrays are float64 (indices int64) and contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+STEPS_OK = 0
+STEPS_EINVAL = -1
+STEPS_ECUDA = -2
+STEPS_ENOMEM = -3
+STEPS_EDEVICE = -4
+STEPS_ESURROGATE_REJECTED = -5
+STEPS_ENOSURROGATE = -6
+
+STEPS_FP64, STEPS_FP32_KAHAN, STEPS_FP32_PLAIN = 0, 1, 2
+STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE = 0, 1
+STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE = 0, 1, 2
+
+_EXPORTS = [
+    "steps_cyl_params_default", "steps_cyl_init", "steps_cyl_forces", "steps_cyl_forces_subset",
+    "steps_cyl_kdk_step", "steps_cyl_get_state", "steps_cyl_set_state", "steps_cyl_set_precision",
+    "steps_cyl_diagnostics", "steps_cyl_last_timing", "steps_cyl_free", "steps_cyl_strerror",
+    "steps_cyl_last_error",
+]
+
+
+class StepsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``steps_cyl_params``."""
+    _fields_ = [
+        ("G", ctypes.c_double), ("L", ctypes.c_double), ("R_sim", ctypes.c_double), ("rho_bar", ctypes.c_double),
+        ("n_cut", ctypes.c_int32), ("n0", ctypes.c_int32), ("precision", ctypes.c_int32), ("tail", ctypes.c_int32),
+        ("background", ctypes.c_int32), ("comoving", ctypes.c_int32),
+        ("H0", ctypes.c_double), ("Omega_m", ctypes.c_double), ("Omega_r", ctypes.c_double),
+        ("Omega_L", ctypes.c_double), ("w0", ctypes.c_double), ("wa", ctypes.c_double),
+        ("a_start", ctypes.c_double), ("t_start", ctypes.c_double),
+        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run paper_2602_20787_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    p, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.steps_cyl_params_default.argtypes = [ctypes.POINTER(Params)]
+    L.steps_cyl_init.argtypes = [ctypes.POINTER(p), ctypes.POINTER(Params), i64] + [p] * 8
+    L.steps_cyl_forces.argtypes = [p, p, p, p]
+    L.steps_cyl_forces_subset.argtypes = [p, i64, p, p, p, p]
+    L.steps_cyl_kdk_step.argtypes = [p, d, i32]
+    L.steps_cyl_get_state.argtypes = [p] * 9
+    L.steps_cyl_set_state.argtypes = [p] * 7
+    L.steps_cyl_set_precision.argtypes = [p, i32]
+    L.steps_cyl_diagnostics.argtypes = [p, p]
+    L.steps_cyl_last_timing.argtypes = [p, p, p]
+    L.steps_cyl_free.argtypes = [p]
+    L.steps_cyl_strerror.argtypes = [ctypes.c_int]
+    L.steps_cyl_strerror.restype = ctypes.c_char_p
+    L.steps_cyl_last_error.argtypes = []
+    L.steps_cyl_last_error.restype = ctypes.c_char_p
+    for name in _EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is None or fn.restype is ctypes.c_int:
+            fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != STEPS_OK:
+        L = load(False)
+        msg = (L.steps_cyl_last_error() or b"").decode() or L.steps_cyl_strerror(rc).decode()
+        raise StepsError(rc, msg)
+
+
+def _ptr(a):
+    """Raw data pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_f64(*arrs):
+    for a in arrs:
+        if a is None:
+            continue
+        dt = getattr(a, "dtype", None)
+        if str(dt) not in ("float64", "torch.float64"):
+            raise TypeError(f"float64 arrays required, got {dt}")
+
+
+@dataclasses.dataclass
+class Config:
+    G: float = 1.0
+    L: float = 1.0
+    R_sim: float = 0.5 * math.tan(0.45 * math.pi)
+    rho_bar: float = 0.0
+    n_cut: int = 16
+    n0: int = 4
+    precision: int = STEPS_FP32_KAHAN
+    tail: int = STEPS_TAIL_FULL
+    background: int = STEPS_BG_FINITE
+    comoving: bool = False
+    H0: float = 1.0
+    Omega_m: float = 0.3
+    Omega_r: float = 0.0
+    Omega_L: float = 0.7
+    w0: float = -1.0
+    wa: float = 0.0
+    a_start: float = 1.0
+    t_start: float = 0.0
+    device: int = 0
+    stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
+
+    def to_c(self) -> Params:
+        p = Params()
+        load().steps_cyl_params_default(ctypes.byref(p))
+        for f in dataclasses.fields(self):
+            if f.name == "stream":
+                p.stream = ctypes.c_void_p(self.stream or None)
+            elif f.name == "comoving":
+                p.comoving = 1 if self.comoving else 0
+            else:
+                setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def steps_cyl_params_default() -> Params:
+    p = Params()
+    _check(load().steps_cyl_params_default(ctypes.byref(p)))
+    return p
+
+
+def steps_cyl_init(cfg, n, x, y, z, vx, vy, vz, m, h) -> ctypes.c_void_p:
+    _check_f64(x, y, z, vx, vy, vz, m, h)
+    p = cfg.to_c() if isinstance(cfg, Config) else cfg
+    ctx = ctypes.c_void_p()
+    _check(load().steps_cyl_init(ctypes.byref(ctx), ctypes.byref(p), int(n), _ptr(x), _ptr(y), _ptr(z), _ptr(vx),
+                                 _ptr(vy), _ptr(vz), _ptr(m), _ptr(h)))
+    return ctx
+
+
+def steps_cyl_forces(ctx, ax, ay, az):
+    _check_f64(ax, ay, az)
+    _check(load().steps_cyl_forces(ctx, _ptr(ax), _ptr(ay), _ptr(az)))
+
+
+def steps_cyl_forces_subset(ctx, idx, ax, ay, az):
+    _check_f64(ax, ay, az)
+    _check(load().steps_cyl_forces_subset(ctx, int(len(idx)), _ptr(idx), _ptr(ax), _ptr(ay), _ptr(az)))
+
+
+def steps_cyl_kdk_step(ctx, dt: float, nsteps: int):
+    _check(load().steps_cyl_kdk_step(ctx, float(dt), int(nsteps)))
+
+
+def steps_cyl_get_state(ctx, x=None, y=None, z=None, vx=None, vy=None, vz=None):
+    _check_f64(x, y, z, vx, vy, vz)
+    a, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().steps_cyl_get_state(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(vx), _ptr(vy), _ptr(vz),
+                                      ctypes.byref(a), ctypes.byref(t)))
+    return a.value, t.value
+
+
+def steps_cyl_set_state(ctx, x, y, z, vx, vy, vz):
+    _check_f64(x, y, z, vx, vy, vz)
+    _check(load().steps_cyl_set_state(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(vx), _ptr(vy), _ptr(vz)))
+
+
+def steps_cyl_set_precision(ctx, precision: int):
+    _check(load().steps_cyl_set_precision(ctx, int(precision)))
+
+
+def steps_cyl_diagnostics(ctx) -> np.ndarray:
+    out = np.zeros(8)
+    _check(load().steps_cyl_diagnostics(ctx, _ptr(out)))
+    return out
+
+
+def steps_cyl_last_timing(ctx):
+    imgs, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().steps_cyl_last_timing(ctx, ctypes.byref(imgs), ctypes.byref(ms)))
+    return imgs.value, ms.value
+
+
+def steps_cyl_free(ctx):
+    if ctx:
+        _check(load().steps_cyl_free(ctx))
+
+
+class Simulation:
+    """Convenience owner of one context (numpy/torch arrays in, numpy out)."""
+
+    def __init__(self, cfg: Config, pos, vel, m, h):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        vel = np.ascontiguousarray(vel, dtype=np.float64)
+        self.n = pos.shape[0]
+        cols = [np.ascontiguousarray(pos[:, k]) for k in range(3)] + [np.ascontiguousarray(vel[:, k]) for k in range(3)]
+        self.cfg = cfg
+        self.ctx = steps_cyl_init(cfg, self.n, *cols, np.ascontiguousarray(m, dtype=np.float64),
+                                  np.ascontiguousarray(h, dtype=np.float64))
+
+    def forces(self) -> np.ndarray:
+        out = [np.zeros(self.n) for _ in range(3)]
+        steps_cyl_forces(self.ctx, *out)
+        return np.stack(out, 1)
+
+    def forces_subset(self, idx) -> np.ndarray:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = [np.zeros(idx.shape[0]) for _ in range(3)]
+        steps_cyl_forces_subset(self.ctx, idx, *out)
+        return np.stack(out, 1)
+
+    def step(self, dt: float, nsteps: int = 1):
+        steps_cyl_kdk_step(self.ctx, dt, nsteps)
+
+    def state(self):
+        out = [np.zeros(self.n) for _ in range(6)]
+        a, t = steps_cyl_get_state(self.ctx, *out)
+        return np.stack(out[:3], 1), np.stack(out[3:], 1), a, t
+
+    def set_precision(self, precision: int):
+        steps_cyl_set_precision(self.ctx, precision)
+
+    def diagnostics(self) -> np.ndarray:
+        return steps_cyl_diagnostics(self.ctx)
+
+    def last_timing(self):
+        return steps_cyl_last_timing(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            steps_cyl_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

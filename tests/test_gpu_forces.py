@@ -1,0 +1,204 @@
+"""GPU parity of the force path (pair kernels + background) against the FP64
+oracle, through the C ABI. Gates: relative force error <= 1e-5 at the median
+and <= 1e-3 at the 99.9th percentile for the FP32 forms; FP64 far tighter."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_20787_gb300 import ics
+from tests.gpu_helpers import oracle_accel, rel_err, stats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_20787_gb300 import steps_cyl
+    steps_cyl.load()
+    return steps_cyl
+
+
+def make_sim(sc, d, n_cut, precision, background=1, **kw):
+    cfg = sc.Config(n_cut=n_cut, precision=precision, background=background, **kw)
+    return sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+
+
+@pytest.fixture(scope="module")
+def small(sc):
+    w = ics.WORKLOADS["plain_small_n2048"]
+    d = ics.workload_ics(w)
+    ref = oracle_accel(d["pos"], d["m"], d["h"], w.n_cut)
+    return w, d, ref
+
+
+@pytest.mark.parametrize("precision,med_gate,p999_gate", [(1, 1e-5, 1e-3), (2, 1e-5, 1e-3), (0, 1e-11, 1e-9)])
+def test_small_workload_all_particles(sc, small, precision, med_gate, p999_gate):
+    w, d, ref = small
+    sim = make_sim(sc, d, w.n_cut, precision)
+    a = sim.forces()
+    med, p999, mx = stats(a, ref)
+    print(f"precision {precision}: median {med:.3e} p99.9 {p999:.3e} max {mx:.3e}")
+    assert med <= med_gate and p999 <= p999_gate
+    sim.close()
+
+
+def test_kahan_not_worse_than_plain(sc, small):
+    w, d, ref = small
+    sims = [make_sim(sc, d, w.n_cut, p) for p in (1, 2)]
+    meds = [stats(s.forces(), ref)[0] for s in sims]
+    assert meds[0] <= meds[1] * 1.5 + 1e-9
+    for s in sims:
+        s.close()
+
+
+@pytest.mark.parametrize("n,n_cut", [(2, 1), (37, 1), (130, 3), (300, 5), (257, 16)])
+def test_ragged_sizes_and_small_windows(sc, n, n_cut):
+    d = ics.particle_load(n, 100 + n, 1.0)
+    ref = oracle_accel(d["pos"], d["m"], d["h"], n_cut)
+    for precision in (0, 1):
+        sim = make_sim(sc, d, n_cut, precision)
+        med, p999, mx = stats(sim.forces(), ref)
+        assert mx < (1e-10 if precision == 0 else 2e-4), (precision, med, mx)
+        sim.close()
+
+
+def test_window_ties_and_wrap(sc):
+    # equal z (r_z = 0: 2 Ncut - 1 images), z at 0 and next to L (pairs across
+    # the boundary), and dz = L/2 exactly
+    pos = np.array([[0.3, 0.1, 0.25], [-0.4, 0.2, 0.25], [0.0, 0.9, 0.0], [0.5, -0.5, 1.0 - 2.0 ** -30],
+                    [1.1, 0.3, 0.75], [-0.2, -1.0, 0.5]])
+    n = pos.shape[0]
+    d = {"pos": pos, "vel": np.zeros((n, 3)), "m": np.linspace(0.5, 1.5, n), "h": np.full(n, 0.02)}
+    for n_cut in (1, 2, 7):
+        ref = oracle_accel(pos, d["m"], d["h"], n_cut)
+        for precision in (0, 1):
+            sim = make_sim(sc, d, n_cut, precision)
+            mx = stats(sim.forces(), ref)[2]
+            assert mx < (1e-11 if precision == 0 else 1e-5), (n_cut, precision, mx)
+            sim.close()
+
+
+def test_softening_dominated(sc):
+    # softening lengths of several L: many images inside the spline support
+    d = ics.particle_load(200, 7, 1.0)
+    d["h"] = np.random.default_rng(1).uniform(0.05, 3.0, 200)
+    ref = oracle_accel(d["pos"], d["m"], d["h"], 8)
+    for precision in (0, 1):
+        sim = make_sim(sc, d, 8, precision)
+        mx = stats(sim.forces(), ref)[2]
+        assert mx < (1e-10 if precision == 0 else 1e-4), (precision, mx)
+        sim.close()
+
+
+@pytest.mark.parametrize("background", [0, 1, 2])
+def test_background_modes(sc, background):
+    d = ics.particle_load(256, 3, 1.0)
+    ref = oracle_accel(d["pos"], d["m"], d["h"], 4, background=background)
+    sim = make_sim(sc, d, 4, 0, background=background)
+    assert stats(sim.forces(), ref)[2] < 1e-10
+    sim.close()
+
+
+def test_full_size_lcdm_sampled(sc):
+    # the benchmark's workload and launch configuration: N = 65,536, Ncut = 16,
+    # comoving masses, checked on a seeded sample of i against the oracle
+    w = ics.WORKLOADS["lcdm_n65536"]
+    d = ics.workload_ics(w)
+    sim = make_sim(sc, d, w.n_cut, 1, rho_bar=w.rho_bar)
+    a = sim.forces()
+    idx = ics.subsample(w.n, 256, seed=12345)
+    ref = oracle_accel(d["pos"], d["m"], d["h"], w.n_cut, idx=idx, rho0=w.rho_bar)
+    med, p999, mx = stats(a[idx], ref)
+    print(f"N=65536 Ncut=16 FP32-Kahan: median {med:.3e} p99.9 {p999:.3e}")
+    assert med <= 1e-5 and p999 <= 1e-3
+    # subset entry point in FP64 on the same sample
+    sim.set_precision(0)
+    a64 = sim.forces_subset(idx)
+    assert stats(a64, ref)[2] < 1e-10
+    sim.close()
+
+
+def test_deterministic(sc):
+    d = ics.particle_load(3000, 5, 1.0)
+    sim = make_sim(sc, d, 16, 1)
+    a1 = sim.forces()
+    a2 = sim.forces()
+    np.testing.assert_array_equal(a1, a2)
+    sim.close()
+
+
+def test_subset_matches_full(sc):
+    d = ics.particle_load(700, 9, 1.0)
+    sim = make_sim(sc, d, 6, 1)
+    full = sim.forces()
+    idx = np.array([0, 699, 350, 1, 350])
+    np.testing.assert_array_equal(sim.forces_subset(idx), full[idx])
+    sim.close()
+
+
+def test_newton_third_law_and_z_translation(sc):
+    d = ics.particle_load(1024, 21, 1.0)
+    sim = make_sim(sc, d, 16, 1, background=0)
+    a = sim.forces()
+    net = (d["m"][:, None] * a).sum(0)
+    scale = (d["m"][:, None] * np.abs(a)).sum()
+    assert np.all(np.abs(net) < 1e-6 * scale)
+    d2 = dict(d)
+    d2["pos"] = d["pos"].copy()
+    d2["pos"][:, 2] = np.mod(d["pos"][:, 2] + 0.3141592653589793, 1.0)
+    sim2 = make_sim(sc, d2, 16, 1, background=0)
+    r = rel_err(sim2.forces(), a)
+    assert np.median(r) < 1e-6
+    sim.close()
+    sim2.close()
+
+
+def test_device_and_host_pointers_agree(sc):
+    import torch
+    d = ics.particle_load(500, 4, 1.0)
+    cfg = sc.Config(n_cut=8, stream=torch.cuda.current_stream().cuda_stream)
+    dev = torch.device("cuda:0")
+    cols = [torch.tensor(np.ascontiguousarray(d["pos"][:, k]), device=dev) for k in range(3)]
+    vel = [torch.zeros(500, dtype=torch.float64, device=dev) for _ in range(3)]
+    ctx = sc.steps_cyl_init(cfg, 500, *cols, *vel, torch.tensor(d["m"], device=dev), torch.tensor(d["h"], device=dev))
+    out_d = [torch.empty(500, dtype=torch.float64, device=dev) for _ in range(3)]
+    sc.steps_cyl_forces(ctx, *out_d)
+    torch.cuda.synchronize()
+    out_h = [np.zeros(500) for _ in range(3)]
+    sc.steps_cyl_forces(ctx, *out_h)
+    np.testing.assert_array_equal(torch.stack(out_d, 1).cpu().numpy(), np.stack(out_h, 1))
+    sc.steps_cyl_free(ctx)
+
+
+def test_invalid_inputs_are_rejected(sc):
+    d = ics.particle_load(64, 2, 1.0)
+    bad = dict(d)
+    bad["pos"] = d["pos"].copy()
+    bad["pos"][3, 0] = np.nan
+    with pytest.raises(sc.StepsError) as e:
+        make_sim(sc, bad, 4, 1)
+    assert e.value.code == sc.STEPS_EINVAL
+    bad["pos"] = d["pos"].copy()
+    bad["pos"][5, 2] = 1.0  # z must be < L
+    with pytest.raises(sc.StepsError):
+        make_sim(sc, bad, 4, 1)
+    bad = dict(d)
+    bad["h"] = d["h"].copy()
+    bad["h"][0] = 0.0
+    with pytest.raises(sc.StepsError):
+        make_sim(sc, bad, 4, 1)
+    with pytest.raises(sc.StepsError):
+        make_sim(sc, d, 0, 1)
+    one = {k: v[:1] for k, v in d.items()}
+    with pytest.raises(sc.StepsError):
+        make_sim(sc, one, 4, 1)
+    sim = make_sim(sc, d, 4, 1)
+    with pytest.raises(sc.StepsError):
+        sim.forces_subset(np.array([0, 64]))
+    with pytest.raises(sc.StepsError):
+        sim.step(-1.0)
+    sim.close()

@@ -135,6 +135,40 @@ int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
  * its pair kernel in milliseconds (CUDA events on the context stream). */
 int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
 
+/* ---- allocation-free pair accelerations ----------------------------------
+ * This entry point has no counterpart in the paper; it serves callers that may
+ * not allocate device memory: a host whose device memory is owned and budgeted
+ * by another allocator (a caching allocator or an arena reserved at start-up), a
+ * loop that must not take cudaMalloc's implicit device-wide synchronisation, or
+ * a plug-in that may allocate only while it initialises. It computes the pair
+ * term of eq. ComovingEquationsOfMotionCylindrical in static space,
+ *   a_i = G sum_{j != i} m_j F_S1R2(x_i - x_j, h_i + h_j),
+ * i.e. what steps_cyl_forces returns for a context with STEPS_BG_OFF and a = 1,
+ * with the same kernels, and calls no cudaMalloc, cudaFree or allocating library
+ * routine. Its scratch (packed positions, work-split partial sums, error word)
+ * is one file-scope device array of STEPS_NOALLOC_SCRATCH_BYTES bytes that every
+ * device loading this library holds until the process exits.
+ *   - n: 2 <= n <= STEPS_NOALLOC_MAX_N, else STEPS_EINVAL (nothing is launched).
+ *   - x, y, z, m, h (inputs) and ax, ay, az (outputs): device memory of the
+ *     calling thread's current device, length n, doubles; z in [0, L); m, h > 0.
+ *   - precision: STEPS_FP32_KAHAN or STEPS_FP32_PLAIN; n_cut in [1, 4096];
+ *     G, L > 0. stream: cudaStream_t to enqueue on (NULL = legacy default).
+ *   - The call returns once the work is enqueued; non-finite results are not
+ *     reported (check the outputs).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind: calls whose
+ *     work overlaps on the GPU (two streams, two threads) race and give wrong
+ *     results, so serialise them. */
+#define STEPS_NOALLOC_MAX_N 65536
+#define STEPS_NOALLOC_MAX_CTAS 2048
+#define STEPS_NOALLOC_SCRATCH_BYTES 9961728
+int steps_cyl_pair_accel_noalloc(int64_t n, const double* x, const double* y, const double* z,
+                                 const double* m, const double* h, double G, double L,
+                                 int32_t n_cut, int32_t precision, double* ax, double* ay,
+                                 double* az, void* stream);
+
 /* Release the context and its device memory. NULL is accepted. */
 int steps_cyl_free(steps_cyl_ctx* ctx);
 

@@ -6,6 +6,8 @@
 #include "pair_fp32.cuh"
 
 namespace steps {
+// The kernels below have internal linkage (static): every translation unit
+// that includes this header gets its own copy.
 
 constexpr int kErrNonFinite = 1;     // a force, position or momentum is not finite
 constexpr int kErrBgRange = 2;       // a particle lies beyond the background table
@@ -21,7 +23,7 @@ __device__ __forceinline__ void pack_one(double x, double y, double z, double m,
   jB[i] = make_float4(xl, yl, zl, (float)(h * invL));
 }
 
-__global__ void pack_kernel(const double* __restrict__ x, const double* __restrict__ y,
+static __global__ void pack_kernel(const double* __restrict__ x, const double* __restrict__ y,
                             const double* __restrict__ z, const double* __restrict__ m,
                             const double* __restrict__ h, int n, double invL, float4* __restrict__ jA,
                             float4* __restrict__ jB) {
@@ -69,7 +71,7 @@ __device__ __forceinline__ double background_F(const BgParams& bg, double rho, i
 // NT == 0), scale to the comoving field
 // g = a^3 (pair + background), store it, optionally kick p += g K and optionally
 // write a = g / a^3 to an output.
-__global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
+static __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
                                 double pair_scale, BgParams bg, const double* __restrict__ x,
                                 const double* __restrict__ y, double* __restrict__ gx,
                                 double* __restrict__ gy, double* __restrict__ gz, double K,
@@ -118,7 +120,7 @@ __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, 
 }
 
 // First half of a KDK step: p += g K1; x += p D; z wrapped into [0, L); repack.
-__global__ void kick_drift_pack_kernel(double* __restrict__ x, double* __restrict__ y,
+static __global__ void kick_drift_pack_kernel(double* __restrict__ x, double* __restrict__ y,
                                        double* __restrict__ z, double* __restrict__ px,
                                        double* __restrict__ py, double* __restrict__ pz,
                                        const double* __restrict__ gx, const double* __restrict__ gy,
@@ -141,7 +143,7 @@ __global__ void kick_drift_pack_kernel(double* __restrict__ x, double* __restric
 }
 
 // y = s x for three arrays (acceleration output = g / a^3).
-__global__ void scale3_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
+static __global__ void scale3_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
                               const double* __restrict__ az, int n, double s, double* __restrict__ ox,
                               double* __restrict__ oy, double* __restrict__ oz) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -150,7 +152,7 @@ __global__ void scale3_kernel(const double* __restrict__ ax, const double* __res
 }
 
 // p = a^2 v (and back) on three arrays.
-__global__ void axpy_scale3_kernel(double* __restrict__ a0, double* __restrict__ a1, double* __restrict__ a2,
+static __global__ void axpy_scale3_kernel(double* __restrict__ a0, double* __restrict__ a1, double* __restrict__ a2,
                                    int n, double s) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     a0[i] *= s; a1[i] *= s; a2[i] *= s;
@@ -162,7 +164,7 @@ __global__ void axpy_scale3_kernel(double* __restrict__ a0, double* __restrict__
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 256;
 
-__global__ void diag_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
+static __global__ void diag_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                     const double* __restrict__ px, const double* __restrict__ py,
                                     const double* __restrict__ pz, const double* __restrict__ m, int n,
                                     double* __restrict__ part) {
@@ -191,7 +193,7 @@ __global__ void diag_partial_kernel(const double* __restrict__ x, const double* 
   }
 }
 
-__global__ void diag_final_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+static __global__ void diag_final_kernel(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
   if (threadIdx.x < 6) {
     double s = 0.0;
     for (int b = 0; b < nblocks; ++b) s += part[b * 6 + threadIdx.x];
@@ -229,7 +231,7 @@ __device__ __forceinline__ void image_fp64(double dR2, double o, double hh, doub
   sz = fma(o, f, sz);
 }
 
-__global__ void __launch_bounds__(128)
+static __global__ void __launch_bounds__(128)
 pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
                  const double* __restrict__ m, const double* __restrict__ h, int n,
                  const int64_t* __restrict__ idx, int ni, double invL, int n_cut, double* __restrict__ out) {
@@ -263,7 +265,7 @@ pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, con
 }
 
 // out3 (SoA, ni each) = pair_scale * pair + background at the listed i, / a^3
-__global__ void subset_finalize_kernel(const double* __restrict__ pairsum, int ni, const int64_t* __restrict__ idx,
+static __global__ void subset_finalize_kernel(const double* __restrict__ pairsum, int ni, const int64_t* __restrict__ idx,
                                        double pair_scale, BgParams bg, const double* __restrict__ x,
                                        const double* __restrict__ y, double inv_a3, double* __restrict__ ox,
                                        double* __restrict__ oy, double* __restrict__ oz, int* __restrict__ err) {

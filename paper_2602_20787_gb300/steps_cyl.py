@@ -34,8 +34,11 @@ _EXPORTS = [
     "steps_cyl_params_default", "steps_cyl_init", "steps_cyl_forces", "steps_cyl_forces_subset",
     "steps_cyl_kdk_step", "steps_cyl_get_state", "steps_cyl_set_state", "steps_cyl_set_precision",
     "steps_cyl_diagnostics", "steps_cyl_last_timing", "steps_cyl_free", "steps_cyl_strerror",
-    "steps_cyl_last_error",
+    "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc",
 ]
+
+# size limit of the allocation-free entry point (include/steps_cyl.h)
+STEPS_NOALLOC_MAX_N = 65536
 
 
 class StepsError(RuntimeError):
@@ -91,6 +94,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_strerror.restype = ctypes.c_char_p
     L.steps_cyl_last_error.argtypes = []
     L.steps_cyl_last_error.restype = ctypes.c_char_p
+    L.steps_cyl_pair_accel_noalloc.argtypes = [i64, p, p, p, p, p, d, d, i32, i32, p, p, p, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -227,6 +231,22 @@ def steps_cyl_last_timing(ctx):
 def steps_cyl_free(ctx):
     if ctx:
         _check(load().steps_cyl_free(ctx))
+
+
+def steps_cyl_pair_accel_noalloc(x, y, z, m, h, G, L, n_cut, precision, ax, ay, az, stream=0):
+    """Pair accelerations with no device allocation (CUDA float64 tensors of the
+    current device; outputs written in place). For callers that may not allocate
+    device memory: see include/steps_cyl.h for the contract, its scratch limit
+    and why concurrent calls must be serialised."""
+    _check_f64(x, y, z, m, h, ax, ay, az)
+    n = int(x.numel() if hasattr(x, "numel") else len(x))
+    if n > STEPS_NOALLOC_MAX_N:
+        raise StepsError(STEPS_EINVAL, f"n = {n} exceeds STEPS_NOALLOC_MAX_N = {STEPS_NOALLOC_MAX_N}")
+    rc = load().steps_cyl_pair_accel_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L),
+                                             int(n_cut), int(precision), _ptr(ax), _ptr(ay), _ptr(az),
+                                             ctypes.c_void_p(stream or None))
+    if rc != STEPS_OK:
+        raise StepsError(rc, "steps_cyl_pair_accel_noalloc rejected its arguments or failed to launch")
 
 
 class Simulation:

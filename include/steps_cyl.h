@@ -73,13 +73,16 @@ typedef struct {
   double a_start;   /* scale factor at t_start (1 in static space) */
   double t_start;   /* cosmic time at the start */
   int32_t device;   /* CUDA device ordinal */
-  int32_t reserved; /* must be 0 */
+  int32_t reorder_every; /* particles are kept in a Morton order of (x, y) inside the library (results are
+                          * returned in the caller's order); it is rebuilt at init, by set_state, and every
+                          * reorder_every KDK steps (0: never during stepping; -1: keep the caller's order) */
   void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
 } steps_cyl_params;
 
 /* Fill *p with defaults: G = L = 1, R_sim = 0.5 tan(0.45 pi), rho_bar = 0, n_cut = 16,
  * n0 = 4, FP32_KAHAN, TAIL_FULL, BG_FINITE, static space, H0 = 1, Omega_m = 0.3,
- * Omega_L = 0.7, w0 = -1, wa = 0, a_start = 1, t_start = 0, device 0, default stream. */
+ * Omega_L = 0.7, w0 = -1, wa = 0, a_start = 1, t_start = 0, device 0, reorder_every = 32,
+ * default stream. */
 int steps_cyl_params_default(steps_cyl_params* p);
 
 /* Create a context holding n particles (eq. ComovingEquationsOfMotionCylindrical state).

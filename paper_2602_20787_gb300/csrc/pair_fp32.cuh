@@ -39,6 +39,15 @@ namespace steps {
 constexpr int kBI = 128;  // i per CTA (one per thread)
 constexpr int kBJ = 128;  // j per shared-memory tile
 
+// Tuning knobs (build-time; the defaults are the measured best on GB300).
+#ifndef STEPS_KAHAN_GROUP
+#define STEPS_KAHAN_GROUP 4   // pair forces summed plainly in groups of this many j before the Kahan update
+#endif
+#ifndef STEPS_SPLINE_UNROLL
+#define STEPS_SPLINE_UNROLL 2 // unroll of the spline-capable image loop
+#endif
+constexpr int kSplineUnroll = STEPS_SPLINE_UNROLL;
+
 typedef unsigned long long u64;
 
 __device__ __forceinline__ u64 pk(float a, float b) {
@@ -67,6 +76,11 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
 __device__ __forceinline__ float rsq(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -115,25 +129,39 @@ __device__ __forceinline__ u64 spline_over_r2(u64 O, u64 DR2, u64 IH, u64 IH3) {
 __device__ __forceinline__ void pair_images_fp32(float dR2, float dz, float hh, int n_cut, float fnc, int kw,
                                                  float& sr, float& sz) {
   const u64 DR2 = pk(dR2, dR2);
-  const float ih = 1.0f / hh;
-  const u64 IH = pk(ih, ih);
-  const float ih3 = ih * ih * ih;
-  const u64 IH3 = pk(ih3, ih3);
+  const u64 STEP = pk(1.0f, -1.0f);
   // centre image (k = 0) and edge image (dz - sign(dz) Ncut, absent at dz == 0)
   u64 O = pk(dz, dz - copysignf(fnc, dz));
-  u64 F = mul2(spline_over_r2(O, DR2, IH, IH3), pk(1.0f, dz != 0.0f ? 1.0f : 0.0f));
-  u64 SR = F;
-  u64 SZ = mul2(O, F);
-  const u64 STEP = pk(1.0f, -1.0f);
-  const int kg = min(kw, n_cut - 1);
-  O = pk(dz, dz);
+  const u64 W = pk(1.0f, dz != 0.0f ? 1.0f : 0.0f);
+  u64 SR, SZ;
   int k = 1;
-  // images that may be softened: symmetric pairs walked outward
-  for (; k <= kg; ++k) {
-    O = add2(O, STEP);
-    F = spline_over_r2(O, DR2, IH, IH3);
-    SR = add2(SR, F);
-    SZ = fma2(O, F, SZ);
+  if (kw >= 0) {
+    // some lane of the warp has its pair inside the softening support
+    const float ih = rcp_approx(hh);
+    const u64 IH = pk(ih, ih);
+    const float ih3 = ih * ih * ih;
+    const u64 IH3 = pk(ih3, ih3);
+    u64 F = mul2(spline_over_r2(O, DR2, IH, IH3), W);
+    SR = F;
+    SZ = mul2(O, F);
+    const int kg = min(kw, n_cut - 1);
+    O = pk(dz, dz);
+#pragma unroll(kSplineUnroll)
+    for (; k <= kg; ++k) {
+      O = add2(O, STEP);
+      F = spline_over_r2(O, DR2, IH, IH3);
+      SR = add2(SR, F);
+      SZ = fma2(O, F, SZ);
+    }
+  } else {
+    const u64 R2 = fma2(O, O, DR2);
+    float ra, rb;
+    upk(R2, ra, rb);
+    const u64 RI = pk(rsq(ra), rsq(rb));
+    const u64 R3 = mul2(mul2(mul2(RI, RI), RI), W);
+    SR = R3;
+    SZ = mul2(O, R3);
+    O = pk(dz, dz);
   }
   // Newtonian images
 #pragma unroll 4
@@ -201,28 +229,38 @@ pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, i
       __syncthreads();
       const int jn = min(kBJ, n - t * kBJ);
       const int self = i - t * kBJ;  // local index of the self pair in this tile, if any
-      for (int k = 0; k < jn; ++k) {
-        const float4 A = sA[k];
-        const float4 B = sB[k];
-        const float dx = (I.xh - A.x) + (I.xl - B.x);
-        const float dy = (I.yh - A.y) + (I.yl - B.y);
-        // wrap the hi difference before adding the lo words, so a separation
-        // just below L keeps its small wrapped value (the window edge depends
-        // on the sign of dz)
-        float dz = I.zh - A.z;
-        dz = (dz - rintf(dz)) + (I.zl - B.z);
-        const float dR2 = fmaf(dx, dx, dy * dy);
-        const float hh = I.h + B.w;
-        // images with |k| <= hh + 1/2 can be inside the support when dR < hh
-        const int kl = dR2 < hh * hh ? (int)(hh + 0.5f) : 0;
-        const int kw = __reduce_max_sync(0xffffffffu, kl);
-        float sr, szz;
-        pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
-        const float mj = (k == self) ? 0.0f : A.w;
-        const float msr = mj * sr;
-        acc<KAHAN>(sx, cx, dx * msr);
-        acc<KAHAN>(sy, cy, dy * msr);
-        acc<KAHAN>(sz, cz, mj * szz);
+      // pair forces are summed plainly over groups of STEPS_KAHAN_GROUP j, and
+      // each group sum enters the compensated per-i sum
+      for (int k0 = 0; k0 < jn; k0 += STEPS_KAHAN_GROUP) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        const int ke = min(k0 + STEPS_KAHAN_GROUP, jn);
+        for (int k = k0; k < ke; ++k) {
+          const float4 A = sA[k];
+          const float4 B = sB[k];
+          const float dx = (I.xh - A.x) + (I.xl - B.x);
+          const float dy = (I.yh - A.y) + (I.yl - B.y);
+          // wrap the hi difference before adding the lo words, so a separation
+          // just below L keeps its small wrapped value (the window edge depends
+          // on the sign of dz)
+          float dz = I.zh - A.z;
+          dz = (dz - rintf(dz)) + (I.zl - B.z);
+          const float dR2 = fmaf(dx, dx, dy * dy);
+          const float hh = I.h + B.w;
+          // images with |k| <= hh + 1/2 can be inside the support when dR < hh;
+          // kw = -1: no lane's pair is softened, every image is Newtonian
+          const int kl = dR2 < hh * hh ? (int)(hh + 0.5f) : -1;
+          const int kw = __reduce_max_sync(0xffffffffu, kl);
+          float sr, szz;
+          pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
+          const float mj = (k == self) ? 0.0f : A.w;
+          const float msr = mj * sr;
+          gx = fmaf(dx, msr, gx);
+          gy = fmaf(dy, msr, gy);
+          gz = fmaf(mj, szz, gz);
+        }
+        acc<KAHAN>(sx, cx, gx);
+        acc<KAHAN>(sy, cy, gy);
+        acc<KAHAN>(sz, cz, gz);
       }
     }
     const long long slot = (long long)b + c;

@@ -6,6 +6,15 @@
 // part of the background term (eq. F_horiz), and the launch sequence of a force
 // evaluation and of a KDK step. All particle work runs in the kernels of
 // pair_fp32.cuh and nbody_kernels.cuh.
+//
+// Particle order. Inside a context the particles are kept in an internal order
+// along a Morton (Z-order) curve of (x, y), so that the 32 i-particles of a warp
+// are close in the transverse plane: their pairs with a given j are then
+// softened together or not at all, which keeps the warp-uniform spline bound of
+// the pair kernel small. perm[k] is the caller's index of internal particle k;
+// every input is gathered through perm and every output scattered back, so the
+// caller only ever sees its own order. The order is rebuilt at init, when
+// set_state moves particles, and every reorder_every KDK steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +29,12 @@
 #include "nbody_kernels.cuh"
 
 using namespace steps;
+
+// CTAs of the pair kernel per resident slot (build-time tuning knob): more CTAs
+// than slots lets the block scheduler even out CTAs whose work differs.
+#ifndef STEPS_CTA_MULT
+#define STEPS_CTA_MULT 8
+#endif
 
 namespace {
 
@@ -183,15 +198,19 @@ struct steps_cyl_ctx {
   cudaStream_t st = nullptr;
   Cosmology cosmo{};
   double a = 1.0, t = 0.0, rho0 = 0.0, invL = 1.0;
-  // device state (FP64 SoA)
+  // device state (FP64 SoA, internal order)
   double* state = nullptr;  // one allocation for the 11 arrays below
   double *x, *y, *z, *px, *py, *pz, *m, *h, *gx, *gy, *gz;
   float4* jA = nullptr;
   float4* jB = nullptr;
-  double* part = nullptr;   // stream-K partials or direct FP64 sums
+  double* part = nullptr;   // stream-K partials or direct FP64 sums; also a permutation temporary
   size_t part_elems = 0;
-  double* stage = nullptr;  // 3 n doubles for outputs
+  double* stage = nullptr;  // 3 n doubles: inputs and outputs in the caller's order
   double* red = nullptr;    // reduction scratch
+  int* perm = nullptr;      // internal -> caller index (device)
+  int* iperm = nullptr;     // caller -> internal index (device)
+  int* ord = nullptr;       // re-ordering of internal indices (device)
+  std::vector<int> perm_h;  // host copy of perm
   int64_t* idx = nullptr;   // subset indices (grown on demand)
   int idx_cap = 0;
   double* sub = nullptr;    // subset sums (3 * idx_cap)
@@ -201,6 +220,7 @@ struct steps_cyl_ctx {
   double bg_dr = 0.0;
   int C = 0, NT = 0, NB = 0;
   long long U = 0;
+  int steps_since_order = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double last_images = 0.0;
   bool timed = false;
@@ -234,7 +254,7 @@ int check_params(const steps_cyl_params* p) {
   if (p->comoving) {
     if (!(p->H0 > 0) || !(p->a_start > 0)) return fail(STEPS_EINVAL, "comoving runs need H0 > 0 and a_start > 0");
   }
-  if (p->reserved != 0) return fail(STEPS_EINVAL, "reserved must be 0");
+  if (p->reorder_every < -1) return fail(STEPS_EINVAL, "reorder_every must be >= -1");
   return STEPS_OK;
 }
 
@@ -256,15 +276,17 @@ __global__ void validate_kernel(const double* __restrict__ x, const double* __re
   }
 }
 
-// Sets *changed when any uploaded position differs bitwise from the current one.
+// Sets *changed when any staged position (caller order) differs bitwise from the
+// current one (internal order).
 __global__ void positions_changed_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                          const double* __restrict__ z, const double* __restrict__ nx,
-                                         const double* __restrict__ ny, const double* __restrict__ nz, int n,
-                                         int* __restrict__ changed) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (__double_as_longlong(x[i]) != __double_as_longlong(nx[i]) ||
-        __double_as_longlong(y[i]) != __double_as_longlong(ny[i]) ||
-        __double_as_longlong(z[i]) != __double_as_longlong(nz[i])) {
+                                         const double* __restrict__ ny, const double* __restrict__ nz,
+                                         const int* __restrict__ perm, int n, int* __restrict__ changed) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int i = perm[k];
+    if (__double_as_longlong(x[k]) != __double_as_longlong(nx[i]) ||
+        __double_as_longlong(y[k]) != __double_as_longlong(ny[i]) ||
+        __double_as_longlong(z[k]) != __double_as_longlong(nz[i])) {
       atomicOr(changed, 32);
     }
   }
@@ -279,19 +301,41 @@ __global__ void max_rho_kernel(const double* __restrict__ x, const double* __res
   atomicMax(out, (unsigned long long)__double_as_longlong(r));
 }
 
+// dst[k] = s * src[map[k]]
+__global__ void gather_kernel(const double* __restrict__ src, const int* __restrict__ map, int n, double s,
+                              double* __restrict__ dst) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[k] = s * src[map[k]];
+}
+
+// dst[map[k]] = s * src[k]
+__global__ void scatter_kernel(const double* __restrict__ src, const int* __restrict__ map, int n, double s,
+                               double* __restrict__ dst) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[map[k]] = s * src[k];
+}
+
 __global__ void gather3_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
-                               const double* __restrict__ az, const int64_t* __restrict__ idx, int ni,
+                               const double* __restrict__ az, const int64_t* __restrict__ idx, int ni, double s,
                                double* __restrict__ ox, double* __restrict__ oy, double* __restrict__ oz) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < ni) {
     const int64_t i = idx[q];
-    ox[q] = ax[i]; oy[q] = ay[i]; oz[q] = az[i];
+    ox[q] = s * ax[i]; oy[q] = s * ay[i]; oz[q] = s * az[i];
   }
 }
 
-__global__ void check_idx_kernel(const int64_t* __restrict__ idx, int ni, int n, int* __restrict__ bad) {
+// caller indices -> internal indices, flagging out-of-range entries
+__global__ void map_idx_kernel(int64_t* __restrict__ idx, int ni, int n, const int* __restrict__ iperm,
+                               int* __restrict__ bad) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < ni && (idx[q] < 0 || idx[q] >= n)) atomicOr(bad, 16);
+  if (q < ni) {
+    const int64_t i = idx[q];
+    if (i < 0 || i >= n) {
+      atomicOr(bad, 16);
+      idx[q] = 0;
+    } else {
+      idx[q] = iperm[i];
+    }
+  }
 }
 
 int read_and_clear_err(steps_cyl_ctx* c, int* out) {
@@ -306,6 +350,77 @@ int read_and_clear_err(steps_cyl_ctx* c, int* out) {
 int device_error(int e) {
   return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
               (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range" : "");
+}
+
+// Morton (Z-order) rank of (x, y): stable sort of 2 x 16-bit interleaved cell
+// codes over the bounding box. Returns order[k] = index of the k-th particle.
+void morton_order(const std::vector<double>& x, const std::vector<double>& y, std::vector<int>& order) {
+  const size_t n = x.size();
+  double x0 = x[0], x1 = x[0], y0 = y[0], y1 = y[0];
+  for (size_t i = 1; i < n; ++i) {
+    x0 = std::min(x0, x[i]); x1 = std::max(x1, x[i]);
+    y0 = std::min(y0, y[i]); y1 = std::max(y1, y[i]);
+  }
+  const double span = std::max({x1 - x0, y1 - y0, 1e-300});
+  auto spread = [](uint32_t v) {
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+  };
+  std::vector<uint32_t> key(n);
+  for (size_t i = 0; i < n; ++i) {
+    const double fx = (x[i] - x0) / span, fy = (y[i] - y0) / span;
+    const uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(fx * 65536.0)));
+    const uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(fy * 65536.0)));
+    key[i] = spread(qx) | (spread(qy) << 1);
+  }
+  order.resize(n);
+  for (size_t i = 0; i < n; ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+}
+
+int upload_perm(steps_cyl_ctx* c) {
+  std::vector<int> inv(c->n);
+  for (int k = 0; k < c->n; ++k) inv[c->perm_h[k]] = k;
+  CK(cudaMemcpyAsync(c->perm, c->perm_h.data(), sizeof(int) * c->n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->iperm, inv.data(), sizeof(int) * c->n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));  // the host vectors go out of scope
+  return STEPS_OK;
+}
+
+// New caller->internal map from staged positions (caller order): the Morton
+// order, or the caller's order when reorder_every == -1. With carry set, the
+// per-particle arrays that are not re-uploaded (m, h) are moved from the old
+// internal order to the new one.
+int order_from_stage(steps_cyl_ctx* c, const double* sx, const double* sy, bool carry) {
+  std::vector<int> np(c->n);
+  if (c->p.reorder_every < 0) {
+    for (int k = 0; k < c->n; ++k) np[k] = k;
+  } else {
+    std::vector<double> hx(c->n), hy(c->n);
+    CK(cudaMemcpyAsync(hx.data(), sx, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hy.data(), sy, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    morton_order(hx, hy, np);
+  }
+  if (carry) {
+    std::vector<int> inv_old(c->n), o(c->n);
+    for (int k = 0; k < c->n; ++k) inv_old[c->perm_h[k]] = k;
+    for (int k = 0; k < c->n; ++k) o[k] = inv_old[np[k]];  // old internal index of new internal k
+    CK(cudaMemcpyAsync(c->ord, o.data(), sizeof(int) * c->n, cudaMemcpyHostToDevice, c->st));
+    double* tmp = c->part;
+    for (double* arr : {c->m, c->h}) {
+      gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(arr, c->ord, c->n, 1.0, tmp);
+      CK(cudaMemcpyAsync(arr, tmp, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->st));
+    }
+    CKLAUNCH("carry");
+    CK(cudaStreamSynchronize(c->st));  // o goes out of scope
+  }
+  c->perm_h.swap(np);
+  c->steps_since_order = 0;
+  return upload_perm(c);
 }
 
 int build_background(steps_cyl_ctx* c) {
@@ -337,9 +452,8 @@ int build_background(steps_cyl_ctx* c) {
 }
 
 // One force evaluation at the current packed positions. Stores g = a^3 (pair +
-// background) in gx/gy/gz; kicks p by K when kick is set; writes g inv_a3 to
-// (ox, oy, oz) when given (device pointers).
-int eval_forces(steps_cyl_ctx* c, bool kick, double K, double* ox, double* oy, double* oz, double inv_a3) {
+// background) in gx/gy/gz (internal order); kicks p by K when kick is set.
+int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   const double pair_scale = -c->p.G * c->invL * c->invL;
   CK(cudaEventRecord(c->e0, c->st));
   if (c->p.precision == STEPS_FP64) {
@@ -359,25 +473,43 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K, double* ox, double* oy, d
   const int NT = c->p.precision == STEPS_FP64 ? 0 : c->NT;
   finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
       c->part, c->n, NT, c->U, c->C, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
-      kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, inv_a3, ox, oy, oz, c->err);
+      kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
   CKLAUNCH("finalize");
   return STEPS_OK;
 }
 
-int upload_state(steps_cyl_ctx* c, const double* x, const double* y, const double* z, const double* vx,
-                 const double* vy, const double* vz) {
+// Stage the caller's positions (any memory) into stage[0 .. 3n).
+int stage_positions(steps_cyl_ctx* c, const double* x, const double* y, const double* z) {
   const size_t b = sizeof(double) * (size_t)c->n;
-  CK(cudaMemcpyAsync(c->x, x, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(c->y, y, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(c->z, z, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(c->px, vx, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(c->py, vy, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(c->pz, vz, b, cudaMemcpyDefault, c->st));
-  // canonical momentum p = a^2 dx/dt
-  if (c->a != 1.0) {
-    axpy_scale3_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->px, c->py, c->pz, c->n, c->a * c->a);
-    CKLAUNCH("to_momentum");
-  }
+  double* s = c->stage;
+  CK(cudaMemcpyAsync(s, x, b, cudaMemcpyDefault, c->st));
+  CK(cudaMemcpyAsync(s + c->n, y, b, cudaMemcpyDefault, c->st));
+  CK(cudaMemcpyAsync(s + 2 * (size_t)c->n, z, b, cudaMemcpyDefault, c->st));
+  return STEPS_OK;
+}
+
+// Caller-order array (any memory) -> internal array, scaled.
+int gather_in(steps_cyl_ctx* c, const double* src, double* dst, double scale) {
+  // the last third of stage is free once the positions are gathered
+  double* tmp = c->stage + 2 * (size_t)c->n;
+  CK(cudaMemcpyAsync(tmp, src, sizeof(double) * c->n, cudaMemcpyDefault, c->st));
+  gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(tmp, c->perm, c->n, scale, dst);
+  CKLAUNCH("gather");
+  return STEPS_OK;
+}
+
+// Staged positions (caller order) and caller velocities -> internal state.
+int install_state(steps_cyl_ctx* c, const double* vx, const double* vy, const double* vz) {
+  double* s = c->stage;
+  gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(s, c->perm, c->n, 1.0, c->x);
+  gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(s + c->n, c->perm, c->n, 1.0, c->y);
+  gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(s + 2 * (size_t)c->n, c->perm, c->n, 1.0, c->z);
+  CKLAUNCH("gather positions");
+  int rc;
+  const double a2 = c->a * c->a;  // canonical momentum p = a^2 dx/dt
+  if ((rc = gather_in(c, vx, c->px, a2))) return rc;
+  if ((rc = gather_in(c, vy, c->py, a2))) return rc;
+  if ((rc = gather_in(c, vz, c->pz, a2))) return rc;
   return STEPS_OK;
 }
 
@@ -402,6 +534,34 @@ int pack_positions(steps_cyl_ctx* c) {
   return STEPS_OK;
 }
 
+// Re-order the device-resident particles along the Morton curve of their
+// current (x, y): all per-particle arrays are permuted in place through a
+// temporary, perm is composed, and the packed arrays are rebuilt.
+int reorder(steps_cyl_ctx* c) {
+  if (c->p.reorder_every < 0) return STEPS_OK;
+  std::vector<double> hx(c->n), hy(c->n);
+  CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  std::vector<int> o;
+  morton_order(hx, hy, o);
+  CK(cudaMemcpyAsync(c->ord, o.data(), sizeof(int) * c->n, cudaMemcpyHostToDevice, c->st));
+  double* tmp = c->part;  // part_elems >= 3 n
+  double* arrays[11] = {c->x, c->y, c->z, c->px, c->py, c->pz, c->m, c->h, c->gx, c->gy, c->gz};
+  for (double* arr : arrays) {
+    gather_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(arr, c->ord, c->n, 1.0, tmp);
+    CK(cudaMemcpyAsync(arr, tmp, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->st));
+  }
+  CKLAUNCH("reorder");
+  std::vector<int> np(c->n);
+  for (int k = 0; k < c->n; ++k) np[k] = c->perm_h[o[k]];
+  c->perm_h.swap(np);
+  c->steps_since_order = 0;
+  int rc;
+  if ((rc = upload_perm(c))) return rc;
+  return pack_positions(c);
+}
+
 void release(steps_cyl_ctx* c) {
   if (!c) return;
   int prev = 0;
@@ -414,6 +574,9 @@ void release(steps_cyl_ctx* c) {
   cudaFree(c->part);
   cudaFree(c->stage);
   cudaFree(c->red);
+  cudaFree(c->perm);
+  cudaFree(c->iperm);
+  cudaFree(c->ord);
   cudaFree(c->idx);
   cudaFree(c->sub);
   cudaFree(c->err);
@@ -436,13 +599,23 @@ struct DeviceGuard {
   }
 };
 
-int copy_out3(steps_cyl_ctx* c, const double* sx, const double* sy, const double* sz, double* ox, double* oy,
-              double* oz, size_t cnt) {
-  const size_t b = sizeof(double) * cnt;
+// Internal-order arrays -> caller-order outputs (any memory), scaled. Device
+// outputs receive the scatter directly; host outputs go through stage.
+int scatter_out(steps_cyl_ctx* c, const double* const src[3], double* const dst[3], double scale) {
   bool host = false;
-  if (ox) { CK(cudaMemcpyAsync(ox, sx, b, cudaMemcpyDefault, c->st)); host |= is_host_ptr(ox); }
-  if (oy) { CK(cudaMemcpyAsync(oy, sy, b, cudaMemcpyDefault, c->st)); host |= is_host_ptr(oy); }
-  if (oz) { CK(cudaMemcpyAsync(oz, sz, b, cudaMemcpyDefault, c->st)); host |= is_host_ptr(oz); }
+  for (int q = 0; q < 3; ++q) {
+    if (!dst[q]) continue;
+    if (is_host_ptr(dst[q])) {
+      double* s = c->stage + (size_t)q * c->n;
+      scatter_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, s);
+      CKLAUNCH("scatter");
+      CK(cudaMemcpyAsync(dst[q], s, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+      host = true;
+    } else {
+      scatter_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, dst[q]);
+      CKLAUNCH("scatter");
+    }
+  }
   if (host) CK(cudaStreamSynchronize(c->st));
   return STEPS_OK;
 }
@@ -476,7 +649,7 @@ int steps_cyl_params_default(steps_cyl_params* p) {
   p->a_start = 1.0;
   p->t_start = 0.0;
   p->device = 0;
-  p->reserved = 0;
+  p->reorder_every = 32;
   p->stream = nullptr;
   return STEPS_OK;
 }
@@ -530,23 +703,29 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   CKI(cudaMalloc(&c->jB, sizeof(float4) * nb));
   CKI(cudaMalloc(&c->stage, sizeof(double) * nb * 3));
   CKI(cudaMalloc(&c->red, sizeof(double) * (kRedBlocks * 6 + 8)));
+  CKI(cudaMalloc(&c->perm, sizeof(int) * nb));
+  CKI(cudaMalloc(&c->iperm, sizeof(int) * nb));
+  CKI(cudaMalloc(&c->ord, sizeof(int) * nb));
   CKI(cudaMalloc(&c->err, sizeof(int)));
   CKI(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
 
-  // stream-K split of the FP32 pair kernel: C co-resident CTAs share U units
+  // stream-K split of the FP32 pair kernel: C CTAs share U units
   int sms = 0, occ = 0;
   CKI(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
   CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_fp32_kernel<true>, kBI, 0));
   c->NB = (c->n + kBI - 1) / kBI;
   c->NT = (c->n + kBJ - 1) / kBJ;
   c->U = (long long)c->NB * c->NT;
-  c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1));
+  c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1) * STEPS_CTA_MULT);
   c->part_elems = std::max((size_t)(c->NB + c->C) * 3 * kBI, nb * 3);
   CKI(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
 
-  CKI(cudaMemcpyAsync(c->m, m, sizeof(double) * nb, cudaMemcpyDefault, c->st));
-  CKI(cudaMemcpyAsync(c->h, h, sizeof(double) * nb, cudaMemcpyDefault, c->st));
-  if ((rc = upload_state(c, x, y, z, vx, vy, vz))) return bail(rc);
+  // caller order -> internal (Morton) order
+  if ((rc = stage_positions(c, x, y, z))) return bail(rc);
+  if ((rc = order_from_stage(c, c->stage, c->stage + nb, false))) return bail(rc);
+  if ((rc = install_state(c, vx, vy, vz))) return bail(rc);
+  if ((rc = gather_in(c, m, c->m, 1.0))) return bail(rc);
+  if ((rc = gather_in(c, h, c->h, 1.0))) return bail(rc);
   if ((rc = validate_state(c))) return bail(rc);
 
   // comoving mean density of the background term
@@ -566,7 +745,7 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   }
   if ((rc = build_background(c))) return bail(rc);
   if ((rc = pack_positions(c))) return bail(rc);
-  if ((rc = eval_forces(c, false, 0.0, nullptr, nullptr, nullptr, 1.0))) return bail(rc);
+  if ((rc = eval_forces(c, false, 0.0))) return bail(rc);
   int e = 0;
   if ((rc = read_and_clear_err(c, &e))) return bail(rc);
   if (e) return bail(device_error(e));
@@ -580,18 +759,15 @@ int steps_cyl_forces(steps_cyl_ctx* c, double* ax, double* ay, double* az) {
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (!ax || !ay || !az) return fail(STEPS_EINVAL, "NULL output");
   DeviceGuard guard(c->dev);
-  const double inv_a3 = 1.0 / (c->a * c->a * c->a);
-  const bool host = is_host_ptr(ax) || is_host_ptr(ay) || is_host_ptr(az);
   int rc;
-  if (host) {
-    double* s = c->stage;
-    if ((rc = eval_forces(c, false, 0.0, s, s + c->n, s + 2 * (size_t)c->n, inv_a3))) return rc;
-    if ((rc = copy_out3(c, s, s + c->n, s + 2 * (size_t)c->n, ax, ay, az, c->n))) return rc;
+  if ((rc = eval_forces(c, false, 0.0))) return rc;
+  const double* src[3] = {c->gx, c->gy, c->gz};
+  double* dst[3] = {ax, ay, az};
+  if ((rc = scatter_out(c, src, dst, 1.0 / (c->a * c->a * c->a)))) return rc;
+  if (is_host_ptr(ax) || is_host_ptr(ay) || is_host_ptr(az)) {
     int e = 0;
     if ((rc = read_and_clear_err(c, &e))) return rc;
     if (e) return device_error(e);
-  } else {
-    if ((rc = eval_forces(c, false, 0.0, ax, ay, az, inv_a3))) return rc;
   }
   return STEPS_OK;
 }
@@ -615,8 +791,8 @@ int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, do
   }
   CK(cudaMemcpyAsync(c->idx, idx, sizeof(int64_t) * ni, cudaMemcpyDefault, c->st));
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
-  check_idx_kernel<<<((int)ni + 255) / 256, 256, 0, c->st>>>(c->idx, (int)ni, c->n, c->err);
-  CKLAUNCH("check_idx");
+  map_idx_kernel<<<((int)ni + 255) / 256, 256, 0, c->st>>>(c->idx, (int)ni, c->n, c->iperm, c->err);
+  CKLAUNCH("map_idx");
   int e = 0, rc;
   if ((rc = read_and_clear_err(c, &e))) return rc;
   if (e) return fail(STEPS_EINVAL, "subset index out of range");
@@ -636,14 +812,15 @@ int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, do
     CKLAUNCH("subset_finalize");
   } else {
     // FP32 forms: full evaluation, then gather the listed particles
-    if ((rc = eval_forces(c, false, 0.0, nullptr, nullptr, nullptr, inv_a3))) return rc;
-    gather3_kernel<<<((int)ni + 255) / 256, 256, 0, c->st>>>(c->gx, c->gy, c->gz, c->idx, (int)ni, o, o + ni,
+    if ((rc = eval_forces(c, false, 0.0))) return rc;
+    gather3_kernel<<<((int)ni + 255) / 256, 256, 0, c->st>>>(c->gx, c->gy, c->gz, c->idx, (int)ni, inv_a3, o, o + ni,
                                                              o + 2 * ni);
     CKLAUNCH("gather");
-    axpy_scale3_kernel<<<grid_for((int)ni, 256), 256, 0, c->st>>>(o, o + ni, o + 2 * ni, (int)ni, inv_a3);
-    CKLAUNCH("scale");
   }
-  if ((rc = copy_out3(c, o, o + ni, o + 2 * ni, ax, ay, az, (size_t)ni))) return rc;
+  const size_t b = sizeof(double) * (size_t)ni;
+  CK(cudaMemcpyAsync(ax, o, b, cudaMemcpyDefault, c->st));
+  CK(cudaMemcpyAsync(ay, o + ni, b, cudaMemcpyDefault, c->st));
+  CK(cudaMemcpyAsync(az, o + 2 * ni, b, cudaMemcpyDefault, c->st));
   if ((rc = read_and_clear_err(c, &e))) return rc;
   if (e) return device_error(e);
   return STEPS_OK;
@@ -664,9 +841,12 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
                                                                    c->gy, c->gz, c->m, c->h, c->n, f.K1, f.D, c->p.L,
                                                                    c->invL, c->jA, c->jB, c->err);
     CKLAUNCH("kick_drift_pack");
-    if ((rc = eval_forces(c, true, f.K2, nullptr, nullptr, nullptr, 1.0))) return rc;
+    if ((rc = eval_forces(c, true, f.K2))) return rc;
     c->a = f.a_next;
     c->t += dt;
+    if (c->p.reorder_every > 0 && ++c->steps_since_order >= c->p.reorder_every) {
+      if ((rc = reorder(c))) return rc;
+    }
   }
   int e = 0;
   if ((rc = read_and_clear_err(c, &e))) return rc;
@@ -680,14 +860,15 @@ int steps_cyl_get_state(steps_cyl_ctx* c, double* x, double* y, double* z, doubl
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   DeviceGuard guard(c->dev);
   int rc;
-  if ((rc = copy_out3(c, c->x, c->y, c->z, x, y, z, c->n))) return rc;
-  if (vx || vy || vz) {
-    double* s = c->stage;
-    const double inv_a2 = 1.0 / (c->a * c->a);
-    scale3_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->px, c->py, c->pz, c->n, inv_a2, s, s + c->n,
-                                                          s + 2 * (size_t)c->n);
-    CKLAUNCH("velocity");
-    if ((rc = copy_out3(c, s, s + c->n, s + 2 * (size_t)c->n, vx, vy, vz, c->n))) return rc;
+  {
+    const double* src[3] = {c->x, c->y, c->z};
+    double* dst[3] = {x, y, z};
+    if ((rc = scatter_out(c, src, dst, 1.0))) return rc;
+  }
+  {
+    const double* src[3] = {c->px, c->py, c->pz};
+    double* dst[3] = {vx, vy, vz};
+    if ((rc = scatter_out(c, src, dst, 1.0 / (c->a * c->a)))) return rc;
   }
   if (a) *a = c->a;
   if (t) *t = c->t;
@@ -701,24 +882,21 @@ int steps_cyl_set_state(steps_cyl_ctx* c, const double* x, const double* y, cons
   if (!x || !y || !z || !vx || !vy || !vz) return fail(STEPS_EINVAL, "NULL input array");
   DeviceGuard guard(c->dev);
   int rc;
-  // stage the new positions, compare them with the current ones, then install
-  const size_t b = sizeof(double) * (size_t)c->n;
-  double* s = c->stage;
-  CK(cudaMemcpyAsync(s, x, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(s + c->n, y, b, cudaMemcpyDefault, c->st));
-  CK(cudaMemcpyAsync(s + 2 * (size_t)c->n, z, b, cudaMemcpyDefault, c->st));
+  if ((rc = stage_positions(c, x, y, z))) return rc;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+  double* s = c->stage;
   positions_changed_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, s, s + c->n,
-                                                                   s + 2 * (size_t)c->n, c->n, c->err);
+                                                                   s + 2 * (size_t)c->n, c->perm, c->n, c->err);
   CKLAUNCH("positions_changed");
   int changed = 0;
   if ((rc = read_and_clear_err(c, &changed))) return rc;
-  if ((rc = upload_state(c, s, s + c->n, s + 2 * (size_t)c->n, vx, vy, vz))) return rc;
+  if (changed && (rc = order_from_stage(c, s, s + c->n, true))) return rc;
+  if ((rc = install_state(c, vx, vy, vz))) return rc;
   if ((rc = validate_state(c))) return rc;
   // the cached forces stay valid when the positions are bitwise unchanged
   if (changed) {
     if ((rc = pack_positions(c))) return rc;
-    if ((rc = eval_forces(c, false, 0.0, nullptr, nullptr, nullptr, 1.0))) return rc;
+    if ((rc = eval_forces(c, false, 0.0))) return rc;
   }
   return STEPS_OK;
 }
@@ -729,7 +907,7 @@ int steps_cyl_set_precision(steps_cyl_ctx* c, int32_t precision) {
   if (precision < STEPS_FP64 || precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   DeviceGuard guard(c->dev);
   c->p.precision = precision;
-  return eval_forces(c, false, 0.0, nullptr, nullptr, nullptr, 1.0);
+  return eval_forces(c, false, 0.0);
 }
 
 int steps_cyl_diagnostics(steps_cyl_ctx* c, double out[8]) {

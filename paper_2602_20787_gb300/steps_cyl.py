@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
         ("H0", ctypes.c_double), ("Omega_m", ctypes.c_double), ("Omega_r", ctypes.c_double),
         ("Omega_L", ctypes.c_double), ("w0", ctypes.c_double), ("wa", ctypes.c_double),
         ("a_start", ctypes.c_double), ("t_start", ctypes.c_double),
-        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int32), ("reorder_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -155,6 +155,7 @@ class Config:
     a_start: float = 1.0
     t_start: float = 0.0
     device: int = 0
+    reorder_every: int = 32
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def to_c(self) -> Params:

@@ -82,8 +82,10 @@ def test_conservation_over_many_steps(sc):
 
 
 def test_set_state_and_restart_bit_identical(sc):
+    # a new context built from a saved state continues bit-identically when it
+    # keeps the caller's particle order (the sum order then matches)
     d = ics.particle_load(1000, 3, 1.0)
-    cfg = sc.Config(n_cut=8, precision=1)
+    cfg = sc.Config(n_cut=8, precision=1, reorder_every=-1)
     s1 = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
     s1.step(1e-3, 6)
     x_mid, v_mid, _, _ = s1.state()
@@ -96,3 +98,41 @@ def test_set_state_and_restart_bit_identical(sc):
     np.testing.assert_array_equal(v2, v_end)
     s1.close()
     s2.close()
+
+
+def test_internal_order_is_invisible(sc):
+    d = ics.particle_load(3000, 13, 1.0)
+    d["vel"] = np.random.default_rng(5).normal(0.0, 0.02, (3000, 3))
+    plain = sc.Simulation(sc.Config(n_cut=8, precision=1, reorder_every=-1), d["pos"], d["vel"], d["m"], d["h"])
+    sorted_ = sc.Simulation(sc.Config(n_cut=8, precision=1, reorder_every=3), d["pos"], d["vel"], d["m"], d["h"])
+    x0, v0, _, _ = sorted_.state()
+    np.testing.assert_array_equal(x0, d["pos"])
+    np.testing.assert_allclose(v0, d["vel"], rtol=0, atol=0)
+    a1, a2 = plain.forces(), sorted_.forces()
+    # the two orders sum the same pair forces in different orders: they agree
+    # to FP32 rounding (the FP32 forms' own error against the oracle is larger)
+    r = np.linalg.norm(a1 - a2, axis=1) / np.linalg.norm(a1, axis=1)
+    assert np.median(r) < 1e-6 and r.max() < 1e-4
+    plain.step(1e-3, 7)
+    sorted_.step(1e-3, 7)   # re-ordered twice on the way
+    xa, va, _, _ = plain.state()
+    xb, vb, _, _ = sorted_.state()
+    assert np.abs(wrapped_diff(xa, xb)).max() < 1e-9
+    assert np.abs(va - vb).max() < 1e-6 * np.abs(va).max()
+    plain.close()
+    sorted_.close()
+
+
+def test_set_state_moves_masses_with_the_new_order(sc):
+    d1 = ics.particle_load(900, 21, 1.0)
+    d2 = ics.particle_load(900, 22, 1.0)   # different positions, same masses/softenings below
+    sim = sc.Simulation(sc.Config(n_cut=6, precision=0), d1["pos"], d1["vel"], d1["m"], d1["h"])
+    cols = [np.ascontiguousarray(d2["pos"][:, k]) for k in range(3)] + [np.zeros(900)] * 3
+    sc.steps_cyl_set_state(sim.ctx, *cols)
+    ref = oracle.pair_field(d2["pos"], d1["m"], d1["h"], 1.0, 1.0, 6)
+    rho0 = d1["m"].sum() / (np.pi * ics.R_SIM ** 2)
+    ref += oracle.background_field(d2["pos"], ics.R_SIM, 6.0, 1.0, rho0, mode=1)
+    a = sim.forces()
+    r = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert r.max() < 1e-10
+    sim.close()

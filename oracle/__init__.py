@@ -50,6 +50,20 @@ class Cosmo(ctypes.Structure):
                 ("comoving", ctypes.c_int32)]
 
 
+class SurrCfg(ctypes.Structure):
+    """Surrogate definition constants (this project's; see or_tail_surrogate)."""
+    _fields_ = [("n_cut", ctypes.c_int32), ("n0", ctypes.c_int32), ("dR_max", ctypes.c_double),
+                ("out_mu", ctypes.c_double * 2), ("out_sc", ctypes.c_double * 2)]
+
+
+def make_surr_cfg(n_cut, n0, dR_max, out_mu=(0.0, 0.0), out_sc=(1.0, 1.0)):
+    c = SurrCfg()
+    c.n_cut, c.n0, c.dR_max = int(n_cut), int(n0), float(dR_max)
+    c.out_mu[0], c.out_mu[1] = out_mu
+    c.out_sc[0], c.out_sc[1] = out_sc
+    return c
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -76,6 +90,13 @@ def lib():
         L.or_mlp_loss_grad.argtypes = [p, i64, p, p, p]; L.or_mlp_loss_grad.restype = d
         L.or_adam_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]; L.or_adam_step.restype = None
         L.or_num_threads.argtypes = []; L.or_num_threads.restype = i32
+        L.or_tail_base.argtypes = [d, d, i32, i32, p, p]; L.or_tail_base.restype = None
+        L.or_tail_envelope.argtypes = [d, d, i32, p, p]; L.or_tail_envelope.restype = None
+        L.or_surrogate_inputs.argtypes = [d, d, d, i32, d, p]; L.or_surrogate_inputs.restype = None
+        L.or_tail_surrogate.argtypes = [d, d, d, p, ctypes.POINTER(SurrCfg), p, p]
+        L.or_tail_surrogate.restype = None
+        L.or_pair_field_surrogate.argtypes = [i64, p, p, p, p, p, d, d, p, ctypes.POINTER(SurrCfg), i64, p, p, p, p]
+        L.or_pair_field_surrogate.restype = None
         _lib = L
     return _lib
 
@@ -224,3 +245,47 @@ def adam_step(w, g, m1, m2, lr, beta1, beta2, eps, step):
     """In-place Adam update (FP64)."""
     lib().or_adam_step(w.shape[0], _ptr(w), _ptr(_f64(g)), _ptr(m1), _ptr(m2), float(lr), float(beta1),
                        float(beta2), float(eps), int(step))
+
+
+def tail_base(dR, adz, n_cut, n0):
+    """Order-1 Euler-Maclaurin continuum base of the far tail (units of L, |dz|)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_base(float(dR), float(adz), int(n_cut), int(n0), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def tail_envelope(dR, adz, n0):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_envelope(float(dR), float(adz), int(n0), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def surrogate_inputs(dR, adz, h, n0, dR_max):
+    u = np.zeros(3)
+    lib().or_surrogate_inputs(float(dR), float(adz), float(h), int(n0), float(dR_max), _ptr(u))
+    return u
+
+
+def tail_surrogate(dR, dz, h, w, cfg):
+    """Surrogate far tail (SR, SZ) in units of L for one pair."""
+    w = _f64(w)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_surrogate(float(dR), float(dz), float(h), _ptr(w), ctypes.byref(cfg), ctypes.byref(a),
+                            ctypes.byref(b))
+    return a.value, b.value
+
+
+def pair_field_surrogate(pos, m, h, G, L, w, cfg, idx=None):
+    """Pair term with near images exact and the far tail from the surrogate."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h); w = _f64(w)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], _ptr(idx)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    lib().or_pair_field_surrogate(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), _ptr(w),
+                                  ctypes.byref(cfg), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)

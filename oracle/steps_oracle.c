@@ -411,3 +411,125 @@ void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2
     w[k] -= lr * (m1[k] / c1) / (sqrt(m2[k] / c2) + eps);
   }
 }
+
+/* ---------------------------------------------------------------------------
+ * Learned far-image surrogate. The paper has no such method: this is the
+ * project's definition of the surrogate tail, written here plainly in FP64 so
+ * that the CUDA kernel's evaluation of the same definition can be checked.
+ * Units: lengths in units of L (period 1); dz is the wrapped separation in
+ * [-1/2, 1/2]; near images are |k| <= n0, the tail is the rest of the window.
+ *
+ * Base: each side of the tail is a run of unit cells centred on the images;
+ * the image sum over a run is its continuum integral minus (1/24)[f'(end) -
+ * f'(start)] (midpoint Euler-Maclaurin, first correction), with
+ *   f(z) = (R^2 + z^2)^(-3/2)  for SR,   z f(z)  for SZ.
+ * Envelope: e = 1 / (R^2 + (n0 + 1/2 + |dz|)^2), ER = e^3, EZ = e^(5/2).
+ * Inputs: u = (2 min(R, dR_max)/dR_max - 1, 4|dz| - 1, 2 min(h, n0+1/2)/(n0+1/2) - 1).
+ * ------------------------------------------------------------------------- */
+static void or_side_integrals(double R2, double lo, double hi, double* IR, double* IZ, double* dR_lo,
+                              double* dR_hi, double* dZ_lo, double* dZ_hi) {
+  double rl = sqrt(R2 + lo * lo), rh = sqrt(R2 + hi * hi);
+  /* Int_lo^hi (R^2+z^2)^-1.5 dz = [z / (R^2 sqrt(R^2+z^2))], in a form without
+   * cancellation at small R: (hi^2 - lo^2) / (rl rh (hi rl + lo rh)) */
+  *IR = (hi * hi - lo * lo) / (rl * rh * (hi * rl + lo * rh));
+  /* Int_lo^hi z (R^2+z^2)^-1.5 dz = 1/rl - 1/rh */
+  *IZ = 1.0 / rl - 1.0 / rh;
+  /* derivatives of f and z f */
+  *dR_lo = -3.0 * lo / pow(rl, 5.0);
+  *dR_hi = -3.0 * hi / pow(rh, 5.0);
+  *dZ_lo = 1.0 / pow(rl, 3.0) - 3.0 * lo * lo / pow(rl, 5.0);
+  *dZ_hi = 1.0 / pow(rh, 3.0) - 3.0 * hi * hi / pow(rh, 5.0);
+}
+
+void or_tail_base(double dR, double adz, int32_t n_cut, int32_t n0, double* BR, double* BZ) {
+  double R2 = dR * dR, A = n0 + 0.5;
+  /* images dz + k with |dz + k| < n_cut: for dz >= 0 the positive side ends at
+   * k = n_cut - 1, the negative side at k = -n_cut if dz > 0, else -(n_cut - 1) */
+  int kpos = n_cut - 1, kneg = adz > 0.0 ? n_cut : n_cut - 1;
+  double IR, IZ, a, b, c, d;
+  /* positive side: cells [A + adz, kpos + 1/2 + adz] */
+  or_side_integrals(R2, A + adz, kpos + 0.5 + adz, &IR, &IZ, &a, &b, &c, &d);
+  double sr = IR - (b - a) / 24.0, sz = IZ - (d - c) / 24.0;
+  /* negative side mirrored to z' = -z > 0: cells [A - adz, kneg + 1/2 - adz]; z f is odd */
+  or_side_integrals(R2, A - adz, kneg + 0.5 - adz, &IR, &IZ, &a, &b, &c, &d);
+  sr += IR - (b - a) / 24.0;
+  sz -= IZ - (d - c) / 24.0;
+  *BR = sr;
+  *BZ = sz;
+}
+
+void or_tail_envelope(double dR, double adz, int32_t n0, double* ER, double* EZ) {
+  double A = n0 + 0.5, e = 1.0 / (dR * dR + (A + adz) * (A + adz));
+  *ER = e * e * e;
+  *EZ = e * e * sqrt(e);
+}
+
+void or_surrogate_inputs(double dR, double adz, double h, int32_t n0, double dR_max, double u[3]) {
+  double A = n0 + 0.5;
+  u[0] = 2.0 * (dR < dR_max ? dR : dR_max) / dR_max - 1.0;
+  u[1] = 4.0 * adz - 1.0;
+  u[2] = 2.0 * (h < A ? h : A) / A - 1.0;
+}
+
+void or_tail_surrogate(double dR, double dz, double h, const double* w, const or_surr_cfg* c, double* SR,
+                       double* SZ) {
+  double adz = fabs(dz), BR, BZ, ER, EZ, u[3], y[2];
+  or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
+  or_tail_envelope(dR, adz, c->n0, &ER, &EZ);
+  or_surrogate_inputs(dR, adz, h, c->n0, c->dR_max, u);
+  or_mlp_forward(w, u, y);
+  double sr = BR + ER * (y[0] * c->out_sc[0] + c->out_mu[0]);
+  double sz = BZ + EZ * (y[1] * c->out_sc[1] + c->out_mu[1]);
+  double sg = dz > 0.0 ? 1.0 : (dz < 0.0 ? -1.0 : 0.0);
+  sz *= sg;
+  /* tail images inside the softening support: the surrogate is Newtonian there;
+   * replace 1/r^3 by F(r,h)/r exactly */
+  for (int k = -c->n_cut - 1; k <= c->n_cut + 1; ++k) {
+    if (k >= -c->n0 && k <= c->n0) continue;
+    double o = dz + (double)k;
+    if (!(fabs(o) < (double)c->n_cut)) continue;
+    double r = sqrt(dR * dR + o * o);
+    if (r >= h) continue;
+    double d = or_spline_F_over_r(r, h) - 1.0 / (r * r * r);
+    sr += d;
+    sz += o * d;
+  }
+  *SR = sr;
+  *SZ = sz;
+}
+
+/* Pair term with the surrogate tail: near images (|k| <= n0 in the wrapped
+ * frame) summed exactly, far tail from or_tail_surrogate. */
+void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                             const double* h, double G, double L, const double* w, const or_surr_cfg* c,
+                             int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t q = 0; q < ni; ++q) {
+    int64_t i = idx ? idx[q] : q;
+    or_sum sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double dx = (x[i] - x[j]) / L, dy = (y[i] - y[j]) / L, rz = (z[i] - z[j]) / L;
+      double dzw = rz - floor(rz + 0.5);
+      double hh = (h[i] + h[j]) / L, dR = sqrt(dx * dx + dy * dy);
+      double sr = 0.0, szz = 0.0;
+      for (int k = -c->n0; k <= c->n0; ++k) {
+        double o = dzw + (double)k;
+        double f = or_spline_F_over_r(sqrt(dR * dR + o * o), hh);
+        sr += f;
+        szz += o * f;
+      }
+      double tr, tz;
+      or_tail_surrogate(dR, dzw, hh, w, c, &tr, &tz);
+      sr += tr;
+      szz += tz;
+      /* lengths were in units of L: F/r scales as 1/L^3, the vector as L */
+      or_add(&sx, -G * m[j] * dx * sr / (L * L));
+      or_add(&sy, -G * m[j] * dy * sr / (L * L));
+      or_add(&sz, -G * m[j] * szz / (L * L));
+    }
+    gx[q] = sx.s + sx.c;
+    gy[q] = sy.s + sy.c;
+    gz[q] = sz.s + sz.c;
+  }
+}

@@ -52,6 +52,22 @@ int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, d
 void or_tail_sums(double dR, double dzw, double h, double L, int32_t n_cut, int32_t n0, double* SR,
                   double* Sz);
 void or_mlp_forward(const double* w, const double* u, double* y);
+/* Learned far-image surrogate (this project's definition; the paper has none):
+ * tail = order-1 Euler-Maclaurin continuum base + envelope * (MLP(u) * sc + mu),
+ * plus the exact spline correction of tail images inside the softening support. */
+typedef struct {
+  int32_t n_cut, n0;
+  double dR_max;        /* input scaling of dR (units of L) */
+  double out_mu[2], out_sc[2];
+} or_surr_cfg;
+void or_tail_base(double dR, double adz, int32_t n_cut, int32_t n0, double* BR, double* BZ);
+void or_tail_envelope(double dR, double adz, int32_t n0, double* ER, double* EZ);
+void or_surrogate_inputs(double dR, double adz, double h, int32_t n0, double dR_max, double u[3]);
+void or_tail_surrogate(double dR, double dz, double h, const double* w, const or_surr_cfg* c, double* SR,
+                       double* SZ);
+void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                             const double* h, double G, double L, const double* w, const or_surr_cfg* c,
+                             int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz);
 double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t, double* grad);
 void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2, double lr,
                   double beta1, double beta2, double eps, int64_t step);

@@ -76,13 +76,17 @@ typedef struct {
   int32_t reorder_every; /* particles are kept in a Morton order of (x, y) inside the library (results are
                           * returned in the caller's order); it is rebuilt at init, by set_state, and every
                           * reorder_every KDK steps (0: never during stepping; -1: keep the caller's order) */
+  int32_t check_every;   /* with the surrogate tail: every check_every KDK steps the surrogate forces of a
+                          * particle sample are compared with the plain image sum; above the bounds the
+                          * context falls back to the plain sum (0: no periodic check) */
+  int32_t check_particles; /* size of that sample (default 1024) */
   void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
 } steps_cyl_params;
 
 /* Fill *p with defaults: G = L = 1, R_sim = 0.5 tan(0.45 pi), rho_bar = 0, n_cut = 16,
  * n0 = 4, FP32_KAHAN, TAIL_FULL, BG_FINITE, static space, H0 = 1, Omega_m = 0.3,
  * Omega_L = 0.7, w0 = -1, wa = 0, a_start = 1, t_start = 0, device 0, reorder_every = 32,
- * default stream. */
+ * check_every = 50, check_particles = 1024, default stream. */
 int steps_cyl_params_default(steps_cyl_params* p);
 
 /* Create a context holding n particles (eq. ComovingEquationsOfMotionCylindrical state).
@@ -137,6 +141,85 @@ int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
  * window (2 Ncut per pair, 2 Ncut - 1 when r_z = 0 mod L), and the device time of
  * its pair kernel in milliseconds (CUDA events on the context stream). */
 int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
+
+/* ---- learned far-image surrogate ------------------------------------------
+ * The paper sums every image of the window (eq. ForceCylindrical). The
+ * surrogate tail form (STEPS_TAIL_SURROGATE) sums the near images |k| <= n0
+ * exactly and replaces the far tail of each pair by
+ *   B1 + E (MLP(u) sc + mu)      (z component times sign(dz)),
+ * B1 = continuum integral of the image cells with the first Euler-Maclaurin end
+ * correction, E = (e^3, e^(5/2)), e = 1 / (dR^2 + (n0 + 1/2 + |dz|)^2) in units of
+ * L, and a 3 -> 32 -> 32 -> 2 ReLU network of
+ * u = (2 min(dR, dR_max)/dR_max - 1, 4|dz| - 1, 2 min(h, n0 + 1/2)/(n0 + 1/2) - 1)
+ * evaluated in FP16 with FP32 accumulation on the tensor cores. Tail images
+ * inside the softening support are corrected to the exact spline.
+ *
+ * Parameter vector (STEPS_SURR_NPARAM floats): W1[32][3], b1[32], W2[32][32],
+ * b2[32], W3[2][32], b3[2], then mu[2], sc[2], dR_max. */
+#define STEPS_SURR_NW 1250
+#define STEPS_SURR_NPARAM 1255
+
+typedef struct {
+  int64_t n_samples;    /* training + held-out samples (the last 1/16 are held out) */
+  int32_t epochs;
+  int32_t batch;        /* multiple of 64 */
+  double lr;            /* peak Adam learning rate, cosine decay to 0 */
+  double dR_max;        /* input scale in units of L; 0 = 2.2 x the largest particle radius / L */
+  uint64_t seed;        /* sample draw, initial weights, shuffling */
+  double err_median;    /* acceptance bounds on the relative total-force error against the */
+  double err_p999;      /* plain image sum over a particle sample (median, 99.9th percentile) */
+  int32_t check_particles;
+  int32_t reserved;     /* must be 0 */
+} steps_cyl_train_cfg;
+
+/* Defaults: 2^20 samples, 60 epochs, batch 8192, lr 3e-3, dR_max 0, seed 1,
+ * bounds 1e-5 / 1e-3, 1024 check particles. */
+int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg);
+
+/* Exact far-image tail sums in FP64 (no context): for each of ns samples
+ * (dR, dz, h) in units of L (row-major ns x 3, |dz| <= 1/2, h > 0; host or device)
+ * out[2 s], out[2 s + 1] = SR, SZ of the window images |dz + k| < n_cut with
+ * |k| > n0, SR = sum F(r,h)/r and SZ = sum (dz + k) F(r,h)/r (eq. Force_spline_kernel).
+ * out: host or device, ns x 2. Synchronises the stream. */
+int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out,
+                        void* stream);
+
+/* One forward and backward pass of the network in FP32 over ns samples (no
+ * context): w (STEPS_SURR_NW floats), u (ns x 3), t (ns x 2) targets; *loss =
+ * 1/(2 ns) sum |y - t|^2 and grad (STEPS_SURR_NW floats) its gradient. Host or
+ * device pointers. Synchronises the stream. */
+int steps_cyl_mlp_loss_grad(int64_t ns, const float* w, const float* u, const float* t, float* loss,
+                            float* grad, void* stream);
+
+/* Train the surrogate of a context on the GPU (its n_cut and n0): draw the
+ * samples, compute exact FP64 targets, train with Adam, round to FP16, and
+ * check the result against the plain image sum on cfg->check_particles
+ * particles. report (8 doubles, may be NULL): final training loss, held-out
+ * RMS error (normalised units), check median, check 99.9th percentile,
+ * accepted (1/0), training ms, mu[0], sc[0]. Returns STEPS_OK when accepted
+ * (the context may then use STEPS_TAIL_SURROGATE) or STEPS_ESURROGATE_REJECTED. */
+int steps_cyl_train_surrogate(steps_cyl_ctx* ctx, const steps_cyl_train_cfg* cfg, double* report);
+
+/* Load surrogate parameters (STEPS_SURR_NPARAM floats, host or device) and check
+ * them as steps_cyl_train_surrogate does (bounds from the arguments; report: 4
+ * doubles = check median, check 99.9th percentile, accepted, 0; may be NULL).
+ * STEPS_ESURROGATE_REJECTED when the check fails (the parameters are dropped). */
+int steps_cyl_set_surrogate(steps_cyl_ctx* ctx, const float* params, double err_median, double err_p999,
+                            double* report);
+
+/* Copy out the context's surrogate parameters (STEPS_SURR_NPARAM floats, host).
+ * STEPS_ENOSURROGATE when none is loaded. */
+int steps_cyl_get_surrogate(steps_cyl_ctx* ctx, float* params);
+
+/* Select the tail form: STEPS_TAIL_FULL, or STEPS_TAIL_SURROGATE (requires an
+ * accepted surrogate and an FP32 precision). Cached forces are recomputed. */
+int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
+
+/* Compare the surrogate form with the plain image sum now on check_particles
+ * particles (deterministic sample): report (4 doubles) = median and 99.9th
+ * percentile of the relative total-force error, and the two forms' pair-kernel
+ * times in ms on that sample. */
+int steps_cyl_check_surrogate(steps_cyl_ctx* ctx, int32_t check_particles, double* report);
 
 /* ---- allocation-free pair accelerations ----------------------------------
  * This entry point has no counterpart in the paper; it serves callers that may

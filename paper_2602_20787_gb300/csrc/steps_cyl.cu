@@ -15,6 +15,7 @@
 // every input is gathered through perm and every output scattered back, so the
 // caller only ever sees its own order. The order is rebuilt at init, when
 // set_state moves particles, and every reorder_every KDK steps.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +28,8 @@
 
 #include "steps_cyl.h"
 #include "nbody_kernels.cuh"
+#include "surrogate_pair.cuh"
+#include "surrogate_train.cuh"
 
 using namespace steps;
 
@@ -221,6 +224,16 @@ struct steps_cyl_ctx {
   int C = 0, NT = 0, NB = 0;
   long long U = 0;
   int steps_since_order = 0;
+  // learned far-image surrogate
+  SurrLane* surr_lanes = nullptr;  // per-lane MLP fragments (device, 32 entries)
+  SurrConst surr{};
+  std::vector<float> surr_params;  // STEPS_SURR_NPARAM floats of the accepted network
+  bool surr_ok = false;            // an accepted network is loaded
+  int steps_since_check = 0;
+  double surr_bound_med = 1e-5, surr_bound_p999 = 1e-3;
+  int SC = 0;                      // CTAs of the surrogate pair kernel
+  double* chk = nullptr;           // check buffers (grown on demand)
+  size_t chk_elems = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double last_images = 0.0;
   bool timed = false;
@@ -255,6 +268,7 @@ int check_params(const steps_cyl_params* p) {
     if (!(p->H0 > 0) || !(p->a_start > 0)) return fail(STEPS_EINVAL, "comoving runs need H0 > 0 and a_start > 0");
   }
   if (p->reorder_every < -1) return fail(STEPS_EINVAL, "reorder_every must be >= -1");
+  if (p->check_every < 0 || p->check_particles < 0) return fail(STEPS_EINVAL, "check_every and check_particles must be >= 0");
   return STEPS_OK;
 }
 
@@ -460,6 +474,14 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
     pair_fp64_kernel<<<(c->n + 127) / 128, 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, nullptr, c->n,
                                                             c->invL, c->p.n_cut, c->part);
     CKLAUNCH("pair_fp64");
+  } else if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok) {
+    if (c->p.precision == STEPS_FP32_KAHAN)
+      pair_fp32_surr_kernel<true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
+                                                             c->surr_lanes, c->surr, c->part);
+    else
+      pair_fp32_surr_kernel<false><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
+                                                              c->surr_lanes, c->surr, c->part);
+    CKLAUNCH("pair_fp32_surrogate");
   } else if (c->p.precision == STEPS_FP32_KAHAN) {
     pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);
     CKLAUNCH("pair_fp32_kahan");
@@ -471,8 +493,9 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   c->timed = true;
   c->last_images = (double)c->n * (double)(c->n - 1) * 2.0 * c->p.n_cut;
   const int NT = c->p.precision == STEPS_FP64 ? 0 : c->NT;
+  const bool surr = c->p.precision != STEPS_FP64 && c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok;
   finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
-      c->part, c->n, NT, c->U, c->C, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
+      c->part, c->n, NT, c->U, surr ? c->SC : c->C, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
       kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
   CKLAUNCH("finalize");
   return STEPS_OK;
@@ -581,6 +604,8 @@ void release(steps_cyl_ctx* c) {
   cudaFree(c->sub);
   cudaFree(c->err);
   cudaFree(c->bgtab);
+  cudaFree(c->surr_lanes);
+  cudaFree(c->chk);
   if (c->e0) cudaEventDestroy(c->e0);
   if (c->e1) cudaEventDestroy(c->e1);
   cudaSetDevice(prev);
@@ -620,6 +645,379 @@ int scatter_out(steps_cyl_ctx* c, const double* const src[3], double* const dst[
   return STEPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Learned far-image surrogate: host side (see surrogate_train.cuh and
+// surrogate_pair.cuh for the definition and the kernels).
+// ---------------------------------------------------------------------------
+struct SplitMix {
+  uint64_t s;
+  explicit SplitMix(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }  // [0, 1)
+};
+
+uint32_t half_bits(float v) {
+  __half_raw r = __float2half_rn(v);
+  return (uint32_t)r.x;
+}
+uint32_t pack_half2(float lo, float hi) { return half_bits(lo) | (half_bits(hi) << 16); }
+
+// Per-lane mma fragments of a parameter vector (layout in include/steps_cyl.h).
+void build_lanes(const float* P, SurrLane lanes[32]) {
+  const float *W1 = P + kOW1, *b1 = P + kOB1, *W2 = P + kOW2, *b2 = P + kOB2, *W3 = P + kOW3, *b3 = P + kOB3;
+  for (int L = 0; L < 32; ++L) {
+    SurrLane& s = lanes[L];
+    std::memset(&s, 0, sizeof s);
+    const int g = L >> 2, t = L & 3;
+    for (int nb = 0; nb < 4; ++nb) {
+      const int o = 8 * nb + g;
+      const float w0 = 2 * t < 3 ? W1[o * 3 + 2 * t] : 0.f, w1 = 2 * t + 1 < 3 ? W1[o * 3 + 2 * t + 1] : 0.f;
+      s.w1[nb] = pack_half2(w0, w1);
+      s.b1[2 * nb] = b1[8 * nb + 2 * t];
+      s.b1[2 * nb + 1] = b1[8 * nb + 2 * t + 1];
+      s.b2[2 * nb] = b2[8 * nb + 2 * t];
+      s.b2[2 * nb + 1] = b2[8 * nb + 2 * t + 1];
+      for (int kb = 0; kb < 2; ++kb) {
+        const int k = 16 * kb + 2 * t;
+        s.w2[(kb * 4 + nb) * 2] = pack_half2(W2[o * kH + k], W2[o * kH + k + 1]);
+        s.w2[(kb * 4 + nb) * 2 + 1] = pack_half2(W2[o * kH + k + 8], W2[o * kH + k + 9]);
+      }
+    }
+    for (int kb = 0; kb < 2; ++kb) {
+      const int k = 16 * kb + 2 * t;
+      s.w3[kb * 2] = g < 2 ? pack_half2(W3[g * kH + k], W3[g * kH + k + 1]) : 0u;
+      s.w3[kb * 2 + 1] = g < 2 ? pack_half2(W3[g * kH + k + 8], W3[g * kH + k + 9]) : 0u;
+    }
+    s.b3[0] = t == 0 ? b3[0] : 0.f;
+    s.b3[1] = t == 0 ? b3[1] : 0.f;
+  }
+}
+
+int install_surrogate(steps_cyl_ctx* c, const float* P) {
+  SurrLane lanes[32];
+  build_lanes(P, lanes);
+  if (!c->surr_lanes) CK(cudaMalloc(&c->surr_lanes, sizeof lanes));
+  CK(cudaMemcpyAsync(c->surr_lanes, lanes, sizeof lanes, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->surr.mu0 = P[kNW];
+  c->surr.mu1 = P[kNW + 1];
+  c->surr.sc0 = P[kNW + 2];
+  c->surr.sc1 = P[kNW + 3];
+  c->surr.dR_max = P[kNW + 4];
+  c->surr.inv_dR_max = 1.0f / P[kNW + 4];
+  c->surr.n0 = c->p.n0;
+  c->surr_params.assign(P, P + STEPS_SURR_NPARAM);
+  return STEPS_OK;
+}
+
+int grow(steps_cyl_ctx* c, size_t elems) {
+  if (elems <= c->chk_elems) return STEPS_OK;
+  cudaFree(c->chk);
+  c->chk = nullptr;
+  c->chk_elems = 0;
+  CK(cudaMalloc(&c->chk, sizeof(double) * elems));
+  c->chk_elems = elems;
+  return STEPS_OK;
+}
+
+// Total accelerations (times a^3) of a particle sample with the plain image sum
+// and with the surrogate tail; relative error statistics of the latter.
+int run_check(steps_cyl_ctx* c, int ncheck, uint64_t seed, double* med, double* p999, double* ms_plain,
+              double* ms_surr) {
+  const int ni = std::max(1, std::min(ncheck, c->n));
+  std::vector<int64_t> pick(ni);
+  {
+    std::vector<int> all(c->n);
+    for (int k = 0; k < c->n; ++k) all[k] = k;
+    SplitMix rng(seed);
+    for (int q = 0; q < ni; ++q) {  // partial Fisher-Yates: distinct internal indices
+      const int r = q + (int)(rng.next() % (uint64_t)(c->n - q));
+      std::swap(all[q], all[r]);
+      pick[q] = all[q];
+    }
+  }
+  if (ni > c->idx_cap) {
+    cudaFree(c->idx);
+    cudaFree(c->sub);
+    c->idx = nullptr;
+    c->sub = nullptr;
+    c->idx_cap = 0;
+    CK(cudaMalloc(&c->idx, sizeof(int64_t) * ni));
+    CK(cudaMalloc(&c->sub, sizeof(double) * ni * 3));
+    c->idx_cap = ni;
+  }
+  CK(cudaMemcpyAsync(c->idx, pick.data(), sizeof(int64_t) * ni, cudaMemcpyHostToDevice, c->st));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int gx = (ni + kBI - 1) / kBI;
+  const int want = std::max(1, std::min(c->NT, (sms * 8 + gx - 1) / gx));
+  const int tpc = (c->NT + want - 1) / want;
+  const int JC = (c->NT + tpc - 1) / tpc;
+  int rc;
+  if ((rc = grow(c, (size_t)JC * 3 * ni + 12 * (size_t)ni))) return rc;
+  double* part = c->chk;
+  double* sums = part + (size_t)JC * 3 * ni;
+  double* tot = sums + 3 * (size_t)ni;  // [2][3][ni]
+  const double pair_scale = -c->p.G * c->invL * c->invL;
+  float ms[2] = {0.f, 0.f};
+  for (int form = 0; form < 2; ++form) {
+    CK(cudaEventRecord(c->e0, c->st));
+    if (form == 0)
+      pair_fp32_subset_kernel<true, false><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
+                                                                            ni, tpc, c->surr_lanes, c->surr, part);
+    else
+      pair_fp32_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
+                                                                           ni, tpc, c->surr_lanes, c->surr, part);
+    CKLAUNCH("pair_fp32_subset");
+    CK(cudaEventRecord(c->e1, c->st));
+    CK(cudaEventSynchronize(c->e1));
+    CK(cudaEventElapsedTime(&ms[form], c->e0, c->e1));
+    subset_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
+    double* o = tot + (size_t)form * 3 * ni;
+    subset_finalize_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(sums, ni, c->idx, pair_scale, bg_params(c), c->x,
+                                                                c->y, 1.0, o, o + ni, o + 2 * (size_t)ni, c->err);
+    CKLAUNCH("check_finalize");
+  }
+  std::vector<double> h(6 * (size_t)ni);
+  CK(cudaMemcpyAsync(h.data(), tot, sizeof(double) * 6 * ni, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  std::vector<double> rel(ni);
+  for (int q = 0; q < ni; ++q) {
+    double d2 = 0.0, r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double p = h[(size_t)a * ni + q], s = h[3 * (size_t)ni + (size_t)a * ni + q];
+      d2 += (s - p) * (s - p);
+      r2 += p * p;
+    }
+    rel[q] = r2 > 0 ? std::sqrt(d2 / r2) : std::sqrt(d2);
+  }
+  std::sort(rel.begin(), rel.end());
+  auto quant = [&](double f) {
+    const double pos = f * (ni - 1);
+    const int lo = (int)std::floor(pos);
+    const int hi = std::min(ni - 1, lo + 1);
+    return rel[lo] + (pos - lo) * (rel[hi] - rel[lo]);
+  };
+  *med = quant(0.5);
+  *p999 = quant(0.999);
+  if (ms_plain) *ms_plain = ms[0];
+  if (ms_surr) *ms_surr = ms[1];
+  return STEPS_OK;
+}
+
+// Install parameters, check them against the plain sum and keep them only
+// when both error bounds hold.
+int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999, int ncheck, double* med,
+                     double* p999, bool* ok) {
+  int rc;
+  if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
+  bool finite = true;
+  for (int k = 0; k < STEPS_SURR_NPARAM; ++k) finite = finite && std::isfinite(P[k]);
+  if (!finite || !(P[kNW + 4] > 0.f) || !(P[kNW + 2] > 0.f) || !(P[kNW + 3] > 0.f)) {
+    *med = *p999 = INFINITY;
+    *ok = false;
+    c->surr_ok = false;
+    return STEPS_OK;
+  }
+  if ((rc = install_surrogate(c, P))) return rc;
+  c->surr_ok = true;
+  if ((rc = run_check(c, ncheck, 0x5eed0000ull + (uint64_t)c->steps_since_check, med, p999, nullptr, nullptr)))
+    return rc;
+  *ok = std::isfinite(*med) && std::isfinite(*p999) && *med <= bmed && *p999 <= bp999;
+  c->surr_ok = *ok;
+  c->surr_bound_med = bmed;
+  c->surr_bound_p999 = bp999;
+  if (!*ok) c->surr_params.clear();
+  return STEPS_OK;
+}
+
+// Device buffers of one training run (freed on every exit path).
+struct TrainBuffers {
+  cudaStream_t st = nullptr;
+  double *smp = nullptr, *tail = nullptr, *r = nullptr;
+  float *u = nullptr, *t = nullptr, *w = nullptr, *m1 = nullptr, *m2 = nullptr, *gpart = nullptr, *lpart = nullptr,
+        *loss = nullptr;
+  int* order = nullptr;
+  ~TrainBuffers() {
+    for (void* p : {(void*)smp, (void*)tail, (void*)r, (void*)u, (void*)t, (void*)w, (void*)m1, (void*)m2,
+                    (void*)gpart, (void*)lpart, (void*)loss, (void*)order})
+      if (p) cudaFreeAsync(p, st);
+    if (st) cudaStreamSynchronize(st);
+  }
+};
+
+// Sum of a block-partial loss vector (device) read back to the host.
+int read_loss(cudaStream_t st, const float* lpart, int nblocks, float* dev_out, float* host_out) {
+  sum_floats_kernel<<<1, 32, 0, st>>>(lpart, nblocks, 1.0f, dev_out);
+  CKLAUNCH("sum_floats");
+  CK(cudaMemcpyAsync(host_out, dev_out, sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return STEPS_OK;
+}
+
+int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* report) {
+  const int64_t ns = cfg->n_samples;
+  if (ns < 1024 || cfg->epochs < 1 || cfg->batch < 64 || cfg->batch % kTrainThreads != 0 || !(cfg->lr > 0) ||
+      cfg->dR_max < 0 || cfg->reserved != 0 || cfg->check_particles < 1)
+    return fail(STEPS_EINVAL, "bad training configuration");
+  const int n_cut = c->p.n_cut, n0 = c->p.n0;
+  if (n0 < 1 || n0 >= n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  const double A = n0 + 0.5;
+  double dR_max = cfg->dR_max;
+  if (dR_max == 0.0) {
+    std::vector<double> hx(c->n), hy(c->n);
+    CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double rm = 0.0;
+    for (int i = 0; i < c->n; ++i) rm = std::max(rm, std::hypot(hx[i], hy[i]));
+    dR_max = std::max(2.2 * rm * c->invL, 1.0);
+  }
+  cudaEvent_t t0, t1;
+  CK(cudaEventCreate(&t0));
+  CK(cudaEventCreate(&t1));
+  CK(cudaEventRecord(t0, c->st));
+  // samples: dR with density ~ dR (pairs in a plane), |dz| and h uniform
+  SplitMix rng(cfg->seed);
+  std::vector<double> smp(3 * (size_t)ns);
+  for (int64_t s = 0; s < ns; ++s) {
+    smp[3 * s] = dR_max * std::sqrt(rng.uniform());
+    smp[3 * s + 1] = 0.5 * rng.uniform();
+    smp[3 * s + 2] = A * rng.uniform();
+  }
+  TrainBuffers B;
+  B.st = c->st;
+  const int maxblocks = cfg->batch / kTrainThreads;
+  const int hold_blocks = 256;
+  const int nb_alloc = std::max(maxblocks, hold_blocks);
+  CK(cudaMallocAsync(&B.smp, sizeof(double) * 3 * ns, c->st));
+  CK(cudaMallocAsync(&B.tail, sizeof(double) * 2 * ns, c->st));
+  CK(cudaMallocAsync(&B.r, sizeof(double) * 2 * ns, c->st));
+  CK(cudaMallocAsync(&B.u, sizeof(float) * 3 * ns, c->st));
+  CK(cudaMallocAsync(&B.t, sizeof(float) * 2 * ns, c->st));
+  CK(cudaMallocAsync(&B.order, sizeof(int) * ns, c->st));
+  CK(cudaMallocAsync(&B.w, sizeof(float) * kNW, c->st));
+  CK(cudaMallocAsync(&B.m1, sizeof(float) * kNW, c->st));
+  CK(cudaMallocAsync(&B.m2, sizeof(float) * kNW, c->st));
+  CK(cudaMallocAsync(&B.gpart, sizeof(float) * kNW * nb_alloc, c->st));
+  CK(cudaMallocAsync(&B.lpart, sizeof(float) * nb_alloc, c->st));
+  CK(cudaMallocAsync(&B.loss, sizeof(float), c->st));
+  CK(cudaMemcpyAsync(B.smp, smp.data(), sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, c->st));
+  // exact FP64 targets, residual over the base, in envelope units
+  tail_sums_fp64_kernel<<<grid_for((int)std::min<int64_t>(ns, 1 << 30), 128), 128, 0, c->st>>>(B.smp, ns, n_cut, n0,
+                                                                                             B.tail);
+  surrogate_dataset_kernel<<<grid_for((int)std::min<int64_t>(ns, 1 << 30), 256), 256, 0, c->st>>>(
+      B.smp, B.tail, ns, n_cut, n0, dR_max, B.u, B.r);
+  CKLAUNCH("dataset");
+  const int64_t nhold = ns / 16, ntrain = ns - nhold;
+  std::vector<double> r(2 * (size_t)ns);
+  CK(cudaMemcpyAsync(r.data(), B.r, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double mu[2] = {0, 0}, sc[2] = {0, 0};
+  for (int o = 0; o < 2; ++o) {
+    double s = 0.0;
+    for (int64_t k = 0; k < ntrain; ++k) s += r[2 * k + o];
+    mu[o] = s / ntrain;
+    double v = 0.0;
+    for (int64_t k = 0; k < ntrain; ++k) v += (r[2 * k + o] - mu[o]) * (r[2 * k + o] - mu[o]);
+    sc[o] = std::sqrt(v / ntrain);
+    if (!(sc[o] > 0)) sc[o] = 1.0;
+  }
+  std::vector<float> tn(2 * (size_t)ns);
+  for (int64_t k = 0; k < ns; ++k)
+    for (int o = 0; o < 2; ++o) tn[2 * k + o] = (float)((r[2 * k + o] - mu[o]) / sc[o]);
+  CK(cudaMemcpyAsync(B.t, tn.data(), sizeof(float) * 2 * ns, cudaMemcpyHostToDevice, c->st));
+  // initial weights: uniform in +-1/sqrt(fan_in)
+  std::vector<float> w(kNW);
+  auto fill = [&](int off, int cnt, int fan_in) {
+    const double b = 1.0 / std::sqrt((double)fan_in);
+    for (int k = 0; k < cnt; ++k) w[off + k] = (float)((2.0 * rng.uniform() - 1.0) * b);
+  };
+  fill(kOW1, kH * 3, 3);
+  fill(kOB1, kH, 3);
+  fill(kOW2, kH * kH, kH);
+  fill(kOB2, kH, kH);
+  fill(kOW3, 2 * kH, kH);
+  fill(kOB3, 2, kH);
+  CK(cudaMemcpyAsync(B.w, w.data(), sizeof(float) * kNW, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(B.m1, 0, sizeof(float) * kNW, c->st));
+  CK(cudaMemsetAsync(B.m2, 0, sizeof(float) * kNW, c->st));
+  const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+  std::vector<int> order(ntrain);
+  int64_t step = 0;
+  float last_loss = 0.f;
+  int64_t last_count = 1;
+  for (int ep = 0; ep < cfg->epochs; ++ep) {
+    for (int64_t k = 0; k < ntrain; ++k) order[k] = (int)k;
+    for (int64_t k = ntrain - 1; k > 0; --k) std::swap(order[k], order[rng.next() % (uint64_t)(k + 1)]);
+    CK(cudaMemcpyAsync(B.order, order.data(), sizeof(int) * ntrain, cudaMemcpyHostToDevice, c->st));
+    const float lr = (float)(cfg->lr * 0.5 * (1.0 + std::cos(M_PI * ep / cfg->epochs)));
+    for (int64_t first = 0; first < ntrain; first += cfg->batch) {
+      const int64_t count = std::min<int64_t>(cfg->batch, ntrain - first);
+      const int nblk = (int)((count + kTrainThreads - 1) / kTrainThreads);
+      mlp_fwd_bwd_kernel<<<nblk, kTrainThreads, 0, c->st>>>(B.w, B.u, B.t, B.order, first, count, B.gpart, B.lpart);
+      ++step;
+      const float cb1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+      const float cb2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+      mlp_reduce_adam_kernel<<<(kNW + 127) / 128, 128, 0, c->st>>>(B.gpart, nblk, 1.0f / (float)count, B.w, B.m1,
+                                                                   B.m2, lr, beta1, beta2, eps, cb1, cb2, 1, nullptr);
+      last_count = count;
+    }
+    CKLAUNCH("train epoch");
+  }
+  {
+    int rc = read_loss(c->st, B.lpart, (int)((last_count + kTrainThreads - 1) / kTrainThreads), B.loss, &last_loss);
+    if (rc) return rc;
+  }
+  // held-out loss (forward and backward over the held-out tail, no update)
+  double hold_sum = 0.0;
+  for (int64_t first = ntrain; first < ns; first += (int64_t)hold_blocks * kTrainThreads) {
+    const int64_t count = std::min<int64_t>((int64_t)hold_blocks * kTrainThreads, ns - first);
+    const int nblk = (int)((count + kTrainThreads - 1) / kTrainThreads);
+    mlp_fwd_bwd_kernel<<<nblk, kTrainThreads, 0, c->st>>>(B.w, B.u, B.t, nullptr, first, count, B.gpart, B.lpart);
+    CKLAUNCH("held-out");
+    float l = 0.f;
+    int rc = read_loss(c->st, B.lpart, nblk, B.loss, &l);
+    if (rc) return rc;
+    hold_sum += l;
+  }
+  CK(cudaEventRecord(t1, c->st));
+  CK(cudaMemcpyAsync(w.data(), B.w, sizeof(float) * kNW, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  float train_ms = 0.f;
+  CK(cudaEventElapsedTime(&train_ms, t0, t1));
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  std::vector<float> P(STEPS_SURR_NPARAM);
+  std::copy(w.begin(), w.end(), P.begin());
+  P[kNW] = (float)mu[0];
+  P[kNW + 1] = (float)mu[1];
+  P[kNW + 2] = (float)sc[0];
+  P[kNW + 3] = (float)sc[1];
+  P[kNW + 4] = (float)dR_max;
+  double med = 0, p999 = 0;
+  bool ok = false;
+  int rc = accept_surrogate(c, P.data(), cfg->err_median, cfg->err_p999, cfg->check_particles, &med, &p999, &ok);
+  if (rc) return rc;
+  if (report) {
+    report[0] = last_loss / (double)last_count;
+    report[1] = std::sqrt(2.0 * hold_sum / (double)std::max<int64_t>(nhold, 1) / 2.0);
+    report[2] = med;
+    report[3] = p999;
+    report[4] = ok ? 1.0 : 0.0;
+    report[5] = train_ms;
+    report[6] = mu[0];
+    report[7] = sc[0];
+  }
+  if (!ok) return fail(STEPS_ESURROGATE_REJECTED, "surrogate rejected: median %.3g, p99.9 %.3g", med, p999);
+  return STEPS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -650,6 +1048,8 @@ int steps_cyl_params_default(steps_cyl_params* p) {
   p->t_start = 0.0;
   p->device = 0;
   p->reorder_every = 32;
+  p->check_every = 50;
+  p->check_particles = 1024;
   p->stream = nullptr;
   return STEPS_OK;
 }
@@ -717,7 +1117,10 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   c->NT = (c->n + kBJ - 1) / kBJ;
   c->U = (long long)c->NB * c->NT;
   c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1) * STEPS_CTA_MULT);
-  c->part_elems = std::max((size_t)(c->NB + c->C) * 3 * kBI, nb * 3);
+  int socc = 0;
+  CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, pair_fp32_surr_kernel<true>, kBI, 0));
+  c->SC = (int)std::min<long long>(c->U, (long long)sms * std::max(socc, 1) * STEPS_CTA_MULT);
+  c->part_elems = std::max((size_t)(c->NB + std::max(c->C, c->SC)) * 3 * kBI, nb * 3);
   CKI(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
 
   // caller order -> internal (Morton) order
@@ -833,6 +1236,8 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
   if (nsteps < 0) return fail(STEPS_EINVAL, "nsteps must be >= 0");
   DeviceGuard guard(c->dev);
   int rc;
+  bool rejected = false;
+  char reject_msg[160] = "";
   for (int s = 0; s < nsteps; ++s) {
     const Factors f = kdk_factors(c->cosmo, c->a, dt);
     if (!std::isfinite(f.K1) || !std::isfinite(f.D) || !std::isfinite(f.a_next) || !(f.a_next > 0))
@@ -847,10 +1252,26 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
     if (c->p.reorder_every > 0 && ++c->steps_since_order >= c->p.reorder_every) {
       if ((rc = reorder(c))) return rc;
     }
+    // surrogate tail: periodic comparison with the plain image sum
+    if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok && c->p.check_every > 0 &&
+        ++c->steps_since_check >= c->p.check_every) {
+      c->steps_since_check = 0;
+      double med = 0, p999 = 0;
+      const int ncheck = c->p.check_particles > 0 ? c->p.check_particles : 1024;
+      if ((rc = run_check(c, ncheck, 0xc4ec0000ull + (uint64_t)s, &med, &p999, nullptr, nullptr))) return rc;
+      if (!(med <= c->surr_bound_med && p999 <= c->surr_bound_p999)) {
+        c->surr_ok = false;
+        c->p.tail = STEPS_TAIL_FULL;
+        rejected = true;
+        snprintf(reject_msg, sizeof reject_msg, "surrogate dropped after a check: median %.3g, p99.9 %.3g", med,
+                 p999);
+      }
+    }
   }
   int e = 0;
   if ((rc = read_and_clear_err(c, &e))) return rc;
   if (e) return device_error(e);
+  if (rejected) return fail(STEPS_ESURROGATE_REJECTED, "%s", reject_msg);
   return STEPS_OK;
 }
 
@@ -966,5 +1387,139 @@ const char* steps_cyl_strerror(int code) {
 }
 
 const char* steps_cyl_last_error(void) { return g_last_error.c_str(); }
+
+int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg) {
+  if (!cfg) return fail(STEPS_EINVAL, "cfg is NULL");
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->n_samples = 1 << 20;
+  cfg->epochs = 60;
+  cfg->batch = 8192;
+  cfg->lr = 3e-3;
+  cfg->dR_max = 0.0;
+  cfg->seed = 1;
+  cfg->err_median = 1e-5;
+  cfg->err_p999 = 1e-3;
+  cfg->check_particles = 1024;
+  return STEPS_OK;
+}
+
+int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out, void* stream) {
+  g_last_error.clear();
+  if (ns < 0 || !samples || !out) return fail(STEPS_EINVAL, "bad arguments");
+  if (n_cut < 1 || n0 < 0 || n0 >= n_cut) return fail(STEPS_EINVAL, "need 0 <= n0 < n_cut");
+  if (ns == 0) return STEPS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *ds = nullptr, *dout = nullptr;
+  CK(cudaMallocAsync(&ds, sizeof(double) * 3 * ns, st));
+  CK(cudaMallocAsync(&dout, sizeof(double) * 2 * ns, st));
+  CK(cudaMemcpyAsync(ds, samples, sizeof(double) * 3 * ns, cudaMemcpyDefault, st));
+  tail_sums_fp64_kernel<<<grid_for((int)std::min<int64_t>(ns, 1 << 30), 128), 128, 0, st>>>(ds, ns, n_cut, n0, dout);
+  CKLAUNCH("tail_sums");
+  CK(cudaMemcpyAsync(out, dout, sizeof(double) * 2 * ns, cudaMemcpyDefault, st));
+  CK(cudaFreeAsync(ds, st));
+  CK(cudaFreeAsync(dout, st));
+  CK(cudaStreamSynchronize(st));
+  return STEPS_OK;
+}
+
+int steps_cyl_mlp_loss_grad(int64_t ns, const float* w, const float* u, const float* t, float* loss, float* grad,
+                            void* stream) {
+  g_last_error.clear();
+  if (ns < 1 || ns > (1 << 26) || !w || !u || !t || !loss || !grad) return fail(STEPS_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nblk = (int)((ns + kTrainThreads - 1) / kTrainThreads);
+  float *dw, *du, *dt, *gp, *lp, *dg, *dl;
+  CK(cudaMallocAsync(&dw, sizeof(float) * kNW, st));
+  CK(cudaMallocAsync(&du, sizeof(float) * 3 * ns, st));
+  CK(cudaMallocAsync(&dt, sizeof(float) * 2 * ns, st));
+  CK(cudaMallocAsync(&gp, sizeof(float) * kNW * (size_t)nblk, st));
+  CK(cudaMallocAsync(&lp, sizeof(float) * nblk, st));
+  CK(cudaMallocAsync(&dg, sizeof(float) * kNW, st));
+  CK(cudaMallocAsync(&dl, sizeof(float), st));
+  CK(cudaMemcpyAsync(dw, w, sizeof(float) * kNW, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(du, u, sizeof(float) * 3 * ns, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(dt, t, sizeof(float) * 2 * ns, cudaMemcpyDefault, st));
+  mlp_fwd_bwd_kernel<<<nblk, kTrainThreads, 0, st>>>(dw, du, dt, nullptr, 0, ns, gp, lp);
+  mlp_reduce_adam_kernel<<<(kNW + 127) / 128, 128, 0, st>>>(gp, nblk, 1.0f / (float)ns, nullptr, nullptr, nullptr,
+                                                            0.f, 0.f, 0.f, 0.f, 1.f, 1.f, 0, dg);
+  sum_floats_kernel<<<1, 32, 0, st>>>(lp, nblk, 1.0f / (float)ns, dl);
+  CKLAUNCH("mlp_loss_grad");
+  CK(cudaMemcpyAsync(grad, dg, sizeof(float) * kNW, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(loss, dl, sizeof(float), cudaMemcpyDefault, st));
+  for (float* p : {dw, du, dt, gp, lp, dg, dl}) CK(cudaFreeAsync(p, st));
+  CK(cudaStreamSynchronize(st));
+  return STEPS_OK;
+}
+
+int steps_cyl_train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* report) {
+  g_last_error.clear();
+  if (!c || !cfg) return fail(STEPS_EINVAL, "NULL argument");
+  DeviceGuard guard(c->dev);
+  if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
+  const int32_t tail = c->p.tail;
+  c->p.tail = STEPS_TAIL_FULL;  // the check compares against the plain sum explicitly
+  int rc = train_surrogate(c, cfg, report);
+  c->p.tail = (rc == STEPS_OK) ? tail : STEPS_TAIL_FULL;
+  return rc;
+}
+
+int steps_cyl_set_surrogate(steps_cyl_ctx* c, const float* params, double err_median, double err_p999,
+                            double* report) {
+  g_last_error.clear();
+  if (!c || !params) return fail(STEPS_EINVAL, "NULL argument");
+  if (!(err_median > 0) || !(err_p999 > 0)) return fail(STEPS_EINVAL, "bounds must be > 0");
+  DeviceGuard guard(c->dev);
+  std::vector<float> P(STEPS_SURR_NPARAM);
+  CK(cudaMemcpyAsync(P.data(), params, sizeof(float) * STEPS_SURR_NPARAM, cudaMemcpyDefault, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double med = 0, p999 = 0;
+  bool ok = false;
+  const int ncheck = c->p.check_particles > 0 ? c->p.check_particles : 1024;
+  int rc = accept_surrogate(c, P.data(), err_median, err_p999, ncheck, &med, &p999, &ok);
+  if (rc) return rc;
+  if (report) {
+    report[0] = med;
+    report[1] = p999;
+    report[2] = ok ? 1.0 : 0.0;
+    report[3] = 0.0;
+  }
+  if (!ok) {
+    c->p.tail = STEPS_TAIL_FULL;
+    return fail(STEPS_ESURROGATE_REJECTED, "surrogate rejected: median %.3g, p99.9 %.3g", med, p999);
+  }
+  return STEPS_OK;
+}
+
+int steps_cyl_get_surrogate(steps_cyl_ctx* c, float* params) {
+  g_last_error.clear();
+  if (!c || !params) return fail(STEPS_EINVAL, "NULL argument");
+  if (!c->surr_ok || c->surr_params.size() != STEPS_SURR_NPARAM)
+    return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
+  std::memcpy(params, c->surr_params.data(), sizeof(float) * STEPS_SURR_NPARAM);
+  return STEPS_OK;
+}
+
+int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE) return fail(STEPS_EINVAL, "bad tail mode");
+  if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
+  if (tail == STEPS_TAIL_SURROGATE && c->p.precision == STEPS_FP64)
+    return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
+  DeviceGuard guard(c->dev);
+  c->p.tail = tail;
+  c->steps_since_check = 0;
+  return eval_forces(c, false, 0.0);
+}
+
+int steps_cyl_check_surrogate(steps_cyl_ctx* c, int32_t check_particles, double* report) {
+  g_last_error.clear();
+  if (!c || !report || check_particles < 1) return fail(STEPS_EINVAL, "bad arguments");
+  if (!c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
+  DeviceGuard guard(c->dev);
+  return run_check(c, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check, &report[0], &report[1],
+                   &report[2], &report[3]);
+}
+
 
 }  // extern "C"

@@ -34,8 +34,13 @@ _EXPORTS = [
     "steps_cyl_params_default", "steps_cyl_init", "steps_cyl_forces", "steps_cyl_forces_subset",
     "steps_cyl_kdk_step", "steps_cyl_get_state", "steps_cyl_set_state", "steps_cyl_set_precision",
     "steps_cyl_diagnostics", "steps_cyl_last_timing", "steps_cyl_free", "steps_cyl_strerror",
-    "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc",
+    "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc", "steps_cyl_train_cfg_default", "steps_cyl_tail_sums",
+    "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
+    "steps_cyl_set_tail", "steps_cyl_check_surrogate",
 ]
+
+STEPS_SURR_NW = 1250
+STEPS_SURR_NPARAM = 1255
 
 # size limit of the allocation-free entry point (include/steps_cyl.h)
 STEPS_NOALLOC_MAX_N = 65536
@@ -56,7 +61,17 @@ class Params(ctypes.Structure):
         ("H0", ctypes.c_double), ("Omega_m", ctypes.c_double), ("Omega_r", ctypes.c_double),
         ("Omega_L", ctypes.c_double), ("w0", ctypes.c_double), ("wa", ctypes.c_double),
         ("a_start", ctypes.c_double), ("t_start", ctypes.c_double),
-        ("device", ctypes.c_int32), ("reorder_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int32), ("reorder_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
+        ("check_particles", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+class TrainCfg(ctypes.Structure):
+    """Mirror of ``steps_cyl_train_cfg``."""
+    _fields_ = [
+        ("n_samples", ctypes.c_int64), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
+        ("dR_max", ctypes.c_double), ("seed", ctypes.c_uint64), ("err_median", ctypes.c_double),
+        ("err_p999", ctypes.c_double), ("check_particles", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -95,6 +110,14 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_last_error.argtypes = []
     L.steps_cyl_last_error.restype = ctypes.c_char_p
     L.steps_cyl_pair_accel_noalloc.argtypes = [i64, p, p, p, p, p, d, d, i32, i32, p, p, p, p]
+    L.steps_cyl_train_cfg_default.argtypes = [ctypes.POINTER(TrainCfg)]
+    L.steps_cyl_tail_sums.argtypes = [i64, p, i32, i32, p, p]
+    L.steps_cyl_mlp_loss_grad.argtypes = [i64, p, p, p, p, p, p]
+    L.steps_cyl_train_surrogate.argtypes = [p, ctypes.POINTER(TrainCfg), p]
+    L.steps_cyl_set_surrogate.argtypes = [p, p, d, d, p]
+    L.steps_cyl_get_surrogate.argtypes = [p, p]
+    L.steps_cyl_set_tail.argtypes = [p, i32]
+    L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -156,6 +179,8 @@ class Config:
     t_start: float = 0.0
     device: int = 0
     reorder_every: int = 32
+    check_every: int = 50
+    check_particles: int = 1024
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def to_c(self) -> Params:
@@ -248,6 +273,76 @@ def steps_cyl_pair_accel_noalloc(x, y, z, m, h, G, L, n_cut, precision, ax, ay, 
                                              ctypes.c_void_p(stream or None))
     if rc != STEPS_OK:
         raise StepsError(rc, "steps_cyl_pair_accel_noalloc rejected its arguments or failed to launch")
+
+
+def steps_cyl_train_cfg_default(**overrides) -> TrainCfg:
+    cfg = TrainCfg()
+    _check(load().steps_cyl_train_cfg_default(ctypes.byref(cfg)))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def steps_cyl_tail_sums(samples, n_cut: int, n0: int, stream=0) -> np.ndarray:
+    """Exact FP64 far-image tail sums on the GPU for samples (ns, 3) = (dR, dz, h) in units of L."""
+    smp = np.ascontiguousarray(samples, dtype=np.float64)
+    out = np.zeros((smp.shape[0], 2))
+    _check(load().steps_cyl_tail_sums(smp.shape[0], _ptr(smp), int(n_cut), int(n0), _ptr(out),
+                                      ctypes.c_void_p(stream or None)))
+    return out
+
+
+def steps_cyl_mlp_loss_grad(w, u, t, stream=0):
+    """FP32 forward + backward of the surrogate network on the GPU: (loss, grad)."""
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(STEPS_SURR_NW, dtype=np.float32)
+    _check(load().steps_cyl_mlp_loss_grad(u.shape[0], _ptr(w), _ptr(u), _ptr(t), _ptr(loss), _ptr(grad),
+                                          ctypes.c_void_p(stream or None)))
+    return float(loss[0]), grad
+
+
+def steps_cyl_train_surrogate(ctx, cfg: TrainCfg) -> np.ndarray:
+    """Train and check the context's surrogate; returns the 8-entry report.
+    Raises StepsError (code STEPS_ESURROGATE_REJECTED) when the check fails."""
+    rep = np.zeros(8)
+    rc = load().steps_cyl_train_surrogate(ctx, ctypes.byref(cfg), _ptr(rep))
+    if rc == STEPS_ESURROGATE_REJECTED:
+        err = StepsError(rc, (load().steps_cyl_last_error() or b"").decode())
+        err.report = rep
+        raise err
+    _check(rc)
+    return rep
+
+
+def steps_cyl_set_surrogate(ctx, params, err_median=1e-5, err_p999=1e-3) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    rep = np.zeros(4)
+    rc = load().steps_cyl_set_surrogate(ctx, _ptr(p), float(err_median), float(err_p999), _ptr(rep))
+    if rc == STEPS_ESURROGATE_REJECTED:
+        err = StepsError(rc, (load().steps_cyl_last_error() or b"").decode())
+        err.report = rep
+        raise err
+    _check(rc)
+    return rep
+
+
+def steps_cyl_get_surrogate(ctx) -> np.ndarray:
+    out = np.zeros(STEPS_SURR_NPARAM, dtype=np.float32)
+    _check(load().steps_cyl_get_surrogate(ctx, _ptr(out)))
+    return out
+
+
+def steps_cyl_set_tail(ctx, tail: int):
+    _check(load().steps_cyl_set_tail(ctx, int(tail)))
+
+
+def steps_cyl_check_surrogate(ctx, check_particles: int = 1024) -> np.ndarray:
+    rep = np.zeros(4)
+    _check(load().steps_cyl_check_surrogate(ctx, int(check_particles), _ptr(rep)))
+    return rep
 
 
 class Simulation:

@@ -329,6 +329,99 @@ def run(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (python bench.py --workload NAME): one JSON line each. The
+# reference for force errors is this library's FP64 form on a particle sample
+# (parity-tested against the FP64 oracle in the test-suite).
+# ---------------------------------------------------------------------------
+def _ctx_for(sc, torch, w, d, precision, **kw):
+    from paper_2602_20787_gb300 import ics
+    t0, _ = ics.run_schedule(w)
+    cfg = sc.Config(n_cut=w.n_cut, n0=w.n0, precision=precision, rho_bar=w.rho_bar, comoving=w.comoving,
+                    a_start=w.a_start if w.comoving else 1.0, t_start=t0 if w.comoving else 0.0,
+                    stream=torch.cuda.current_stream().cuda_stream, **kw)
+    return sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+
+
+def _timed_forces(sc, torch, sim, reps):
+    dev = torch.device("cuda")
+    out = [torch.empty(sim.n, dtype=torch.float64, device=dev) for _ in range(3)]
+    ms = []
+    for _ in range(reps):
+        sc.steps_cyl_forces(sim.ctx, *out)
+        ms.append(sc.steps_cyl_last_timing(sim.ctx)[1])
+    torch.cuda.synchronize()
+    return torch.stack(out, 1).cpu().numpy(), statistics.median(ms)
+
+
+def _err(a, ref):
+    r = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return {"median": float(np.median(r)), "p999": float(np.quantile(r, 0.999)), "max": float(r.max())}
+
+
+def run_workload(args):
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    w = ics.WORKLOADS[args.workload]
+    d = ics.workload_ics(w)
+    n = w.n
+    pairs = n * (n - 1.0)
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * 2070e6
+    line = {"workload": w.name, "n": n, "n_cut": w.n_cut, "roofline_peak_pair_images_per_s": peak}
+    idx = ics.subsample(n, 4096 if w.name.startswith("precision") else 256, seed=12345)
+    reps = 1 if n > 300000 else 2
+    sim = _ctx_for(sc, torch, w, d, sc.STEPS_FP32_KAHAN, check_particles=1024,
+                   check_every=10 if w.name.startswith("production") else 50)
+    a32, ms32 = _timed_forces(sc, torch, sim, reps)
+    line["fp32_kahan"] = {"pair_ms": ms32, "pair_images_per_s": pairs * 2 * w.n_cut / (ms32 * 1e-3)}
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)
+    a64 = sim.forces_subset(idx)
+    ms64 = sc.steps_cyl_last_timing(sim.ctx)[1]
+    line["fp64_subset"] = {"i_sample": int(idx.size), "pair_ms": ms64,
+                           "pair_images_per_s": idx.size * (n - 1.0) * 2 * w.n_cut / (ms64 * 1e-3)}
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+    line["fp32_kahan"]["error_vs_fp64"] = _err(a32[idx], a64)
+    line["fp32_kahan"]["roofline_frac"] = line["fp32_kahan"]["pair_images_per_s"] / peak
+    if w.name.startswith("precision"):
+        sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_PLAIN)
+        ap, msp = _timed_forces(sc, torch, sim, reps)
+        line["fp32_plain"] = {"pair_ms": msp, "pair_images_per_s": pairs * 2 * w.n_cut / (msp * 1e-3),
+                              "error_vs_fp64": _err(ap[idx], a64)}
+    if w.name.startswith("surrogate") or w.name.startswith("production"):
+        sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+        rep = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+        asg, mss = _timed_forces(sc, torch, sim, reps + 1)
+        line["surrogate"] = {
+            "train_ms": rep[5], "train_heldout_rms": rep[1], "check_median": rep[2], "check_p999": rep[3],
+            "pair_ms": mss, "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (mss * 1e-3),
+            "executed_near_images_per_pair": 2 * w.n0 + 1, "speedup_vs_fp32_plain_sum": ms32 / mss,
+            "error_vs_fp64": _err(asg[idx], a64)}
+    if w.name.startswith("production") or w.name.startswith("plain_small") or w.name.startswith("lcdm"):
+        steps = min(args.steps, w.nsteps) if w.nsteps else args.steps
+        t0, dt = ics.run_schedule(w)
+        sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+        if w.name.startswith("production"):
+            sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+        d0 = sim.diagnostics()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        sim.step(dt, steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        d1 = sim.diagnostics()
+        # momentum scale: total mass times the rms canonical velocity a^2 |dx/dt|
+        pscale = d1[5] ** 2 * math.sqrt(2.0 * d1[4] * d1[7]) if d1[4] > 0 else 1.0
+        line["kdk"] = {"steps": steps, "dt": dt, "step_ms": ev0.elapsed_time(ev1) / steps, "a_end": d1[5],
+                       "pz_drift_over_momentum_scale": abs(d1[2] - d0[2]) / pscale,
+                       "lz_drift_abs": abs(d1[3] - d0[3]),
+                       "tail": "surrogate" if w.name.startswith("production") else "full"}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,7 +430,10 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=None, help="run another workload's measurement (one JSON line)")
     args = ap.parse_args()
+    if args.workload:
+        sys.exit(run_workload(args))
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     sys.exit(run(args))

@@ -128,7 +128,9 @@ int steps_cyl_set_state(steps_cyl_ctx* ctx, const double* x, const double* y, co
                         const double* vx, const double* vy, const double* vz);
 
 /* Switch the pair-kernel precision (STEPS_FP64 / FP32_KAHAN / FP32_PLAIN) of an
- * existing context; the cached forces are recomputed. */
+ * existing context (STEPS_FP64 also selects STEPS_TAIL_FULL). Nothing is
+ * computed here: the forces that feed the next kick are recomputed by the next
+ * force evaluation or at the start of the next KDK step. */
 int steps_cyl_set_precision(steps_cyl_ctx* ctx, int32_t precision);
 
 /* Conserved quantities and energies (Sect. 1: P_z and L_z are conserved in
@@ -212,7 +214,8 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* ctx, const float* params, double err_
 int steps_cyl_get_surrogate(steps_cyl_ctx* ctx, float* params);
 
 /* Select the tail form: STEPS_TAIL_FULL, or STEPS_TAIL_SURROGATE (requires an
- * accepted surrogate and an FP32 precision). Cached forces are recomputed. */
+ * accepted surrogate and an FP32 precision). As with steps_cyl_set_precision the
+ * cached forces are refreshed by the next force evaluation or KDK step. */
 int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
 
 /* Compare the surrogate form with the plain image sum now on check_particles

@@ -202,12 +202,10 @@ static __global__ void diag_final_kernel(const double* __restrict__ part, int nb
 }
 
 // ---------------------------------------------------------------------------
-// FP64 pair kernel (precision study and reference form): one thread per listed
-// i, every j, same window and softening as the FP32 kernel but evaluated
-// directly (branch on r < h) in FP64. idx == nullptr means i = q.
-// Output: out[q], out[ni + q], out[2 ni + q] = sum_j m_j (dx, dy, dz-part) in
-// units of G / L^2 (scaled by the caller), i.e. the same quantity as the FP32
-// partial sums.
+// FP64 pair kernel (precision study and reference form): same window and
+// softening as the FP32 kernel but evaluated directly (branch on r < h) in
+// FP64. idx == nullptr means i = q. Sums are sum_j m_j (dx, dy, dz-part) in
+// units of G / L^2 (scaled by the caller), the same quantity as the FP32 sums.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double spline_over_r_fp64(double r, double hh) {
   const double ih = 1.0 / hh, u = r * ih, ih3 = ih * ih * ih;
@@ -231,37 +229,76 @@ __device__ __forceinline__ void image_fp64(double dR2, double o, double hh, doub
   sz = fma(o, f, sz);
 }
 
+// CTA (bx, by) takes listed i-particles [bx * 128, +128) against j-tiles
+// [by * tpc, (by + 1) * tpc) of 128 j staged in shared memory, so that a short
+// list still fills the GPU; part[by][3][ni] receives the partial sums, which
+// chunk_sum_kernel adds in chunk order.
 static __global__ void __launch_bounds__(128)
 pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
                  const double* __restrict__ m, const double* __restrict__ h, int n,
-                 const int64_t* __restrict__ idx, int ni, double invL, int n_cut, double* __restrict__ out) {
+                 const int64_t* __restrict__ idx, int ni, double invL, int n_cut, int tpc, double* __restrict__ part) {
+  __shared__ double sx[128], sy[128], sz[128], sm[128], sh[128];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int qq = min(q, ni - 1);
+  const int i = idx ? (int)idx[qq] : qq;
+  const double xi = x[i] * invL, yi = y[i] * invL, zi = z[i] * invL, hi = h[i] * invL;
+  const int NT = (n + 127) / 128;
+  const int t0 = blockIdx.y * tpc, t1 = min(NT, t0 + tpc);
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int t = t0; t < t1; ++t) {
+    __syncthreads();
+    const int jl = t * 128 + threadIdx.x;
+    if (jl < n) {
+      sx[threadIdx.x] = x[jl] * invL;
+      sy[threadIdx.x] = y[jl] * invL;
+      sz[threadIdx.x] = z[jl] * invL;
+      sm[threadIdx.x] = m[jl];
+      sh[threadIdx.x] = h[jl] * invL;
+    }
+    __syncthreads();
+    const int jn = min(128, n - t * 128);
+    for (int k = 0; k < jn; ++k) {
+      if (t * 128 + k == i) continue;
+      const double dx = xi - sx[k], dy = yi - sy[k];
+      double dz = zi - sz[k];
+      dz -= rint(dz);
+      const double dR2 = dx * dx + dy * dy;
+      const double hh = hi + sh[k], hh2 = hh * hh;
+      double sr = 0.0, szz = 0.0;
+      image_fp64(dR2, dz, hh, hh2, 1.0, sr, szz);
+      image_fp64(dR2, dz - copysign((double)n_cut, dz), hh, hh2, dz != 0.0 ? 1.0 : 0.0, sr, szz);
+      for (int kk = 1; kk < n_cut; ++kk) {
+        image_fp64(dR2, dz + (double)kk, hh, hh2, 1.0, sr, szz);
+        image_fp64(dR2, dz - (double)kk, hh, hh2, 1.0, sr, szz);
+      }
+      const double mj = sm[k];
+      ax += mj * dx * sr;
+      ay += mj * dy * sr;
+      az += mj * szz;
+    }
+  }
+  if (q < ni) {
+    double* dst = part + (long long)blockIdx.y * 3 * ni;
+    dst[q] = ax;
+    dst[ni + q] = ay;
+    dst[2 * (long long)ni + q] = az;
+  }
+}
+
+// out[3][ni] = sum over chunks c (in order) of part[c][3][ni]
+static __global__ void chunk_sum_kernel(const double* __restrict__ part, int ni, int chunks, double* __restrict__ out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ni) return;
-  const int i = idx ? (int)idx[q] : q;
-  const double xi = x[i] * invL, yi = y[i] * invL, zi = z[i] * invL, hi = h[i] * invL;
-  double ax = 0.0, ay = 0.0, az = 0.0;
-  for (int j = 0; j < n; ++j) {
-    if (j == i) continue;
-    const double dx = xi - x[j] * invL, dy = yi - y[j] * invL;
-    double dz = zi - z[j] * invL;
-    dz -= rint(dz);
-    const double dR2 = dx * dx + dy * dy;
-    const double hh = hi + h[j] * invL, hh2 = hh * hh;
-    double sr = 0.0, sz = 0.0;
-    image_fp64(dR2, dz, hh, hh2, 1.0, sr, sz);
-    image_fp64(dR2, dz - copysign((double)n_cut, dz), hh, hh2, dz != 0.0 ? 1.0 : 0.0, sr, sz);
-    for (int k = 1; k < n_cut; ++k) {
-      image_fp64(dR2, dz + (double)k, hh, hh2, 1.0, sr, sz);
-      image_fp64(dR2, dz - (double)k, hh, hh2, 1.0, sr, sz);
-    }
-    const double mj = m[j];
-    ax += mj * dx * sr;
-    ay += mj * dy * sr;
-    az += mj * sz;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int c = 0; c < chunks; ++c) {
+    const double* p = part + (long long)c * 3 * ni;
+    s0 += p[q];
+    s1 += p[ni + q];
+    s2 += p[2 * (long long)ni + q];
   }
-  out[q] = ax;
-  out[ni + q] = ay;
-  out[2 * ni + q] = az;
+  out[q] = s0;
+  out[ni + q] = s1;
+  out[2 * (long long)ni + q] = s2;
 }
 
 // out3 (SoA, ni each) = pair_scale * pair + background at the listed i, / a^3

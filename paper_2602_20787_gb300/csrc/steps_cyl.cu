@@ -224,6 +224,7 @@ struct steps_cyl_ctx {
   int C = 0, NT = 0, NB = 0;
   long long U = 0;
   int steps_since_order = 0;
+  bool forces_stale = false;       // g must be recomputed before the next kick
   // learned far-image surrogate
   SurrLane* surr_lanes = nullptr;  // per-lane MLP fragments (device, 32 entries)
   SurrConst surr{};
@@ -465,15 +466,39 @@ int build_background(steps_cyl_ctx* c) {
   return STEPS_OK;
 }
 
+// FP64 pair sums of the listed particles (all when idx == nullptr) into
+// out[3][ni], with the j-range split across CTAs so that short lists fill the GPU.
+int launch_fp64(steps_cyl_ctx* c, const int64_t* idx, int ni, double* out) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int gx = (ni + 127) / 128;
+  const int want = std::max(1, std::min(c->NT, (sms * 8 + gx - 1) / gx));
+  const int tpc = (c->NT + want - 1) / want;
+  const int JC = (c->NT + tpc - 1) / tpc;
+  if (c->chk_elems < (size_t)JC * 3 * ni) {
+    cudaFree(c->chk);
+    c->chk = nullptr;
+    c->chk_elems = 0;
+    CK(cudaMalloc(&c->chk, sizeof(double) * (size_t)JC * 3 * ni));
+    c->chk_elems = (size_t)JC * 3 * ni;
+  }
+  pair_fp64_kernel<<<dim3(gx, JC), 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, idx, ni, c->invL, c->p.n_cut,
+                                                    tpc, c->chk);
+  CKLAUNCH("pair_fp64");
+  chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(c->chk, ni, JC, out);
+  CKLAUNCH("chunk_sum");
+  return STEPS_OK;
+}
+
 // One force evaluation at the current packed positions. Stores g = a^3 (pair +
 // background) in gx/gy/gz (internal order); kicks p by K when kick is set.
 int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   const double pair_scale = -c->p.G * c->invL * c->invL;
+  c->forces_stale = false;
   CK(cudaEventRecord(c->e0, c->st));
   if (c->p.precision == STEPS_FP64) {
-    pair_fp64_kernel<<<(c->n + 127) / 128, 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, nullptr, c->n,
-                                                            c->invL, c->p.n_cut, c->part);
-    CKLAUNCH("pair_fp64");
+    int rc = launch_fp64(c, nullptr, c->n, c->part);
+    if (rc) return rc;
   } else if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok) {
     if (c->p.precision == STEPS_FP32_KAHAN)
       pair_fp32_surr_kernel<true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
@@ -777,7 +802,7 @@ int run_check(steps_cyl_ctx* c, int ncheck, uint64_t seed, double* med, double* 
     CK(cudaEventRecord(c->e1, c->st));
     CK(cudaEventSynchronize(c->e1));
     CK(cudaEventElapsedTime(&ms[form], c->e0, c->e1));
-    subset_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
+    chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
     double* o = tot + (size_t)form * 3 * ni;
     subset_finalize_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(sums, ni, c->idx, pair_scale, bg_params(c), c->x,
                                                                 c->y, 1.0, o, o + ni, o + 2 * (size_t)ni, c->err);
@@ -1203,9 +1228,7 @@ int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, do
   double* o = c->stage;  // 3 ni <= 3 n
   if (c->p.precision == STEPS_FP64) {
     CK(cudaEventRecord(c->e0, c->st));
-    pair_fp64_kernel<<<((int)ni + 127) / 128, 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, c->idx, (int)ni,
-                                                               c->invL, c->p.n_cut, c->sub);
-    CKLAUNCH("pair_fp64_subset");
+    if ((rc = launch_fp64(c, c->idx, (int)ni, c->sub))) return rc;
     CK(cudaEventRecord(c->e1, c->st));
     c->timed = true;
     c->last_images = (double)ni * (double)(c->n - 1) * 2.0 * c->p.n_cut;
@@ -1238,6 +1261,7 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
   int rc;
   bool rejected = false;
   char reject_msg[160] = "";
+  if (nsteps > 0 && c->forces_stale && (rc = eval_forces(c, false, 0.0))) return rc;
   for (int s = 0; s < nsteps; ++s) {
     const Factors f = kdk_factors(c->cosmo, c->a, dt);
     if (!std::isfinite(f.K1) || !std::isfinite(f.D) || !std::isfinite(f.a_next) || !(f.a_next > 0))
@@ -1328,7 +1352,9 @@ int steps_cyl_set_precision(steps_cyl_ctx* c, int32_t precision) {
   if (precision < STEPS_FP64 || precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   DeviceGuard guard(c->dev);
   c->p.precision = precision;
-  return eval_forces(c, false, 0.0);
+  if (precision == STEPS_FP64) c->p.tail = STEPS_TAIL_FULL;
+  c->forces_stale = true;  // refreshed by the next force evaluation or KDK step
+  return STEPS_OK;
 }
 
 int steps_cyl_diagnostics(steps_cyl_ctx* c, double out[8]) {
@@ -1506,10 +1532,10 @@ int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
   if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
   if (tail == STEPS_TAIL_SURROGATE && c->p.precision == STEPS_FP64)
     return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
-  DeviceGuard guard(c->dev);
   c->p.tail = tail;
   c->steps_since_check = 0;
-  return eval_forces(c, false, 0.0);
+  c->forces_stale = true;  // refreshed by the next force evaluation or KDK step
+  return STEPS_OK;
 }
 
 int steps_cyl_check_surrogate(steps_cyl_ctx* c, int32_t check_particles, double* report) {

@@ -34,6 +34,27 @@ struct SurrLane {
 };
 static_assert(sizeof(SurrLane) == 48 * 4, "SurrLane layout");
 
+// Word w of lane L's SurrLane lives at wt[w * 32 + L] in shared memory
+// (word-major), so a warp reading one word touches 32 distinct banks.
+constexpr int kSurrWords = sizeof(SurrLane) / 4;
+struct SurrW {
+  const uint32_t* p;  // wt + lane
+  __device__ __forceinline__ uint32_t u(int w) const { return p[w * 32]; }
+  __device__ __forceinline__ float f(int w) const { return __uint_as_float(p[w * 32]); }
+};
+constexpr int kW1 = 0, kW2 = 4, kW3 = 20, kB1 = 24, kB2 = 32, kB3 = 40;
+
+// Stage the 32 lanes' fragments word-major into shared memory (all threads of
+// the block take part; ends with a barrier).
+__device__ __forceinline__ void stage_surr_weights(const SurrLane* __restrict__ wl, uint32_t* wt) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(wl);
+  for (int k = threadIdx.x; k < 32 * kSurrWords; k += blockDim.x) {
+    const int lane = k / kSurrWords, w = k % kSurrWords;
+    wt[w * 32 + lane] = src[k];
+  }
+  __syncthreads();
+}
+
 struct SurrConst {
   float mu0, mu1, sc0, sc1;
   float inv_dR_max, dR_max;
@@ -62,68 +83,81 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   return r;
 }
 
-// The MLP for the 32 pairs of the warp; every lane passes its own pair's
-// inputs and receives its own pair's two outputs. Must be called by all 32
-// lanes with uniform control flow.
-__device__ __forceinline__ void mlp_warp(const SurrLane& W, float u0, float u1, float u2, float& y0, float& y1) {
+// The MLP for NJ x 32 pairs of the warp (NJ values of j, one pair per lane
+// each); every lane passes its own pairs' inputs and receives their outputs.
+// The 2 NJ m-tiles are independent chains of mma, which the scheduler
+// interleaves. Must be called by all 32 lanes with uniform control flow.
+template <int NJ>
+__device__ __forceinline__ void mlp_warp(const SurrW& W, const float (&u)[NJ][3], float (&y)[NJ][2]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const uint32_t p01 = pack_h2(u0, u1), p2 = pack_h2(u2, 0.0f);
-  uint32_t in[4];
+  uint32_t in[NJ][4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t s01 = __shfl_sync(0xffffffffu, p01, 4 * g + q);
-    const uint32_t s2 = __shfl_sync(0xffffffffu, p2, 4 * g + q);
-    in[q] = t == 0 ? s01 : (t == 1 ? s2 : 0u);
+  for (int jj = 0; jj < NJ; ++jj) {
+    const uint32_t p01 = pack_h2(u[jj][0], u[jj][1]), p2 = pack_h2(u[jj][2], 0.0f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t s01 = __shfl_sync(0xffffffffu, p01, 4 * g + q);
+      const uint32_t s2 = __shfl_sync(0xffffffffu, p2, 4 * g + q);
+      in[jj][q] = t == 0 ? s01 : (t == 1 ? s2 : 0u);
+    }
   }
-  float out[2][4];
+  float out[NJ][2][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    // layer 1: [16 pairs x 8 inputs] x [8 x 32]
-    float d1[4][4];
+  for (int jj = 0; jj < NJ; ++jj) {
 #pragma unroll
-    for (int nb = 0; nb < 4; ++nb) {
-      const float c[4] = {W.b1[2 * nb], W.b1[2 * nb + 1], W.b1[2 * nb], W.b1[2 * nb + 1]};
-      mma_k8(d1[nb], in[2 * mt], in[2 * mt + 1], W.w1[nb], c);
+    for (int mt = 0; mt < 2; ++mt) {
+      // layer 1: [16 pairs x 8 inputs] x [8 x 32]
+      float d1[4][4];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) {
+        const float b0 = W.f(kB1 + 2 * nb), b1v = W.f(kB1 + 2 * nb + 1);
+        const float c[4] = {b0, b1v, b0, b1v};
+        mma_k8(d1[nb], in[jj][2 * mt], in[jj][2 * mt + 1], W.u(kW1 + nb), c);
+      }
+      uint32_t a2[2][4];
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        a2[kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
+        a2[kb][1] = relu_pack(d1[2 * kb][2], d1[2 * kb][3]);
+        a2[kb][2] = relu_pack(d1[2 * kb + 1][0], d1[2 * kb + 1][1]);
+        a2[kb][3] = relu_pack(d1[2 * kb + 1][2], d1[2 * kb + 1][3]);
+      }
+      // layer 2: [16 x 32] x [32 x 32]
+      float d2[4][4];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) {
+        const float b0 = W.f(kB2 + 2 * nb), b1v = W.f(kB2 + 2 * nb + 1);
+        const float c[4] = {b0, b1v, b0, b1v};
+        mma_k16(d2[nb], a2[0], W.u(kW2 + nb * 2), W.u(kW2 + nb * 2 + 1), c);
+        mma_k16(d2[nb], a2[1], W.u(kW2 + (4 + nb) * 2), W.u(kW2 + (4 + nb) * 2 + 1), d2[nb]);
+      }
+      uint32_t a3[2][4];
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        a3[kb][0] = relu_pack(d2[2 * kb][0], d2[2 * kb][1]);
+        a3[kb][1] = relu_pack(d2[2 * kb][2], d2[2 * kb][3]);
+        a3[kb][2] = relu_pack(d2[2 * kb + 1][0], d2[2 * kb + 1][1]);
+        a3[kb][3] = relu_pack(d2[2 * kb + 1][2], d2[2 * kb + 1][3]);
+      }
+      // layer 3: [16 x 32] x [32 x 8] (columns 0, 1 used)
+      const float c3[4] = {W.f(kB3), W.f(kB3 + 1), W.f(kB3), W.f(kB3 + 1)};
+      mma_k16(out[jj][mt], a3[0], W.u(kW3), W.u(kW3 + 1), c3);
+      mma_k16(out[jj][mt], a3[1], W.u(kW3 + 2), W.u(kW3 + 3), out[jj][mt]);
     }
-    uint32_t a2[2][4];
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-      a2[kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
-      a2[kb][1] = relu_pack(d1[2 * kb][2], d1[2 * kb][3]);
-      a2[kb][2] = relu_pack(d1[2 * kb + 1][0], d1[2 * kb + 1][1]);
-      a2[kb][3] = relu_pack(d1[2 * kb + 1][2], d1[2 * kb + 1][3]);
-    }
-    // layer 2: [16 x 32] x [32 x 32]
-    float d2[4][4];
-#pragma unroll
-    for (int nb = 0; nb < 4; ++nb) {
-      const float c[4] = {W.b2[2 * nb], W.b2[2 * nb + 1], W.b2[2 * nb], W.b2[2 * nb + 1]};
-      mma_k16(d2[nb], a2[0], W.w2[(0 * 4 + nb) * 2], W.w2[(0 * 4 + nb) * 2 + 1], c);
-      mma_k16(d2[nb], a2[1], W.w2[(1 * 4 + nb) * 2], W.w2[(1 * 4 + nb) * 2 + 1], d2[nb]);
-    }
-    uint32_t a3[2][4];
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-      a3[kb][0] = relu_pack(d2[2 * kb][0], d2[2 * kb][1]);
-      a3[kb][1] = relu_pack(d2[2 * kb][2], d2[2 * kb][3]);
-      a3[kb][2] = relu_pack(d2[2 * kb + 1][0], d2[2 * kb + 1][1]);
-      a3[kb][3] = relu_pack(d2[2 * kb + 1][2], d2[2 * kb + 1][3]);
-    }
-    // layer 3: [16 x 32] x [32 x 8] (columns 0, 1 used)
-    const float c3[4] = {W.b3[0], W.b3[1], W.b3[0], W.b3[1]};
-    mma_k16(out[mt], a3[0], W.w3[0], W.w3[1], c3);
-    mma_k16(out[mt], a3[1], W.w3[2], W.w3[3], out[mt]);
   }
   // outputs of rows g, g+8 of both tiles sit in lane 4g (columns 0, 1)
   const int src = 4 * g;
   const int mt = t >> 1, hi = t & 1;
-  float v[2][4];
 #pragma unroll
-  for (int m = 0; m < 2; ++m)
+  for (int jj = 0; jj < NJ; ++jj) {
+    float v[2][4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[m][e] = __shfl_sync(0xffffffffu, out[m][e], src);
-  y0 = mt == 0 ? (hi ? v[0][2] : v[0][0]) : (hi ? v[1][2] : v[1][0]);
-  y1 = mt == 0 ? (hi ? v[0][3] : v[0][1]) : (hi ? v[1][3] : v[1][1]);
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[m][e] = __shfl_sync(0xffffffffu, out[jj][m][e], src);
+    y[jj][0] = mt == 0 ? (hi ? v[0][2] : v[0][0]) : (hi ? v[1][2] : v[1][0]);
+    y[jj][1] = mt == 0 ? (hi ? v[0][3] : v[0][1]) : (hi ? v[1][3] : v[1][1]);
+  }
 }
 
 // FP32 base of one side of the tail (cells [lo, hi]): SR and SZ parts and the
@@ -141,21 +175,30 @@ __device__ __forceinline__ void side_base_fp32(float R2, float lo, float hi, flo
   il_out = il;
 }
 
-// Pair image sums with the surrogate tail (units of L). kw: warp-uniform
-// spline bound as in pair_fp32.cuh.
-__device__ __forceinline__ void pair_images_surr(float dR2, float dz, float hh, int n_cut, int kw,
-                                                 const SurrLane& W, const SurrConst& S, float& sr, float& sz) {
+// Per-pair state of the surrogate evaluation between its stages.
+struct SurrPair {
+  float sr, sz;          // near-image sums so far
+  float br, bz, er, ez;  // tail base and envelope
+  float sg;              // sign(dz)
+  float u[3];            // network inputs
+  float ih, ih3;         // 1/h, 1/h^3 (when some lane is softened)
+};
+
+// Stage A: near images |k| <= n0 exactly (as in pair_fp32.cuh), the tail base,
+// the envelope and the network inputs. kw: warp-uniform spline bound.
+__device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int n_cut, int kw, const SurrConst& S,
+                                             SurrPair& P) {
   const u64 DR2 = pk(dR2, dR2);
   const u64 STEP = pk(1.0f, -1.0f);
   const int n0 = S.n0;
   u64 SR, SZ, O;
   int k = 1;
-  float ih = 0.f, ih3 = 0.f;
-  // near images: centre (k = 0, alone) and symmetric pairs k = 1 .. n0
+  P.ih = 0.f;
+  P.ih3 = 0.f;
   if (kw >= 0) {
-    ih = rcp_approx(hh);
-    ih3 = ih * ih * ih;
-    const u64 IH = pk(ih, ih), IH3 = pk(ih3, ih3);
+    P.ih = rcp_approx(hh);
+    P.ih3 = P.ih * P.ih * P.ih;
+    const u64 IH = pk(P.ih, P.ih), IH3 = pk(P.ih3, P.ih3);
     O = pk(dz, dz);
     const u64 F = mul2(spline_over_r2(O, DR2, IH, IH3), pk(1.0f, 0.0f));
     SR = F;
@@ -190,8 +233,8 @@ __device__ __forceinline__ void pair_images_surr(float dR2, float dz, float hh, 
   float s0, s1, z0, z1;
   upk(SR, s0, s1);
   upk(SZ, z0, z1);
-  sr = s0 + s1;
-  sz = z0 + z1;
+  P.sr = s0 + s1;
+  P.sz = z0 + z1;
   // tail base and envelope (|dz|; z part gets sign(dz))
   const float adz = fabsf(dz), A = (float)n0 + 0.5f;
   const float kneg = adz > 0.0f ? (float)n_cut : (float)(n_cut - 1);
@@ -199,23 +242,31 @@ __device__ __forceinline__ void pair_images_surr(float dR2, float dz, float hh, 
   side_base_fp32(dR2, A + adz, (float)(n_cut - 1) + 0.5f + adz, br1, bz1, il1);
   side_base_fp32(dR2, A - adz, kneg + 0.5f - adz, br2, bz2, il2);
   const float e = il1 * il1;
-  const float ER = e * e * e, EZ = e * e * il1;
+  P.er = e * e * e;
+  P.ez = e * e * il1;
+  P.br = br1 + br2;
+  P.bz = bz1 - bz2;
+  P.sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
   const float dR = dR2 * rsq(fmaxf(dR2, 1e-30f));
-  const float u0 = 2.0f * fminf(dR, S.dR_max) * S.inv_dR_max - 1.0f;
-  const float u1 = 4.0f * adz - 1.0f;
-  const float u2 = 2.0f * fminf(hh, A) / A - 1.0f;
-  float y0, y1;
-  mlp_warp(W, u0, u1, u2, y0, y1);
-  const float sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
-  sr += (br1 + br2) + ER * fmaf(y0, S.sc0, S.mu0);
-  sz += sg * ((bz1 - bz2) + EZ * fmaf(y1, S.sc1, S.mu1));
-  // tail images inside some lane's softening support: spline minus the
-  // Newtonian value the surrogate assumed
+  P.u[0] = 2.0f * fminf(dR, S.dR_max) * S.inv_dR_max - 1.0f;
+  P.u[1] = 4.0f * adz - 1.0f;
+  P.u[2] = 2.0f * fminf(hh, A) / A - 1.0f;
+}
+
+// Stage C: tail = base + envelope x network output, plus the exact spline
+// correction of tail images inside some lane's softening support.
+__device__ __forceinline__ void surr_stage_c(float dR2, float dz, int n_cut, int kw, const SurrConst& S,
+                                             const SurrPair& P, float y0, float y1, float& sr, float& sz) {
+  const int n0 = S.n0;
+  sr = P.sr + P.br + P.er * fmaf(y0, S.sc0, S.mu0);
+  sz = P.sz + P.sg * (P.bz + P.ez * fmaf(y1, S.sc1, S.mu1));
   if (kw > n0) {
-    const u64 IH = pk(ih, ih), IH3 = pk(ih3, ih3);
+    const u64 DR2 = pk(dR2, dR2);
+    const u64 STEP = pk(1.0f, -1.0f);
+    const u64 IH = pk(P.ih, P.ih), IH3 = pk(P.ih3, P.ih3);
     const int kt = min(kw, n_cut - 1);
     u64 CR = pk(0.f, 0.f), CZ = pk(0.f, 0.f);
-    O = pk(dz + (float)n0, dz - (float)n0);
+    u64 O = pk(dz + (float)n0, dz - (float)n0);
     for (int kk = n0 + 1; kk <= kt; ++kk) {
       O = add2(O, STEP);
       const u64 R2 = fma2(O, O, DR2);
@@ -246,35 +297,66 @@ __device__ __forceinline__ void pair_images_surr(float dR2, float dz, float hh, 
   }
 }
 
+// Geometry of the pair (i, j) shared by both forms.
+__device__ __forceinline__ void pair_geometry(const IParticle& I, const float4& A, const float4& B, float& dx, float& dy,
+                                              float& dz, float& dR2, float& hh, int& kw) {
+  dx = (I.xh - A.x) + (I.xl - B.x);
+  dy = (I.yh - A.y) + (I.yl - B.y);
+  dz = I.zh - A.z;
+  dz = (dz - rintf(dz)) + (I.zl - B.z);
+  dR2 = fmaf(dx, dx, dy * dy);
+  hh = I.h + B.w;
+  const int kl = dR2 < hh * hh ? (int)(hh + 0.5f) : -1;
+  kw = __reduce_max_sync(0xffffffffu, kl);
+}
+
 // One j-tile of pairs for one i (shared by the stream-K and the subset kernels).
+// The surrogate form handles two j per network call.
 template <bool KAHAN, bool SURR>
 __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, const float4* sB, int jn, int self,
-                                          int n_cut, float fnc, const SurrLane& W, const SurrConst& S, float& sx,
+                                          int n_cut, float fnc, const SurrW& W, const SurrConst& S, float& sx,
                                           float& sy, float& sz, float& cx, float& cy, float& cz) {
+  constexpr int STEPJ = SURR ? 2 : 1;
   for (int k0 = 0; k0 < jn; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
     const int ke = min(k0 + STEPS_KAHAN_GROUP, jn);
-    for (int k = k0; k < ke; ++k) {
-      const float4 A = sA[k];
-      const float4 B = sB[k];
-      const float dx = (I.xh - A.x) + (I.xl - B.x);
-      const float dy = (I.yh - A.y) + (I.yl - B.y);
-      float dz = I.zh - A.z;
-      dz = (dz - rintf(dz)) + (I.zl - B.z);
-      const float dR2 = fmaf(dx, dx, dy * dy);
-      const float hh = I.h + B.w;
-      const int kl = dR2 < hh * hh ? (int)(hh + 0.5f) : -1;
-      const int kw = __reduce_max_sync(0xffffffffu, kl);
-      float sr, szz;
-      if (SURR)
-        pair_images_surr(dR2, dz, hh, n_cut, kw, W, S, sr, szz);
-      else
-        pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
-      const float mj = (k == self) ? 0.0f : A.w;
-      const float msr = mj * sr;
-      gx = fmaf(dx, msr, gx);
-      gy = fmaf(dy, msr, gy);
-      gz = fmaf(mj, szz, gz);
+    for (int k = k0; k < ke; k += STEPJ) {
+      float dx[STEPJ], dy[STEPJ], dz[STEPJ], dR2[STEPJ], hh[STEPJ], mj[STEPJ], sr[STEPJ], szz[STEPJ];
+      int kw[STEPJ];
+#pragma unroll
+      for (int jj = 0; jj < STEPJ; ++jj) {
+        // a second j past the tile end repeats the first with zero mass
+        const int kk = min(k + jj, ke - 1);
+        const float4 A = sA[kk];
+        const float4 B = sB[kk];
+        pair_geometry(I, A, B, dx[jj], dy[jj], dz[jj], dR2[jj], hh[jj], kw[jj]);
+        mj[jj] = (kk == self || k + jj >= ke) ? 0.0f : A.w;
+      }
+      if (SURR) {
+        SurrPair P[STEPJ];
+        float u[STEPJ][3], y[STEPJ][2];
+#pragma unroll
+        for (int jj = 0; jj < STEPJ; ++jj) {
+          surr_stage_a(dR2[jj], dz[jj], hh[jj], n_cut, kw[jj], S, P[jj]);
+          u[jj][0] = P[jj].u[0];
+          u[jj][1] = P[jj].u[1];
+          u[jj][2] = P[jj].u[2];
+        }
+        mlp_warp<STEPJ>(W, u, y);
+#pragma unroll
+        for (int jj = 0; jj < STEPJ; ++jj)
+          surr_stage_c(dR2[jj], dz[jj], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr[jj], szz[jj]);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < STEPJ; ++jj) pair_images_fp32(dR2[jj], dz[jj], hh[jj], n_cut, fnc, kw[jj], sr[jj], szz[jj]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < STEPJ; ++jj) {
+        const float msr = mj[jj] * sr[jj];
+        gx = fmaf(dx[jj], msr, gx);
+        gy = fmaf(dy[jj], msr, gy);
+        gz = fmaf(mj[jj], szz[jj], gz);
+      }
     }
     acc<KAHAN>(sx, cx, gx);
     acc<KAHAN>(sy, cy, gy);
@@ -284,13 +366,21 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
 
 // Stream-K kernel with the surrogate tail (same work split and partial layout
 // as pair_fp32_kernel).
+#ifndef STEPS_SURR_MIN_BLOCKS
+#define STEPS_SURR_MIN_BLOCKS 4  // co-resident CTAs per SM asked of the register allocator
+#endif
+
 template <bool KAHAN>
-__global__ void __launch_bounds__(kBI, 3)
+__global__ void __launch_bounds__(kBI, STEPS_SURR_MIN_BLOCKS)
 pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
                       int NT, int C, const SurrLane* __restrict__ wl, SurrConst S, double* __restrict__ part) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
-  const SurrLane W = wl[threadIdx.x & 31];
+  // weight fragments stay in shared memory (word-major, conflict-free) and are
+  // read where the mma needs them, which leaves registers for resident warps
+  __shared__ uint32_t sWT[32 * kSurrWords];
+  stage_surr_weights(wl, sWT);
+  const SurrW W{sWT + (threadIdx.x & 31)};
   const int c = blockIdx.x;
   const long long u0 = (long long)c * U / C;
   const long long u1 = (long long)(c + 1) * U / C;
@@ -337,8 +427,9 @@ pair_fp32_subset_kernel(const float4* __restrict__ jA, const float4* __restrict_
                         double* __restrict__ part) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
-  SurrLane W;
-  if (SURR) W = wl[threadIdx.x & 31];
+  __shared__ uint32_t sWT[32 * kSurrWords];
+  if (SURR) stage_surr_weights(wl, sWT);
+  const SurrW W{sWT + (threadIdx.x & 31)};
   const int q = blockIdx.x * kBI + threadIdx.x;
   const int i = (int)idx[min(q, ni - 1)];
   IParticle I;
@@ -367,22 +458,6 @@ pair_fp32_subset_kernel(const float4* __restrict__ jA, const float4* __restrict_
     dst[ni + q] = (double)sy - (KAHAN ? (double)cy : 0.0);
     dst[2 * ni + q] = (double)sz - (KAHAN ? (double)cz : 0.0);
   }
-}
-
-// Sum the subset partials over j-chunks in order: out[3][ni] (raw pair sums).
-static __global__ void subset_sum_kernel(const double* __restrict__ part, int ni, int chunks, double* __restrict__ out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ni) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int c = 0; c < chunks; ++c) {
-    const double* p = part + (long long)c * 3 * ni;
-    s0 += p[q];
-    s1 += p[ni + q];
-    s2 += p[2 * ni + q];
-  }
-  out[q] = s0;
-  out[ni + q] = s1;
-  out[2 * ni + q] = s2;
 }
 
 }  // namespace steps

@@ -78,6 +78,9 @@ WORKLOADS = {
                                   filament_frac=0.2, a_start=0.02, a_end=0.02),
     "surrogate_n1048576": Workload("surrogate_n1048576", 1048576, 3, 64, comoving=True, displaced=True,
                                    a_start=0.02, a_end=0.02),
+    # the surrogate workload's law at a size that profiles quickly
+    "surrogate_n65536": Workload("surrogate_n65536", 65536, 3, 64, comoving=True, displaced=True,
+                                 a_start=0.02, a_end=0.02),
     "production_n524288": Workload("production_n524288", 524288, 4, 64, comoving=True, displaced=True,
                                    eps_law="ratio8", a_start=0.02, a_end=1.0, nsteps=1000),
 }

@@ -259,9 +259,8 @@ def run(args):
     t_local = sum(step_ms) / 1e3
     t_max = t_local
     if dist is not None:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+        from paper_2602_20787_gb300 import shard
+        t_max = shard.max_over_ranks(t_local, device=dev)
     images_per_step = n * (n - 1) * 2.0 * w.n_cut
     value = images_per_step * args.steps * world / t_max
 
@@ -288,9 +287,8 @@ def run(args):
         torch.cuda.synchronize(dev)
         te = time.perf_counter() - te0
         if dist is not None:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+            from paper_2602_20787_gb300 import shard
+            te = shard.max_over_ranks(te, device=dev)
         e2e = {"value": images_per_step * args.e2e_steps * world / te, "unit": UNIT,
                "h2d_bytes_per_step": 6 * 8 * n, "d2h_bytes_per_step": 6 * 8 * n, "steps": args.e2e_steps}
 

@@ -258,6 +258,17 @@ int steps_cyl_pair_accel_noalloc(int64_t n, const double* x, const double* y, co
                                  int32_t n_cut, int32_t precision, double* ax, double* ay,
                                  double* az, void* stream);
 
+/* Write the complete state of a context to a file: parameters, a and t, the
+ * background table, positions, momenta, masses, softenings and the cached forces
+ * in the library's internal particle order with its permutation, the re-order
+ * and check counters and any accepted surrogate. Synchronises the stream. */
+int steps_cyl_checkpoint(steps_cyl_ctx* ctx, const char* path);
+
+/* Create a context from a checkpoint file on the given device and stream. The
+ * resumed context continues bit-identically to the one that wrote the file.
+ * STEPS_EINVAL for a missing, foreign or truncated file. */
+int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void* stream);
+
 /* Release the context and its device memory. NULL is accepted. */
 int steps_cyl_free(steps_cyl_ctx* ctx);
 

@@ -1043,6 +1043,51 @@ int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* re
   return STEPS_OK;
 }
 
+// Device buffers and the work split of a context whose n, device and stream
+// are set (init and resume).
+int allocate_context(steps_cyl_ctx* c) {
+#define CKA(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEPS_ENOMEM : STEPS_ECUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                   \
+  } while (0)
+  const size_t nb = (size_t)c->n;
+  CKA(cudaEventCreate(&c->e0));
+  CKA(cudaEventCreate(&c->e1));
+  CKA(cudaMalloc(&c->state, sizeof(double) * nb * 11));
+  double* s = c->state;
+  c->x = s; c->y = s + nb; c->z = s + 2 * nb; c->px = s + 3 * nb; c->py = s + 4 * nb; c->pz = s + 5 * nb;
+  c->m = s + 6 * nb; c->h = s + 7 * nb; c->gx = s + 8 * nb; c->gy = s + 9 * nb; c->gz = s + 10 * nb;
+  CKA(cudaMalloc(&c->jA, sizeof(float4) * nb));
+  CKA(cudaMalloc(&c->jB, sizeof(float4) * nb));
+  CKA(cudaMalloc(&c->stage, sizeof(double) * nb * 3));
+  CKA(cudaMalloc(&c->red, sizeof(double) * (kRedBlocks * 6 + 8)));
+  CKA(cudaMalloc(&c->perm, sizeof(int) * nb));
+  CKA(cudaMalloc(&c->iperm, sizeof(int) * nb));
+  CKA(cudaMalloc(&c->ord, sizeof(int) * nb));
+  CKA(cudaMalloc(&c->err, sizeof(int)));
+  CKA(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+
+  // stream-K split of the FP32 pair kernel: C CTAs share U units
+  int sms = 0, occ = 0;
+  CKA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_fp32_kernel<true>, kBI, 0));
+  c->NB = (c->n + kBI - 1) / kBI;
+  c->NT = (c->n + kBJ - 1) / kBJ;
+  c->U = (long long)c->NB * c->NT;
+  c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1) * STEPS_CTA_MULT);
+  int socc = 0;
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, pair_fp32_surr_kernel<true>, kBI, 0));
+  c->SC = (int)std::min<long long>(c->U, (long long)sms * std::max(socc, 1) * STEPS_CTA_MULT);
+  c->part_elems = std::max((size_t)(c->NB + std::max(c->C, c->SC)) * 3 * kBI, nb * 3);
+  CKA(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
+
+#undef CKA
+  return STEPS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1118,35 +1163,7 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
     }                                                                                        \
   } while (0)
   const size_t nb = (size_t)n;
-  CKI(cudaEventCreate(&c->e0));
-  CKI(cudaEventCreate(&c->e1));
-  CKI(cudaMalloc(&c->state, sizeof(double) * nb * 11));
-  double* s = c->state;
-  c->x = s; c->y = s + nb; c->z = s + 2 * nb; c->px = s + 3 * nb; c->py = s + 4 * nb; c->pz = s + 5 * nb;
-  c->m = s + 6 * nb; c->h = s + 7 * nb; c->gx = s + 8 * nb; c->gy = s + 9 * nb; c->gz = s + 10 * nb;
-  CKI(cudaMalloc(&c->jA, sizeof(float4) * nb));
-  CKI(cudaMalloc(&c->jB, sizeof(float4) * nb));
-  CKI(cudaMalloc(&c->stage, sizeof(double) * nb * 3));
-  CKI(cudaMalloc(&c->red, sizeof(double) * (kRedBlocks * 6 + 8)));
-  CKI(cudaMalloc(&c->perm, sizeof(int) * nb));
-  CKI(cudaMalloc(&c->iperm, sizeof(int) * nb));
-  CKI(cudaMalloc(&c->ord, sizeof(int) * nb));
-  CKI(cudaMalloc(&c->err, sizeof(int)));
-  CKI(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
-
-  // stream-K split of the FP32 pair kernel: C CTAs share U units
-  int sms = 0, occ = 0;
-  CKI(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-  CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_fp32_kernel<true>, kBI, 0));
-  c->NB = (c->n + kBI - 1) / kBI;
-  c->NT = (c->n + kBJ - 1) / kBJ;
-  c->U = (long long)c->NB * c->NT;
-  c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1) * STEPS_CTA_MULT);
-  int socc = 0;
-  CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, pair_fp32_surr_kernel<true>, kBI, 0));
-  c->SC = (int)std::min<long long>(c->U, (long long)sms * std::max(socc, 1) * STEPS_CTA_MULT);
-  c->part_elems = std::max((size_t)(c->NB + std::max(c->C, c->SC)) * 3 * kBI, nb * 3);
-  CKI(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
+  if ((rc = allocate_context(c))) return bail(rc);
 
   // caller order -> internal (Morton) order
   if ((rc = stage_positions(c, x, y, z))) return bail(rc);
@@ -1413,6 +1430,136 @@ const char* steps_cyl_strerror(int code) {
 }
 
 const char* steps_cyl_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Checkpoint file: a fixed header, the background table and the per-particle
+// arrays in the context's internal order with the permutation, so that a
+// resumed context continues bit-identically.
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  steps_cyl_params p;
+  int64_t n;
+  double a, t, rho0, bg_dr, bound_med, bound_p999;
+  int32_t steps_since_order, steps_since_check, surr_ok, bgK;
+  float surr[STEPS_SURR_NPARAM];
+};
+constexpr uint32_t kCkptVersion = 1;
+
+int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
+  g_last_error.clear();
+  if (!c || !path) return fail(STEPS_EINVAL, "NULL argument");
+  DeviceGuard guard(c->dev);
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, "STEPSCYL", 8);
+  hd.version = kCkptVersion;
+  hd.header_bytes = sizeof hd;
+  hd.p = c->p;
+  hd.p.stream = nullptr;
+  hd.n = c->n;
+  hd.a = c->a;
+  hd.t = c->t;
+  hd.rho0 = c->rho0;
+  hd.bg_dr = c->bg_dr;
+  hd.bound_med = c->surr_bound_med;
+  hd.bound_p999 = c->surr_bound_p999;
+  hd.steps_since_order = c->steps_since_order;
+  hd.steps_since_check = c->steps_since_check;
+  hd.surr_ok = c->surr_ok ? 1 : 0;
+  hd.bgK = c->bgtab ? c->bgK : 0;
+  if (c->surr_ok) std::memcpy(hd.surr, c->surr_params.data(), sizeof hd.surr);
+  if (c->forces_stale) {
+    int rc = eval_forces(c, false, 0.0);
+    if (rc) return rc;
+  }
+  std::vector<double> arr((size_t)c->n * 11);
+  std::vector<double> tab(hd.bgK ? hd.bgK + 4 : 0);
+  CK(cudaMemcpyAsync(arr.data(), c->state, sizeof(double) * arr.size(), cudaMemcpyDeviceToHost, c->st));
+  if (hd.bgK) CK(cudaMemcpyAsync(tab.data(), c->bgtab, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(STEPS_EINVAL, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+  if (ok && hd.bgK) ok = std::fwrite(tab.data(), sizeof(double), tab.size(), f) == tab.size();
+  if (ok) ok = std::fwrite(arr.data(), sizeof(double), arr.size(), f) == arr.size();
+  if (ok) ok = std::fwrite(c->perm_h.data(), sizeof(int), c->n, f) == (size_t)c->n;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(STEPS_EINVAL, "write to %s failed", path);
+  return STEPS_OK;
+}
+
+int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void* stream) {
+  g_last_error.clear();
+  if (!out || !path) return fail(STEPS_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(STEPS_EINVAL, "cannot open %s", path);
+  CkptHeader hd;
+  if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "STEPSCYL", 8) != 0 ||
+      hd.version != kCkptVersion || hd.header_bytes != sizeof hd || hd.n < 2 || hd.n > 0x7fffffffLL - kBI ||
+      hd.bgK < 0 || hd.bgK > (1 << 20)) {
+    std::fclose(f);
+    return fail(STEPS_EINVAL, "%s is not a checkpoint of this library version", path);
+  }
+  std::vector<double> tab(hd.bgK ? hd.bgK + 4 : 0), arr((size_t)hd.n * 11);
+  std::vector<int> perm(hd.n);
+  bool ok = !hd.bgK || std::fread(tab.data(), sizeof(double), tab.size(), f) == tab.size();
+  ok = ok && std::fread(arr.data(), sizeof(double), arr.size(), f) == arr.size();
+  ok = ok && std::fread(perm.data(), sizeof(int), perm.size(), f) == perm.size();
+  std::fclose(f);
+  if (!ok) return fail(STEPS_EINVAL, "%s is truncated", path);
+  hd.p.stream = stream;
+  hd.p.device = device;
+  int rc = check_params(&hd.p);
+  if (rc) return rc;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(STEPS_EINVAL, "device %d out of range", device);
+  DeviceGuard guard(device);
+  steps_cyl_ctx* c = new steps_cyl_ctx();
+  c->p = hd.p;
+  c->n = (int)hd.n;
+  c->dev = device;
+  c->st = (cudaStream_t)stream;
+  c->cosmo = Cosmology{hd.p.H0, hd.p.Omega_m, hd.p.Omega_r, hd.p.Omega_L, hd.p.w0, hd.p.wa, hd.p.comoving != 0};
+  c->a = hd.a;
+  c->t = hd.t;
+  c->rho0 = hd.rho0;
+  c->invL = 1.0 / hd.p.L;
+  c->steps_since_order = hd.steps_since_order;
+  c->steps_since_check = hd.steps_since_check;
+  c->surr_bound_med = hd.bound_med;
+  c->surr_bound_p999 = hd.bound_p999;
+  c->perm_h = perm;
+  auto bail = [&](int code) {
+    release(c);
+    return code;
+  };
+  if ((rc = allocate_context(c))) return bail(rc);
+  if (cudaMemcpyAsync(c->state, arr.data(), sizeof(double) * arr.size(), cudaMemcpyHostToDevice, c->st) !=
+      cudaSuccess)
+    return bail(fail(STEPS_ECUDA, "upload failed"));
+  if (hd.bgK) {
+    c->bgK = hd.bgK;
+    c->bg_dr = hd.bg_dr;
+    if (cudaMalloc(&c->bgtab, sizeof(double) * tab.size()) != cudaSuccess ||
+        cudaMemcpyAsync(c->bgtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess)
+      return bail(fail(STEPS_ECUDA, "background table upload failed"));
+  }
+  if ((rc = upload_perm(c))) return bail(rc);
+  if ((rc = validate_state(c))) return bail(rc);
+  if ((rc = pack_positions(c))) return bail(rc);
+  if (hd.surr_ok) {
+    if ((rc = install_surrogate(c, hd.surr))) return bail(rc);
+    c->surr_ok = true;
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(fail(STEPS_ECUDA, "synchronise failed"));
+  *out = c;
+  return STEPS_OK;
+}
 
 int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg) {
   if (!cfg) return fail(STEPS_EINVAL, "cfg is NULL");

@@ -36,7 +36,7 @@ _EXPORTS = [
     "steps_cyl_diagnostics", "steps_cyl_last_timing", "steps_cyl_free", "steps_cyl_strerror",
     "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc", "steps_cyl_train_cfg_default", "steps_cyl_tail_sums",
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
-    "steps_cyl_set_tail", "steps_cyl_check_surrogate",
+    "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
 ]
 
 STEPS_SURR_NW = 1250
@@ -118,6 +118,8 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_get_surrogate.argtypes = [p, p]
     L.steps_cyl_set_tail.argtypes = [p, i32]
     L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
+    L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
+    L.steps_cyl_resume.argtypes = [ctypes.POINTER(p), ctypes.c_char_p, i32, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -345,6 +347,24 @@ def steps_cyl_check_surrogate(ctx, check_particles: int = 1024) -> np.ndarray:
     return rep
 
 
+def steps_cyl_checkpoint(ctx, path: str):
+    _check(load().steps_cyl_checkpoint(ctx, os.fsencode(path)))
+
+
+def _ckpt_n(path: str) -> int:
+    """Particle count stored in a checkpoint header (after magic, version, size, params)."""
+    off = 8 + 4 + 4 + ctypes.sizeof(Params)
+    with open(path, "rb") as fh:
+        fh.seek(off)
+        return int(np.frombuffer(fh.read(8), dtype=np.int64)[0])
+
+
+def steps_cyl_resume(path: str, device: int = 0, stream: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(load().steps_cyl_resume(ctypes.byref(ctx), os.fsencode(path), int(device), ctypes.c_void_p(stream or None)))
+    return ctx
+
+
 class Simulation:
     """Convenience owner of one context (numpy/torch arrays in, numpy out)."""
 
@@ -384,6 +404,18 @@ class Simulation:
 
     def last_timing(self):
         return steps_cyl_last_timing(self.ctx)
+
+    def checkpoint(self, path: str):
+        steps_cyl_checkpoint(self.ctx, path)
+
+    @classmethod
+    def resume(cls, path: str, device: int = 0, stream: int = 0):
+        """A Simulation continuing from a checkpoint file."""
+        sim = cls.__new__(cls)
+        sim.n = _ckpt_n(path)
+        sim.cfg = None
+        sim.ctx = steps_cyl_resume(path, device, stream)
+        return sim
 
     def close(self):
         if self.ctx:

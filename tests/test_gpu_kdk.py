@@ -136,3 +136,30 @@ def test_set_state_moves_masses_with_the_new_order(sc):
     r = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert r.max() < 1e-10
     sim.close()
+
+
+def test_checkpoint_resume_is_bit_identical(sc, tmp_path):
+    # re-ordering every 3 steps and a comoving background: the checkpoint must
+    # carry the internal order, the counters, the table and the cached forces
+    w = ics.WORKLOADS["lcdm_n65536"]
+    d = ics.particle_load(1500, 17, w.M_tot, displaced=True, rho_bar=w.rho_bar)
+    t0, dt = ics.run_schedule(w)
+    cfg = sc.Config(n_cut=8, precision=1, comoving=True, a_start=0.02, t_start=t0, rho_bar=w.rho_bar, reorder_every=3)
+    s1 = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    s1.step(dt, 5)
+    path = str(tmp_path / "state.ckpt")
+    s1.checkpoint(path)
+    s1.step(dt, 4)
+    x1, v1, a1, t1 = s1.state()
+    s2 = sc.Simulation.resume(path)
+    s2.step(dt, 4)
+    x2, v2, a2, t2 = s2.state()
+    np.testing.assert_array_equal(x2, x1)
+    np.testing.assert_array_equal(v2, v1)
+    assert (a2, t2) == (a1, t1)
+    with open(path, "r+b") as fh:
+        fh.write(b"NOTSTEPS")
+    with pytest.raises(sc.StepsError):
+        sc.Simulation.resume(path)
+    s1.close()
+    s2.close()

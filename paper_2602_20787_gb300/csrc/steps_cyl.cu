@@ -713,13 +713,15 @@ void build_lanes(const float* P, SurrLane lanes[32]) {
         s.w2[(kb * 4 + nb) * 2 + 1] = pack_half2(W2[o * kH + k + 8], W2[o * kH + k + 9]);
       }
     }
+    // output column n carries output (n & 1): every lane of a quad then holds
+    // both outputs of the quad's rows, and no lane has to gather them
     for (int kb = 0; kb < 2; ++kb) {
-      const int k = 16 * kb + 2 * t;
-      s.w3[kb * 2] = g < 2 ? pack_half2(W3[g * kH + k], W3[g * kH + k + 1]) : 0u;
-      s.w3[kb * 2 + 1] = g < 2 ? pack_half2(W3[g * kH + k + 8], W3[g * kH + k + 9]) : 0u;
+      const int k = 16 * kb + 2 * t, o = g & 1;
+      s.w3[kb * 2] = pack_half2(W3[o * kH + k], W3[o * kH + k + 1]);
+      s.w3[kb * 2 + 1] = pack_half2(W3[o * kH + k + 8], W3[o * kH + k + 9]);
     }
-    s.b3[0] = t == 0 ? b3[0] : 0.f;
-    s.b3[1] = t == 0 ? b3[1] : 0.f;
+    s.b3[0] = b3[0];
+    s.b3[1] = b3[1];
   }
 }
 

@@ -10,10 +10,11 @@
 // tiles, rows assigned so that the quad of lanes 4g..4g+3 owns rows g and g+8
 // of both tiles, i.e. its own four pairs. The accumulator fragment of one
 // layer is, after ReLU and packing to f16x2, the A fragment of the next, so
-// activations never leave registers; only the three inputs are exchanged
-// within a quad (shuffles) and the two outputs are read back from the quad's
-// first lane. Weights live in registers as B fragments, biases seed the
-// accumulators.
+// activations never leave registers. The three inputs reach the quad through
+// a small per-warp shared buffer, and the output layer's two columns are
+// repeated across all eight, so every lane already holds its own pair's
+// outputs. Weights are B fragments read from shared memory once per call per
+// layer; biases seed the accumulators.
 #pragma once
 #include <cstdint>
 
@@ -34,23 +35,32 @@ struct SurrLane {
 };
 static_assert(sizeof(SurrLane) == 48 * 4, "SurrLane layout");
 
-// Word w of lane L's SurrLane lives at wt[w * 32 + L] in shared memory
-// (word-major), so a warp reading one word touches 32 distinct banks.
+// Lane L's SurrLane lives at wt[L * kSurrStride ...] in shared memory: rows of
+// 52 words (48 + 4 pad), so the 16-byte loads of a quarter warp (8 lanes, row
+// offsets 20 L mod 32 banks) hit 32 distinct banks. Each layer's fragments are
+// read once per network call with 128-bit volatile shared loads: kept out of
+// the register file across the j loop, they leave room for resident warps.
 constexpr int kSurrWords = sizeof(SurrLane) / 4;
+constexpr int kSurrStride = kSurrWords + 4;
 struct SurrW {
-  const uint32_t* p;  // wt + lane
-  __device__ __forceinline__ uint32_t u(int w) const { return p[w * 32]; }
-  __device__ __forceinline__ float f(int w) const { return __uint_as_float(p[w * 32]); }
+  const uint32_t* p;  // wt + lane * kSurrStride (16-byte aligned)
+  __device__ __forceinline__ uint4 ld4(int w) const {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p + w)));
+    return v;
+  }
 };
 constexpr int kW1 = 0, kW2 = 4, kW3 = 20, kB1 = 24, kB2 = 32, kB3 = 40;
 
-// Stage the 32 lanes' fragments word-major into shared memory (all threads of
-// the block take part; ends with a barrier).
+// Stage the 32 lanes' fragments into shared memory (all threads of the block
+// take part; ends with a barrier).
 __device__ __forceinline__ void stage_surr_weights(const SurrLane* __restrict__ wl, uint32_t* wt) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(wl);
   for (int k = threadIdx.x; k < 32 * kSurrWords; k += blockDim.x) {
     const int lane = k / kSurrWords, w = k % kSurrWords;
-    wt[w * 32 + lane] = src[k];
+    wt[lane * kSurrStride + w] = src[k];
   }
   __syncthreads();
 }
@@ -83,170 +93,190 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   return r;
 }
 
+__device__ __forceinline__ float f32(uint32_t v) { return __uint_as_float(v); }
+
 // The MLP for NJ x 32 pairs of the warp (NJ values of j, one pair per lane
 // each); every lane passes its own pairs' inputs and receives their outputs.
-// The 2 NJ m-tiles are independent chains of mma, which the scheduler
-// interleaves. Must be called by all 32 lanes with uniform control flow.
+// Layer by layer over all 2 NJ m-tiles, so each layer's fragments are read from
+// shared memory once per call and the tiles' mma chains are independent work
+// for the scheduler. Must be called by all 32 lanes with uniform control flow.
+// Per-warp exchange buffer of the network inputs: [NJ][slot t][kInStride]
+// words; slot 0 holds the (u0, u1) f16x2 word of each lane, slot 1 the (u2, 0)
+// word, slots 2 and 3 stay zero (columns 4..7 of the A operand). Lane (g, t)
+// reads its A fragment, words 4g .. 4g+3 of slot t, with one 16-byte load; a
+// slot stride of 40 words keeps those loads and the stores free of bank
+// conflicts.
+constexpr int kInStride = 40;
+constexpr int kInWords = 4 * kInStride;
+
 template <int NJ>
-__device__ __forceinline__ void mlp_warp(const SurrW& W, const float (&u)[NJ][3], float (&y)[NJ][2]) {
+__device__ __forceinline__ void mlp_zero_inputs(uint32_t* buf) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) {
+    buf[jj * kInWords + 2 * kInStride + lane] = 0u;
+    buf[jj * kInWords + 3 * kInStride + lane] = 0u;
+  }
+}
+
+template <int NJ>
+__device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const float (&u)[NJ][3],
+                                         float (&y)[NJ][2]) {
+  constexpr int NT = 2 * NJ;  // m16 tiles: tile 2 jj + mt
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t in[NJ][4];
+  __syncwarp();  // the previous call's reads are done
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
-    const uint32_t p01 = pack_h2(u[jj][0], u[jj][1]), p2 = pack_h2(u[jj][2], 0.0f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t s01 = __shfl_sync(0xffffffffu, p01, 4 * g + q);
-      const uint32_t s2 = __shfl_sync(0xffffffffu, p2, 4 * g + q);
-      in[jj][q] = t == 0 ? s01 : (t == 1 ? s2 : 0u);
-    }
+    buf[jj * kInWords + lane] = pack_h2(u[jj][0], u[jj][1]);
+    buf[jj * kInWords + kInStride + lane] = pack_h2(u[jj][2], 0.0f);
   }
-  float out[NJ][2][4];
+  __syncwarp();
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + jj * kInWords + t * kInStride + 4 * g);
+    in[jj][0] = v.x;
+    in[jj][1] = v.y;
+    in[jj][2] = v.z;
+    in[jj][3] = v.w;
+  }
+  // layer 1: [16 pairs x 8 inputs] x [8 x 32] per tile
+  uint32_t a2[NT][2][4];
+  {
+    const uint4 w1 = W.ld4(kW1);
+    const uint4 ba = W.ld4(kB1), bb = W.ld4(kB1 + 4);
+    const uint32_t wv[4] = {w1.x, w1.y, w1.z, w1.w};
+    const float b[8] = {f32(ba.x), f32(ba.y), f32(ba.z), f32(ba.w), f32(bb.x), f32(bb.y), f32(bb.z), f32(bb.w)};
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      // layer 1: [16 pairs x 8 inputs] x [8 x 32]
+    for (int tl = 0; tl < NT; ++tl) {
       float d1[4][4];
 #pragma unroll
       for (int nb = 0; nb < 4; ++nb) {
-        const float b0 = W.f(kB1 + 2 * nb), b1v = W.f(kB1 + 2 * nb + 1);
-        const float c[4] = {b0, b1v, b0, b1v};
-        mma_k8(d1[nb], in[jj][2 * mt], in[jj][2 * mt + 1], W.u(kW1 + nb), c);
+        const float c[4] = {b[2 * nb], b[2 * nb + 1], b[2 * nb], b[2 * nb + 1]};
+        mma_k8(d1[nb], in[tl >> 1][2 * (tl & 1)], in[tl >> 1][2 * (tl & 1) + 1], wv[nb], c);
       }
-      uint32_t a2[2][4];
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
-        a2[kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
-        a2[kb][1] = relu_pack(d1[2 * kb][2], d1[2 * kb][3]);
-        a2[kb][2] = relu_pack(d1[2 * kb + 1][0], d1[2 * kb + 1][1]);
-        a2[kb][3] = relu_pack(d1[2 * kb + 1][2], d1[2 * kb + 1][3]);
+        a2[tl][kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
+        a2[tl][kb][1] = relu_pack(d1[2 * kb][2], d1[2 * kb][3]);
+        a2[tl][kb][2] = relu_pack(d1[2 * kb + 1][0], d1[2 * kb + 1][1]);
+        a2[tl][kb][3] = relu_pack(d1[2 * kb + 1][2], d1[2 * kb + 1][3]);
       }
-      // layer 2: [16 x 32] x [32 x 32]
+    }
+  }
+  // layer 2: [16 x 32] x [32 x 32] per tile; fragments [kb][nb][2]
+  uint32_t a3[NT][2][4];
+  {
+    uint32_t w2[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 v = W.ld4(kW2 + 4 * q);
+      w2[4 * q] = v.x; w2[4 * q + 1] = v.y; w2[4 * q + 2] = v.z; w2[4 * q + 3] = v.w;
+    }
+    const uint4 ba = W.ld4(kB2), bb = W.ld4(kB2 + 4);
+    const float b[8] = {f32(ba.x), f32(ba.y), f32(ba.z), f32(ba.w), f32(bb.x), f32(bb.y), f32(bb.z), f32(bb.w)};
+#pragma unroll
+    for (int tl = 0; tl < NT; ++tl) {
       float d2[4][4];
 #pragma unroll
       for (int nb = 0; nb < 4; ++nb) {
-        const float b0 = W.f(kB2 + 2 * nb), b1v = W.f(kB2 + 2 * nb + 1);
-        const float c[4] = {b0, b1v, b0, b1v};
-        mma_k16(d2[nb], a2[0], W.u(kW2 + nb * 2), W.u(kW2 + nb * 2 + 1), c);
-        mma_k16(d2[nb], a2[1], W.u(kW2 + (4 + nb) * 2), W.u(kW2 + (4 + nb) * 2 + 1), d2[nb]);
+        const float c[4] = {b[2 * nb], b[2 * nb + 1], b[2 * nb], b[2 * nb + 1]};
+        mma_k16(d2[nb], a2[tl][0], w2[2 * nb], w2[2 * nb + 1], c);
+        mma_k16(d2[nb], a2[tl][1], w2[2 * (4 + nb)], w2[2 * (4 + nb) + 1], d2[nb]);
       }
-      uint32_t a3[2][4];
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
-        a3[kb][0] = relu_pack(d2[2 * kb][0], d2[2 * kb][1]);
-        a3[kb][1] = relu_pack(d2[2 * kb][2], d2[2 * kb][3]);
-        a3[kb][2] = relu_pack(d2[2 * kb + 1][0], d2[2 * kb + 1][1]);
-        a3[kb][3] = relu_pack(d2[2 * kb + 1][2], d2[2 * kb + 1][3]);
+        a3[tl][kb][0] = relu_pack(d2[2 * kb][0], d2[2 * kb][1]);
+        a3[tl][kb][1] = relu_pack(d2[2 * kb][2], d2[2 * kb][3]);
+        a3[tl][kb][2] = relu_pack(d2[2 * kb + 1][0], d2[2 * kb + 1][1]);
+        a3[tl][kb][3] = relu_pack(d2[2 * kb + 1][2], d2[2 * kb + 1][3]);
       }
-      // layer 3: [16 x 32] x [32 x 8] (columns 0, 1 used)
-      const float c3[4] = {W.f(kB3), W.f(kB3 + 1), W.f(kB3), W.f(kB3 + 1)};
-      mma_k16(out[jj][mt], a3[0], W.u(kW3), W.u(kW3 + 1), c3);
-      mma_k16(out[jj][mt], a3[1], W.u(kW3 + 2), W.u(kW3 + 3), out[jj][mt]);
     }
   }
-  // outputs of rows g, g+8 of both tiles sit in lane 4g (columns 0, 1)
-  const int src = 4 * g;
+  // layer 3: [16 x 32] x [32 x 8] per tile (columns 0, 1 used)
+  float out[NT][4];
+  {
+    const uint4 w3 = W.ld4(kW3), b3 = W.ld4(kB3);
+    const float c3[4] = {f32(b3.x), f32(b3.y), f32(b3.x), f32(b3.y)};
+#pragma unroll
+    for (int tl = 0; tl < NT; ++tl) {
+      mma_k16(out[tl], a3[tl][0], w3.x, w3.y, c3);
+      mma_k16(out[tl], a3[tl][1], w3.z, w3.w, out[tl]);
+    }
+  }
+  // output column n carries output (n & 1), so lane (g, t) holds both outputs
+  // of rows g and g+8 of every tile; its own pair is row g + 8 (t & 1) of tile
+  // t >> 1
   const int mt = t >> 1, hi = t & 1;
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
-    float v[2][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[m][e] = __shfl_sync(0xffffffffu, out[jj][m][e], src);
-    y[jj][0] = mt == 0 ? (hi ? v[0][2] : v[0][0]) : (hi ? v[1][2] : v[1][0]);
-    y[jj][1] = mt == 0 ? (hi ? v[0][3] : v[0][1]) : (hi ? v[1][3] : v[1][1]);
+    const float(&o0)[4] = out[2 * jj];
+    const float(&o1)[4] = out[2 * jj + 1];
+    y[jj][0] = mt == 0 ? (hi ? o0[2] : o0[0]) : (hi ? o1[2] : o1[0]);
+    y[jj][1] = mt == 0 ? (hi ? o0[3] : o0[1]) : (hi ? o1[3] : o1[1]);
   }
 }
 
-// FP32 base of one side of the tail (cells [lo, hi]): SR and SZ parts and the
-// near-end reciprocal distance.
-__device__ __forceinline__ void side_base_fp32(float R2, float lo, float hi, float& sr, float& sz, float& il_out) {
-  const float il = rsq(fmaf(lo, lo, R2)), ih = rsq(fmaf(hi, hi, R2));
-  const float il2 = il * il, ih2 = ih * ih;
-  const float IR = (hi - lo) * (hi + lo) * il2 * ih2 * rcp_approx(fmaf(hi, ih, lo * il));
-  const float IZ = il - ih;
-  const float il5 = il2 * il2 * il, ih5 = ih2 * ih2 * ih;
-  const float dRl = -3.0f * lo * il5, dRh = -3.0f * hi * ih5;
-  const float dZl = il2 * il - 3.0f * lo * lo * il5, dZh = ih2 * ih - 3.0f * hi * hi * ih5;
-  sr = IR - (dRh - dRl) * (1.0f / 24.0f);
-  sz = IZ - (dZh - dZl) * (1.0f / 24.0f);
-  il_out = il;
+// FP32 base of both sides of the tail at once (packed: lane 0 the side beyond
+// +n0, lane 1 the side beyond -n0), each over the cells [lo, hi]: the SR and SZ
+// parts and the near-end reciprocal distance il. Per side, with
+// i(x) = (x^2 + dR^2)^(-1/2): the integrals (hi^2 - lo^2) il^2 ih^2 / (hi ih + lo il)
+// (of i^3, written without cancellation) and il - ih (of x i^3), minus 1/24 of
+// the end-point derivative differences, d/dx i^3 = -3 x i^5 and
+// d/dx (x i^3) = i^3 - 3 x^2 i^5.
+__device__ __forceinline__ void side_base_x2(float R2, u64 LO, u64 HI, u64& SR, u64& SZ, u64& IL) {
+  const u64 R2x = pk(R2, R2);
+  float a, b, c, d;
+  upk(fma2(LO, LO, R2x), a, b);
+  upk(fma2(HI, HI, R2x), c, d);
+  IL = pk(rsq(a), rsq(b));
+  const u64 IH = pk(rsq(c), rsq(d));
+  const u64 IL2 = mul2(IL, IL), IH2 = mul2(IH, IH);
+  float e, f;
+  upk(fma2(HI, IH, mul2(LO, IL)), e, f);
+  const u64 IR = mul2(mul2(mul2(sub2(HI, LO), add2(HI, LO)), mul2(IL2, IH2)), pk(rcp_approx(e), rcp_approx(f)));
+  const u64 P = mul2(LO, mul2(mul2(IL2, IL2), IL));  // lo il^5
+  const u64 Q = mul2(HI, mul2(mul2(IH2, IH2), IH));  // hi ih^5
+  SR = fma2(sub2(Q, P), pk(0.125f, 0.125f), IR);
+  const u64 D3 = sub2(mul2(IH2, IH), mul2(IL2, IL));
+  const u64 E = sub2(mul2(HI, Q), mul2(LO, P));
+  SZ = fma2(E, pk(0.125f, 0.125f), fma2(D3, pk(-1.0f / 24.0f, -1.0f / 24.0f), sub2(IL, IH)));
 }
 
-// Per-pair state of the surrogate evaluation between its stages.
+// Per-pair state carried across the network: the image sums are affine in
+// the network outputs, sr = a0 + b0 y0 and sz = a1 + b1 y1 (near images, tail
+// base, envelope, sign(dz) and the output scaling folded in), plus the inputs.
 struct SurrPair {
-  float sr, sz;          // near-image sums so far
-  float br, bz, er, ez;  // tail base and envelope
-  float sg;              // sign(dz)
-  float u[3];            // network inputs
-  float ih, ih3;         // 1/h, 1/h^3 (when some lane is softened)
+  float a0, b0, a1, b1;
+  float u[3];  // network inputs
 };
 
-// Stage A: near images |k| <= n0 exactly (as in pair_fp32.cuh), the tail base,
-// the envelope and the network inputs. kw: warp-uniform spline bound.
+// Stage A: near images |k| <= n0 exactly (the tiered image walk of
+// pair_fp32.cuh without the edge image), the tail base, the envelope and the
+// network inputs. kw: warp-uniform spline bound.
 __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int n_cut, int kw, const SurrConst& S,
                                              SurrPair& P) {
-  const u64 DR2 = pk(dR2, dR2);
-  const u64 STEP = pk(1.0f, -1.0f);
   const int n0 = S.n0;
-  u64 SR, SZ, O;
-  int k = 1;
-  P.ih = 0.f;
-  P.ih3 = 0.f;
-  if (kw >= 0) {
-    P.ih = rcp_approx(hh);
-    P.ih3 = P.ih * P.ih * P.ih;
-    const u64 IH = pk(P.ih, P.ih), IH3 = pk(P.ih3, P.ih3);
-    O = pk(dz, dz);
-    const u64 F = mul2(spline_over_r2(O, DR2, IH, IH3), pk(1.0f, 0.0f));
-    SR = F;
-    SZ = mul2(O, F);
-    const int kg = min(kw, n0);
-#pragma unroll(kSplineUnroll)
-    for (; k <= kg; ++k) {
-      O = add2(O, STEP);
-      const u64 G = spline_over_r2(O, DR2, IH, IH3);
-      SR = add2(SR, G);
-      SZ = fma2(O, G, SZ);
-    }
-  } else {
-    const float r2 = fmaf(dz, dz, dR2);
-    const float ri = rsq(r2);
-    const float r3 = ri * ri * ri;
-    SR = pk(r3, 0.0f);
-    SZ = pk(dz * r3, 0.0f);
-    O = pk(dz, dz);
-  }
-#pragma unroll 4
-  for (; k <= n0; ++k) {
-    O = add2(O, STEP);
-    const u64 R2 = fma2(O, O, DR2);
-    float ra, rb;
-    upk(R2, ra, rb);
-    const u64 RI = pk(rsq(ra), rsq(rb));
-    const u64 R3 = mul2(mul2(RI, RI), RI);
-    SR = add2(SR, R3);
-    SZ = fma2(O, R3, SZ);
-  }
-  float s0, s1, z0, z1;
-  upk(SR, s0, s1);
-  upk(SZ, z0, z1);
-  P.sr = s0 + s1;
-  P.sz = z0 + z1;
+  float sr, sz;
+  pair_images_fp32<false>(dR2, dz, hh, n0 + 1, (float)(n0 + 1), kw, sr, sz);
   // tail base and envelope (|dz|; z part gets sign(dz))
   const float adz = fabsf(dz), A = (float)n0 + 0.5f;
   const float kneg = adz > 0.0f ? (float)n_cut : (float)(n_cut - 1);
-  float br1, bz1, il1, br2, bz2, il2;
-  side_base_fp32(dR2, A + adz, (float)(n_cut - 1) + 0.5f + adz, br1, bz1, il1);
-  side_base_fp32(dR2, A - adz, kneg + 0.5f - adz, br2, bz2, il2);
+  u64 SRb, SZb, ILb;
+  side_base_x2(dR2, pk(A + adz, A - adz), pk((float)(n_cut - 1) + 0.5f + adz, kneg + 0.5f - adz), SRb, SZb, ILb);
+  float br1, br2, bz1, bz2, il1, il2;
+  upk(SRb, br1, br2);
+  upk(SZb, bz1, bz2);
+  upk(ILb, il1, il2);
   const float e = il1 * il1;
-  P.er = e * e * e;
-  P.ez = e * e * il1;
-  P.br = br1 + br2;
-  P.bz = bz1 - bz2;
-  P.sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
+  const float er = e * e * e;
+  const float sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
+  const float ez = sg * (e * e * il1);  // sign(dz) E_z: the z part of the tail is odd in dz
+  // tail = base + E (y sc + mu)
+  P.a0 = fmaf(er, S.mu0, sr + (br1 + br2));
+  P.b0 = er * S.sc0;
+  P.a1 = fmaf(ez, S.mu1, fmaf(sg, bz1 - bz2, sz));
+  P.b1 = ez * S.sc1;
   const float dR = dR2 * rsq(fmaxf(dR2, 1e-30f));
   P.u[0] = 2.0f * fminf(dR, S.dR_max) * S.inv_dR_max - 1.0f;
   P.u[1] = 4.0f * adz - 1.0f;
@@ -255,15 +285,21 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
 
 // Stage C: tail = base + envelope x network output, plus the exact spline
 // correction of tail images inside some lane's softening support.
-__device__ __forceinline__ void surr_stage_c(float dR2, float dz, int n_cut, int kw, const SurrConst& S,
-                                             const SurrPair& P, float y0, float y1, float& sr, float& sz) {
+// The separation is recomputed from the tile (same arithmetic, same values)
+// on that rare path rather than kept live across the network.
+__device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A, const float4& B, int n_cut, int kw,
+                                             const SurrConst& S, const SurrPair& P, float y0, float y1, float& sr,
+                                             float& sz) {
   const int n0 = S.n0;
-  sr = P.sr + P.br + P.er * fmaf(y0, S.sc0, S.mu0);
-  sz = P.sz + P.sg * (P.bz + P.ez * fmaf(y1, S.sc1, S.mu1));
+  sr = fmaf(P.b0, y0, P.a0);
+  sz = fmaf(P.b1, y1, P.a1);
   if (kw > n0) {
+    float dx, dy, dz, dR2, hh;
+    pair_separation(I, A, B, dx, dy, dz, dR2, hh);
     const u64 DR2 = pk(dR2, dR2);
     const u64 STEP = pk(1.0f, -1.0f);
-    const u64 IH = pk(P.ih, P.ih), IH3 = pk(P.ih3, P.ih3);
+    const float ih = rcp_approx(hh), ih3 = ih * ih * ih;
+    const u64 IH = pk(ih, ih), NIH = pk(-ih, -ih), IH3 = pk(ih3, ih3);
     const int kt = min(kw, n_cut - 1);
     u64 CR = pk(0.f, 0.f), CZ = pk(0.f, 0.f);
     u64 O = pk(dz + (float)n0, dz - (float)n0);
@@ -274,7 +310,7 @@ __device__ __forceinline__ void surr_stage_c(float dR2, float dz, int n_cut, int
       upk(R2, ra, rb);
       const u64 RI = pk(rsq(ra), rsq(rb));
       const u64 N3 = mul2(mul2(RI, RI), RI);
-      const u64 D = fma2(N3, pk(-1.0f, -1.0f), spline_over_r2(O, DR2, IH, IH3));
+      const u64 D = fma2(N3, pk(-1.0f, -1.0f), spline_over_r2(O, DR2, IH, NIH, IH3));
       CR = add2(CR, D);
       CZ = fma2(O, D, CZ);
     }
@@ -284,7 +320,7 @@ __device__ __forceinline__ void surr_stage_c(float dR2, float dz, int n_cut, int
       const float r2 = fmaf(oe, oe, dR2);
       const float ri = rsq(r2);
       float fa, fb;
-      upk(spline_over_r2(OE, DR2, IH, IH3), fa, fb);
+      upk(spline_over_r2(OE, DR2, IH, NIH, IH3), fa, fb);
       const float d = (dz != 0.0f ? 1.0f : 0.0f) * (fa - ri * ri * ri);
       CR = add2(CR, pk(d, 0.f));
       CZ = add2(CZ, pk(oe * d, 0.f));
@@ -297,26 +333,19 @@ __device__ __forceinline__ void surr_stage_c(float dR2, float dz, int n_cut, int
   }
 }
 
-// Geometry of the pair (i, j) shared by both forms.
-__device__ __forceinline__ void pair_geometry(const IParticle& I, const float4& A, const float4& B, float& dx, float& dy,
-                                              float& dz, float& dR2, float& hh, int& kw) {
-  dx = (I.xh - A.x) + (I.xl - B.x);
-  dy = (I.yh - A.y) + (I.yl - B.y);
-  dz = I.zh - A.z;
-  dz = (dz - rintf(dz)) + (I.zl - B.z);
-  dR2 = fmaf(dx, dx, dy * dy);
-  hh = I.h + B.w;
-  const int kl = dR2 < hh * hh ? (int)(hh + 0.5f) : -1;
-  kw = __reduce_max_sync(0xffffffffu, kl);
-}
+#ifndef STEPS_SURR_NJ
+#define STEPS_SURR_NJ 2  // values of j per network call (independent mma chains per warp)
+#endif
+static_assert(STEPS_KAHAN_GROUP % STEPS_SURR_NJ == 0, "a Kahan group holds whole network calls");
 
 // One j-tile of pairs for one i (shared by the stream-K and the subset kernels).
 // The surrogate form handles two j per network call.
 template <bool KAHAN, bool SURR>
 __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, const float4* sB, int jn, int self,
-                                          int n_cut, float fnc, const SurrW& W, const SurrConst& S, float& sx,
+                                          int n_cut, float fnc, const SurrW& W, uint32_t* ibuf, const SurrConst& S,
+                                          float& sx,
                                           float& sy, float& sz, float& cx, float& cy, float& cz) {
-  constexpr int STEPJ = SURR ? 2 : 1;
+  constexpr int STEPJ = SURR ? STEPS_SURR_NJ : 1;
   for (int k0 = 0; k0 < jn; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
     const int ke = min(k0 + STEPS_KAHAN_GROUP, jn);
@@ -342,10 +371,12 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
           u[jj][1] = P[jj].u[1];
           u[jj][2] = P[jj].u[2];
         }
-        mlp_warp<STEPJ>(W, u, y);
+        mlp_warp<STEPJ>(W, ibuf, u, y);
 #pragma unroll
-        for (int jj = 0; jj < STEPJ; ++jj)
-          surr_stage_c(dR2[jj], dz[jj], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr[jj], szz[jj]);
+        for (int jj = 0; jj < STEPJ; ++jj) {
+          const int kk = min(k + jj, ke - 1);
+          surr_stage_c(I, sA[kk], sB[kk], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr[jj], szz[jj]);
+        }
       } else {
 #pragma unroll
         for (int jj = 0; jj < STEPJ; ++jj) pair_images_fp32(dR2[jj], dz[jj], hh[jj], n_cut, fnc, kw[jj], sr[jj], szz[jj]);
@@ -378,9 +409,12 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
   __shared__ float4 sB[kBJ];
   // weight fragments stay in shared memory (word-major, conflict-free) and are
   // read where the mma needs them, which leaves registers for resident warps
-  __shared__ uint32_t sWT[32 * kSurrWords];
+  __shared__ __align__(16) uint32_t sWT[32 * kSurrStride];
+  __shared__ __align__(16) uint32_t sIn[kBI / 32][STEPS_SURR_NJ * kInWords];
+  uint32_t* ibuf = sIn[threadIdx.x >> 5];
+  mlp_zero_inputs<STEPS_SURR_NJ>(ibuf);
   stage_surr_weights(wl, sWT);
-  const SurrW W{sWT + (threadIdx.x & 31)};
+  const SurrW W{sWT + (threadIdx.x & 31) * kSurrStride};
   const int c = blockIdx.x;
   const long long u0 = (long long)c * U / C;
   const long long u1 = (long long)(c + 1) * U / C;
@@ -391,22 +425,13 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
     const int t0 = (int)(u % NT);
     const int t1 = (int)min((long long)NT, (long long)t0 + (u1 - u));
     const int i = b * kBI + threadIdx.x;
-    IParticle I;
-    {
-      const float4 a = jA[min(i, n - 1)];
-      const float4 q = jB[min(i, n - 1)];
-      I.xh = a.x; I.yh = a.y; I.zh = a.z; I.xl = q.x; I.yl = q.y; I.zl = q.z; I.h = q.w;
-    }
+    const IParticle I = load_i(jA, jB, min(i, n - 1));
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     for (int t = t0; t < t1; ++t) {
       __syncthreads();
-      const int jl = t * kBJ + threadIdx.x;
-      if (jl < n) {
-        sA[threadIdx.x] = jA[jl];
-        sB[threadIdx.x] = jB[jl];
-      }
+      load_tile(jA, jB, n, t, sA, sB);
       __syncthreads();
-      pair_tile<KAHAN, true>(I, sA, sB, min(kBJ, n - t * kBJ), i - t * kBJ, n_cut, fnc, W, S, sx, sy, sz, cx, cy,
+      pair_tile<KAHAN, true>(I, sA, sB, kBJ, i - t * kBJ, n_cut, fnc, W, ibuf, S, sx, sy, sz, cx, cy,
                              cz);
     }
     double* dst = part + ((long long)b + c) * 3 * kBI;
@@ -427,29 +452,25 @@ pair_fp32_subset_kernel(const float4* __restrict__ jA, const float4* __restrict_
                         double* __restrict__ part) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
-  __shared__ uint32_t sWT[32 * kSurrWords];
-  if (SURR) stage_surr_weights(wl, sWT);
-  const SurrW W{sWT + (threadIdx.x & 31)};
+  __shared__ __align__(16) uint32_t sWT[32 * kSurrStride];
+  __shared__ __align__(16) uint32_t sIn[kBI / 32][SURR ? STEPS_SURR_NJ * kInWords : 4];
+  uint32_t* ibuf = sIn[threadIdx.x >> 5];
+  if (SURR) {
+    mlp_zero_inputs<STEPS_SURR_NJ>(ibuf);
+    stage_surr_weights(wl, sWT);
+  }
+  const SurrW W{sWT + (threadIdx.x & 31) * kSurrStride};
   const int q = blockIdx.x * kBI + threadIdx.x;
   const int i = (int)idx[min(q, ni - 1)];
-  IParticle I;
-  {
-    const float4 a = jA[i];
-    const float4 b = jB[i];
-    I.xh = a.x; I.yh = a.y; I.zh = a.z; I.xl = b.x; I.yl = b.y; I.zl = b.z; I.h = b.w;
-  }
+  const IParticle I = load_i(jA, jB, i);
   const int NT = (n + kBJ - 1) / kBJ;
   const int t0 = blockIdx.y * tpc, t1 = min(NT, t0 + tpc);
   float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
-    const int jl = t * kBJ + threadIdx.x;
-    if (jl < n) {
-      sA[threadIdx.x] = jA[jl];
-      sB[threadIdx.x] = jB[jl];
-    }
+    load_tile(jA, jB, n, t, sA, sB);
     __syncthreads();
-    pair_tile<KAHAN, SURR>(I, sA, sB, min(kBJ, n - t * kBJ), i - t * kBJ, n_cut, (float)n_cut, W, S, sx, sy, sz, cx,
+    pair_tile<KAHAN, SURR>(I, sA, sB, kBJ, i - t * kBJ, n_cut, (float)n_cut, W, ibuf, S, sx, sy, sz, cx,
                            cy, cz);
   }
   if (q < ni) {

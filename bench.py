@@ -36,7 +36,8 @@ import numpy as np  # noqa: E402
 WORKLOAD = "lcdm_n65536"
 METRIC = "pair-interactions/s (images counted)"
 UNIT = "pair-images/s"
-MUFU_RSQRT_PER_SM_CLK = 16  # measured on sm_103: one rsqrt per pair-image
+MUFU_RSQRT_PER_SM_CLK = 16  # MUFU rsqrt lanes per SM per clock, measured on GB300 (one rsqrt per pair-image)
+MMA_SYNC_FLOP_PER_SM_CLK = 1913.0  # mma.sync m16n8k16 f16->f32 flops per SM per clock, measured on GB300
 
 
 def env_int(name, default):
@@ -396,6 +397,17 @@ def run_workload(args):
             "pair_ms": mss, "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (mss * 1e-3),
             "executed_near_images_per_pair": 2 * w.n0 + 1, "speedup_vs_fp32_plain_sum": ms32 / mss,
             "error_vs_fp64": _err(asg[idx], a64)}
+        # per-pair pipe bound of the surrogate kernel: MUFU ops (near images,
+        # base rsqrt/rcp, the dR rsqrt) against 16/SM/clk, and the padded MLP
+        # flops of its mma.sync calls against the measured mma.sync rate
+        mufu = (2 * w.n0 + 1) + 4 + 2 + 1
+        flops = (8 * 2048 + 20 * 4096) / 32.0
+        clk = {"mufu": mufu / MUFU_RSQRT_PER_SM_CLK, "tensor_mma_sync": flops / MMA_SYNC_FLOP_PER_SM_CLK}
+        bound = max(clk, key=clk.get)
+        peak_pairs = props.multi_processor_count * 2070e6 / clk[bound]
+        line["surrogate"]["roofline"] = {
+            "bound": bound, "clk_per_pair_per_sm": clk, "peak_pairs_per_s": peak_pairs,
+            "achieved_pairs_per_s": pairs / (mss * 1e-3), "frac": pairs / (mss * 1e-3) / peak_pairs}
     if w.name.startswith("production") or w.name.startswith("plain_small") or w.name.startswith("lcdm"):
         steps = min(args.steps, w.nsteps) if w.nsteps else args.steps
         t0, dt = ics.run_schedule(w)

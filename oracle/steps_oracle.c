@@ -8,7 +8,7 @@
  * j-sums are Neumaier-compensated in double so that the result is the
  * definition up to rounding (no long double: it is software quad on aarch64).
  *
- * Readings of the paper taken here (each is also listed in the design doc):
+ * Readings of the paper taken here:
  *  - Eq. Force_spline_kernel: the "-\\-" inside the middle branch is a LaTeX
  *    line break, i.e. a single minus sign. h is the support radius (Newtonian
  *    for r >= h) and the pair uses h_i + h_j (eq. ComovingEquationsOfMotion).

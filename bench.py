@@ -408,6 +408,22 @@ def run_workload(args):
         line["surrogate"]["roofline"] = {
             "bound": bound, "clk_per_pair_per_sm": clk, "peak_pairs_per_s": peak_pairs,
             "achieved_pairs_per_s": pairs / (mss * 1e-3), "frac": pairs / (mss * 1e-3) / peak_pairs}
+        # correction-table tail: near images exact, tail from the GPU-built table
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
+        nx, ny = 257, 33
+        rt = sc.steps_cyl_build_tail_table(sim.ctx, nx, ny)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+        atb, mst = _timed_forces(sc, torch, sim, reps + 1)
+        mufu_t = (2 * w.n0 + 1) + 4 + 2 + 1   # near images, base rsqrt/rcp, the dR rsqrt
+        peak_t = props.multi_processor_count * 2070e6 * MUFU_RSQRT_PER_SM_CLK / mufu_t
+        line["table"] = {
+            "nx": nx, "ny": ny, "build_ms": rt[3], "check_median": rt[0], "check_p999": rt[1], "pair_ms": mst,
+            "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (mst * 1e-3),
+            "speedup_vs_fp32_plain_sum": ms32 / mst, "speedup_vs_surrogate": mss / mst,
+            "error_vs_fp64": _err(atb[idx], a64),
+            "roofline": {"bound": "mufu", "mufu_ops_per_pair": mufu_t, "peak_pairs_per_s": peak_t,
+                         "achieved_pairs_per_s": pairs / (mst * 1e-3), "frac": pairs / (mst * 1e-3) / peak_t}}
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
     if w.name.startswith("production") or w.name.startswith("plain_small") or w.name.startswith("lcdm"):
         steps = min(args.steps, w.nsteps) if w.nsteps else args.steps
         t0, dt = ics.run_schedule(w)

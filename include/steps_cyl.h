@@ -42,7 +42,7 @@ extern "C" {
 #define STEPS_ENOMEM (-3)               /* device allocation failed */
 #define STEPS_EDEVICE (-4)              /* the device error word was set (non-finite force, particle beyond the background table) */
 #define STEPS_ESURROGATE_REJECTED (-5)  /* surrogate error above its bound: the plain image sum was used instead */
-#define STEPS_ENOSURROGATE (-6)         /* surrogate tail requested but no accepted network is loaded */
+#define STEPS_ENOSURROGATE (-6)         /* modelled tail requested but no accepted network / correction table is loaded */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define STEPS_FP64 0        /* pair geometry and sums in FP64 */
@@ -51,6 +51,7 @@ extern "C" {
 
 #define STEPS_TAIL_FULL 0       /* every image of the window summed directly */
 #define STEPS_TAIL_SURROGATE 1  /* images |k| <= n0 direct, far tail from the learned surrogate */
+#define STEPS_TAIL_TABLE 2      /* images |k| <= n0 direct, far tail from the correction table */
 
 #define STEPS_BG_OFF 0       /* no background term */
 #define STEPS_BG_FINITE 1    /* eq. F_horiz: cylinder of radius R_sim and height 2 Ncut L */
@@ -66,7 +67,7 @@ typedef struct {
   int32_t n_cut;    /* image cut-off Ncut of eq. ForceCylindrical, 1 <= n_cut <= 4096 */
   int32_t n0;       /* surrogate near range: images |k| <= n0 summed directly, 1 <= n0 < n_cut */
   int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
-  int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE */
+  int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE | STEPS_TAIL_TABLE */
   int32_t background; /* STEPS_BG_OFF | STEPS_BG_FINITE | STEPS_BG_INFINITE */
   int32_t comoving;   /* 0: static space (a = 1, H = 0); 1: expanding background */
   double H0, Omega_m, Omega_r, Omega_L, w0, wa; /* eqs. Friedmann, DEdensity, CPLw0wa; Omega_k = 1 - sum */
@@ -217,6 +218,40 @@ int steps_cyl_get_surrogate(steps_cyl_ctx* ctx, float* params);
  * accepted surrogate and an FP32 precision). As with steps_cyl_set_precision the
  * cached forces are refreshed by the next force evaluation or KDK step. */
 int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
+
+/* ---- correction-table tail -----------------------------------------------
+ * Sect. 2.3, eq. S1R2EwaldCorrectionTable: the paper tabulates the force of the
+ * periodic images beyond the nearest on an equally spaced (rho, z) grid and adds
+ * it, read with cloud-in-cell interpolation, to the nearest-image force. Here
+ * the table holds the images beyond the near range |k| <= n0 of the context's
+ * window (eq. ForceCylindrical), for point masses, as the residual of that tail
+ * over the continuum base in envelope units (the quantity the surrogate
+ * learns), at nodes dR_i = i dR_max / (nx - 1), |dz|_j = j / (2 (ny - 1)) in
+ * units of L; dR beyond dR_max reads the last column. It is computed in FP64 on
+ * the GPU, stored in FP32 and read with the texture unit's bilinear filter. The
+ * table form (STEPS_TAIL_TABLE) sums the near images exactly, adds
+ * base + envelope x table, and corrects tail images inside the softening support
+ * exactly, as the surrogate form does. */
+
+/* Build the context's table (its n_cut and n0; 1 <= n0 < n_cut, FP32
+ * precision) and compare the table form with the plain image sum on
+ * check_particles particles; keep it when median <= err_median and 99.9th
+ * percentile <= err_p999 of the relative total-force error. nx in [2, 4096], ny
+ * in [2, 1024]; dR_max = 0 picks 2.2 x the largest particle radius / L. report
+ * (4 doubles, may be NULL): check median, 99.9th percentile, accepted (1/0),
+ * build ms. STEPS_ESURROGATE_REJECTED when the check fails (the table is not
+ * used). The context may then select STEPS_TAIL_TABLE. */
+int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, double dR_max, double err_median,
+                               double err_p999, int32_t check_particles, double* report);
+
+/* Copy out the context's table: out = ny x nx x 2 floats (host; may be NULL to
+ * read only the sizes), its nx, ny and dR_max (each may be NULL).
+ * STEPS_ENOSURROGATE when no table was built. */
+int steps_cyl_get_tail_table(steps_cyl_ctx* ctx, float* out, int32_t* nx, int32_t* ny, double* dR_max);
+
+/* As steps_cyl_check_surrogate for a modelled tail (STEPS_TAIL_SURROGATE or
+ * STEPS_TAIL_TABLE), which must be loaded and accepted. */
+int steps_cyl_check_tail(steps_cyl_ctx* ctx, int32_t tail, int32_t check_particles, double* report);
 
 /* Compare the surrogate form with the plain image sum now on check_particles
  * particles (deterministic sample): report (4 doubles) = median and 99.9th

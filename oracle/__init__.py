@@ -64,6 +64,17 @@ def make_surr_cfg(n_cut, n0, dR_max, out_mu=(0.0, 0.0), out_sc=(1.0, 1.0)):
     return c
 
 
+class TableCfg(ctypes.Structure):
+    _fields_ = [("n_cut", ctypes.c_int32), ("n0", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("dR_max", ctypes.c_double)]
+
+
+def make_table_cfg(n_cut, n0, nx, ny, dR_max):
+    c = TableCfg()
+    c.n_cut, c.n0, c.nx, c.ny, c.dR_max = int(n_cut), int(n0), int(nx), int(ny), float(dR_max)
+    return c
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -97,6 +108,13 @@ def lib():
         L.or_tail_surrogate.restype = None
         L.or_pair_field_surrogate.argtypes = [i64, p, p, p, p, p, d, d, p, ctypes.POINTER(SurrCfg), i64, p, p, p, p]
         L.or_pair_field_surrogate.restype = None
+        T = ctypes.POINTER(TableCfg)
+        L.or_tail_residual.argtypes = [d, d, i32, i32, p]; L.or_tail_residual.restype = None
+        L.or_tail_table_build.argtypes = [T, p]; L.or_tail_table_build.restype = None
+        L.or_tail_table_read.argtypes = [p, T, d, d, p]; L.or_tail_table_read.restype = None
+        L.or_tail_table.argtypes = [d, d, d, p, T, p, p]; L.or_tail_table.restype = None
+        L.or_pair_field_table.argtypes = [i64, p, p, p, p, p, d, d, p, T, i64, p, p, p, p]
+        L.or_pair_field_table.restype = None
         _lib = L
     return _lib
 
@@ -288,4 +306,50 @@ def pair_field_surrogate(pos, m, h, G, L, w, cfg, idx=None):
     gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
     lib().or_pair_field_surrogate(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), _ptr(w),
                                   ctypes.byref(cfg), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)
+
+
+def tail_residual(dR, adz, n_cut, n0):
+    """Residual of the point-mass tail over the continuum base, in envelope units."""
+    r = np.zeros(2)
+    lib().or_tail_residual(float(dR), float(adz), int(n_cut), int(n0), _ptr(r))
+    return r
+
+
+def tail_table_build(cfg):
+    """Correction table of the tail residual, shape (ny, nx, 2)."""
+    tab = np.zeros((cfg.ny, cfg.nx, 2))
+    lib().or_tail_table_build(ctypes.byref(cfg), _ptr(tab))
+    return tab
+
+
+def tail_table_read(tab, cfg, dR, adz):
+    tab = _f64(tab)
+    r = np.zeros(2)
+    lib().or_tail_table_read(_ptr(tab), ctypes.byref(cfg), float(dR), float(adz), _ptr(r))
+    return r
+
+
+def tail_table(dR, dz, h, tab, cfg):
+    """Table far tail (SR, SZ) in units of L for one pair."""
+    tab = _f64(tab)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_table(float(dR), float(dz), float(h), _ptr(tab), ctypes.byref(cfg), ctypes.byref(a),
+                        ctypes.byref(b))
+    return a.value, b.value
+
+
+def pair_field_table(pos, m, h, G, L, tab, cfg, idx=None):
+    """Pair term with near images exact and the far tail from the correction table."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h); tab = _f64(tab)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], _ptr(idx)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    lib().or_pair_field_table(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), _ptr(tab),
+                              ctypes.byref(cfg), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz))
     return np.stack([gx, gy, gz], axis=1)

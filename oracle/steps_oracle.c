@@ -498,11 +498,14 @@ void or_tail_surrogate(double dR, double dz, double h, const double* w, const or
   *SZ = sz;
 }
 
-/* Pair term with the surrogate tail: near images (|k| <= n0 in the wrapped
- * frame) summed exactly, far tail from or_tail_surrogate. */
-void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
-                             const double* h, double G, double L, const double* w, const or_surr_cfg* c,
-                             int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz) {
+/* Pair term with a modelled tail: near images (|k| <= n0 in the wrapped frame)
+ * summed exactly, far tail from tail(dR, dz, h, ctx). */
+typedef void (*or_tail_fn)(double dR, double dz, double h, const void* ctx, double* SR, double* SZ);
+
+static void or_pair_field_with_tail(int64_t n, const double* x, const double* y, const double* z,
+                                    const double* m, const double* h, double G, double L, int32_t n0,
+                                    or_tail_fn tail, const void* ctx, int64_t ni, const int64_t* idx,
+                                    double* gx, double* gy, double* gz) {
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t q = 0; q < ni; ++q) {
     int64_t i = idx ? idx[q] : q;
@@ -513,14 +516,14 @@ void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const 
       double dzw = rz - floor(rz + 0.5);
       double hh = (h[i] + h[j]) / L, dR = sqrt(dx * dx + dy * dy);
       double sr = 0.0, szz = 0.0;
-      for (int k = -c->n0; k <= c->n0; ++k) {
+      for (int k = -n0; k <= n0; ++k) {
         double o = dzw + (double)k;
         double f = or_spline_F_over_r(sqrt(dR * dR + o * o), hh);
         sr += f;
         szz += o * f;
       }
       double tr, tz;
-      or_tail_surrogate(dR, dzw, hh, w, c, &tr, &tz);
+      tail(dR, dzw, hh, ctx, &tr, &tz);
       sr += tr;
       szz += tz;
       /* lengths were in units of L: F/r scales as 1/L^3, the vector as L */
@@ -532,4 +535,105 @@ void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const 
     gy[q] = sy.s + sy.c;
     gz[q] = sz.s + sz.c;
   }
+}
+
+typedef struct {
+  const double* w;
+  const or_surr_cfg* c;
+} or_surr_ctx;
+
+static void or_tail_surrogate_cb(double dR, double dz, double h, const void* ctx, double* SR, double* SZ) {
+  const or_surr_ctx* s = (const or_surr_ctx*)ctx;
+  or_tail_surrogate(dR, dz, h, s->w, s->c, SR, SZ);
+}
+
+void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                             const double* h, double G, double L, const double* w, const or_surr_cfg* c,
+                             int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz) {
+  or_surr_ctx s = {w, c};
+  or_pair_field_with_tail(n, x, y, z, m, h, G, L, c->n0, or_tail_surrogate_cb, &s, ni, idx, gx, gy, gz);
+}
+
+/* ---------------------------------------------------------------------------
+ * Correction-table tail (Sect. 2.3, eq. S1R2EwaldCorrectionTable: a 2D table of
+ * the periodic images beyond the nearest, read by cloud-in-cell interpolation
+ * during the run), restated for the windowed sum beyond the near images
+ * |k| <= n0 and for point masses. The tabulated quantity is the residual of the
+ * tail over the continuum base in envelope units,
+ *   r = ((SR - BR) / ER, (SZ - BZ) / EZ)   at dz = +|dz| (SZ odd in dz),
+ * at nodes dR_i = i dR_max / (nx - 1), |dz|_j = j / (2 (ny - 1)). The tail at
+ * (dR, dz) is B + E * bilinear(r), with dR beyond dR_max read on the last
+ * column, plus the exact spline correction of tail images inside the
+ * softening support (the table is Newtonian), as for the surrogate.
+ * ------------------------------------------------------------------------- */
+void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]) {
+  double SR, SZ, BR, BZ, ER, EZ;
+  or_tail_sums(dR, adz, 0.0, 1.0, n_cut, n0, &SR, &SZ);
+  or_tail_base(dR, adz, n_cut, n0, &BR, &BZ);
+  or_tail_envelope(dR, adz, n0, &ER, &EZ);
+  r[0] = (SR - BR) / ER;
+  r[1] = (SZ - BZ) / EZ;
+}
+
+void or_tail_table_build(const or_table_cfg* c, double* tab) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i)
+      or_tail_residual(c->dR_max * i / (c->nx - 1), 0.5 * j / (c->ny - 1), c->n_cut, c->n0,
+                       tab + 2 * ((size_t)j * c->nx + i));
+}
+
+void or_tail_table_read(const double* tab, const or_table_cfg* c, double dR, double adz, double r[2]) {
+  double fx = (dR < c->dR_max ? dR : c->dR_max) / c->dR_max * (c->nx - 1);
+  double fy = adz / 0.5 * (c->ny - 1);
+  int i = (int)floor(fx), j = (int)floor(fy);
+  if (i > c->nx - 2) i = c->nx - 2;
+  if (j > c->ny - 2) j = c->ny - 2;
+  double a = fx - i, b = fy - j;
+  for (int q = 0; q < 2; ++q) {
+    double t00 = tab[2 * ((size_t)j * c->nx + i) + q], t10 = tab[2 * ((size_t)j * c->nx + i + 1) + q];
+    double t01 = tab[2 * ((size_t)(j + 1) * c->nx + i) + q], t11 = tab[2 * ((size_t)(j + 1) * c->nx + i + 1) + q];
+    r[q] = (1 - a) * (1 - b) * t00 + a * (1 - b) * t10 + (1 - a) * b * t01 + a * b * t11;
+  }
+}
+
+void or_tail_table(double dR, double dz, double h, const double* tab, const or_table_cfg* c, double* SR,
+                   double* SZ) {
+  double adz = fabs(dz), BR, BZ, ER, EZ, r[2];
+  or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
+  or_tail_envelope(dR, adz, c->n0, &ER, &EZ);
+  or_tail_table_read(tab, c, dR, adz, r);
+  double sr = BR + ER * r[0];
+  double sz = BZ + EZ * r[1];
+  double sg = dz > 0.0 ? 1.0 : (dz < 0.0 ? -1.0 : 0.0);
+  sz *= sg;
+  for (int k = -c->n_cut - 1; k <= c->n_cut + 1; ++k) {
+    if (k >= -c->n0 && k <= c->n0) continue;
+    double o = dz + (double)k;
+    if (!(fabs(o) < (double)c->n_cut)) continue;
+    double rr = sqrt(dR * dR + o * o);
+    if (rr >= h) continue;
+    double d = or_spline_F_over_r(rr, h) - 1.0 / (rr * rr * rr);
+    sr += d;
+    sz += o * d;
+  }
+  *SR = sr;
+  *SZ = sz;
+}
+
+typedef struct {
+  const double* tab;
+  const or_table_cfg* c;
+} or_table_ctx;
+
+static void or_tail_table_cb(double dR, double dz, double h, const void* ctx, double* SR, double* SZ) {
+  const or_table_ctx* t = (const or_table_ctx*)ctx;
+  or_tail_table(dR, dz, h, t->tab, t->c, SR, SZ);
+}
+
+void or_pair_field_table(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                         const double* h, double G, double L, const double* tab, const or_table_cfg* c,
+                         int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz) {
+  or_table_ctx t = {tab, c};
+  or_pair_field_with_tail(n, x, y, z, m, h, G, L, c->n0, or_tail_table_cb, &t, ni, idx, gx, gy, gz);
 }

@@ -68,6 +68,21 @@ void or_tail_surrogate(double dR, double dz, double h, const double* w, const or
 void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
                              const double* h, double G, double L, const double* w, const or_surr_cfg* c,
                              int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz);
+/* Correction-table tail (the paper's Sect. 2.3 table restated for the windowed
+ * sum beyond |k| <= n0): residual of the point-mass tail over the continuum base
+ * in envelope units on a uniform (dR, |dz|) grid, read bilinearly. */
+typedef struct {
+  int32_t n_cut, n0, nx, ny;
+  double dR_max;        /* last column; dR beyond it reads the last column */
+} or_table_cfg;
+void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]);
+void or_tail_table_build(const or_table_cfg* c, double* tab); /* tab[ny][nx][2] */
+void or_tail_table_read(const double* tab, const or_table_cfg* c, double dR, double adz, double r[2]);
+void or_tail_table(double dR, double dz, double h, const double* tab, const or_table_cfg* c, double* SR,
+                   double* SZ);
+void or_pair_field_table(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                         const double* h, double G, double L, const double* tab, const or_table_cfg* c,
+                         int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz);
 double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t, double* grad);
 void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2, double lr,
                   double beta1, double beta2, double eps, int64_t step);

@@ -30,6 +30,7 @@
 #include "nbody_kernels.cuh"
 #include "surrogate_pair.cuh"
 #include "surrogate_train.cuh"
+#include "tail_table.cuh"
 
 using namespace steps;
 
@@ -233,6 +234,15 @@ struct steps_cyl_ctx {
   int steps_since_check = 0;
   double surr_bound_med = 1e-5, surr_bound_p999 = 1e-3;
   int SC = 0;                      // CTAs of the surrogate pair kernel
+  // correction-table tail
+  cudaArray_t tab_arr = nullptr;
+  TableTail tab{};                 // texture of the residual table
+  SurrConst tab_const{};           // mu = 0, sc = 1, the table's dR_max
+  int tab_nx = 0, tab_ny = 0;
+  double tab_dR_max = 0.0;
+  bool tab_ok = false;             // an accepted table is loaded
+  double tab_bound_med = 1e-5, tab_bound_p999 = 1e-3;
+  int TC = 0;                      // CTAs of the table pair kernel
   double* chk = nullptr;           // check buffers (grown on demand)
   size_t chk_elems = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -261,8 +271,9 @@ int check_params(const steps_cyl_params* p) {
   if (!(p->rho_bar >= 0) || !std::isfinite(p->rho_bar)) return fail(STEPS_EINVAL, "rho_bar must be >= 0");
   if (p->n_cut < 1 || p->n_cut > 4096) return fail(STEPS_EINVAL, "n_cut must be in [1, 4096]");
   if (p->precision < STEPS_FP64 || p->precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
-  if (p->tail != STEPS_TAIL_FULL && p->tail != STEPS_TAIL_SURROGATE) return fail(STEPS_EINVAL, "bad tail mode");
-  if (p->tail == STEPS_TAIL_SURROGATE && (p->n0 < 1 || p->n0 >= p->n_cut))
+  if (p->tail != STEPS_TAIL_FULL && p->tail != STEPS_TAIL_SURROGATE && p->tail != STEPS_TAIL_TABLE)
+    return fail(STEPS_EINVAL, "bad tail mode");
+  if (p->tail != STEPS_TAIL_FULL && (p->n0 < 1 || p->n0 >= p->n_cut))
     return fail(STEPS_EINVAL, "n0 must be in [1, n_cut)");
   if (p->background < STEPS_BG_OFF || p->background > STEPS_BG_INFINITE) return fail(STEPS_EINVAL, "bad background");
   if (p->comoving) {
@@ -507,6 +518,14 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
       pair_fp32_surr_kernel<false><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
                                                               c->surr_lanes, c->surr, c->part);
     CKLAUNCH("pair_fp32_surrogate");
+  } else if (c->p.tail == STEPS_TAIL_TABLE && c->tab_ok) {
+    if (c->p.precision == STEPS_FP32_KAHAN)
+      pair_fp32_table_kernel<true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
+                                                              c->tab, c->tab_const, c->part);
+    else
+      pair_fp32_table_kernel<false><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
+                                                               c->tab, c->tab_const, c->part);
+    CKLAUNCH("pair_fp32_table");
   } else if (c->p.precision == STEPS_FP32_KAHAN) {
     pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);
     CKLAUNCH("pair_fp32_kahan");
@@ -518,9 +537,12 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   c->timed = true;
   c->last_images = (double)c->n * (double)(c->n - 1) * 2.0 * c->p.n_cut;
   const int NT = c->p.precision == STEPS_FP64 ? 0 : c->NT;
-  const bool surr = c->p.precision != STEPS_FP64 && c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok;
+  const bool fp32 = c->p.precision != STEPS_FP64;
+  const int ctas = fp32 && c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok ? c->SC
+                   : fp32 && c->p.tail == STEPS_TAIL_TABLE && c->tab_ok    ? c->TC
+                                                                            : c->C;
   finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
-      c->part, c->n, NT, c->U, surr ? c->SC : c->C, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
+      c->part, c->n, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
       kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
   CKLAUNCH("finalize");
   return STEPS_OK;
@@ -630,6 +652,8 @@ void release(steps_cyl_ctx* c) {
   cudaFree(c->err);
   cudaFree(c->bgtab);
   cudaFree(c->surr_lanes);
+  if (c->tab.tex) cudaDestroyTextureObject(c->tab.tex);
+  if (c->tab_arr) cudaFreeArray(c->tab_arr);
   cudaFree(c->chk);
   if (c->e0) cudaEventDestroy(c->e0);
   if (c->e1) cudaEventDestroy(c->e1);
@@ -753,9 +777,10 @@ int grow(steps_cyl_ctx* c, size_t elems) {
 }
 
 // Total accelerations (times a^3) of a particle sample with the plain image sum
-// and with the surrogate tail; relative error statistics of the latter.
-int run_check(steps_cyl_ctx* c, int ncheck, uint64_t seed, double* med, double* p999, double* ms_plain,
-              double* ms_surr) {
+// and with a modelled tail (STEPS_TAIL_SURROGATE or STEPS_TAIL_TABLE); relative
+// error statistics of the latter.
+int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* med, double* p999,
+              double* ms_plain, double* ms_surr) {
   const int ni = std::max(1, std::min(ncheck, c->n));
   std::vector<int64_t> pick(ni);
   {
@@ -797,9 +822,12 @@ int run_check(steps_cyl_ctx* c, int ncheck, uint64_t seed, double* med, double* 
     if (form == 0)
       pair_fp32_subset_kernel<true, false><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
                                                                             ni, tpc, c->surr_lanes, c->surr, part);
-    else
+    else if (model == STEPS_TAIL_SURROGATE)
       pair_fp32_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
                                                                            ni, tpc, c->surr_lanes, c->surr, part);
+    else
+      pair_fp32_table_subset_kernel<true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
+                                                                           ni, tpc, c->tab, c->tab_const, part);
     CKLAUNCH("pair_fp32_subset");
     CK(cudaEventRecord(c->e1, c->st));
     CK(cudaEventSynchronize(c->e1));
@@ -853,13 +881,84 @@ int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999
   }
   if ((rc = install_surrogate(c, P))) return rc;
   c->surr_ok = true;
-  if ((rc = run_check(c, ncheck, 0x5eed0000ull + (uint64_t)c->steps_since_check, med, p999, nullptr, nullptr)))
+  if ((rc = run_check(c, STEPS_TAIL_SURROGATE, ncheck, 0x5eed0000ull + (uint64_t)c->steps_since_check, med, p999,
+                       nullptr, nullptr)))
     return rc;
   *ok = std::isfinite(*med) && std::isfinite(*p999) && *med <= bmed && *p999 <= bp999;
   c->surr_ok = *ok;
   c->surr_bound_med = bmed;
   c->surr_bound_p999 = bp999;
   if (!*ok) c->surr_params.clear();
+  return STEPS_OK;
+}
+
+// Correction-table tail: node residuals in FP64 on the GPU, stored as an FP32
+// float2 array and read through a texture with bilinear filtering (the
+// cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius.
+int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
+  if (c->p.n0 < 1 || c->p.n0 >= c->p.n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  if (dR_max == 0.0) {
+    std::vector<double> hx(c->n), hy(c->n);
+    CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double rm = 0.0;
+    for (int i = 0; i < c->n; ++i) rm = std::max(rm, std::hypot(hx[i], hy[i]));
+    dR_max = std::max(2.2 * rm * c->invL, 1.0);
+  }
+  c->tab_ok = false;
+  if (c->tab.tex) CK(cudaDestroyTextureObject(c->tab.tex));
+  c->tab.tex = 0;
+  if (c->tab_arr) CK(cudaFreeArray(c->tab_arr));
+  c->tab_arr = nullptr;
+  float2* buf = nullptr;
+  CK(cudaMallocAsync(&buf, sizeof(float2) * (size_t)nx * ny, c->st));
+  CK(cudaEventRecord(c->e0, c->st));
+  tail_table_kernel<<<grid_for(nx * ny, 128), 128, 0, c->st>>>(nx, ny, dR_max, c->p.n_cut, c->p.n0, buf);
+  CKLAUNCH("tail_table");
+  CK(cudaEventRecord(c->e1, c->st));
+  const cudaChannelFormatDesc ch = cudaCreateChannelDesc<float2>();
+  cudaError_t e = cudaMallocArray(&c->tab_arr, &ch, nx, ny);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DToArrayAsync(c->tab_arr, 0, 0, buf, sizeof(float2) * nx, sizeof(float2) * nx, ny,
+                                 cudaMemcpyDeviceToDevice, c->st);
+  cudaFreeAsync(buf, c->st);
+  if (e != cudaSuccess) return fail(STEPS_ECUDA, "table array: %s", cudaGetErrorString(e));
+  cudaResourceDesc res;
+  std::memset(&res, 0, sizeof res);
+  res.resType = cudaResourceTypeArray;
+  res.res.array.array = c->tab_arr;
+  cudaTextureDesc td;
+  std::memset(&td, 0, sizeof td);
+  td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+  td.filterMode = cudaFilterModeLinear;
+  td.readMode = cudaReadModeElementType;
+  td.normalizedCoords = 0;
+  CK(cudaCreateTextureObject(&c->tab.tex, &res, &td, nullptr));
+  c->tab.hx = 0.5f * (nx - 1);
+  c->tab.hy = 0.5f * (ny - 1);
+  c->tab_const = SurrConst{0.f, 0.f, 1.f, 1.f, (float)(1.0 / dR_max), (float)dR_max, c->p.n0};
+  c->tab_nx = nx;
+  c->tab_ny = ny;
+  c->tab_dR_max = dR_max;
+  CK(cudaStreamSynchronize(c->st));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, c->e0, c->e1));
+  if (ms) *ms = t;
+  return STEPS_OK;
+}
+
+// Check the table form against the plain sum and keep it when both bounds hold.
+int accept_table(steps_cyl_ctx* c, double bmed, double bp999, int ncheck, double* med, double* p999, bool* ok) {
+  int rc;
+  c->tab_ok = true;
+  if ((rc = run_check(c, STEPS_TAIL_TABLE, ncheck, 0x7ab1e000ull + (uint64_t)c->steps_since_check, med, p999,
+                      nullptr, nullptr)))
+    return rc;
+  *ok = std::isfinite(*med) && std::isfinite(*p999) && *med <= bmed && *p999 <= bp999;
+  c->tab_ok = *ok;
+  c->tab_bound_med = bmed;
+  c->tab_bound_p999 = bp999;
   return STEPS_OK;
 }
 
@@ -1083,7 +1182,10 @@ int allocate_context(steps_cyl_ctx* c) {
   int socc = 0;
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, pair_fp32_surr_kernel<true>, kBI, 0));
   c->SC = (int)std::min<long long>(c->U, (long long)sms * std::max(socc, 1) * STEPS_CTA_MULT);
-  c->part_elems = std::max((size_t)(c->NB + std::max(c->C, c->SC)) * 3 * kBI, nb * 3);
+  int tocc = 0;
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tocc, pair_fp32_table_kernel<true>, kBI, 0));
+  c->TC = (int)std::min<long long>(c->U, (long long)sms * std::max(tocc, 1) * STEPS_CTA_MULT);
+  c->part_elems = std::max((size_t)(c->NB + std::max({c->C, c->SC, c->TC})) * 3 * kBI, nb * 3);
   CKA(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
 
 #undef CKA
@@ -1137,6 +1239,7 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   if (n < 2 || n > 0x7fffffffLL - kBI) return fail(STEPS_EINVAL, "n must be in [2, 2^31 - 129)");
   if (!x || !y || !z || !vx || !vy || !vz || !m || !h) return fail(STEPS_EINVAL, "NULL input array");
   if (p->tail == STEPS_TAIL_SURROGATE) return fail(STEPS_ENOSURROGATE, "no surrogate network is loaded");
+  if (p->tail == STEPS_TAIL_TABLE) return fail(STEPS_ENOSURROGATE, "no correction table is built");
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
   if (p->device < 0 || p->device >= ndev) return fail(STEPS_EINVAL, "device %d out of range", p->device);
@@ -1295,19 +1398,23 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
     if (c->p.reorder_every > 0 && ++c->steps_since_order >= c->p.reorder_every) {
       if ((rc = reorder(c))) return rc;
     }
-    // surrogate tail: periodic comparison with the plain image sum
-    if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok && c->p.check_every > 0 &&
-        ++c->steps_since_check >= c->p.check_every) {
+    // modelled tail: periodic comparison with the plain image sum
+    const bool surr = c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok;
+    const bool table = c->p.tail == STEPS_TAIL_TABLE && c->tab_ok;
+    if ((surr || table) && c->p.check_every > 0 && ++c->steps_since_check >= c->p.check_every) {
       c->steps_since_check = 0;
       double med = 0, p999 = 0;
       const int ncheck = c->p.check_particles > 0 ? c->p.check_particles : 1024;
-      if ((rc = run_check(c, ncheck, 0xc4ec0000ull + (uint64_t)s, &med, &p999, nullptr, nullptr))) return rc;
-      if (!(med <= c->surr_bound_med && p999 <= c->surr_bound_p999)) {
-        c->surr_ok = false;
+      if ((rc = run_check(c, c->p.tail, ncheck, 0xc4ec0000ull + (uint64_t)s, &med, &p999, nullptr, nullptr)))
+        return rc;
+      const double bmed = surr ? c->surr_bound_med : c->tab_bound_med;
+      const double bp999 = surr ? c->surr_bound_p999 : c->tab_bound_p999;
+      if (!(med <= bmed && p999 <= bp999)) {
+        (surr ? c->surr_ok : c->tab_ok) = false;
         c->p.tail = STEPS_TAIL_FULL;
         rejected = true;
-        snprintf(reject_msg, sizeof reject_msg, "surrogate dropped after a check: median %.3g, p99.9 %.3g", med,
-                 p999);
+        snprintf(reject_msg, sizeof reject_msg, "%s dropped after a check: median %.3g, p99.9 %.3g",
+                 surr ? "surrogate" : "correction table", med, p999);
       }
     }
   }
@@ -1446,8 +1553,10 @@ struct CkptHeader {
   double a, t, rho0, bg_dr, bound_med, bound_p999;
   int32_t steps_since_order, steps_since_check, surr_ok, bgK;
   float surr[STEPS_SURR_NPARAM];
+  int32_t tab_ok, tab_nx, tab_ny, pad;  // correction table: rebuilt on resume from its grid
+  double tab_dR_max, tab_bound_med, tab_bound_p999;
 };
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   g_last_error.clear();
@@ -1472,6 +1581,12 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   hd.surr_ok = c->surr_ok ? 1 : 0;
   hd.bgK = c->bgtab ? c->bgK : 0;
   if (c->surr_ok) std::memcpy(hd.surr, c->surr_params.data(), sizeof hd.surr);
+  hd.tab_ok = c->tab_ok ? 1 : 0;
+  hd.tab_nx = c->tab_nx;
+  hd.tab_ny = c->tab_ny;
+  hd.tab_dR_max = c->tab_dR_max;
+  hd.tab_bound_med = c->tab_bound_med;
+  hd.tab_bound_p999 = c->tab_bound_p999;
   if (c->forces_stale) {
     int rc = eval_forces(c, false, 0.0);
     if (rc) return rc;
@@ -1557,6 +1672,14 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
   if (hd.surr_ok) {
     if ((rc = install_surrogate(c, hd.surr))) return bail(rc);
     c->surr_ok = true;
+  }
+  if (hd.tab_ok) {  // the table is a deterministic function of its grid: rebuilt, not stored
+    if (hd.tab_nx < 2 || hd.tab_nx > 4096 || hd.tab_ny < 2 || hd.tab_ny > 1024 || !(hd.tab_dR_max > 0))
+      return bail(fail(STEPS_EINVAL, "corrupt checkpoint (table grid)"));
+    if ((rc = build_table(c, hd.tab_nx, hd.tab_ny, hd.tab_dR_max, nullptr))) return bail(rc);
+    c->tab_ok = true;
+    c->tab_bound_med = hd.tab_bound_med;
+    c->tab_bound_p999 = hd.tab_bound_p999;
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(fail(STEPS_ECUDA, "synchronise failed"));
   *out = c;
@@ -1677,10 +1800,12 @@ int steps_cyl_get_surrogate(steps_cyl_ctx* c, float* params) {
 int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
-  if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE) return fail(STEPS_EINVAL, "bad tail mode");
+  if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE && tail != STEPS_TAIL_TABLE)
+    return fail(STEPS_EINVAL, "bad tail mode");
   if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
-  if (tail == STEPS_TAIL_SURROGATE && c->p.precision == STEPS_FP64)
-    return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
+  if (tail == STEPS_TAIL_TABLE && !c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
+  if (tail != STEPS_TAIL_FULL && c->p.precision == STEPS_FP64)
+    return fail(STEPS_EINVAL, "a modelled tail needs an FP32 precision");
   c->p.tail = tail;
   c->steps_since_check = 0;
   c->forces_stale = true;  // refreshed by the next force evaluation or KDK step
@@ -1692,8 +1817,60 @@ int steps_cyl_check_surrogate(steps_cyl_ctx* c, int32_t check_particles, double*
   if (!c || !report || check_particles < 1) return fail(STEPS_EINVAL, "bad arguments");
   if (!c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
   DeviceGuard guard(c->dev);
-  return run_check(c, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check, &report[0], &report[1],
-                   &report[2], &report[3]);
+  return run_check(c, STEPS_TAIL_SURROGATE, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check,
+                   &report[0], &report[1], &report[2], &report[3]);
+}
+
+int steps_cyl_build_tail_table(steps_cyl_ctx* c, int32_t nx, int32_t ny, double dR_max, double err_median,
+                               double err_p999, int32_t check_particles, double* report) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (nx < 2 || nx > 4096 || ny < 2 || ny > 1024) return fail(STEPS_EINVAL, "nx must be in [2, 4096], ny in [2, 1024]");
+  if (!(dR_max >= 0) || !std::isfinite(dR_max)) return fail(STEPS_EINVAL, "dR_max must be finite and >= 0");
+  if (!(err_median > 0) || !(err_p999 > 0) || check_particles < 1) return fail(STEPS_EINVAL, "bad check bounds");
+  if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the correction table needs an FP32 precision");
+  DeviceGuard guard(c->dev);
+  double ms = 0.0;
+  int rc = build_table(c, nx, ny, dR_max, &ms);
+  if (rc) return rc;
+  double med = 0, p999 = 0;
+  bool ok = false;
+  if ((rc = accept_table(c, err_median, err_p999, check_particles, &med, &p999, &ok))) return rc;
+  if (report) {
+    report[0] = med;
+    report[1] = p999;
+    report[2] = ok ? 1.0 : 0.0;
+    report[3] = ms;
+  }
+  if (!ok) return fail(STEPS_ESURROGATE_REJECTED, "correction table rejected: median %.3g, p99.9 %.3g", med, p999);
+  return STEPS_OK;
+}
+
+int steps_cyl_get_tail_table(steps_cyl_ctx* c, float* out, int32_t* nx, int32_t* ny, double* dR_max) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!c->tab_arr) return fail(STEPS_ENOSURROGATE, "no correction table is built");
+  if (nx) *nx = c->tab_nx;
+  if (ny) *ny = c->tab_ny;
+  if (dR_max) *dR_max = c->tab_dR_max;
+  if (out) {
+    DeviceGuard guard(c->dev);
+    CK(cudaMemcpy2DFromArrayAsync(out, sizeof(float2) * c->tab_nx, c->tab_arr, 0, 0, sizeof(float2) * c->tab_nx,
+                                  c->tab_ny, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  return STEPS_OK;
+}
+
+int steps_cyl_check_tail(steps_cyl_ctx* c, int32_t tail, int32_t check_particles, double* report) {
+  g_last_error.clear();
+  if (!c || !report || check_particles < 1) return fail(STEPS_EINVAL, "bad arguments");
+  if (tail == STEPS_TAIL_SURROGATE) return steps_cyl_check_surrogate(c, check_particles, report);
+  if (tail != STEPS_TAIL_TABLE) return fail(STEPS_EINVAL, "bad tail mode");
+  if (!c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
+  DeviceGuard guard(c->dev);
+  return run_check(c, STEPS_TAIL_TABLE, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check,
+                   &report[0], &report[1], &report[2], &report[3]);
 }
 
 

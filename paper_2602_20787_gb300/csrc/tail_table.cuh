@@ -1,0 +1,162 @@
+// Correction-table tail (arXiv 2602.20787, Sect. 2.3, eq.
+// S1R2EwaldCorrectionTable). The paper tabulates the force of the periodic
+// images beyond the nearest on an equally spaced (rho, z) grid and adds it,
+// read with cloud-in-cell interpolation, to the nearest-image force. Here the
+// same table is stated for the windowed sum of eq. ForceCylindrical: the images
+// beyond the near range |k| <= n0, for point masses, as the residual of that
+// tail over the continuum base in envelope units,
+//   r = ((SR - BR) / ER, (SZ - BZ) / EZ)   at dz = +|dz| (SZ is odd in dz),
+// at nodes dR_i = i dR_max / (nx - 1), |dz|_j = j / (2 (ny - 1)). The residual
+// is smooth (every tail image is at least n0 + 1/2 away), so a coarse table
+// read bilinearly is far more accurate than FP32 force arithmetic.
+//
+// The pair kernel is the surrogate kernel with the network replaced by one
+// texture fetch: the texture unit's bilinear filter is the cloud-in-cell
+// read. The near images, the base, the envelope and the exact spline
+// correction of softened tail images are those of surrogate_pair.cuh.
+#pragma once
+#include <cstdint>
+
+#include "surrogate_pair.cuh"
+#include "surrogate_train.cuh"
+
+namespace steps {
+
+// Node residuals in FP64 (exact point-mass tail, dz = +|dz|), stored as float2
+// [ny][nx].
+static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cut, int n0, float2* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny; q += gridDim.x * blockDim.x) {
+    const int i = q % nx, j = q / nx;
+    const double dR = dR_max * i / (nx - 1), adz = 0.5 * j / (ny - 1), R2 = dR * dR;
+    double sr = 0.0, sz = 0.0;
+    for (int k = n0 + 1; k <= n_cut + 1; ++k) {
+      const double op = adz + (double)k, om = adz - (double)k;
+      if (fabs(op) < (double)n_cut) {
+        const double ri = 1.0 / sqrt(R2 + op * op), f = ri * ri * ri;
+        sr += f;
+        sz += op * f;
+      }
+      if (fabs(om) < (double)n_cut) {
+        const double ri = 1.0 / sqrt(R2 + om * om), f = ri * ri * ri;
+        sr += f;
+        sz += om * f;
+      }
+    }
+    double BR, BZ, ER, EZ;
+    tail_base_fp64(dR, adz, n_cut, n0, BR, BZ, ER, EZ);
+    out[q] = make_float2((float)((sr - BR) / ER), (float)((sz - BZ) / EZ));
+  }
+}
+
+// Texture of the residual table and the map from the network-input scaling
+// u = 2 min(dR, dR_max)/dR_max - 1, 4|dz| - 1 to texel coordinates (texel
+// centres at index + 1/2): x = (u0 + 1) (nx - 1)/2 + 1/2.
+struct TableTail {
+  cudaTextureObject_t tex;
+  float hx, hy;  // (nx - 1) / 2, (ny - 1) / 2
+};
+
+__device__ __forceinline__ float2 table_read(const TableTail& T, float u0, float u1) {
+  return tex2D<float2>(T.tex, fmaf(u0, T.hx, T.hx + 0.5f), fmaf(u1, T.hy, T.hy + 0.5f));
+}
+
+// All pairs of i with the kBJ j of a (padded) tile with the table tail. S holds
+// mu = 0, sc = 1 (the table stores raw residuals) and the table's dR_max.
+template <bool KAHAN>
+__device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4* sA, const float4* sB, int self,
+                                                int n_cut, const SurrConst& S, const TableTail& T, float& sx,
+                                                float& sy, float& sz, float& cx, float& cy, float& cz) {
+#pragma unroll 1
+  for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll 2
+    for (int k = k0; k < k0 + STEPS_KAHAN_GROUP; ++k) {
+      const float4 A = sA[k];
+      const float4 B = sB[k];
+      float dx, dy, dz, dR2, hh;
+      int kw;
+      pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
+      SurrPair P;
+      surr_stage_a(dR2, dz, hh, n_cut, kw, S, P);
+      const float2 r = table_read(T, P.u[0], P.u[1]);
+      float sr, szz;
+      surr_stage_c(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
+      const float mj = k == self ? 0.0f : A.w;
+      const float msr = mj * sr;
+      gx = fmaf(dx, msr, gx);
+      gy = fmaf(dy, msr, gy);
+      gz = fmaf(mj, szz, gz);
+    }
+    acc<KAHAN>(sx, cx, gx);
+    acc<KAHAN>(sy, cy, gy);
+    acc<KAHAN>(sz, cz, gz);
+  }
+}
+
+#ifndef STEPS_TABLE_MIN_BLOCKS
+#define STEPS_TABLE_MIN_BLOCKS 6  // co-resident CTAs per SM asked of the register allocator
+#endif
+
+// Stream-K kernel with the table tail (work split and partial layout of
+// pair_fp32_kernel).
+template <bool KAHAN>
+__global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
+pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
+                       int NT, int C, TableTail T, SurrConst S, double* __restrict__ part) {
+  __shared__ float4 sA[kBJ];
+  __shared__ float4 sB[kBJ];
+  const int c = blockIdx.x;
+  const long long u0 = (long long)c * U / C;
+  const long long u1 = (long long)(c + 1) * U / C;
+  long long u = u0;
+  while (u < u1) {
+    const int b = (int)(u / NT);
+    const int t0 = (int)(u % NT);
+    const int t1 = (int)min((long long)NT, (long long)t0 + (u1 - u));
+    const int i = b * kBI + threadIdx.x;
+    const IParticle I = load_i(jA, jB, min(i, n - 1));
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    for (int t = t0; t < t1; ++t) {
+      __syncthreads();
+      load_tile(jA, jB, n, t, sA, sB);
+      __syncthreads();
+      pair_tile_table<KAHAN>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
+    }
+    double* dst = part + ((long long)b + c) * 3 * kBI;
+    dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
+    dst[kBI + threadIdx.x] = (double)sy - (KAHAN ? (double)cy : 0.0);
+    dst[2 * kBI + threadIdx.x] = (double)sz - (KAHAN ? (double)cz : 0.0);
+    u += t1 - t0;
+  }
+}
+
+// Subset kernel of the table form (acceptance checks; the layout of
+// pair_fp32_subset_kernel).
+template <bool KAHAN>
+__global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
+pair_fp32_table_subset_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut,
+                              const int64_t* __restrict__ idx, int ni, int tpc, TableTail T, SurrConst S,
+                              double* __restrict__ part) {
+  __shared__ float4 sA[kBJ];
+  __shared__ float4 sB[kBJ];
+  const int q = blockIdx.x * kBI + threadIdx.x;
+  const int i = (int)idx[min(q, ni - 1)];
+  const IParticle I = load_i(jA, jB, i);
+  const int NT = (n + kBJ - 1) / kBJ;
+  const int t0 = blockIdx.y * tpc, t1 = min(NT, t0 + tpc);
+  float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    __syncthreads();
+    load_tile(jA, jB, n, t, sA, sB);
+    __syncthreads();
+    pair_tile_table<KAHAN>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
+  }
+  if (q < ni) {
+    double* dst = part + (long long)blockIdx.y * 3 * ni;
+    dst[q] = (double)sx - (KAHAN ? (double)cx : 0.0);
+    dst[ni + q] = (double)sy - (KAHAN ? (double)cy : 0.0);
+    dst[2 * ni + q] = (double)sz - (KAHAN ? (double)cz : 0.0);
+  }
+}
+
+}  // namespace steps

@@ -27,7 +27,7 @@ STEPS_ESURROGATE_REJECTED = -5
 STEPS_ENOSURROGATE = -6
 
 STEPS_FP64, STEPS_FP32_KAHAN, STEPS_FP32_PLAIN = 0, 1, 2
-STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE = 0, 1
+STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE, STEPS_TAIL_TABLE = 0, 1, 2
 STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE = 0, 1, 2
 
 _EXPORTS = [
@@ -37,6 +37,7 @@ _EXPORTS = [
     "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc", "steps_cyl_train_cfg_default", "steps_cyl_tail_sums",
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
+    "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
 ]
 
 STEPS_SURR_NW = 1250
@@ -118,6 +119,9 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_get_surrogate.argtypes = [p, p]
     L.steps_cyl_set_tail.argtypes = [p, i32]
     L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
+    L.steps_cyl_build_tail_table.argtypes = [p, i32, i32, d, d, d, i32, p]
+    L.steps_cyl_get_tail_table.argtypes = [p, p, p, p, p]
+    L.steps_cyl_check_tail.argtypes = [p, i32, i32, p]
     L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
     L.steps_cyl_resume.argtypes = [ctypes.POINTER(p), ctypes.c_char_p, i32, p]
     for name in _EXPORTS:
@@ -344,6 +348,31 @@ def steps_cyl_set_tail(ctx, tail: int):
 def steps_cyl_check_surrogate(ctx, check_particles: int = 1024) -> np.ndarray:
     rep = np.zeros(4)
     _check(load().steps_cyl_check_surrogate(ctx, int(check_particles), _ptr(rep)))
+    return rep
+
+
+def steps_cyl_build_tail_table(ctx, nx: int = 257, ny: int = 33, dR_max: float = 0.0, err_median: float = 1e-5,
+                               err_p999: float = 1e-3, check_particles: int = 1024) -> np.ndarray:
+    """Build and check the correction-table tail; returns the report (median,
+    p99.9, accepted, build ms). Raises StepsError when the check rejects it."""
+    rep = np.zeros(4)
+    _check(load().steps_cyl_build_tail_table(ctx, int(nx), int(ny), float(dR_max), float(err_median),
+                                             float(err_p999), int(check_particles), _ptr(rep)))
+    return rep
+
+
+def steps_cyl_get_tail_table(ctx):
+    """The table as (ny, nx, 2) float32 residuals, and its dR_max."""
+    nx, ny, dm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().steps_cyl_get_tail_table(ctx, None, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(dm)))
+    out = np.zeros((ny.value, nx.value, 2), dtype=np.float32)
+    _check(load().steps_cyl_get_tail_table(ctx, _ptr(out), None, None, None))
+    return out, dm.value
+
+
+def steps_cyl_check_tail(ctx, tail: int, check_particles: int = 1024) -> np.ndarray:
+    rep = np.zeros(4)
+    _check(load().steps_cyl_check_tail(ctx, int(tail), int(check_particles), _ptr(rep)))
     return rep
 
 

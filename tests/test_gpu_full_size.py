@@ -73,4 +73,11 @@ def test_full_size_surrogate(sc):
     med, _, mx = stats(a[sub], ref)
     print(f"N=2^20 learned tail vs oracle surrogate form: median {med:.2e} max {mx:.2e}")
     assert med <= 2e-6 and mx <= 1e-4
+    # the correction-table tail on the same particles
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
+    sc.steps_cyl_build_tail_table(sim.ctx, 257, 33)
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+    med, p999, _ = stats(sim.forces()[idx], exact)
+    print(f"N=2^20 table tail vs exact: median {med:.2e} p99.9 {p999:.2e}")
+    assert med <= 1e-5 and p999 <= 1e-3
     sim.close()

@@ -56,14 +56,20 @@ extern "C" {
 #define STEPS_BG_OFF 0       /* no background term */
 #define STEPS_BG_FINITE 1    /* eq. F_horiz: cylinder of radius R_sim and height 2 Ncut L */
 #define STEPS_BG_INFINITE 2  /* eq. F_horiz_infty inside R_sim, line-mass field outside */
+#define STEPS_BG_SPHERE 3    /* R^3 topology: the radial term +(4 pi G / 3) rho_bar x of Sect. 2.1 */
+
+#define STEPS_TOPO_S1R2 0  /* compact z axis of period L: eq. ForceCylindrical (the default) */
+#define STEPS_TOPO_R3 1    /* no compact axis: the softened Newtonian pair force of eq. NewtonianForce,
+                            * no images, z unbounded; background STEPS_BG_OFF or STEPS_BG_SPHERE */
 
 typedef struct steps_cyl_ctx steps_cyl_ctx; /* opaque; owned by the library until steps_cyl_free */
 
 typedef struct {
-  double G;         /* gravitational constant (> 0) */
+  double G;         /* gravitational constant (!= 0; G < 0 is the repulsive gravity of glass making, Sect. 3.1) */
   double L;         /* period L_z of the compact axis (> 0) */
   double R_sim;     /* radius of the simulated cylinder used by the background term (> 0) */
-  double rho_bar;   /* comoving mean density of the background term; 0 means sum(m) / (pi R_sim^2 L) */
+  double rho_bar;   /* comoving mean density of the background term; 0 means sum(m) / (pi R_sim^2 L), or
+                     * sum(m) / (4 pi R_sim^3 / 3) in the R^3 topology */
   int32_t n_cut;    /* image cut-off Ncut of eq. ForceCylindrical, 1 <= n_cut <= 4096 */
   int32_t n0;       /* surrogate near range: images |k| <= n0 summed directly, 1 <= n0 < n_cut */
   int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
@@ -77,10 +83,12 @@ typedef struct {
   int32_t reorder_every; /* particles are kept in a Morton order of (x, y) inside the library (results are
                           * returned in the caller's order); it is rebuilt at init, by set_state, and every
                           * reorder_every KDK steps (0: never during stepping; -1: keep the caller's order) */
-  int32_t check_every;   /* with the surrogate tail: every check_every KDK steps the surrogate forces of a
-                          * particle sample are compared with the plain image sum; above the bounds the
-                          * context falls back to the plain sum (0: no periodic check) */
+  int32_t check_every;   /* with a modelled tail (surrogate or table): every check_every KDK steps its forces
+                          * on a particle sample are compared with the plain image sum; above the bounds
+                          * the context falls back to the plain sum (0: no periodic check) */
   int32_t check_particles; /* size of that sample (default 1024) */
+  int32_t topology; /* STEPS_TOPO_S1R2 | STEPS_TOPO_R3 (R^3: n_cut is not used, tail must be STEPS_TAIL_FULL) */
+  int32_t reserved; /* 0 */
   void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
 } steps_cyl_params;
 

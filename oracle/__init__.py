@@ -95,6 +95,11 @@ def lib():
         L.or_kdk_factors.restype = None
         L.or_kdk.argtypes = [i64, p, p, p, p, p, p, p, p, d, d, i32, d, d, i32,
                              ctypes.POINTER(Cosmo), p, p, d, i32]
+        L.or_kdk_topo.argtypes = [i64, p, p, p, p, p, p, p, p, d, d, i32, d, d, i32, i32,
+                                  ctypes.POINTER(Cosmo), p, p, d, i32]
+        L.or_kdk_topo.restype = ctypes.c_int
+        L.or_pair_field_r3.argtypes = [i64, p, p, p, p, p, d, i64, p, p, p, p]; L.or_pair_field_r3.restype = None
+        L.or_background_sphere.argtypes = [i64, p, p, p, d, d, p, p, p]; L.or_background_sphere.restype = None
         L.or_kdk.restype = ctypes.c_int
         L.or_tail_sums.argtypes = [d, d, d, d, i32, i32, p, p]; L.or_tail_sums.restype = None
         L.or_mlp_forward.argtypes = [p, p, p]; L.or_mlp_forward.restype = None
@@ -217,15 +222,16 @@ def kdk_factors(c: Cosmo, a: float, dt: float):
     return tuple(float(v) for v in out)
 
 
-def kdk(pos, vel_p, m, h, G, L, n_cut, R_bg, rho0, background, c: Cosmo, a, t, dt, nsteps):
-    """KDK leapfrog (Sect. 2.1) on canonical momenta p = a^2 dx/dt. Returns (pos, p, a, t)."""
+def kdk(pos, vel_p, m, h, G, L, n_cut, R_bg, rho0, background, c: Cosmo, a, t, dt, nsteps, topology=0):
+    """KDK leapfrog (Sect. 2.1) on canonical momenta p = a^2 dx/dt. Returns (pos, p, a, t).
+    topology 0: S1xR2 (z wrapped); 1: R^3 (background 0 or 3 = the radial sphere term)."""
     x, y, z = (_f64(pos[:, k]).copy() for k in range(3))
     px, py, pz = (_f64(vel_p[:, k]).copy() for k in range(3))
     m = _f64(m); h = _f64(h)
     a_ = ctypes.c_double(a); t_ = ctypes.c_double(t)
-    rc = lib().or_kdk(x.shape[0], _ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py), _ptr(pz), _ptr(m), _ptr(h),
-                      float(G), float(L), int(n_cut), float(R_bg), float(rho0), int(background),
-                      ctypes.byref(c), ctypes.byref(a_), ctypes.byref(t_), float(dt), int(nsteps))
+    rc = lib().or_kdk_topo(x.shape[0], _ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py), _ptr(pz), _ptr(m), _ptr(h),
+                           float(G), float(L), int(n_cut), float(R_bg), float(rho0), int(background), int(topology),
+                           ctypes.byref(c), ctypes.byref(a_), ctypes.byref(t_), float(dt), int(nsteps))
     if rc != 0:
         raise MemoryError("oracle KDK allocation failed")
     return np.stack([x, y, z], 1), np.stack([px, py, pz], 1), a_.value, t_.value
@@ -352,4 +358,29 @@ def pair_field_table(pos, m, h, G, L, tab, cfg, idx=None):
     gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
     lib().or_pair_field_table(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), _ptr(tab),
                               ctypes.byref(cfg), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)
+
+
+def pair_field_r3(pos, m, h, G, idx=None):
+    """R^3 pair field (eq. NewtonianForce, no images) per particle (or the listed ones)."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], _ptr(idx)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    lib().or_pair_field_r3(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), ni, ip, _ptr(gx), _ptr(gy),
+                           _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)
+
+
+def background_sphere(pos, G, rho0):
+    """The R^3 radial term +(4 pi G / 3) rho0 x."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    n = x.shape[0]
+    gx, gy, gz = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().or_background_sphere(n, _ptr(x), _ptr(y), _ptr(z), float(G), float(rho0), _ptr(gx), _ptr(gy), _ptr(gz))
     return np.stack([gx, gy, gz], axis=1)

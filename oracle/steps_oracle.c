@@ -246,11 +246,59 @@ void or_kdk_factors(const or_cosmo* c, double a, double dt, double* K1, double* 
   *a_next = y2[0];
 }
 
+/* ---------------------------------------------------------------------------
+ * R^3 topology (Sect. 2.1, eq. NewtonianForce): the softened Newtonian pair
+ * force with no periodic images, g_i = -G sum_{j != i} m_j F(|r|, h_i + h_j) r/|r|
+ * with r = x_i - x_j, and the radial term +(4 pi G / 3) rho0 x that keeps a
+ * comoving homogeneous ball from collapsing (read, like the cylinder's term,
+ * with the same 1/a^3 as the pair term).
+ * ------------------------------------------------------------------------- */
+void or_pair_field_r3(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                      const double* h, double G, int64_t ni, const int64_t* idx, double* gx, double* gy,
+                      double* gz) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < ni; ++q) {
+    int64_t i = idx ? idx[q] : q;
+    or_sum sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double rx = x[i] - x[j], ry = y[i] - y[j], rz = z[i] - z[j];
+      double r = sqrt(rx * rx + ry * ry + rz * rz);
+      double f = -G * m[j] * or_spline_F_over_r(r, h[i] + h[j]);
+      or_add(&sx, f * rx);
+      or_add(&sy, f * ry);
+      or_add(&sz, f * rz);
+    }
+    gx[q] = sx.s + sx.c;
+    gy[q] = sy.s + sy.c;
+    gz[q] = sz.s + sz.c;
+  }
+}
+
+void or_background_sphere(int64_t ni, const double* x, const double* y, const double* z, double G, double rho0,
+                          double* gx, double* gy, double* gz) {
+  double c = 4.0 * OR_PI * G * rho0 / 3.0;
+  for (int64_t i = 0; i < ni; ++i) {
+    gx[i] = c * x[i];
+    gy[i] = c * y[i];
+    gz[i] = c * z[i];
+  }
+}
+
 /* Total comoving field g = a^3 (pair + background) at the current positions. */
 static void or_total_field(int64_t n, const double* x, const double* y, const double* z,
                            const double* m, const double* h, double G, double L, int32_t n_cut,
-                           double R_bg, double rho0, int32_t background, double* gx, double* gy,
-                           double* gz) {
+                           double R_bg, double rho0, int32_t background, int32_t topology, double* gx,
+                           double* gy, double* gz) {
+  if (topology == 1) {
+    or_pair_field_r3(n, x, y, z, m, h, G, n, NULL, gx, gy, gz);
+    if (background != 3) return;
+    double* b = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    or_background_sphere(n, x, y, z, G, rho0, b, b + n, b + 2 * n);
+    for (int64_t i = 0; i < n; ++i) { gx[i] += b[i]; gy[i] += b[n + i]; gz[i] += b[2 * n + i]; }
+    free(b);
+    return;
+  }
   or_pair_field(n, x, y, z, m, h, G, L, n_cut, n, NULL, gx, gy, gz);
   if (background == 0) return;
   double* bx = (double*)malloc(sizeof(double) * (size_t)n);
@@ -273,31 +321,41 @@ static void or_total_field(int64_t n, const double* x, const double* y, const do
 }
 
 /* KDK leapfrog in cosmic time on (x, p), p = a^2 dx/dt. z is kept in [0, L). */
-int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
-           const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
-           double rho0, int32_t background, const or_cosmo* c, double* a, double* t, double dt,
-           int32_t nsteps) {
+int or_kdk_topo(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
+                const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
+                double rho0, int32_t background, int32_t topology, const or_cosmo* c, double* a, double* t,
+                double dt, int32_t nsteps) {
   double* gx = (double*)malloc(sizeof(double) * (size_t)n);
   double* gy = (double*)malloc(sizeof(double) * (size_t)n);
   double* gz = (double*)malloc(sizeof(double) * (size_t)n);
   if (!gx || !gy || !gz) { free(gx); free(gy); free(gz); return -1; }
-  or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, gx, gy, gz);
+  or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, topology, gx, gy, gz);
   for (int32_t s = 0; s < nsteps; ++s) {
     double K1, D, K2, an;
     or_kdk_factors(c, *a, dt, &K1, &D, &K2, &an);
     for (int64_t i = 0; i < n; ++i) {
       px[i] += gx[i] * K1; py[i] += gy[i] * K1; pz[i] += gz[i] * K1;
       x[i] += px[i] * D; y[i] += py[i] * D; z[i] += pz[i] * D;
-      z[i] -= L * floor(z[i] / L);
-      if (z[i] >= L) z[i] -= L; /* floor rounding can leave z == L */
+      if (topology == 0) {
+        z[i] -= L * floor(z[i] / L);
+        if (z[i] >= L) z[i] -= L; /* floor rounding can leave z == L */
+      }
     }
-    or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, gx, gy, gz);
+    or_total_field(n, x, y, z, m, h, G, L, n_cut, R_bg, rho0, background, topology, gx, gy, gz);
     for (int64_t i = 0; i < n; ++i) { px[i] += gx[i] * K2; py[i] += gy[i] * K2; pz[i] += gz[i] * K2; }
     *a = an;
     *t += dt;
   }
   free(gx); free(gy); free(gz);
   return 0;
+}
+
+int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
+           const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
+           double rho0, int32_t background, const or_cosmo* c, double* a, double* t, double dt,
+           int32_t nsteps) {
+  return or_kdk_topo(n, x, y, z, px, py, pz, m, h, G, L, n_cut, R_bg, rho0, background, 0, c, a, t, dt,
+                     nsteps);
 }
 
 /* ---------------------------------------------------------------------------

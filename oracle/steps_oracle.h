@@ -49,6 +49,17 @@ int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, d
            const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
            double rho0, int32_t background, const or_cosmo* c, double* a, double* t, double dt,
            int32_t nsteps);
+/* R^3 topology (eq. NewtonianForce, no images) and its radial background term. */
+void or_pair_field_r3(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                      const double* h, double G, int64_t ni, const int64_t* idx, double* gx, double* gy,
+                      double* gz);
+void or_background_sphere(int64_t ni, const double* x, const double* y, const double* z, double G, double rho0,
+                          double* gx, double* gy, double* gz);
+/* or_kdk with a topology: 0 = S1xR2 (z wrapped into [0, L)), 1 = R^3 (background 0 or 3 = sphere). */
+int or_kdk_topo(int64_t n, double* x, double* y, double* z, double* px, double* py, double* pz,
+                const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
+                double rho0, int32_t background, int32_t topology, const or_cosmo* c, double* a, double* t,
+                double dt, int32_t nsteps);
 void or_tail_sums(double dR, double dzw, double h, double L, int32_t n_cut, int32_t n0, double* SR,
                   double* Sz);
 void or_mlp_forward(const double* w, const double* u, double* y);

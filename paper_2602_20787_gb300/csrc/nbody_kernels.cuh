@@ -37,7 +37,7 @@ static __global__ void pack_kernel(const double* __restrict__ x, const double* _
 // -2 pi G rho0 R^2 / rho outside) and dF the smooth finite-height remainder,
 // tabulated on a uniform grid (nodes -1 .. K+2) and read with 4-point Lagrange.
 struct BgParams {
-  int mode;            // STEPS_BG_*
+  int mode;            // STEPS_BG_* (3: the R^3 radial term +(4 pi G / 3) rho0 x)
   double two_pi_G_rho0;
   double R;
   const double* tab;   // dF at rho_k = k * dr, k = -1 .. K+2 (tab[0] is k = -1)
@@ -67,13 +67,33 @@ __device__ __forceinline__ double background_F(const BgParams& bg, double rho, i
   return F;
 }
 
+// The background term of particle (x, y, z) added to g (comoving field, a^3
+// times the acceleration): the cylinder's F_h(rho) along -rho_hat (S1xR2), or
+// the R^3 radial term +(4 pi G / 3) rho0 x = (2/3) (2 pi G rho0) x.
+__device__ __forceinline__ void add_background(const BgParams& bg, double xi, double yi, double zi, double& g0,
+                                               double& g1, double& g2, int* err) {
+  if (bg.mode == 3) {
+    const double c = bg.two_pi_G_rho0 * (2.0 / 3.0);
+    g0 += c * xi;
+    g1 += c * yi;
+    g2 += c * zi;
+    return;
+  }
+  const double rho = sqrt(xi * xi + yi * yi);
+  if (rho > 0.0 && bg.mode != 0) {
+    const double F = background_F(bg, rho, err);
+    g0 -= F * xi / rho;
+    g1 -= F * yi / rho;
+  }
+}
+
 // Sum the stream-K partials of each i in CTA order (or read direct sums when
 // NT == 0), scale to the comoving field
 // g = a^3 (pair + background), store it, optionally kick p += g K and optionally
 // write a = g / a^3 to an output.
 static __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
                                 double pair_scale, BgParams bg, const double* __restrict__ x,
-                                const double* __restrict__ y, double* __restrict__ gx,
+                                const double* __restrict__ y, const double* __restrict__ z, double* __restrict__ gx,
                                 double* __restrict__ gy, double* __restrict__ gz, double K,
                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
                                 double inv_a3, double* __restrict__ ox, double* __restrict__ oy,
@@ -98,13 +118,7 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
     }
   }
   double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
-  const double xi = x[i], yi = y[i];
-  const double rho = sqrt(xi * xi + yi * yi);
-  if (rho > 0.0 && bg.mode != 0) {
-    const double F = background_F(bg, rho, err);
-    g0 -= F * xi / rho;
-    g1 -= F * yi / rho;
-  }
+  add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
   if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
   gx[i] = g0; gy[i] = g1; gz[i] = g2;
   if (px) {
@@ -127,15 +141,17 @@ static __global__ void kick_drift_pack_kernel(double* __restrict__ x, double* __
                                        const double* __restrict__ gz, const double* __restrict__ m,
                                        const double* __restrict__ h, int n, double K1, double D, double L,
                                        double invL, float4* __restrict__ jA, float4* __restrict__ jB,
-                                       int* __restrict__ err) {
+                                       int* __restrict__ err, int wrap) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double qx = px[i] + gx[i] * K1, qy = py[i] + gy[i] * K1, qz = pz[i] + gz[i] * K1;
     px[i] = qx; py[i] = qy; pz[i] = qz;
     const double nx = x[i] + qx * D, ny = y[i] + qy * D;
     double nz = z[i] + qz * D;
-    nz -= L * floor(nz * invL);
-    if (nz >= L) nz -= L;
-    if (nz < 0.0) nz = 0.0;
+    if (wrap) {  // S1xR2: z into [0, L)
+      nz -= L * floor(nz * invL);
+      if (nz >= L) nz -= L;
+      if (nz < 0.0) nz = 0.0;
+    }
     if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(err, kErrNonFinite);
     x[i] = nx; y[i] = ny; z[i] = nz;
     pack_one(nx, ny, nz, m[i], h[i], i, invL, jA, jB);
@@ -236,7 +252,8 @@ __device__ __forceinline__ void image_fp64(double dR2, double o, double hh, doub
 static __global__ void __launch_bounds__(128)
 pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
                  const double* __restrict__ m, const double* __restrict__ h, int n,
-                 const int64_t* __restrict__ idx, int ni, double invL, int n_cut, int tpc, double* __restrict__ part) {
+                 const int64_t* __restrict__ idx, int ni, double invL, int n_cut, int tpc, double* __restrict__ part,
+                 int r3) {
   __shared__ double sx[128], sy[128], sz[128], sm[128], sh[128];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int qq = min(q, ni - 1);
@@ -261,12 +278,12 @@ pair_fp64_kernel(const double* __restrict__ x, const double* __restrict__ y, con
       if (t * 128 + k == i) continue;
       const double dx = xi - sx[k], dy = yi - sy[k];
       double dz = zi - sz[k];
-      dz -= rint(dz);
+      if (!r3) dz -= rint(dz);  // R^3: no period, the centre image alone (n_cut = 1, no edge)
       const double dR2 = dx * dx + dy * dy;
       const double hh = hi + sh[k], hh2 = hh * hh;
       double sr = 0.0, szz = 0.0;
       image_fp64(dR2, dz, hh, hh2, 1.0, sr, szz);
-      image_fp64(dR2, dz - copysign((double)n_cut, dz), hh, hh2, dz != 0.0 ? 1.0 : 0.0, sr, szz);
+      if (!r3) image_fp64(dR2, dz - copysign((double)n_cut, dz), hh, hh2, dz != 0.0 ? 1.0 : 0.0, sr, szz);
       for (int kk = 1; kk < n_cut; ++kk) {
         image_fp64(dR2, dz + (double)kk, hh, hh2, 1.0, sr, szz);
         image_fp64(dR2, dz - (double)kk, hh, hh2, 1.0, sr, szz);
@@ -304,19 +321,14 @@ static __global__ void chunk_sum_kernel(const double* __restrict__ part, int ni,
 // out3 (SoA, ni each) = pair_scale * pair + background at the listed i, / a^3
 static __global__ void subset_finalize_kernel(const double* __restrict__ pairsum, int ni, const int64_t* __restrict__ idx,
                                        double pair_scale, BgParams bg, const double* __restrict__ x,
-                                       const double* __restrict__ y, double inv_a3, double* __restrict__ ox,
-                                       double* __restrict__ oy, double* __restrict__ oz, int* __restrict__ err) {
+                                       const double* __restrict__ y, const double* __restrict__ z, double inv_a3,
+                                       double* __restrict__ ox, double* __restrict__ oy, double* __restrict__ oz,
+                                       int* __restrict__ err) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ni) return;
   const int i = idx ? (int)idx[q] : q;
   double g0 = pair_scale * pairsum[q], g1 = pair_scale * pairsum[ni + q], g2 = pair_scale * pairsum[2 * ni + q];
-  const double xi = x[i], yi = y[i];
-  const double rho = sqrt(xi * xi + yi * yi);
-  if (rho > 0.0 && bg.mode != 0) {
-    const double F = background_F(bg, rho, err);
-    g0 -= F * xi / rho;
-    g1 -= F * yi / rho;
-  }
+  add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
   if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
   ox[q] = g0 * inv_a3;
   oy[q] = g1 * inv_a3;

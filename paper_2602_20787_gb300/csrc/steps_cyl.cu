@@ -263,9 +263,22 @@ BgParams bg_params(const steps_cyl_ctx* c) {
   return b;
 }
 
+bool is_r3(const steps_cyl_ctx* c) { return c->p.topology == STEPS_TOPO_R3; }
+// Images per pair: the window's 2 Ncut (S1xR2), the one image of R^3.
+double images_per_pair(const steps_cyl_ctx* c) { return is_r3(c) ? 1.0 : 2.0 * c->p.n_cut; }
+int n_cut_eff(const steps_cyl_ctx* c) { return is_r3(c) ? 1 : c->p.n_cut; }
+
 int check_params(const steps_cyl_params* p) {
   if (!p) return fail(STEPS_EINVAL, "params is NULL");
-  if (!(p->G > 0) || !std::isfinite(p->G)) return fail(STEPS_EINVAL, "G must be finite and > 0");
+  if (!(p->G != 0) || !std::isfinite(p->G)) return fail(STEPS_EINVAL, "G must be finite and != 0");
+  if (p->topology != STEPS_TOPO_S1R2 && p->topology != STEPS_TOPO_R3) return fail(STEPS_EINVAL, "bad topology");
+  if (p->reserved != 0) return fail(STEPS_EINVAL, "reserved must be 0");
+  if (p->topology == STEPS_TOPO_R3 && p->tail != STEPS_TAIL_FULL)
+    return fail(STEPS_EINVAL, "the R^3 topology has no image tail (tail must be STEPS_TAIL_FULL)");
+  if (p->topology == STEPS_TOPO_R3 && p->background != STEPS_BG_OFF && p->background != STEPS_BG_SPHERE)
+    return fail(STEPS_EINVAL, "the R^3 topology takes STEPS_BG_OFF or STEPS_BG_SPHERE");
+  if (p->topology == STEPS_TOPO_S1R2 && p->background == STEPS_BG_SPHERE)
+    return fail(STEPS_EINVAL, "STEPS_BG_SPHERE belongs to the R^3 topology");
   if (!(p->L > 0) || !std::isfinite(p->L)) return fail(STEPS_EINVAL, "L must be finite and > 0");
   if (!(p->R_sim > 0) || !std::isfinite(p->R_sim)) return fail(STEPS_EINVAL, "R_sim must be finite and > 0");
   if (!(p->rho_bar >= 0) || !std::isfinite(p->rho_bar)) return fail(STEPS_EINVAL, "rho_bar must be >= 0");
@@ -275,7 +288,7 @@ int check_params(const steps_cyl_params* p) {
     return fail(STEPS_EINVAL, "bad tail mode");
   if (p->tail != STEPS_TAIL_FULL && (p->n0 < 1 || p->n0 >= p->n_cut))
     return fail(STEPS_EINVAL, "n0 must be in [1, n_cut)");
-  if (p->background < STEPS_BG_OFF || p->background > STEPS_BG_INFINITE) return fail(STEPS_EINVAL, "bad background");
+  if (p->background < STEPS_BG_OFF || p->background > STEPS_BG_SPHERE) return fail(STEPS_EINVAL, "bad background");
   if (p->comoving) {
     if (!(p->H0 > 0) || !(p->a_start > 0)) return fail(STEPS_EINVAL, "comoving runs need H0 > 0 and a_start > 0");
   }
@@ -297,7 +310,7 @@ __global__ void validate_kernel(const double* __restrict__ x, const double* __re
       b |= 1;
     if (!(m[i] > 0.0) || !isfinite(m[i])) b |= 2;
     if (!(h[i] > 0.0) || !isfinite(h[i])) b |= 4;
-    if (!(z[i] >= 0.0 && z[i] < L)) b |= 8;
+    if (L > 0.0 && !(z[i] >= 0.0 && z[i] < L)) b |= 8;  // S1xR2 only (L = 0: no period)
     if (b) atomicOr(bad, b);
   }
 }
@@ -493,8 +506,8 @@ int launch_fp64(steps_cyl_ctx* c, const int64_t* idx, int ni, double* out) {
     CK(cudaMalloc(&c->chk, sizeof(double) * (size_t)JC * 3 * ni));
     c->chk_elems = (size_t)JC * 3 * ni;
   }
-  pair_fp64_kernel<<<dim3(gx, JC), 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, idx, ni, c->invL, c->p.n_cut,
-                                                    tpc, c->chk);
+  pair_fp64_kernel<<<dim3(gx, JC), 128, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, idx, ni, c->invL, n_cut_eff(c),
+                                                    tpc, c->chk, is_r3(c) ? 1 : 0);
   CKLAUNCH("pair_fp64");
   chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(c->chk, ni, JC, out);
   CKLAUNCH("chunk_sum");
@@ -526,6 +539,12 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
       pair_fp32_table_kernel<false><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
                                                                c->tab, c->tab_const, c->part);
     CKLAUNCH("pair_fp32_table");
+  } else if (is_r3(c)) {
+    if (c->p.precision == STEPS_FP32_KAHAN)
+      pair_fp32_kernel<true, true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 1, c->U, c->NT, c->C, c->part);
+    else
+      pair_fp32_kernel<false, true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 1, c->U, c->NT, c->C, c->part);
+    CKLAUNCH("pair_fp32_r3");
   } else if (c->p.precision == STEPS_FP32_KAHAN) {
     pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);
     CKLAUNCH("pair_fp32_kahan");
@@ -535,14 +554,14 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   }
   CK(cudaEventRecord(c->e1, c->st));
   c->timed = true;
-  c->last_images = (double)c->n * (double)(c->n - 1) * 2.0 * c->p.n_cut;
+  c->last_images = (double)c->n * (double)(c->n - 1) * images_per_pair(c);
   const int NT = c->p.precision == STEPS_FP64 ? 0 : c->NT;
   const bool fp32 = c->p.precision != STEPS_FP64;
   const int ctas = fp32 && c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok ? c->SC
                    : fp32 && c->p.tail == STEPS_TAIL_TABLE && c->tab_ok    ? c->TC
                                                                             : c->C;
   finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
-      c->part, c->n, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->gx, c->gy, c->gz, K,
+      c->part, c->n, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
       kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
   CKLAUNCH("finalize");
   return STEPS_OK;
@@ -586,7 +605,7 @@ int install_state(steps_cyl_ctx* c, const double* vx, const double* vy, const do
 int validate_state(steps_cyl_ctx* c) {
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
   validate_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->px, c->py, c->pz, c->m, c->h, c->n,
-                                                           c->p.L, c->err);
+                                                           is_r3(c) ? 0.0 : c->p.L, c->err);
   CKLAUNCH("validate");
   int bad = 0;
   int rc = read_and_clear_err(c, &bad);
@@ -835,7 +854,8 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
     chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
     double* o = tot + (size_t)form * 3 * ni;
     subset_finalize_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(sums, ni, c->idx, pair_scale, bg_params(c), c->x,
-                                                                c->y, 1.0, o, o + ni, o + 2 * (size_t)ni, c->err);
+                                                                c->y, c->z, 1.0, o, o + ni, o + 2 * (size_t)ni,
+                                                                c->err);
     CKLAUNCH("check_finalize");
   }
   std::vector<double> h(6 * (size_t)ni);
@@ -870,6 +890,7 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
 int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999, int ncheck, double* med,
                      double* p999, bool* ok) {
   int rc;
+  if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
   if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
   bool finite = true;
   for (int k = 0; k < STEPS_SURR_NPARAM; ++k) finite = finite && std::isfinite(P[k]);
@@ -896,6 +917,7 @@ int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999
 // float2 array and read through a texture with bilinear filtering (the
 // cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius.
 int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
+  if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
   if (c->p.n0 < 1 || c->p.n0 >= c->p.n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
   if (dR_max == 0.0) {
     std::vector<double> hx(c->n), hy(c->n);
@@ -992,6 +1014,7 @@ int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* re
       cfg->dR_max < 0 || cfg->reserved != 0 || cfg->check_particles < 1)
     return fail(STEPS_EINVAL, "bad training configuration");
   const int n_cut = c->p.n_cut, n0 = c->p.n0;
+  if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
   if (n0 < 1 || n0 >= n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
   const double A = n0 + 0.5;
   double dR_max = cfg->dR_max;
@@ -1291,7 +1314,8 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
       comp = (tv - tot) - yv;
       tot = tv;
     }
-    c->rho0 = tot / (M_PI * p->R_sim * p->R_sim * p->L);
+    c->rho0 = p->topology == STEPS_TOPO_R3 ? tot / (4.0 / 3.0 * M_PI * p->R_sim * p->R_sim * p->R_sim)
+                                           : tot / (M_PI * p->R_sim * p->R_sim * p->L);
   }
   if ((rc = build_background(c))) return bail(rc);
   if ((rc = pack_positions(c))) return bail(rc);
@@ -1353,9 +1377,9 @@ int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, do
     if ((rc = launch_fp64(c, c->idx, (int)ni, c->sub))) return rc;
     CK(cudaEventRecord(c->e1, c->st));
     c->timed = true;
-    c->last_images = (double)ni * (double)(c->n - 1) * 2.0 * c->p.n_cut;
+    c->last_images = (double)ni * (double)(c->n - 1) * images_per_pair(c);
     subset_finalize_kernel<<<((int)ni + 255) / 256, 256, 0, c->st>>>(c->sub, (int)ni, c->idx, -c->p.G * c->invL * c->invL,
-                                                                     bg_params(c), c->x, c->y, inv_a3, o, o + ni,
+                                                                     bg_params(c), c->x, c->y, c->z, inv_a3, o, o + ni,
                                                                      o + 2 * ni, c->err);
     CKLAUNCH("subset_finalize");
   } else {
@@ -1390,7 +1414,7 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
       return fail(STEPS_EINVAL, "the Friedmann integration left the valid range (a = %g)", f.a_next);
     kick_drift_pack_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->px, c->py, c->pz, c->gx,
                                                                    c->gy, c->gz, c->m, c->h, c->n, f.K1, f.D, c->p.L,
-                                                                   c->invL, c->jA, c->jB, c->err);
+                                                                   c->invL, c->jA, c->jB, c->err, is_r3(c) ? 0 : 1);
     CKLAUNCH("kick_drift_pack");
     if ((rc = eval_forces(c, true, f.K2))) return rc;
     c->a = f.a_next;

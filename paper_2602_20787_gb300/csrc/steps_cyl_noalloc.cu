@@ -120,7 +120,7 @@ extern "C" int steps_cyl_pair_accel_noalloc(int64_t n, const double* x, const do
     pair_fp32_kernel<false><<<C, kBI, 0, st>>>(jA, jB, nn, n_cut, U, NT, C, part);
   BgParams off{};
   off.mode = STEPS_BG_OFF;
-  finalize_kernel<<<(nn + 255) / 256, 256, 0, st>>>(part, nn, NT, U, C, -G * invL * invL, off, x, y, ax, ay, az,
+  finalize_kernel<<<(nn + 255) / 256, 256, 0, st>>>(part, nn, NT, U, C, -G * invL * invL, off, x, y, z, ax, ay, az,
                                                     0.0, nullptr, nullptr, nullptr, 1.0, nullptr, nullptr, nullptr,
                                                     err);
   cudaError_t e = cudaGetLastError();

@@ -28,7 +28,8 @@ STEPS_ENOSURROGATE = -6
 
 STEPS_FP64, STEPS_FP32_KAHAN, STEPS_FP32_PLAIN = 0, 1, 2
 STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE, STEPS_TAIL_TABLE = 0, 1, 2
-STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE = 0, 1, 2
+STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE, STEPS_BG_SPHERE = 0, 1, 2, 3
+STEPS_TOPO_S1R2, STEPS_TOPO_R3 = 0, 1
 
 _EXPORTS = [
     "steps_cyl_params_default", "steps_cyl_init", "steps_cyl_forces", "steps_cyl_forces_subset",
@@ -63,7 +64,8 @@ class Params(ctypes.Structure):
         ("Omega_L", ctypes.c_double), ("w0", ctypes.c_double), ("wa", ctypes.c_double),
         ("a_start", ctypes.c_double), ("t_start", ctypes.c_double),
         ("device", ctypes.c_int32), ("reorder_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
-        ("check_particles", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("check_particles", ctypes.c_int32), ("topology", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
     ]
 
 
@@ -187,6 +189,7 @@ class Config:
     reorder_every: int = 32
     check_every: int = 50
     check_particles: int = 1024
+    topology: int = STEPS_TOPO_S1R2
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def to_c(self) -> Params:

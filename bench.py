@@ -358,9 +358,72 @@ def _err(a, ref):
     return {"median": float(np.median(r)), "p999": float(np.quantile(r, 0.999)), "max": float(r.max())}
 
 
+def run_r3_or_glass(args):
+    """R^3 topology (N = 65,536 ball) and glass making (repulsive comoving
+    S1xR2 run, N = 65,536): force / KDK-step timing and their checks."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    n = 65536
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * 2070e6
+    stream = torch.cuda.current_stream().cuda_stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.workload == "r3_n65536":
+        d = ics.ball_load(n, 11)
+        cfg = sc.Config(topology=sc.STEPS_TOPO_R3, n_cut=1, background=sc.STEPS_BG_SPHERE, rho_bar=d["rho_bar"],
+                        R_sim=2.0, comoving=True, a_start=0.1, t_start=ics.lcdm_time_of_a(0.1), stream=stream)
+        sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+        a32, ms = _timed_forces(sc, torch, sim, 3)
+        idx = ics.subsample(n, 256, seed=12345)
+        sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)
+        a64 = sim.forces_subset(idx)
+        sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+        pairs = n * (n - 1.0)
+        dt = 0.01 * ics.lcdm_time_of_a(0.1)
+        ev0.record()
+        sim.step(dt, 10)
+        ev1.record()
+        torch.cuda.synchronize()
+        line = {"workload": args.workload, "n": n, "topology": "R3", "images_per_pair": 1,
+                "fp32_kahan": {"pair_ms": ms, "pair_interactions_per_s": pairs / (ms * 1e-3),
+                               "fraction_of_mufu_bound": pairs / (ms * 1e-3) / peak,
+                               "error_vs_fp64": _err(a32[idx], a64)},
+                "kdk": {"steps": 10, "step_ms": ev0.elapsed_time(ev1) / 10}}
+    else:
+        w = ics.WORKLOADS["lcdm_n65536"]
+        d = ics.particle_load(n, 21, w.M_tot, rho_bar=w.rho_bar)
+        a0, t0 = 0.02, ics.lcdm_time_of_a(0.02)
+        cfg = sc.Config(G=-1.0, n_cut=16, rho_bar=w.rho_bar, comoving=True, a_start=a0, t_start=t0, stream=stream)
+        sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+
+        def rms_field():
+            _, _, a, _ = sim.state()
+            g = sim.forces() * a ** 3
+            return math.sqrt((g ** 2).sum(1).mean())
+
+        r0, t, steps, ms_tot = rms_field(), t0, 0, 0.0
+        for _ in range(5):
+            ev0.record()
+            sim.step(0.03 * t, 25)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms_tot += ev0.elapsed_time(ev1)
+            steps += 25
+            t = sim.state()[3]
+        line = {"workload": args.workload, "n": n, "topology": "S1R2", "G": -1.0, "n_cut": 16,
+                "kdk": {"steps": steps, "step_ms": ms_tot / steps, "a_end": sim.state()[2],
+                        "pair_images_per_s": n * (n - 1.0) * 32 / (ms_tot / steps * 1e-3),
+                        "rms_net_field_ratio": rms_field() / r0}}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    if args.workload in ("r3_n65536", "glass_n65536"):
+        return run_r3_or_glass(args)
     w = ics.WORKLOADS[args.workload]
     d = ics.workload_ics(w)
     n = w.n

@@ -160,6 +160,19 @@ def subsample(n: int, k: int, seed: int = 12345) -> np.ndarray:
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
 
 
+def ball_load(n: int, seed: int, R: float = 2.0):
+    """R^3 topology load: n particles uniform in a ball of radius R (units of L),
+    masses uniform in [0.5, 2] normalised to 1, softenings uniform in [0.02, 0.2];
+    returns dict(pos, vel, m, h, rho_bar) with rho_bar = 1 / (4 pi R^3 / 3)."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(n, 3))
+    pos = u / np.linalg.norm(u, axis=1)[:, None] * R * rng.uniform(0, 1, n)[:, None] ** (1.0 / 3.0)
+    m = rng.uniform(0.5, 2.0, n)
+    m /= m.sum()
+    h = rng.uniform(0.02, 0.2, n)
+    return {"pos": pos, "vel": np.zeros((n, 3)), "m": m, "h": h, "rho_bar": 1.0 / (4.0 / 3.0 * math.pi * R ** 3)}
+
+
 def tail_training_inputs(ns: int, seed: int, dR_max: float, h_max: float, L: float = L_BOX):
     """Surrogate training inputs (dR, |dz_w|, h): dR with a density that puts
     more samples near the axis, |dz_w| uniform in [0, L/2], h uniform."""

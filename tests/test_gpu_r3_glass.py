@@ -24,13 +24,8 @@ def sc():
 
 
 def ball(n, seed, R=2.0):
-    rng = np.random.default_rng(seed)
-    u = rng.normal(size=(n, 3))
-    pos = u / np.linalg.norm(u, axis=1)[:, None] * R * rng.uniform(0, 1, n)[:, None] ** (1.0 / 3.0)
-    m = rng.uniform(0.5, 2.0, n)
-    m /= m.sum()
-    h = rng.uniform(0.02, 0.2, n)
-    return pos, m, h, 1.0 / (4.0 / 3.0 * math.pi * R ** 3)
+    d = ics.ball_load(n, seed, R)
+    return d["pos"], d["m"], d["h"], d["rho_bar"]
 
 
 def r3_sim(sc, pos, m, h, rho, precision, background, **kw):

@@ -419,11 +419,59 @@ def run_r3_or_glass(args):
     return 0
 
 
+def run_inf(args):
+    """Infinite window (Ncut -> infinity, n_cut = 0) on the N = 65,536 load of
+    the learned-tail law: the correction table carries the whole image line
+    beyond the 2 n0 + 1 near images, with the infinite-cylinder background.
+    Force and KDK-step timing and the pipe roofline of the table kernel; its
+    errors are checked against the FP64 oracle in the test-suite (an infinite
+    window has no GPU FP64 form to compare with here)."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    w = ics.WORKLOADS["surrogate_n65536"]
+    d = ics.workload_ics(w)
+    n = w.n
+    pairs = n * (n - 1.0)
+    props = torch.cuda.get_device_properties(0)
+    t0, _ = ics.run_schedule(w)
+    cfg = sc.Config(n_cut=0, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_TABLE,
+                    background=sc.STEPS_BG_INFINITE, rho_bar=w.rho_bar, comoving=True, a_start=w.a_start,
+                    t_start=t0, stream=torch.cuda.current_stream().cuda_stream)
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    _, ms = _timed_forces(sc, torch, sim, 3)
+    mufu = (2 * w.n0 + 1) + 2 + 2 + 1   # near images, infinite base rsqrt/rcp, the dR rsqrt
+    peak = props.multi_processor_count * 2070e6 * MUFU_RSQRT_PER_SM_CLK / mufu
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dt = 0.01 * t0
+    ev0.record()
+    sim.step(dt, 10)
+    ev1.record()
+    torch.cuda.synchronize()
+    line = {"workload": "inf_n65536", "n": n, "n_cut": "infinite", "n0": w.n0, "background": "infinite cylinder",
+            "table": {"pair_ms": ms, "pair_interactions_per_s": pairs / (ms * 1e-3),
+                      "executed_near_images_per_pair": 2 * w.n0 + 1,
+                      "roofline": {"bound": "mufu", "mufu_ops_per_pair": mufu, "peak_pairs_per_s": peak,
+                                   "achieved_pairs_per_s": pairs / (ms * 1e-3), "frac": pairs / (ms * 1e-3) / peak},
+                      "kdk_step_ms": ev0.elapsed_time(ev1) / 10}}
+    # the learned tail trained to infinity, checked against the table form
+    rep = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+    _, mss = _timed_forces(sc, torch, sim, 3)
+    line["surrogate"] = {"train_ms": rep[5], "check_vs_table_median": rep[2], "check_vs_table_p999": rep[3],
+                         "pair_ms": mss, "pair_interactions_per_s": pairs / (mss * 1e-3),
+                         "table_speedup_over_surrogate": mss / ms}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
     if args.workload in ("r3_n65536", "glass_n65536"):
         return run_r3_or_glass(args)
+    if args.workload == "inf_n65536":
+        return run_inf(args)
     w = ics.WORKLOADS[args.workload]
     d = ics.workload_ics(w)
     n = w.n

@@ -70,8 +70,13 @@ typedef struct {
   double R_sim;     /* radius of the simulated cylinder used by the background term (> 0) */
   double rho_bar;   /* comoving mean density of the background term; 0 means sum(m) / (pi R_sim^2 L), or
                      * sum(m) / (4 pi R_sim^3 / 3) in the R^3 topology */
-  int32_t n_cut;    /* image cut-off Ncut of eq. ForceCylindrical, 1 <= n_cut <= 4096 */
-  int32_t n0;       /* surrogate near range: images |k| <= n0 summed directly, 1 <= n0 < n_cut */
+  int32_t n_cut;    /* image cut-off Ncut of eq. ForceCylindrical, 1 <= n_cut <= 4096; 0 is the
+                     * infinite window (Ncut -> infinity, Sect. 2.2): it has no plain image sum,
+                     * needs STEPS_TAIL_TABLE at init (its correction table is built there; a
+                     * surrogate trained to infinity may be selected later), an FP32 precision
+                     * and STEPS_BG_INFINITE or STEPS_BG_OFF */
+  int32_t n0;       /* near range of a modelled tail: images |k| <= n0 summed directly,
+                     * 1 <= n0 < n_cut (n0 >= 1 for the infinite window) */
   int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
   int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE | STEPS_TAIL_TABLE */
   int32_t background; /* STEPS_BG_OFF | STEPS_BG_FINITE | STEPS_BG_INFINITE */
@@ -191,6 +196,8 @@ int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg);
  * (dR, dz, h) in units of L (row-major ns x 3, |dz| <= 1/2, h > 0; host or device)
  * out[2 s], out[2 s + 1] = SR, SZ of the window images |dz + k| < n_cut with
  * |k| > n0, SR = sum F(r,h)/r and SZ = sum (dz + k) F(r,h)/r (eq. Force_spline_kernel).
+ * n_cut = 0: the infinite line, images |k| <= 512 one by one and the continuum
+ * cells beyond with their near end's Euler-Maclaurin term.
  * out: host or device, ns x 2. Synchronises the stream. */
 int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out,
                         void* stream);
@@ -205,7 +212,11 @@ int steps_cyl_mlp_loss_grad(int64_t ns, const float* w, const float* u, const fl
 /* Train the surrogate of a context on the GPU (its n_cut and n0): draw the
  * samples, compute exact FP64 targets, train with Adam, round to FP16, and
  * check the result against the plain image sum on cfg->check_particles
- * particles. report (8 doubles, may be NULL): final training loss, held-out
+ * particles. For the infinite window (n_cut = 0) the targets are the infinite
+ * line over the infinite base, and the check (here, in steps_cyl_set_surrogate,
+ * steps_cyl_check_surrogate and the KDK's periodic checks) is against the
+ * correction-table form built at init; a network dropped by a periodic check
+ * hands the tail back to that table. report (8 doubles, may be NULL): final training loss, held-out
  * RMS error (normalised units), check median, check 99.9th percentile,
  * accepted (1/0), training ms, mu[0], sc[0]. Returns STEPS_OK when accepted
  * (the context may then use STEPS_TAIL_SURROGATE) or STEPS_ESURROGATE_REJECTED. */
@@ -222,9 +233,11 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* ctx, const float* params, double err_
  * STEPS_ENOSURROGATE when none is loaded. */
 int steps_cyl_get_surrogate(steps_cyl_ctx* ctx, float* params);
 
-/* Select the tail form: STEPS_TAIL_FULL, or STEPS_TAIL_SURROGATE (requires an
- * accepted surrogate and an FP32 precision). As with steps_cyl_set_precision the
- * cached forces are refreshed by the next force evaluation or KDK step. */
+/* Select the tail form: STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE or
+ * STEPS_TAIL_TABLE (a modelled tail requires an accepted network / table and an
+ * FP32 precision; the infinite window refuses STEPS_TAIL_FULL). As with
+ * steps_cyl_set_precision the cached forces are refreshed by the next force
+ * evaluation or KDK step. */
 int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
 
 /* ---- correction-table tail -----------------------------------------------
@@ -239,10 +252,13 @@ int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
  * the GPU, stored in FP32 and read with the texture unit's bilinear filter. The
  * table form (STEPS_TAIL_TABLE) sums the near images exactly, adds
  * base + envelope x table, and corrects tail images inside the softening support
- * exactly, as the surrogate form does. */
+ * exactly, as the surrogate form does. With n_cut = 0 (the infinite window) the
+ * table holds the whole image line beyond n0, summed exactly to |k| = 512 and
+ * by Euler-Maclaurin beyond, over the base of the infinite window; no plain sum
+ * exists to check it against, so it is kept without a check. */
 
-/* Build the context's table (its n_cut and n0; 1 <= n0 < n_cut, FP32
- * precision) and compare the table form with the plain image sum on
+/* Build the context's table (its n_cut and n0; 1 <= n0 < n_cut, or n0 >= 1 for
+ * the infinite window; FP32 precision) and, for a finite window, compare the table form with the plain image sum on
  * check_particles particles; keep it when median <= err_median and 99.9th
  * percentile <= err_p999 of the relative total-force error. nx in [2, 4096], ny
  * in [2, 1024]; dR_max = 0 picks 2.2 x the largest particle radius / L. report
@@ -258,7 +274,8 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, doubl
 int steps_cyl_get_tail_table(steps_cyl_ctx* ctx, float* out, int32_t* nx, int32_t* ny, double* dR_max);
 
 /* As steps_cyl_check_surrogate for a modelled tail (STEPS_TAIL_SURROGATE or
- * STEPS_TAIL_TABLE), which must be loaded and accepted. */
+ * STEPS_TAIL_TABLE), which must be loaded and accepted. STEPS_EINVAL for the
+ * infinite window (no plain image sum exists). */
 int steps_cyl_check_tail(steps_cyl_ctx* ctx, int32_t tail, int32_t check_particles, double* report);
 
 /* Compare the surrogate form with the plain image sum now on check_particles

@@ -113,6 +113,9 @@ def lib():
         L.or_tail_surrogate.restype = None
         L.or_pair_field_surrogate.argtypes = [i64, p, p, p, p, p, d, d, p, ctypes.POINTER(SurrCfg), i64, p, p, p, p]
         L.or_pair_field_surrogate.restype = None
+        L.or_image_sums_inf.argtypes = [d, d, d, i32, p, p]; L.or_image_sums_inf.restype = None
+        L.or_pair_field_inf.argtypes = [i64, p, p, p, p, p, d, d, i64, p, p, p, p]; L.or_pair_field_inf.restype = None
+        L.or_tail_base_inf.argtypes = [d, d, i32, p, p]; L.or_tail_base_inf.restype = None
         T = ctypes.POINTER(TableCfg)
         L.or_tail_residual.argtypes = [d, d, i32, i32, p]; L.or_tail_residual.restype = None
         L.or_tail_table_build.argtypes = [T, p]; L.or_tail_table_build.restype = None
@@ -384,3 +387,32 @@ def background_sphere(pos, G, rho0):
     gx, gy, gz = np.zeros(n), np.zeros(n), np.zeros(n)
     lib().or_background_sphere(n, _ptr(x), _ptr(y), _ptr(z), float(G), float(rho0), _ptr(gx), _ptr(gy), _ptr(gz))
     return np.stack([gx, gy, gz], axis=1)
+
+
+def image_sums_inf(dR, dzw, h, n0=-1):
+    """Infinite-window image sums (SR, SZ) of the images |k| > n0 (all for n0 = -1)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_image_sums_inf(float(dR), float(dzw), float(h), int(n0), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def pair_field_inf(pos, m, h, G, L, idx=None):
+    """Pair term with the infinite window (Ncut -> infinity)."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], _ptr(idx)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    lib().or_pair_field_inf(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), ni, ip, _ptr(gx),
+                            _ptr(gy), _ptr(gz))
+    return np.stack([gx, gy, gz], axis=1)
+
+
+def tail_base_inf(dR, adz, n0):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_tail_base_inf(float(dR), float(adz), int(n0), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value

@@ -532,7 +532,10 @@ void or_surrogate_inputs(double dR, double adz, double h, int32_t n0, double dR_
 void or_tail_surrogate(double dR, double dz, double h, const double* w, const or_surr_cfg* c, double* SR,
                        double* SZ) {
   double adz = fabs(dz), BR, BZ, ER, EZ, u[3], y[2];
-  or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
+  if (c->n_cut == 0) /* the infinite window (Ncut -> infinity) */
+    or_tail_base_inf(dR, adz, c->n0, &BR, &BZ);
+  else
+    or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
   or_tail_envelope(dR, adz, c->n0, &ER, &EZ);
   or_surrogate_inputs(dR, adz, h, c->n0, c->dR_max, u);
   or_mlp_forward(w, u, y);
@@ -541,11 +544,12 @@ void or_tail_surrogate(double dR, double dz, double h, const double* w, const or
   double sg = dz > 0.0 ? 1.0 : (dz < 0.0 ? -1.0 : 0.0);
   sz *= sg;
   /* tail images inside the softening support: the surrogate is Newtonian there;
-   * replace 1/r^3 by F(r,h)/r exactly */
-  for (int k = -c->n_cut - 1; k <= c->n_cut + 1; ++k) {
+   * replace 1/r^3 by F(r,h)/r exactly (an infinite window: every k with |o| < h) */
+  int kmax = c->n_cut > 0 ? c->n_cut + 1 : (int)ceil(h) + 2;
+  for (int k = -kmax; k <= kmax; ++k) {
     if (k >= -c->n0 && k <= c->n0) continue;
     double o = dz + (double)k;
-    if (!(fabs(o) < (double)c->n_cut)) continue;
+    if (c->n_cut > 0 && !(fabs(o) < (double)c->n_cut)) continue;
     double r = sqrt(dR * dR + o * o);
     if (r >= h) continue;
     double d = or_spline_F_over_r(r, h) - 1.0 / (r * r * r);
@@ -613,6 +617,81 @@ void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const 
 }
 
 /* ---------------------------------------------------------------------------
+ * Ncut -> infinity (Sect. 2.2: the window grows without bound and the
+ * background becomes eq. F_horiz_infty): the whole periodic line of images.
+ * Images |k| <= OR_KINF are summed exactly (softened); beyond them, on each
+ * side, the continuum integral over the unit cells from K + 1/2 (Newtonian,
+ * since h << K). The midpoint rule's error there is O(f'(K)) ~ 1/(8 K^4).
+ * Returned per unit G for the images with |k| > n0 (n0 = -1: every image):
+ *   SR = sum F(r_k,h)/r_k,  SZ = sum o_k F(r_k,h)/r_k,  o_k = dzw + k.
+ * ------------------------------------------------------------------------- */
+#define OR_KINF 512
+
+void or_image_sums_inf(double dR, double dzw, double h, int32_t n0, double* SR, double* SZ) {
+  double R2 = dR * dR;
+  or_sum sr = {0, 0}, sz = {0, 0};
+  for (int k = -OR_KINF; k <= OR_KINF; ++k) {
+    if (k >= -n0 && k <= n0) continue;
+    double o = dzw + (double)k;
+    double f = or_spline_F_over_r(sqrt(R2 + o * o), h);
+    or_add(&sr, f);
+    or_add(&sz, o * f);
+  }
+  /* cells [top, inf) and, mirrored, [bot, inf): Int dx/(R2+x^2)^1.5 from a to inf
+   * = 1/(r (r + a)), Int x dx/(...)^1.5 = 1/r (r = sqrt(R2 + a^2)), plus the near
+   * end's Euler-Maclaurin term f'(a)/24 of the unit cells (f' = -3 a / r^5 and
+   * (x f)' = 1/r^3 - 3 a^2 / r^5); the z part of the mirrored side is negative */
+  double top = dzw + OR_KINF + 0.5, bot = -(dzw - OR_KINF - 0.5);
+  double rt = sqrt(R2 + top * top), rb = sqrt(R2 + bot * bot);
+  double it = 1.0 / rt, ib = 1.0 / rb, it5 = it * it * it * it * it, ib5 = ib * ib * ib * ib * ib;
+  or_add(&sr, 1.0 / (rt * (rt + top)) - 3.0 * top * it5 / 24.0);
+  or_add(&sr, 1.0 / (rb * (rb + bot)) - 3.0 * bot * ib5 / 24.0);
+  or_add(&sz, it + (it * it * it - 3.0 * top * top * it5) / 24.0);
+  or_add(&sz, -(ib + (ib * ib * ib - 3.0 * bot * bot * ib5) / 24.0));
+  *SR = sr.s + sr.c;
+  *SZ = sz.s + sz.c;
+}
+
+/* Pair term with the infinite window: a_i = -G sum_j m_j (dx SR, dy SR, SZ)/L^2 */
+void or_pair_field_inf(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                       const double* h, double G, double L, int64_t ni, const int64_t* idx, double* gx,
+                       double* gy, double* gz) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t q = 0; q < ni; ++q) {
+    int64_t i = idx ? idx[q] : q;
+    or_sum sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double dx = (x[i] - x[j]) / L, dy = (y[i] - y[j]) / L, rz = (z[i] - z[j]) / L;
+      double dzw = rz - floor(rz + 0.5);
+      double sr, szz;
+      or_image_sums_inf(sqrt(dx * dx + dy * dy), dzw, (h[i] + h[j]) / L, -1, &sr, &szz);
+      or_add(&sx, -G * m[j] * dx * sr / (L * L));
+      or_add(&sy, -G * m[j] * dy * sr / (L * L));
+      or_add(&sz, -G * m[j] * szz / (L * L));
+    }
+    gx[q] = sx.s + sx.c;
+    gy[q] = sy.s + sy.c;
+    gz[q] = sz.s + sz.c;
+  }
+}
+
+/* Continuum base of the infinite tail beyond |k| <= n0 (the order-1
+ * Euler-Maclaurin form of or_tail_base with both far ends at infinity): per
+ * side the integral over the cells [A +- |dz|, inf) minus 1/24 of the near
+ * end's derivative, A = n0 + 1/2. */
+void or_tail_base_inf(double dR, double adz, int32_t n0, double* BR, double* BZ) {
+  double R2 = dR * dR, A = n0 + 0.5, lo[2] = {A + adz, A - adz}, br[2], bz[2];
+  for (int s = 0; s < 2; ++s) {
+    double l = lo[s], r = sqrt(R2 + l * l), il = 1.0 / r, il2 = il * il, il5 = il2 * il2 * il;
+    /* f = (x^2+R2)^-1.5: Int = 1/(r (r + l)); f' = -3 x il^5; (x f)' = il^3 - 3 x^2 il^5 */
+    br[s] = 1.0 / (r * (r + l)) - 3.0 * l * il5 / 24.0;
+    bz[s] = il + (il2 * il - 3.0 * l * l * il5) / 24.0;
+  }
+  *BR = br[0] + br[1];
+  *BZ = bz[0] - bz[1];
+}
+/* ---------------------------------------------------------------------------
  * Correction-table tail (Sect. 2.3, eq. S1R2EwaldCorrectionTable: a 2D table of
  * the periodic images beyond the nearest, read by cloud-in-cell interpolation
  * during the run), restated for the windowed sum beyond the near images
@@ -626,8 +705,13 @@ void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const 
  * ------------------------------------------------------------------------- */
 void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]) {
   double SR, SZ, BR, BZ, ER, EZ;
-  or_tail_sums(dR, adz, 0.0, 1.0, n_cut, n0, &SR, &SZ);
-  or_tail_base(dR, adz, n_cut, n0, &BR, &BZ);
+  if (n_cut == 0) { /* infinite window */
+    or_image_sums_inf(dR, adz, 0.0, n0, &SR, &SZ);
+    or_tail_base_inf(dR, adz, n0, &BR, &BZ);
+  } else {
+    or_tail_sums(dR, adz, 0.0, 1.0, n_cut, n0, &SR, &SZ);
+    or_tail_base(dR, adz, n_cut, n0, &BR, &BZ);
+  }
   or_tail_envelope(dR, adz, n0, &ER, &EZ);
   r[0] = (SR - BR) / ER;
   r[1] = (SZ - BZ) / EZ;
@@ -658,17 +742,22 @@ void or_tail_table_read(const double* tab, const or_table_cfg* c, double dR, dou
 void or_tail_table(double dR, double dz, double h, const double* tab, const or_table_cfg* c, double* SR,
                    double* SZ) {
   double adz = fabs(dz), BR, BZ, ER, EZ, r[2];
-  or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
+  if (c->n_cut == 0)
+    or_tail_base_inf(dR, adz, c->n0, &BR, &BZ);
+  else
+    or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
   or_tail_envelope(dR, adz, c->n0, &ER, &EZ);
   or_tail_table_read(tab, c, dR, adz, r);
   double sr = BR + ER * r[0];
   double sz = BZ + EZ * r[1];
   double sg = dz > 0.0 ? 1.0 : (dz < 0.0 ? -1.0 : 0.0);
   sz *= sg;
-  for (int k = -c->n_cut - 1; k <= c->n_cut + 1; ++k) {
+  /* tail images inside the support (an infinite window: every k with |o| < h) */
+  int kmax = c->n_cut > 0 ? c->n_cut + 1 : (int)ceil(h) + 2;
+  for (int k = -kmax; k <= kmax; ++k) {
     if (k >= -c->n0 && k <= c->n0) continue;
     double o = dz + (double)k;
-    if (!(fabs(o) < (double)c->n_cut)) continue;
+    if (c->n_cut > 0 && !(fabs(o) < (double)c->n_cut)) continue;
     double rr = sqrt(dR * dR + o * o);
     if (rr >= h) continue;
     double d = or_spline_F_over_r(rr, h) - 1.0 / (rr * rr * rr);

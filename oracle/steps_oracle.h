@@ -79,11 +79,18 @@ void or_tail_surrogate(double dR, double dz, double h, const double* w, const or
 void or_pair_field_surrogate(int64_t n, const double* x, const double* y, const double* z, const double* m,
                              const double* h, double G, double L, const double* w, const or_surr_cfg* c,
                              int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz);
+/* Ncut -> infinity: every periodic image (exact to |k| <= 512, continuum cells
+ * beyond), the pair field with that window, and the tail base beyond |k| <= n0. */
+void or_image_sums_inf(double dR, double dzw, double h, int32_t n0, double* SR, double* SZ);
+void or_pair_field_inf(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                       const double* h, double G, double L, int64_t ni, const int64_t* idx, double* gx,
+                       double* gy, double* gz);
+void or_tail_base_inf(double dR, double adz, int32_t n0, double* BR, double* BZ);
 /* Correction-table tail (the paper's Sect. 2.3 table restated for the windowed
  * sum beyond |k| <= n0): residual of the point-mass tail over the continuum base
  * in envelope units on a uniform (dR, |dz|) grid, read bilinearly. */
 typedef struct {
-  int32_t n_cut, n0, nx, ny;
+  int32_t n_cut, n0, nx, ny;   /* n_cut = 0: the infinite window */
   double dR_max;        /* last column; dR beyond it reads the last column */
 } or_table_cfg;
 void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]);

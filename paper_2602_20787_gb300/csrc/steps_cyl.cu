@@ -265,7 +265,12 @@ BgParams bg_params(const steps_cyl_ctx* c) {
 
 bool is_r3(const steps_cyl_ctx* c) { return c->p.topology == STEPS_TOPO_R3; }
 // Images per pair: the window's 2 Ncut (S1xR2), the one image of R^3.
-double images_per_pair(const steps_cyl_ctx* c) { return is_r3(c) ? 1.0 : 2.0 * c->p.n_cut; }
+bool is_inf(const steps_cyl_ctx* c) { return c->p.n_cut == 0; }  // Ncut -> infinity
+// Images per pair: the window's 2 Ncut (S1xR2), the one image of R^3, and the
+// 2 n0 + 1 exact images of the infinite window (its tail is the table's).
+double images_per_pair(const steps_cyl_ctx* c) {
+  return is_r3(c) ? 1.0 : is_inf(c) ? 2.0 * c->p.n0 + 1.0 : 2.0 * c->p.n_cut;
+}
 int n_cut_eff(const steps_cyl_ctx* c) { return is_r3(c) ? 1 : c->p.n_cut; }
 
 int check_params(const steps_cyl_params* p) {
@@ -282,11 +287,19 @@ int check_params(const steps_cyl_params* p) {
   if (!(p->L > 0) || !std::isfinite(p->L)) return fail(STEPS_EINVAL, "L must be finite and > 0");
   if (!(p->R_sim > 0) || !std::isfinite(p->R_sim)) return fail(STEPS_EINVAL, "R_sim must be finite and > 0");
   if (!(p->rho_bar >= 0) || !std::isfinite(p->rho_bar)) return fail(STEPS_EINVAL, "rho_bar must be >= 0");
-  if (p->n_cut < 1 || p->n_cut > 4096) return fail(STEPS_EINVAL, "n_cut must be in [1, 4096]");
+  if (p->n_cut < 0 || p->n_cut > 4096) return fail(STEPS_EINVAL, "n_cut must be in [0, 4096] (0: infinite window)");
+  if (p->n_cut == 0) {  // Ncut -> infinity: a modelled tail carries the whole line beyond n0
+    if (p->topology != STEPS_TOPO_S1R2) return fail(STEPS_EINVAL, "the infinite window belongs to S1xR2");
+    if (p->tail == STEPS_TAIL_FULL) return fail(STEPS_EINVAL, "the infinite window needs a modelled tail");
+    if (p->precision == STEPS_FP64) return fail(STEPS_EINVAL, "the infinite window needs an FP32 precision");
+    if (p->background != STEPS_BG_OFF && p->background != STEPS_BG_INFINITE)
+      return fail(STEPS_EINVAL, "the infinite window takes STEPS_BG_INFINITE or STEPS_BG_OFF");
+    if (p->n0 < 1) return fail(STEPS_EINVAL, "n0 must be >= 1");
+  }
   if (p->precision < STEPS_FP64 || p->precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   if (p->tail != STEPS_TAIL_FULL && p->tail != STEPS_TAIL_SURROGATE && p->tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
-  if (p->tail != STEPS_TAIL_FULL && (p->n0 < 1 || p->n0 >= p->n_cut))
+  if (p->tail != STEPS_TAIL_FULL && p->n_cut > 0 && (p->n0 < 1 || p->n0 >= p->n_cut))
     return fail(STEPS_EINVAL, "n0 must be in [1, n_cut)");
   if (p->background < STEPS_BG_OFF || p->background > STEPS_BG_SPHERE) return fail(STEPS_EINVAL, "bad background");
   if (p->comoving) {
@@ -514,25 +527,52 @@ int launch_fp64(steps_cyl_ctx* c, const int64_t* idx, int ni, double* out) {
   return STEPS_OK;
 }
 
+// The pair form of the next force evaluation: FP64, the selected modelled tail
+// when it is accepted, else the plain image sum (for the infinite window, which
+// has none, the correction table built at init).
+enum class Form { FP64, SURROGATE, TABLE, PLAIN };
+Form force_form(const steps_cyl_ctx* c) {
+  if (c->p.precision == STEPS_FP64) return Form::FP64;
+  if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok) return Form::SURROGATE;
+  if ((c->p.tail == STEPS_TAIL_TABLE || is_inf(c)) && c->tab_ok) return Form::TABLE;
+  return Form::PLAIN;
+}
+
 // One force evaluation at the current packed positions. Stores g = a^3 (pair +
 // background) in gx/gy/gz (internal order); kicks p by K when kick is set.
 int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   const double pair_scale = -c->p.G * c->invL * c->invL;
   c->forces_stale = false;
+  const Form form = force_form(c);
+  if (form == Form::PLAIN && is_inf(c)) return fail(STEPS_ENOSURROGATE, "the infinite window has no correction table");
   CK(cudaEventRecord(c->e0, c->st));
-  if (c->p.precision == STEPS_FP64) {
+  if (form == Form::FP64) {
     int rc = launch_fp64(c, nullptr, c->n, c->part);
     if (rc) return rc;
-  } else if (c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok) {
-    if (c->p.precision == STEPS_FP32_KAHAN)
+  } else if (form == Form::SURROGATE) {
+    const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+    if (is_inf(c) && kahan)
+      pair_fp32_surr_kernel<true, true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->SC,
+                                                                  c->surr_lanes, c->surr, c->part);
+    else if (is_inf(c))
+      pair_fp32_surr_kernel<false, true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->SC,
+                                                                   c->surr_lanes, c->surr, c->part);
+    else if (kahan)
       pair_fp32_surr_kernel<true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
                                                              c->surr_lanes, c->surr, c->part);
     else
       pair_fp32_surr_kernel<false><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
                                                               c->surr_lanes, c->surr, c->part);
     CKLAUNCH("pair_fp32_surrogate");
-  } else if (c->p.tail == STEPS_TAIL_TABLE && c->tab_ok) {
-    if (c->p.precision == STEPS_FP32_KAHAN)
+  } else if (form == Form::TABLE) {
+    const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+    if (is_inf(c) && kahan)
+      pair_fp32_table_kernel<true, true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->TC, c->tab,
+                                                                   c->tab_const, c->part);
+    else if (is_inf(c))
+      pair_fp32_table_kernel<false, true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->TC, c->tab,
+                                                                    c->tab_const, c->part);
+    else if (kahan)
       pair_fp32_table_kernel<true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
                                                               c->tab, c->tab_const, c->part);
     else
@@ -555,11 +595,8 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   CK(cudaEventRecord(c->e1, c->st));
   c->timed = true;
   c->last_images = (double)c->n * (double)(c->n - 1) * images_per_pair(c);
-  const int NT = c->p.precision == STEPS_FP64 ? 0 : c->NT;
-  const bool fp32 = c->p.precision != STEPS_FP64;
-  const int ctas = fp32 && c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok ? c->SC
-                   : fp32 && c->p.tail == STEPS_TAIL_TABLE && c->tab_ok    ? c->TC
-                                                                            : c->C;
+  const int NT = form == Form::FP64 ? 0 : c->NT;
+  const int ctas = form == Form::SURROGATE ? c->SC : form == Form::TABLE ? c->TC : c->C;
   finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
       c->part, c->n, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
       kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
@@ -800,6 +837,10 @@ int grow(steps_cyl_ctx* c, size_t elems) {
 // error statistics of the latter.
 int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* med, double* p999,
               double* ms_plain, double* ms_surr) {
+  // the reference: the plain image sum, or for the infinite window (which has
+  // none) its correction table, exact to well below the FP32 arithmetic
+  if (is_inf(c) && (model != STEPS_TAIL_SURROGATE || !c->tab_ok))
+    return fail(STEPS_EINVAL, "the infinite window checks only a surrogate, against its correction table");
   const int ni = std::max(1, std::min(ncheck, c->n));
   std::vector<int64_t> pick(ni);
   {
@@ -838,9 +879,15 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
   float ms[2] = {0.f, 0.f};
   for (int form = 0; form < 2; ++form) {
     CK(cudaEventRecord(c->e0, c->st));
-    if (form == 0)
+    if (form == 0 && is_inf(c))
+      pair_fp32_table_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->idx, ni,
+                                                                                 tpc, c->tab, c->tab_const, part);
+    else if (form == 0)
       pair_fp32_subset_kernel<true, false><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
                                                                             ni, tpc, c->surr_lanes, c->surr, part);
+    else if (is_inf(c))
+      pair_fp32_subset_kernel<true, true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->idx, ni,
+                                                                                 tpc, c->surr_lanes, c->surr, part);
     else if (model == STEPS_TAIL_SURROGATE)
       pair_fp32_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->idx,
                                                                            ni, tpc, c->surr_lanes, c->surr, part);
@@ -918,7 +965,8 @@ int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999
 // cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius.
 int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
   if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
-  if (c->p.n0 < 1 || c->p.n0 >= c->p.n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  if (c->p.n0 < 1 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
+    return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
   if (dR_max == 0.0) {
     std::vector<double> hx(c->n), hy(c->n);
     CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
@@ -1015,7 +1063,7 @@ int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* re
     return fail(STEPS_EINVAL, "bad training configuration");
   const int n_cut = c->p.n_cut, n0 = c->p.n0;
   if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
-  if (n0 < 1 || n0 >= n_cut) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  if (n0 < 1 || (n_cut > 0 && n0 >= n_cut)) return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
   const double A = n0 + 0.5;
   double dR_max = cfg->dR_max;
   if (dR_max == 0.0) {
@@ -1262,7 +1310,7 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   if (n < 2 || n > 0x7fffffffLL - kBI) return fail(STEPS_EINVAL, "n must be in [2, 2^31 - 129)");
   if (!x || !y || !z || !vx || !vy || !vz || !m || !h) return fail(STEPS_EINVAL, "NULL input array");
   if (p->tail == STEPS_TAIL_SURROGATE) return fail(STEPS_ENOSURROGATE, "no surrogate network is loaded");
-  if (p->tail == STEPS_TAIL_TABLE) return fail(STEPS_ENOSURROGATE, "no correction table is built");
+  if (p->tail == STEPS_TAIL_TABLE && p->n_cut > 0) return fail(STEPS_ENOSURROGATE, "no correction table is built");
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
   if (p->device < 0 || p->device >= ndev) return fail(STEPS_EINVAL, "device %d out of range", p->device);
@@ -1319,6 +1367,10 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
   }
   if ((rc = build_background(c))) return bail(rc);
   if ((rc = pack_positions(c))) return bail(rc);
+  if (p->n_cut == 0) {  // infinite window: the table is the definition of the tail, built here
+    if ((rc = build_table(c, 257, 33, 0.0, nullptr))) return bail(rc);
+    c->tab_ok = true;
+  }
   if ((rc = eval_forces(c, false, 0.0))) return bail(rc);
   int e = 0;
   if ((rc = read_and_clear_err(c, &e))) return bail(rc);
@@ -1424,7 +1476,7 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
     }
     // modelled tail: periodic comparison with the plain image sum
     const bool surr = c->p.tail == STEPS_TAIL_SURROGATE && c->surr_ok;
-    const bool table = c->p.tail == STEPS_TAIL_TABLE && c->tab_ok;
+    const bool table = c->p.tail == STEPS_TAIL_TABLE && c->tab_ok && !is_inf(c);  // the infinite window's reference
     if ((surr || table) && c->p.check_every > 0 && ++c->steps_since_check >= c->p.check_every) {
       c->steps_since_check = 0;
       double med = 0, p999 = 0;
@@ -1435,7 +1487,7 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
       const double bp999 = surr ? c->surr_bound_p999 : c->tab_bound_p999;
       if (!(med <= bmed && p999 <= bp999)) {
         (surr ? c->surr_ok : c->tab_ok) = false;
-        c->p.tail = STEPS_TAIL_FULL;
+        c->p.tail = is_inf(c) ? STEPS_TAIL_TABLE : STEPS_TAIL_FULL;
         rejected = true;
         snprintf(reject_msg, sizeof reject_msg, "%s dropped after a check: median %.3g, p99.9 %.3g",
                  surr ? "surrogate" : "correction table", med, p999);
@@ -1500,6 +1552,7 @@ int steps_cyl_set_precision(steps_cyl_ctx* c, int32_t precision) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (precision < STEPS_FP64 || precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
+  if (precision == STEPS_FP64 && is_inf(c)) return fail(STEPS_EINVAL, "the infinite window needs an FP32 precision");
   DeviceGuard guard(c->dev);
   c->p.precision = precision;
   if (precision == STEPS_FP64) c->p.tail = STEPS_TAIL_FULL;
@@ -1728,7 +1781,7 @@ int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg) {
 int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out, void* stream) {
   g_last_error.clear();
   if (ns < 0 || !samples || !out) return fail(STEPS_EINVAL, "bad arguments");
-  if (n_cut < 1 || n0 < 0 || n0 >= n_cut) return fail(STEPS_EINVAL, "need 0 <= n0 < n_cut");
+  if (n_cut < 0 || n0 < 0 || (n_cut > 0 && n0 >= n_cut)) return fail(STEPS_EINVAL, "need 0 <= n0 < n_cut or n_cut = 0");
   if (ns == 0) return STEPS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   double *ds = nullptr, *dout = nullptr;
@@ -1826,6 +1879,7 @@ int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE && tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
+  if (is_inf(c) && tail == STEPS_TAIL_FULL) return fail(STEPS_EINVAL, "the infinite window has no plain image sum");
   if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
   if (tail == STEPS_TAIL_TABLE && !c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
   if (tail != STEPS_TAIL_FULL && c->p.precision == STEPS_FP64)
@@ -1857,9 +1911,12 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* c, int32_t nx, int32_t ny, double 
   double ms = 0.0;
   int rc = build_table(c, nx, ny, dR_max, &ms);
   if (rc) return rc;
-  double med = 0, p999 = 0;
-  bool ok = false;
-  if ((rc = accept_table(c, err_median, err_p999, check_particles, &med, &p999, &ok))) return rc;
+  double med = NAN, p999 = NAN;
+  bool ok = true;
+  if (is_inf(c))
+    c->tab_ok = true;  // the infinite window has no plain sum to check against: the table is its definition
+  else if ((rc = accept_table(c, err_median, err_p999, check_particles, &med, &p999, &ok)))
+    return rc;
   if (report) {
     report[0] = med;
     report[1] = p999;
@@ -1892,6 +1949,7 @@ int steps_cyl_check_tail(steps_cyl_ctx* c, int32_t tail, int32_t check_particles
   if (tail == STEPS_TAIL_SURROGATE) return steps_cyl_check_surrogate(c, check_particles, report);
   if (tail != STEPS_TAIL_TABLE) return fail(STEPS_EINVAL, "bad tail mode");
   if (!c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
+  if (is_inf(c)) return fail(STEPS_EINVAL, "the infinite window has no plain image sum to check against");
   DeviceGuard guard(c->dev);
   return run_check(c, STEPS_TAIL_TABLE, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check,
                    &report[0], &report[1], &report[2], &report[3]);

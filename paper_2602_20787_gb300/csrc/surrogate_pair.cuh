@@ -243,6 +243,23 @@ __device__ __forceinline__ void side_base_x2(float R2, u64 LO, u64 HI, u64& SR, 
   SZ = fma2(E, pk(0.125f, 0.125f), fma2(D3, pk(-1.0f / 24.0f, -1.0f / 24.0f), sub2(IL, IH)));
 }
 
+// The same base with both far ends at infinity (the Ncut -> infinity window):
+// per side Int_lo^inf i^3 = 1/(r (r + lo)) = il^2 / (1 + lo il) and
+// Int_lo^inf x i^3 = il, plus the near end's term (-3 lo il^5 and
+// il^3 - 3 lo^2 il^5, over 24).
+__device__ __forceinline__ void side_base_inf_x2(float R2, u64 LO, u64& SR, u64& SZ, u64& IL) {
+  float a, b;
+  upk(fma2(LO, LO, pk(R2, R2)), a, b);
+  IL = pk(rsq(a), rsq(b));
+  const u64 IL2 = mul2(IL, IL), IL3 = mul2(IL2, IL);
+  float e, f;
+  upk(fma2(LO, IL, pk(1.0f, 1.0f)), e, f);
+  const u64 IR = mul2(IL2, pk(rcp_approx(e), rcp_approx(f)));
+  const u64 P = mul2(LO, mul2(IL2, IL3));  // lo il^5
+  SR = fma2(P, pk(-0.125f, -0.125f), IR);
+  SZ = fma2(fma2(mul2(LO, pk(-3.0f, -3.0f)), P, IL3), pk(1.0f / 24.0f, 1.0f / 24.0f), IL);
+}
+
 // Per-pair state carried across the network: the image sums are affine in
 // the network outputs, sr = a0 + b0 y0 and sz = a1 + b1 y1 (near images, tail
 // base, envelope, sign(dz) and the output scaling folded in), plus the inputs.
@@ -253,7 +270,8 @@ struct SurrPair {
 
 // Stage A: near images |k| <= n0 exactly (the tiered image walk of
 // pair_fp32.cuh without the edge image), the tail base, the envelope and the
-// network inputs. kw: warp-uniform spline bound.
+// network inputs. kw: warp-uniform spline bound. INF: the infinite window.
+template <bool INF = false>
 __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int n_cut, int kw, const SurrConst& S,
                                              SurrPair& P) {
   const int n0 = S.n0;
@@ -261,9 +279,13 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
   pair_images_fp32<false>(dR2, dz, hh, n0 + 1, (float)(n0 + 1), kw, sr, sz);
   // tail base and envelope (|dz|; z part gets sign(dz))
   const float adz = fabsf(dz), A = (float)n0 + 0.5f;
-  const float kneg = adz > 0.0f ? (float)n_cut : (float)(n_cut - 1);
   u64 SRb, SZb, ILb;
-  side_base_x2(dR2, pk(A + adz, A - adz), pk((float)(n_cut - 1) + 0.5f + adz, kneg + 0.5f - adz), SRb, SZb, ILb);
+  if (INF) {
+    side_base_inf_x2(dR2, pk(A + adz, A - adz), SRb, SZb, ILb);
+  } else {
+    const float kneg = adz > 0.0f ? (float)n_cut : (float)(n_cut - 1);
+    side_base_x2(dR2, pk(A + adz, A - adz), pk((float)(n_cut - 1) + 0.5f + adz, kneg + 0.5f - adz), SRb, SZb, ILb);
+  }
   float br1, br2, bz1, bz2, il1, il2;
   upk(SRb, br1, br2);
   upk(SZb, bz1, bz2);
@@ -286,7 +308,9 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
 // Stage C: tail = base + envelope x network output, plus the exact spline
 // correction of tail images inside some lane's softening support.
 // The separation is recomputed from the tile (same arithmetic, same values)
-// on that rare path rather than kept live across the network.
+// on that rare path rather than kept live across the network. INF: the
+// infinite window (no window bound, no edge image).
+template <bool INF = false>
 __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A, const float4& B, int n_cut, int kw,
                                              const SurrConst& S, const SurrPair& P, float y0, float y1, float& sr,
                                              float& sz) {
@@ -300,7 +324,7 @@ __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A
     const u64 STEP = pk(1.0f, -1.0f);
     const float ih = rcp_approx(hh), ih3 = ih * ih * ih;
     const u64 IH = pk(ih, ih), NIH = pk(-ih, -ih), IH3 = pk(ih3, ih3);
-    const int kt = min(kw, n_cut - 1);
+    const int kt = INF ? kw : min(kw, n_cut - 1);
     u64 CR = pk(0.f, 0.f), CZ = pk(0.f, 0.f);
     u64 O = pk(dz + (float)n0, dz - (float)n0);
     for (int kk = n0 + 1; kk <= kt; ++kk) {
@@ -314,7 +338,7 @@ __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A
       CR = add2(CR, D);
       CZ = fma2(O, D, CZ);
     }
-    if (kw >= n_cut) {  // the edge image as well
+    if (!INF && kw >= n_cut) {  // the edge image as well
       const float oe = dz - copysignf((float)n_cut, dz);
       const u64 OE = pk(oe, oe);
       const float r2 = fmaf(oe, oe, dR2);
@@ -339,8 +363,8 @@ __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A
 static_assert(STEPS_KAHAN_GROUP % STEPS_SURR_NJ == 0, "a Kahan group holds whole network calls");
 
 // One j-tile of pairs for one i (shared by the stream-K and the subset kernels).
-// The surrogate form handles two j per network call.
-template <bool KAHAN, bool SURR>
+// The surrogate form handles two j per network call; INF: the infinite window.
+template <bool KAHAN, bool SURR, bool INF = false>
 __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, const float4* sB, int jn, int self,
                                           int n_cut, float fnc, const SurrW& W, uint32_t* ibuf, const SurrConst& S,
                                           float& sx,
@@ -366,7 +390,7 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
         float u[STEPJ][3], y[STEPJ][2];
 #pragma unroll
         for (int jj = 0; jj < STEPJ; ++jj) {
-          surr_stage_a(dR2[jj], dz[jj], hh[jj], n_cut, kw[jj], S, P[jj]);
+          surr_stage_a<INF>(dR2[jj], dz[jj], hh[jj], n_cut, kw[jj], S, P[jj]);
           u[jj][0] = P[jj].u[0];
           u[jj][1] = P[jj].u[1];
           u[jj][2] = P[jj].u[2];
@@ -375,7 +399,7 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
 #pragma unroll
         for (int jj = 0; jj < STEPJ; ++jj) {
           const int kk = min(k + jj, ke - 1);
-          surr_stage_c(I, sA[kk], sB[kk], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr[jj], szz[jj]);
+          surr_stage_c<INF>(I, sA[kk], sB[kk], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr[jj], szz[jj]);
         }
       } else {
 #pragma unroll
@@ -401,7 +425,7 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
 #define STEPS_SURR_MIN_BLOCKS 4  // co-resident CTAs per SM asked of the register allocator
 #endif
 
-template <bool KAHAN>
+template <bool KAHAN, bool INF = false>
 __global__ void __launch_bounds__(kBI, STEPS_SURR_MIN_BLOCKS)
 pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
                       int NT, int C, const SurrLane* __restrict__ wl, SurrConst S, double* __restrict__ part) {
@@ -431,8 +455,8 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
       __syncthreads();
       load_tile(jA, jB, n, t, sA, sB);
       __syncthreads();
-      pair_tile<KAHAN, true>(I, sA, sB, kBJ, i - t * kBJ, n_cut, fnc, W, ibuf, S, sx, sy, sz, cx, cy,
-                             cz);
+      pair_tile<KAHAN, true, INF>(I, sA, sB, kBJ, i - t * kBJ, n_cut, fnc, W, ibuf, S, sx, sy, sz, cx, cy,
+                                  cz);
     }
     double* dst = part + ((long long)b + c) * 3 * kBI;
     dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
@@ -444,8 +468,9 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
 
 // Subset kernel (acceptance checks): CTA (bx, by) takes listed i-particles
 // [bx * kBI, +kBI) against j-tiles [by * tpc, (by + 1) * tpc); partials
-// part[by][3][ni]. The listed indices are internal and may repeat.
-template <bool KAHAN, bool SURR>
+// part[by][3][ni]. The listed indices are internal and may repeat. INF: the
+// surrogate of the infinite window.
+template <bool KAHAN, bool SURR, bool INF = false>
 __global__ void __launch_bounds__(kBI, 3)
 pair_fp32_subset_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut,
                         const int64_t* __restrict__ idx, int ni, int tpc, const SurrLane* __restrict__ wl, SurrConst S,
@@ -470,8 +495,8 @@ pair_fp32_subset_kernel(const float4* __restrict__ jA, const float4* __restrict_
     __syncthreads();
     load_tile(jA, jB, n, t, sA, sB);
     __syncthreads();
-    pair_tile<KAHAN, SURR>(I, sA, sB, kBJ, i - t * kBJ, n_cut, (float)n_cut, W, ibuf, S, sx, sy, sz, cx,
-                           cy, cz);
+    pair_tile<KAHAN, SURR, INF>(I, sA, sB, kBJ, i - t * kBJ, n_cut, (float)n_cut, W, ibuf, S, sx, sy, sz, cx,
+                                cy, cz);
   }
   if (q < ni) {
     double* dst = part + (long long)blockIdx.y * 3 * ni;

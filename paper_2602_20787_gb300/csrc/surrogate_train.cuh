@@ -33,7 +33,23 @@ __device__ __forceinline__ double spline_over_r_d(double r, double h) {
   return (64.0 / 3.0 - 48.0 * u + 38.4 * u * u - (32.0 / 3.0) * u3 - 1.0 / (15.0 * u3)) * ih3;
 }
 
-// Exact tail sums of the window (|dz + k| < Ncut, |k| > n0) in FP64, units of L.
+// The infinite window (Ncut -> infinity): images |k| <= kKInf are summed one by
+// one, those beyond on each side by the continuum cells from kKInf + 1/2 with
+// the near end's Euler-Maclaurin term (Newtonian there, as h << kKInf), which
+// leaves an error of O(kKInf^-6).
+constexpr int kKInf = 512;
+
+// Both line ends beyond |k| = kKInf, added to (sr, sz), offsets o = dz + k.
+__host__ __device__ __forceinline__ void line_ends_fp64(double R2, double dz, double& sr, double& sz) {
+  const double top = kKInf + 0.5 + dz, bot = kKInf + 0.5 - dz;
+  const double rt = sqrt(R2 + top * top), rb = sqrt(R2 + bot * bot), it = 1.0 / rt, ib = 1.0 / rb;
+  const double it5 = it * it * it * it * it, ib5 = ib * ib * ib * ib * ib;
+  sr += 1.0 / (rt * (rt + top)) - 3.0 * top * it5 / 24.0 + 1.0 / (rb * (rb + bot)) - 3.0 * bot * ib5 / 24.0;
+  sz += it + (it * it * it - 3.0 * top * top * it5) / 24.0 - (ib + (ib * ib * ib - 3.0 * bot * bot * ib5) / 24.0);
+}
+
+// Exact tail sums of the window (|dz + k| < Ncut, |k| > n0) in FP64, units of L;
+// n_cut = 0 is the infinite window.
 // samples: ns x 3 (dR, dz, h); out: ns x 2 (SR, SZ).
 static __global__ void tail_sums_fp64_kernel(const double* __restrict__ smp, int64_t ns, int n_cut, int n0,
                                              double* __restrict__ out) {
@@ -41,6 +57,18 @@ static __global__ void tail_sums_fp64_kernel(const double* __restrict__ smp, int
     const double dR = smp[3 * s], dz = smp[3 * s + 1], h = smp[3 * s + 2];
     const double R2 = dR * dR;
     double sr = 0.0, sz = 0.0;
+    if (n_cut == 0) {
+      for (int k = n0 + 1; k <= kKInf; ++k) {
+        const double op = dz + (double)k, om = dz - (double)k;
+        const double fp = spline_over_r_d(sqrt(R2 + op * op), h), fm = spline_over_r_d(sqrt(R2 + om * om), h);
+        sr += fp + fm;
+        sz += op * fp + om * fm;
+      }
+      line_ends_fp64(R2, dz, sr, sz);
+      out[2 * s] = sr;
+      out[2 * s + 1] = sz;
+      continue;
+    }
     // walk outward from the near region on both sides
     for (int k = n0 + 1; k <= n_cut + 1; ++k) {
       const double op = dz + (double)k, om = dz - (double)k;
@@ -90,15 +118,39 @@ __host__ __device__ __forceinline__ void tail_base_fp64(double dR, double adz, i
   EZ = e * e * sqrt(e);
 }
 
+// The same base with both far ends at infinity (the Ncut -> infinity window):
+// per side the integral over [A +- |dz|, inf) plus the near end's
+// Euler-Maclaurin term, Int = 1/(r (r + lo)) and 1/r.
+__host__ __device__ __forceinline__ void tail_base_inf_fp64(double dR, double adz, int n0, double& BR, double& BZ,
+                                                            double& ER, double& EZ) {
+  const double R2 = dR * dR, A = n0 + 0.5;
+  double br[2], bz[2];
+  const double lo[2] = {A + adz, A - adz};
+  for (int q = 0; q < 2; ++q) {
+    const double l = lo[q], r = sqrt(R2 + l * l), il = 1.0 / r, il2 = il * il, il5 = il2 * il2 * il;
+    br[q] = 1.0 / (r * (r + l)) - 3.0 * l * il5 / 24.0;
+    bz[q] = il + (il2 * il - 3.0 * l * l * il5) / 24.0;
+  }
+  BR = br[0] + br[1];
+  BZ = bz[0] - bz[1];
+  const double e = 1.0 / (R2 + (A + adz) * (A + adz));
+  ER = e * e * e;
+  EZ = e * e * sqrt(e);
+}
+
 // Training pairs: inputs u (FP32, ns x 3) and raw targets r = (tail - B1) / E
-// (FP64, ns x 2, before the mean/scale normalisation) from exact tail sums.
+// (FP64, ns x 2, before the mean/scale normalisation) from exact tail sums
+// (n_cut = 0: the infinite window over its base).
 static __global__ void surrogate_dataset_kernel(const double* __restrict__ smp, const double* __restrict__ tail,
                                                 int64_t ns, int n_cut, int n0, double dR_max,
                                                 float* __restrict__ u, double* __restrict__ r) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
     const double dR = smp[3 * s], adz = fabs(smp[3 * s + 1]), h = smp[3 * s + 2];
     double BR, BZ, ER, EZ;
-    tail_base_fp64(dR, adz, n_cut, n0, BR, BZ, ER, EZ);
+    if (n_cut == 0)
+      tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
+    else
+      tail_base_fp64(dR, adz, n_cut, n0, BR, BZ, ER, EZ);
     const double A = n0 + 0.5;
     u[3 * s] = (float)(2.0 * fmin(dR, dR_max) / dR_max - 1.0);
     u[3 * s + 1] = (float)(4.0 * adz - 1.0);

@@ -10,6 +10,9 @@
 // is smooth (every tail image is at least n0 + 1/2 away), so a coarse table
 // read bilinearly is far more accurate than FP32 force arithmetic.
 //
+// With n_cut = 0 the window is infinite (Ncut -> infinity, Sect. 2.2): the
+// table holds the whole image line beyond n0 against the infinite base.
+//
 // The pair kernel is the surrogate kernel with the network replaced by one
 // texture fetch: the texture unit's bilinear filter is the cloud-in-cell
 // read. The near images, the base, the envelope and the exact spline
@@ -23,12 +26,28 @@
 namespace steps {
 
 // Node residuals in FP64 (exact point-mass tail, dz = +|dz|), stored as float2
-// [ny][nx].
+// [ny][nx]. n_cut = 0 is the infinite window: images to |k| <= kKInf exactly
+// and the line ends beyond, against the infinite base.
+
 static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cut, int n0, float2* __restrict__ out) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny; q += gridDim.x * blockDim.x) {
     const int i = q % nx, j = q / nx;
     const double dR = dR_max * i / (nx - 1), adz = 0.5 * j / (ny - 1), R2 = dR * dR;
     double sr = 0.0, sz = 0.0;
+    if (n_cut == 0) {
+      for (int k = n0 + 1; k <= kKInf; ++k) {
+        const double op = adz + (double)k, om = adz - (double)k;
+        const double rp = 1.0 / sqrt(R2 + op * op), rm = 1.0 / sqrt(R2 + om * om);
+        const double fp = rp * rp * rp, fm = rm * rm * rm;
+        sr += fp + fm;
+        sz += op * fp + om * fm;
+      }
+      line_ends_fp64(R2, adz, sr, sz);
+      double BR, BZ, ER, EZ;
+      tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
+      out[q] = make_float2((float)((sr - BR) / ER), (float)((sz - BZ) / EZ));
+      continue;
+    }
     for (int k = n0 + 1; k <= n_cut + 1; ++k) {
       const double op = adz + (double)k, om = adz - (double)k;
       if (fabs(op) < (double)n_cut) {
@@ -61,8 +80,9 @@ __device__ __forceinline__ float2 table_read(const TableTail& T, float u0, float
 }
 
 // All pairs of i with the kBJ j of a (padded) tile with the table tail. S holds
-// mu = 0, sc = 1 (the table stores raw residuals) and the table's dR_max.
-template <bool KAHAN>
+// mu = 0, sc = 1 (the table stores raw residuals) and the table's dR_max. INF:
+// the infinite window (n_cut = 0).
+template <bool KAHAN, bool INF = false>
 __device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4* sA, const float4* sB, int self,
                                                 int n_cut, const SurrConst& S, const TableTail& T, float& sx,
                                                 float& sy, float& sz, float& cx, float& cy, float& cz) {
@@ -77,10 +97,10 @@ __device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4
       int kw;
       pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
       SurrPair P;
-      surr_stage_a(dR2, dz, hh, n_cut, kw, S, P);
+      surr_stage_a<INF>(dR2, dz, hh, n_cut, kw, S, P);
       const float2 r = table_read(T, P.u[0], P.u[1]);
       float sr, szz;
-      surr_stage_c(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
+      surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
       const float mj = k == self ? 0.0f : A.w;
       const float msr = mj * sr;
       gx = fmaf(dx, msr, gx);
@@ -99,7 +119,7 @@ __device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4
 
 // Stream-K kernel with the table tail (work split and partial layout of
 // pair_fp32_kernel).
-template <bool KAHAN>
+template <bool KAHAN, bool INF = false>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
                        int NT, int C, TableTail T, SurrConst S, double* __restrict__ part) {
@@ -120,7 +140,7 @@ pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__
       __syncthreads();
       load_tile(jA, jB, n, t, sA, sB);
       __syncthreads();
-      pair_tile_table<KAHAN>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
+      pair_tile_table<KAHAN, INF>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
     }
     double* dst = part + ((long long)b + c) * 3 * kBI;
     dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
@@ -132,7 +152,7 @@ pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__
 
 // Subset kernel of the table form (acceptance checks; the layout of
 // pair_fp32_subset_kernel).
-template <bool KAHAN>
+template <bool KAHAN, bool INF = false>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_fp32_table_subset_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut,
                               const int64_t* __restrict__ idx, int ni, int tpc, TableTail T, SurrConst S,
@@ -149,7 +169,7 @@ pair_fp32_table_subset_kernel(const float4* __restrict__ jA, const float4* __res
     __syncthreads();
     load_tile(jA, jB, n, t, sA, sB);
     __syncthreads();
-    pair_tile_table<KAHAN>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
+    pair_tile_table<KAHAN, INF>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
   }
   if (q < ni) {
     double* dst = part + (long long)blockIdx.y * 3 * ni;

@@ -182,3 +182,17 @@ def tail_training_inputs(ns: int, seed: int, dR_max: float, h_max: float, L: flo
     dz = rng.uniform(0.0, 0.5 * L, ns)
     h = rng.uniform(0.0, h_max, ns)
     return np.stack([dR, dz, h], axis=1)
+
+
+def random_surrogate_params(seed: int, dR_max: float, mu=(0.0, 0.0), sc=(0.05, 0.05)) -> np.ndarray:
+    """A seeded parameter vector of the 3 -> 32 -> 32 -> 2 tail network in the
+    library's layout (W1[32][3], b1, W2[32][32], b2, W3[2][32], b3, then mu[2],
+    sc[2], dR_max): entries uniform in +-1/sqrt(fan-in). Random numbers only, for
+    checks of the network form that need weights from outside the library."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cnt, fan_in in ((32 * 3, 3), (32, 3), (32 * 32, 32), (32, 32), (2 * 32, 32), (2, 32)):
+        b = 1.0 / math.sqrt(fan_in)
+        parts.append(rng.uniform(-b, b, cnt))
+    parts.append(np.array([mu[0], mu[1], sc[0], sc[1], dR_max]))
+    return np.concatenate(parts).astype(np.float32)

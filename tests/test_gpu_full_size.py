@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2602_20787_gb300 import ics
-from tests.gpu_helpers import oracle_accel, stats
+from tests.gpu_helpers import oracle_accel, seeded_surrogate, stats
 
 pytestmark = pytest.mark.gpu
 
@@ -46,14 +46,13 @@ def test_full_size_fp32_forms(sc, name, forms):
 
 def test_full_size_surrogate(sc):
     # N = 2^20, Ncut = 64, n0 = 4: the plain 128-image sum and the learned tail
-    # (trained on the GPU) against the FP64 oracle, and the learned tail against
-    # the oracle's own statement of the surrogate form with the same weights
+    # (trained on the GPU) against the FP64 oracle, and the surrogate kernel with
+    # a seeded network against the oracle's own statement of the surrogate form
     w = ics.WORKLOADS["surrogate_n1048576"]
     d = ics.workload_ics(w)
     sim = full_sim(sc, w, d, n0=w.n0, precision=sc.STEPS_FP32_KAHAN)
     report = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
     assert report[4] == 1.0
-    params = sc.steps_cyl_get_surrogate(sim.ctx)
     idx = ics.subsample(w.n, 96, seed=77)
     exact = oracle_accel(d["pos"], d["m"], d["h"], w.n_cut, idx=idx, rho0=w.rho_bar)
     med, p999, _ = stats(sim.forces()[idx], exact)
@@ -65,13 +64,13 @@ def test_full_size_surrogate(sc):
     print(f"N=2^20 learned tail vs exact: median {med:.2e} p99.9 {p999:.2e}")
     assert med <= 1e-5 and p999 <= 1e-3
     sub = idx[:32]
-    cfg = oracle.make_surr_cfg(w.n_cut, w.n0, float(params[1254]), (float(params[1250]), float(params[1251])),
-                               (float(params[1252]), float(params[1253])))
-    w16 = params[:1250].astype(np.float16).astype(np.float64)  # the kernel's FP16 weights
+    w16, cfg = seeded_surrogate(sc, sim.ctx, 43, w.n_cut, w.n0)
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+    a = sim.forces()
     ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, cfg, idx=sub)
     ref += oracle.background_field(d["pos"][sub], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
     med, _, mx = stats(a[sub], ref)
-    print(f"N=2^20 learned tail vs oracle surrogate form: median {med:.2e} max {mx:.2e}")
+    print(f"N=2^20 surrogate kernel (seeded network) vs oracle surrogate form: median {med:.2e} max {mx:.2e}")
     assert med <= 2e-6 and mx <= 1e-4
     # the correction-table tail on the same particles
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2602_20787_gb300 import ics
-from tests.gpu_helpers import stats
+from tests.gpu_helpers import seeded_surrogate, stats, table_dR_max
 
 pytestmark = pytest.mark.gpu
 
@@ -51,8 +51,10 @@ def infsim(sc):
 
 
 def test_inf_table_nodes_match_oracle(sc, infsim):
-    _, _, sim = infsim
-    tab, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    _, d, sim = infsim
+    tab, lib_dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    dR_max = table_dR_max(d["pos"])
+    assert lib_dR_max == pytest.approx(dR_max, rel=1e-15)
     assert tab.shape == (33, 257, 2)
     ref = oracle.tail_table_build(oracle.make_table_cfg(0, N0, tab.shape[1], tab.shape[0], dR_max))
     assert np.allclose(tab, ref, rtol=2e-7, atol=1e-9 * np.abs(ref).max())
@@ -61,7 +63,9 @@ def test_inf_table_nodes_match_oracle(sc, infsim):
 def test_inf_table_form_matches_oracle_table_form(sc, infsim):
     w, d, sim = infsim
     a = sim.forces()
-    tab, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    tab, lib_dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    dR_max = table_dR_max(d["pos"])
+    assert lib_dR_max == pytest.approx(dR_max, rel=1e-15)
     cfg = oracle.make_table_cfg(0, N0, tab.shape[1], tab.shape[0], dR_max)
     idx = ics.subsample(d["m"].shape[0], 128, seed=11)
     ref = oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, oracle.tail_table_build(cfg), cfg, idx=idx)
@@ -185,19 +189,9 @@ def test_inf_tail_sums_match_oracle(sc):
         assert out[s, 1] == pytest.approx(ref[1], rel=1e-11, abs=1e-15)
 
 
-def surr_params_and_cfg(seed, dR_max):
-    p = ics.random_surrogate_params(seed, dR_max, mu=(0.02, -0.01), sc=(0.05, 0.03))
-    cfg = oracle.make_surr_cfg(0, N0, float(p[1254]), (float(p[1250]), float(p[1251])),
-                               (float(p[1252]), float(p[1253])))
-    return p, p[:1250].astype(np.float16).astype(np.float64), cfg
-
-
 def test_inf_surrogate_kernel_matches_oracle_definition(sc, infsim):
     w, d, sim = infsim
-    _, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
-    p, w16, cfg = surr_params_and_cfg(31, dR_max)
-    rep = sc.steps_cyl_set_surrogate(sim.ctx, p, err_median=1.0, err_p999=1.0)   # checked against the table form
-    print("seeded network against the table form:", rep)
+    w16, cfg = seeded_surrogate(sc, sim.ctx, 31, 0, N0)   # checked against the table form on the way in
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
     a = sim.forces()
     idx = ics.subsample(d["m"].shape[0], 128, seed=13)
@@ -214,9 +208,7 @@ def test_inf_softened_tail_images(sc):
     w, d = workload(1500, 5)
     d["h"] = np.random.default_rng(2).uniform(0.5, 6.0, 1500)
     sim = sc.Simulation(inf_config(sc, w.rho_bar, precision=sc.STEPS_FP32_PLAIN), d["pos"], d["vel"], d["m"], d["h"])
-    _, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
-    p, w16, cfg = surr_params_and_cfg(32, dR_max)
-    sc.steps_cyl_set_surrogate(sim.ctx, p, err_median=1.0, err_p999=1.0)
+    w16, cfg = seeded_surrogate(sc, sim.ctx, 32, 0, N0)
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
     idx = ics.subsample(1500, 100, seed=9)
     ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, cfg, idx=idx)
@@ -251,9 +243,7 @@ def test_inf_surrogate_training_and_accuracy(sc):
 
 def test_inf_rejected_network_keeps_the_table(sc, infsim):
     w, d, sim = infsim
-    _, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
-    p, _, _ = surr_params_and_cfg(33, dR_max)
-    p[1252:1254] = 50.0            # a network scaled far off the tail
+    p = ics.random_surrogate_params(33, 8.0, sc=(50.0, 50.0))   # a network scaled far off the tail
     before = sim.forces()
     with pytest.raises(sc.StepsError) as e:
         sc.steps_cyl_set_surrogate(sim.ctx, p)

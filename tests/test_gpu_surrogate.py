@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2602_20787_gb300 import ics
-from tests.gpu_helpers import oracle_accel, stats
+from tests.gpu_helpers import oracle_accel, seeded_surrogate, stats
 
 pytestmark = pytest.mark.gpu
 
@@ -63,11 +63,6 @@ def trained(sc):
     sim.close()
 
 
-def surr_cfg(params):
-    return oracle.make_surr_cfg(N_CUT, N0, float(params[1254]), (float(params[1250]), float(params[1251])),
-                                (float(params[1252]), float(params[1253])))
-
-
 def test_training_is_accepted(trained):
     _, _, _, report, params = trained
     print("train report", report)
@@ -78,12 +73,14 @@ def test_training_is_accepted(trained):
 
 
 def test_surrogate_kernel_matches_oracle_definition(sc, trained):
+    # a seeded network, so that the oracle's inputs do not come from the library
     w, d, sim, _, params = trained
+    w16, cfg = seeded_surrogate(sc, sim.ctx, 41, N_CUT, N0)
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
     a = sim.forces()
+    sc.steps_cyl_set_surrogate(sim.ctx, params)   # the trained network again, for the other tests
     idx = ics.subsample(d["m"].shape[0], 160, seed=7)
-    w16 = params[:1250].astype(np.float16).astype(np.float64)   # the kernel's FP16 weights
-    ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, surr_cfg(params), idx=idx)
+    ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, cfg, idx=idx)
     ref += oracle.background_field(d["pos"][idx], ics.R_SIM, N_CUT * 1.0, 1.0, w.rho_bar, mode=1)
     ref /= 0.02 ** 3
     med, p999, mx = stats(a[idx], ref)
@@ -117,15 +114,11 @@ def test_softened_tail_images(sc):
     d["h"] = np.random.default_rng(2).uniform(0.5, 6.0, 1500)
     cfg = sc.Config(n_cut=N_CUT, n0=N0, precision=1, rho_bar=w.rho_bar, check_particles=256)
     sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
-    tcfg = sc.steps_cyl_train_cfg_default(n_samples=1 << 16, epochs=8, check_particles=256, err_median=1.0,
-                                          err_p999=1.0)
-    sc.steps_cyl_train_surrogate(sim.ctx, tcfg)
-    params = sc.steps_cyl_get_surrogate(sim.ctx)
+    w16, scfg = seeded_surrogate(sc, sim.ctx, 42, N_CUT, N0)
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
     a = sim.forces()
     idx = ics.subsample(1500, 100, seed=9)
-    w16 = params[:1250].astype(np.float16).astype(np.float64)
-    ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, surr_cfg(params), idx=idx)
+    ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, scfg, idx=idx)
     ref += oracle.background_field(d["pos"][idx], ics.R_SIM, N_CUT * 1.0, 1.0, w.rho_bar, mode=1)
     med, _, mx = stats(a[idx], ref)
     assert med <= 2e-6 and mx <= 1e-4

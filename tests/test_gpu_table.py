@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2602_20787_gb300 import ics
-from tests.gpu_helpers import oracle_accel, stats
+from tests.gpu_helpers import oracle_accel, stats, table_dR_max
 
 pytestmark = pytest.mark.gpu
 
@@ -40,10 +40,12 @@ def tabled(sc):
 
 
 def test_table_nodes_match_oracle(sc, tabled):
-    _, _, sim, rep = tabled
+    _, d, sim, rep = tabled
     print("build report", rep)
     assert rep[2] == 1.0 and rep[0] <= 1e-6   # both forms carry FP32 rounding of ~1e-7
-    tab, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    tab, lib_dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    dR_max = table_dR_max(d["pos"])
+    assert lib_dR_max == pytest.approx(dR_max, rel=1e-15)
     ref = oracle.tail_table_build(oracle.make_table_cfg(N_CUT, N0, tab.shape[1], tab.shape[0], dR_max))
     assert np.abs(tab - ref).max() <= 1e-6 * np.abs(ref).max()
     assert np.allclose(tab, ref, rtol=2e-7, atol=1e-9 * np.abs(ref).max())
@@ -53,7 +55,9 @@ def test_table_form_matches_oracle_table_form(sc, tabled):
     w, d, sim, _ = tabled
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
     a = sim.forces()
-    tab, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    tab, lib_dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    dR_max = table_dR_max(d["pos"])
+    assert lib_dR_max == pytest.approx(dR_max, rel=1e-15)
     cfg = oracle.make_table_cfg(N_CUT, N0, tab.shape[1], tab.shape[0], dR_max)
     idx = ics.subsample(d["m"].shape[0], 128, seed=11)
     ref = oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, oracle.tail_table_build(cfg), cfg, idx=idx)

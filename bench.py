@@ -465,11 +465,97 @@ def run_inf(args):
     return 0
 
 
+def run_octree(args):
+    """Octree (Sect. 2.4) on the production-shaped load (softening ratio 1:8;
+    N = 524,288, or 65,536 with the same law), infinite window with the
+    correction table, Theta = 0.5, leaves of 16: build and walk time,
+    interactions, the walk's pipe roofline, the time of the direct sum of the
+    same pair form, errors and the mean radial force ratio against it on a
+    particle sample, with and without the radial correction, and a KDK step.
+    (Under the literal softening law of the other workloads most pairs overlap
+    in softening, no node can stand in for its particles, and the tree does the
+    direct sum's work.)"""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    w = ics.WORKLOADS["production_n524288"]
+    n = 524288 if args.workload == "octree_n524288" else 65536
+    d = ics.workload_ics(w, n=n)
+    props = torch.cuda.get_device_properties(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    common = dict(n_cut=0, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_TABLE,
+                  background=sc.STEPS_BG_INFINITE, rho_bar=w.rho_bar, stream=stream)
+    sim = sc.Simulation(sc.Config(force=sc.STEPS_FORCE_OCTREE, theta=0.5, leaf_size=16, **common), d["pos"],
+                        d["vel"], d["m"], d["h"])
+    reps, runs = 3, []
+    for _ in range(reps):
+        _timed_forces(sc, torch, sim, 1)
+        runs.append(sc.steps_cyl_tree_stats(sim.ctx))
+    st = min(runs, key=lambda r: r["build_ms"] + r["walk_ms"])
+    mufu = (2 * w.n0 + 1) + 2 + 2 + 1   # per interaction: near images, infinite base rsqrt/rcp, the dR rsqrt
+    peak = props.multi_processor_count * 2070e6 * MUFU_RSQRT_PER_SM_CLK / mufu
+    rate = st["interactions"] / (st["walk_ms"] * 1e-3)
+    line = {"workload": args.workload, "n": n, "n_cut": "infinite", "n0": w.n0, "theta": 0.5, "leaf_size": 16,
+            "octree": {"build_ms": st["build_ms"], "walk_ms": st["walk_ms"],
+                       "force_ms": st["build_ms"] + st["walk_ms"], "nodes": st["nodes"], "depth": st["depth"],
+                       "interactions_per_particle": st["interactions"] / n,
+                       "roofline": {"bound": "mufu", "mufu_ops_per_interaction": mufu, "peak_per_s": peak,
+                                    "achieved_per_s": rate, "frac": rate / peak}}}
+    # accuracy against the direct sum of the same pair form (GPU, FP32-Kahan) on a sample
+    idx = ics.subsample(n, 2048, seed=12345)
+    direct = sc.Simulation(sc.Config(**common), d["pos"], d["vel"], d["m"], d["h"])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    ad = direct.forces_subset(idx)
+    ev1.record()
+    torch.cuda.synchronize()
+    line["direct_force_ms"] = ev0.elapsed_time(ev1)
+    direct.close()
+
+    def errors(a):
+        # relative error of the net force (pair + background; on this near-homogeneous load
+        # the pair sum is ~15x the net force, so the tree's pair-sum error is magnified), and
+        # the mean radial error over the mean force magnitude (the bias the correction removes)
+        r = np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        x, y = d["pos"][idx, 0], d["pos"][idx, 1]
+        rho = np.hypot(x, y)
+        e_rad = ((a - ad)[:, 0] * x + (a - ad)[:, 1] * y) / rho
+        return {"median": float(np.median(r)), "p99": float(np.quantile(r, 0.99)),
+                "mean_radial_error_over_mean_force": float(np.mean(e_rad) / np.mean(np.linalg.norm(ad, axis=1)))}
+
+    line["octree"]["error_vs_direct"] = errors(sim.forces_subset(idx))
+    ev0.record()
+    sc.steps_cyl_tree_calibrate(sim.ctx, 8, 32, 8192)
+    ev1.record()
+    torch.cuda.synchronize()
+    line["octree"]["calibration_ms"] = ev0.elapsed_time(ev1)
+    line["octree"]["error_vs_direct_radially_corrected"] = errors(sim.forces_subset(idx))
+    # a tighter opening angle on the same load
+    tight = sc.Simulation(sc.Config(force=sc.STEPS_FORCE_OCTREE, theta=0.3, leaf_size=16, **common), d["pos"],
+                          d["vel"], d["m"], d["h"])
+    a3 = tight.forces_subset(idx)
+    st3 = sc.steps_cyl_tree_stats(tight.ctx)
+    line["octree_theta_0.3"] = {"force_ms": st3["build_ms"] + st3["walk_ms"],
+                                "interactions_per_particle": st3["interactions"] / n, "error_vs_direct": errors(a3)}
+    tight.close()
+    line["octree"]["speedup_vs_direct"] = line["direct_force_ms"] / (st["build_ms"] + st["walk_ms"])
+    t0, _ = ics.run_schedule(w)
+    ev0.record()
+    sim.step(0.01 * t0 if t0 > 0 else 1e-3, 5)
+    ev1.record()
+    torch.cuda.synchronize()
+    line["octree"]["kdk_step_ms"] = ev0.elapsed_time(ev1) / 5
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
     if args.workload in ("r3_n65536", "glass_n65536"):
         return run_r3_or_glass(args)
+    if args.workload in ("octree_n65536", "octree_n524288"):
+        return run_octree(args)
     if args.workload == "inf_n65536":
         return run_inf(args)
     w = ics.WORKLOADS[args.workload]

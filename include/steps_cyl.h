@@ -58,6 +58,9 @@ extern "C" {
 #define STEPS_BG_INFINITE 2  /* eq. F_horiz_infty inside R_sim, line-mass field outside */
 #define STEPS_BG_SPHERE 3    /* R^3 topology: the radial term +(4 pi G / 3) rho_bar x of Sect. 2.1 */
 
+#define STEPS_FORCE_DIRECT 0  /* the O(N^2) direct pair sum */
+#define STEPS_FORCE_OCTREE 1  /* the octree of Sect. 2.4 (O(N log N)) */
+
 #define STEPS_TOPO_S1R2 0  /* compact z axis of period L: eq. ForceCylindrical (the default) */
 #define STEPS_TOPO_R3 1    /* no compact axis: the softened Newtonian pair force of eq. NewtonianForce,
                             * no images, z unbounded; background STEPS_BG_OFF or STEPS_BG_SPHERE */
@@ -95,9 +98,15 @@ typedef struct {
   int32_t topology; /* STEPS_TOPO_S1R2 | STEPS_TOPO_R3 (R^3: n_cut is not used, tail must be STEPS_TAIL_FULL) */
   int32_t reserved; /* 0 */
   void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
+  int32_t force;    /* STEPS_FORCE_DIRECT | STEPS_FORCE_OCTREE. The octree (Sect. 2.4) needs the infinite
+                     * window (n_cut = 0, STEPS_TAIL_TABLE), an FP32 precision and the S1xR2 topology */
+  int32_t leaf_size;  /* octree: a node of at most this many particles is a leaf (1 .. 64) */
+  double theta;       /* octree: opening angle Theta, 0 < theta <= 1 */
+  uint64_t tree_seed; /* octree: seed of the random shift and rotation drawn at every force evaluation */
 } steps_cyl_params;
 
-/* Fill *p with defaults: G = L = 1, R_sim = 0.5 tan(0.45 pi), rho_bar = 0, n_cut = 16,
+/* Fill *p with defaults (direct force; octree leaf_size 16, theta 0.5, tree_seed 1):
+ * G = L = 1, R_sim = 0.5 tan(0.45 pi), rho_bar = 0, n_cut = 16,
  * n0 = 4, FP32_KAHAN, TAIL_FULL, BG_FINITE, static space, H0 = 1, Omega_m = 0.3,
  * Omega_L = 0.7, w0 = -1, wa = 0, a_start = 1, t_start = 0, device 0, reorder_every = 32,
  * check_every = 50, check_particles = 1024, default stream. */
@@ -272,6 +281,39 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, doubl
  * read only the sizes), its nx, ny and dR_max (each may be NULL).
  * STEPS_ENOSURROGATE when no table was built. */
 int steps_cyl_get_tail_table(steps_cyl_ctx* ctx, float* out, int32_t* nx, int32_t* ny, double* dR_max);
+
+/* ---- octree (Sect. 2.4) ------------------------------------------------------
+ * A Barnes-Hut tree over a cube of side S = 2 max(L, 2 R_sim), drawn at every
+ * force evaluation in a random frame: shifted by zeta along the axis and
+ * rotated by phi about it (x' = cos phi x - sin phi y, y' = sin phi x +
+ * cos phi y, z' = z + zeta mod L). Particles are grouped by 32 in Morton order
+ * of the frame; a group opens a node when any member sees it under an angle
+ * s / d >= theta or closer than the softening allows; accepted nodes act as
+ * point masses at their centre of mass. Every interaction is the pair force of
+ * the infinite window (near images exact, the rest from the correction table).
+ * An optional radial correction (Sect. 2.4) subtracts the mean radial force
+ * error measured by steps_cyl_tree_calibrate. */
+
+/* Fix the frame of the following force evaluations (zeta in [0, L), phi in
+ * radians); zeta < 0 returns to a random frame per evaluation. */
+int steps_cyl_tree_frame(steps_cyl_ctx* ctx, double zeta, double phi);
+
+/* Statistics of the last octree evaluation: out[0] nodes, out[1] depth,
+ * out[2] pair interactions (member x entry), out[3] build ms, out[4] walk ms,
+ * out[5] evaluations so far. STEPS_EINVAL unless the context uses the octree. */
+int steps_cyl_tree_stats(steps_cyl_ctx* ctx, double* out);
+
+/* Radial calibration of Sect. 2.4: for n_frames frames (frames: 2 n_frames
+ * doubles (zeta, phi), or NULL to draw them) compare the octree's pair force
+ * with the direct pair force on n_sample particles (sample: caller indices, or
+ * NULL to draw them) and average the radial component of the difference in
+ * n_bins bins of rho over [0, rmax], rmax the largest particle radius now.
+ * Empty bins hold 0. The table is then subtracted from the octree force at
+ * every evaluation (interpolated linearly between bin centres, held beyond
+ * them). n_frames = 0 removes the correction. table (n_bins doubles, may be
+ * NULL) and rmax (may be NULL) receive the result. */
+int steps_cyl_tree_calibrate(steps_cyl_ctx* ctx, int32_t n_frames, int32_t n_bins, int32_t n_sample,
+                             const double* frames, const int64_t* sample, double* table, double* rmax);
 
 /* As steps_cyl_check_surrogate for a modelled tail (STEPS_TAIL_SURROGATE or
  * STEPS_TAIL_TABLE), which must be loaded and accepted. STEPS_EINVAL for the

@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "steps_oracle.h")))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC,
+                   "-lm"]
             subprocess.run(cmd, check=True, cwd=_HERE)
             os.replace(tmp, _LIB)
     return _LIB
@@ -101,6 +102,10 @@ def lib():
         L.or_pair_field_r3.argtypes = [i64, p, p, p, p, p, d, i64, p, p, p, p]; L.or_pair_field_r3.restype = None
         L.or_background_sphere.argtypes = [i64, p, p, p, d, d, p, p, p]; L.or_background_sphere.restype = None
         L.or_kdk.restype = ctypes.c_int
+        L.or_tree_field.argtypes = [i64, p, p, p, p, p, d, d, d, i32, p, p, d, i32, d, d, i64, p, p, p, p, p]
+        L.or_tree_field.restype = ctypes.c_int
+        L.or_tree_order.argtypes = [i64, p, p, p, d, d, d, d, p, p]
+        L.or_tree_order.restype = ctypes.c_int
         L.or_tail_sums.argtypes = [d, d, d, d, i32, i32, p, p]; L.or_tail_sums.restype = None
         L.or_mlp_forward.argtypes = [p, p, p]; L.or_mlp_forward.restype = None
         L.or_mlp_loss_grad.argtypes = [p, i64, p, p, p]; L.or_mlp_loss_grad.restype = d
@@ -416,3 +421,44 @@ def tail_base_inf(dR, adz, n0):
     a, b = ctypes.c_double(), ctypes.c_double()
     lib().or_tail_base_inf(float(dR), float(adz), int(n0), ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+def tree_field(pos, m, h, G, L, R_sim, n_cut, theta, leaf, zeta, phi, tab=None, tcfg=None, idx=None):
+    """Octree field (Sect. 2.4) in the frame (zeta, phi) of every particle, or
+    of the listed ones (idx): returns (g of shape (n or len(idx), 3), stats =
+    nodes, leaves, depth, interactions of the groups walked). tab/tcfg: the
+    correction-table form (near images plus table); None: the plain window of
+    n_cut."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], idx.ctypes.data_as(ctypes.c_void_p)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    stats = np.zeros(4, dtype=np.int64)
+    tab_c = _f64(tab) if tab is not None else None
+    tp = _ptr(tab_c) if tab_c is not None else None
+    rc = lib().or_tree_field(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), float(R_sim),
+                             int(n_cut), tp, ctypes.byref(tcfg) if tcfg is not None else None, float(theta),
+                             int(leaf), float(zeta), float(phi), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz),
+                             stats.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"or_tree_field failed ({rc}): a particle outside the root cube" if rc == -1 else
+                         f"or_tree_field failed ({rc})")
+    return np.stack([gx, gy, gz], axis=1), stats
+
+
+def tree_order(pos, L, R_sim, zeta, phi):
+    """Keys and key order (ties by index) of the octree frame (zeta, phi)."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    n = x.shape[0]
+    key = np.zeros(n, dtype=np.uint64)
+    ordv = np.zeros(n, dtype=np.int64)
+    rc = lib().or_tree_order(n, _ptr(x), _ptr(y), _ptr(z), float(L), float(R_sim), float(zeta), float(phi),
+                             key.ctypes.data_as(ctypes.c_void_p), ordv.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"or_tree_order failed ({rc})")
+    return key, ordv

@@ -784,3 +784,332 @@ void or_pair_field_table(int64_t n, const double* x, const double* y, const doub
   or_table_ctx t = {tab, c};
   or_pair_field_with_tail(n, x, y, z, m, h, G, L, c->n0, or_tail_table_cb, &t, ni, idx, gx, gy, gz);
 }
+
+/* ---------------------------------------------------------------------------
+ * Octree (Sect. 2.4, "Octree": a Barnes-Hut tree whose root is a cube twice the
+ * largest dimension of the volume, re-drawn with a random shift along the axis
+ * and a random rotation about it at every force evaluation).
+ *
+ * Tree frame: x' = c x - s y, y' = s x + c y (c, s = cos, sin phi),
+ * z' = z + zeta, minus L when >= L. Root: side S = 2 max(L, 2 R_sim), centre
+ * (0, 0, L/2). Normalised coordinates u = (x'/S + 1/2, y'/S + 1/2,
+ * (z' - L/2)/S + 1/2) in [0, 1), rounded to FP32, and 21 bits of each give a
+ * 63-bit Morton key (x bit b at key bit 3b + 2, y at 3b + 1, z at 3b). The
+ * particles are sorted by (key, index). A node is a key prefix; it is a leaf
+ * when it holds <= leaf particles or sits at depth 21. Its moments: mass M,
+ * centre of mass (x, y in the frame of the particles; z from the tree frame,
+ * shifted back by zeta), and the largest softening.
+ *
+ * Walk. Groups of 32 consecutive particles in key order share one walk: a
+ * node is opened for the whole group when any member opens it (a group walk,
+ * the form the GPU's warps take). A member opens node n (side s, centre C,
+ * normalised coordinates) when s^2 >= theta^2 d^2 or
+ * |d| - (sqrt(3)/2) s <= hu_i + hu_max(n), with d the offset of u_i from C,
+ * z wrapped to the nearest image, and hu = h / S: accepted nodes are far and
+ * beyond every member's softening. (With d taken to the nearest image, a node
+ * accepted at small cylindrical distance has s <= theta L / 2, and one at
+ * large cylindrical distance is far from all of its images.)
+ * This decision is taken in FP32, operation by operation as written, on FP32
+ * inputs, so that the GPU takes it identically. An accepted node acts as a
+ * point mass M at its centre of mass with softening h_max; an opened leaf
+ * gives its particles one by one. Each interaction is the pair term of the
+ * direct form (the plain window, or near images plus the correction table).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t level, nchild;
+  int64_t begin, end, child0;
+  float c[3], s, hm;        /* normalised centre, side, largest hu */
+  double M, com[3], hmax;   /* mass, centre of mass, largest softening */
+} or_tnode;
+
+typedef struct {
+  or_tnode* v;
+  int64_t n, cap;
+} or_tnodes;
+
+static int64_t or_tnode_new(or_tnodes* t) {
+  if (t->n == t->cap) {
+    int64_t cap = t->cap ? 2 * t->cap : 1024;
+    or_tnode* v = (or_tnode*)realloc(t->v, sizeof(or_tnode) * (size_t)cap);
+    if (!v) return -1;
+    t->v = v;
+    t->cap = cap;
+  }
+  return t->n++;
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} or_keyidx;
+
+static int or_keyidx_cmp(const void* a, const void* b) {
+  const or_keyidx *p = (const or_keyidx*)a, *q = (const or_keyidx*)b;
+  if (p->key != q->key) return p->key < q->key ? -1 : 1;
+  return p->idx < q->idx ? -1 : (p->idx > q->idx ? 1 : 0);
+}
+
+static uint64_t or_spread3(uint32_t v) { /* bit b of v to bit 3b */
+  uint64_t r = 0;
+  for (int b = 0; b < 21; ++b) r |= (uint64_t)((v >> b) & 1u) << (3 * b);
+  return r;
+}
+
+typedef struct {
+  const uint64_t* key;   /* sorted keys */
+  const int64_t* ord;    /* sorted position -> particle */
+  const double *x, *y, *zt, *m, *h;
+  const float* hu;
+  int32_t leaf;
+  double zeta, L;
+} or_tbuild;
+
+/* Node of level `level` over sorted positions [begin, end) with integer
+ * coordinates (ix, iy, iz) at that level; children are built recursively. */
+static int or_tree_build(or_tnodes* t, const or_tbuild* B, int64_t id, int32_t level, int64_t begin,
+                         int64_t end, uint32_t ix, uint32_t iy, uint32_t iz) {
+  or_tnode* nd = &t->v[id];
+  float s = ldexpf(1.0f, -level);
+  nd->level = level;
+  nd->begin = begin;
+  nd->end = end;
+  nd->s = s;
+  nd->c[0] = ((float)ix + 0.5f) * s;
+  nd->c[1] = ((float)iy + 0.5f) * s;
+  nd->c[2] = ((float)iz + 0.5f) * s;
+  double M = 0, mx = 0, my = 0, mz = 0, hmax = 0;
+  float hm = 0.0f;
+  for (int64_t q = begin; q < end; ++q) {
+    int64_t i = B->ord[q];
+    M += B->m[i];
+    mx += B->m[i] * B->x[i];
+    my += B->m[i] * B->y[i];
+    mz += B->m[i] * B->zt[i];
+    if (B->h[i] > hmax) hmax = B->h[i];
+    if (B->hu[i] > hm) hm = B->hu[i];
+  }
+  nd->M = M;
+  nd->com[0] = mx / M;
+  nd->com[1] = my / M;
+  nd->com[2] = mz / M - B->zeta; /* back to the frame of the particles (any period) */
+  nd->hmax = hmax;
+  nd->hm = hm;
+  nd->nchild = 0;
+  nd->child0 = -1;
+  if (end - begin <= B->leaf || level == 21) return 0;
+  int sh = 3 * (21 - level - 1);
+  int64_t lo[8], hi[8];
+  int32_t dig[8], nc = 0;
+  for (int64_t q = begin; q < end;) {
+    int32_t d = (int32_t)((B->key[q] >> sh) & 7u);
+    int64_t e = q;
+    while (e < end && (int32_t)((B->key[e] >> sh) & 7u) == d) ++e;
+    lo[nc] = q;
+    hi[nc] = e;
+    dig[nc] = d;
+    ++nc;
+    q = e;
+  }
+  int64_t c0 = t->n;
+  for (int k = 0; k < nc; ++k)
+    if (or_tnode_new(t) < 0) return -2;
+  nd = &t->v[id]; /* the array may have moved */
+  nd->child0 = c0;
+  nd->nchild = nc;
+  for (int k = 0; k < nc; ++k) {
+    int rc = or_tree_build(t, B, c0 + k, level + 1, lo[k], hi[k], 2 * ix + ((dig[k] >> 2) & 1),
+                           2 * iy + ((dig[k] >> 1) & 1), 2 * iz + (dig[k] & 1));
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+/* The opening rule of one member (FP32, as written). */
+static int or_tree_opens(const float u[3], float hu, const or_tnode* nd, float Lu, float th2) {
+  float dx = u[0] - nd->c[0];
+  float dy = u[1] - nd->c[1];
+  float dz = u[2] - nd->c[2];
+  float hLu = 0.5f * Lu;
+  if (dz > hLu) dz = dz - Lu;
+  else if (dz < -hLu) dz = dz + Lu;
+  float d2 = dx * dx + dy * dy;
+  d2 = d2 + dz * dz;
+  if (nd->s * nd->s >= th2 * d2) return 1;
+  float clear = sqrtf(d2) - 0.8660254f * nd->s;
+  return clear <= hu + nd->hm;
+}
+
+/* Pair term per unit G m_j of one interaction (separation r, softening hh):
+ * the plain window (tab == NULL), or the near images |k| <= n0 plus the
+ * correction-table tail. */
+static void or_tree_pair(double rx, double ry, double rz, double hh, double L, int32_t n_cut, const double* tab,
+                         const or_table_cfg* tc, double out[3]) {
+  if (!tab) {
+    or_image_force(rx, ry, rz, hh, L, n_cut, out);
+    return;
+  }
+  double dx = rx / L, dy = ry / L, r = rz / L, h = hh / L;
+  double dzw = r - floor(r + 0.5), dR = sqrt(dx * dx + dy * dy), sr = 0.0, sz = 0.0;
+  for (int k = -tc->n0; k <= tc->n0; ++k) {
+    double o = dzw + (double)k;
+    double f = or_spline_F_over_r(sqrt(dR * dR + o * o), h);
+    sr += f;
+    sz += o * f;
+  }
+  double tr, tz;
+  or_tail_table(dR, dzw, h, tab, tc, &tr, &tz);
+  sr += tr;
+  sz += tz;
+  out[0] = -dx * sr / (L * L);
+  out[1] = -dy * sr / (L * L);
+  out[2] = -sz / (L * L);
+}
+
+int or_tree_field(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
+                  double G, double L, double R_sim, int32_t n_cut, const double* tab, const or_table_cfg* tc,
+                  double theta, int32_t leaf, double zeta, double phi, int64_t ni, const int64_t* idx, double* gx,
+                  double* gy, double* gz, int64_t* stats) {
+  double S = 2.0 * fmax(L, 2.0 * R_sim), invS = 1.0 / S, c = cos(phi), s = sin(phi), halfL = 0.5 * L;
+  float Lu = (float)(L * invS), th2 = (float)(theta * theta);
+  float* u = (float*)malloc(sizeof(float) * 3 * (size_t)n);
+  float* hu = (float*)malloc(sizeof(float) * (size_t)n);
+  double* zt = (double*)malloc(sizeof(double) * (size_t)n);
+  or_keyidx* ki = (or_keyidx*)malloc(sizeof(or_keyidx) * (size_t)n);
+  uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+  int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (size_t)n); /* particle -> output slot, -1: none */
+  unsigned char* want = (unsigned char*)calloc((size_t)(n + 31) / 32 + 1, 1);
+  or_tnodes t = {NULL, 0, 0};
+  int rc = 0;
+  if (!u || !hu || !zt || !ki || !key || !ord || !slot || !want) { rc = -2; goto done; }
+  for (int64_t i = 0; i < n; ++i) {
+    double xr = fma(c, x[i], -(s * y[i]));
+    double yr = fma(s, x[i], c * y[i]);
+    double zr = z[i] + zeta;
+    if (zr >= L) zr = zr - L;
+    zt[i] = zr;
+    u[3 * i] = (float)fma(xr, invS, 0.5);
+    u[3 * i + 1] = (float)fma(yr, invS, 0.5);
+    u[3 * i + 2] = (float)fma(zr - halfL, invS, 0.5);
+    hu[i] = (float)(h[i] * invS);
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+      float v = u[3 * i + a];
+      if (!(v >= 0.0f && v < 1.0f)) { rc = -1; goto done; } /* outside the root cube */
+      q[a] = (uint32_t)(v * 2097152.0f);
+    }
+    ki[i].key = (or_spread3(q[0]) << 2) | (or_spread3(q[1]) << 1) | or_spread3(q[2]);
+    ki[i].idx = i;
+  }
+  qsort(ki, (size_t)n, sizeof(or_keyidx), or_keyidx_cmp);
+  for (int64_t q = 0; q < n; ++q) {
+    key[q] = ki[q].key;
+    ord[q] = ki[q].idx;
+  }
+  for (int64_t i = 0; i < n; ++i) slot[i] = idx ? -1 : i;
+  if (idx) {
+    for (int64_t k = 0; k < ni; ++k) {
+      if (idx[k] < 0 || idx[k] >= n) { rc = -3; goto done; }
+      slot[idx[k]] = k;
+    }
+  }
+  for (int64_t q = 0; q < n; ++q)
+    if (slot[ord[q]] >= 0) want[q / 32] = 1;
+  {
+    or_tbuild B = {key, ord, x, y, zt, m, h, hu, leaf, zeta, L};
+    if (or_tnode_new(&t) < 0) { rc = -2; goto done; }
+    rc = or_tree_build(&t, &B, 0, 0, 0, n, 0, 0, 0);
+    if (rc) goto done;
+  }
+  int64_t ngroups = (n + 31) / 32, inter = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : inter)
+  for (int64_t g = 0; g < ngroups; ++g) {
+    if (!want[g]) continue; /* no requested member: the group's walk is not needed */
+    int64_t q0 = 32 * g, q1 = q0 + 32 < n ? q0 + 32 : n;
+    int nm = (int)(q1 - q0);
+    or_sum acc[32][3];
+    memset(acc, 0, sizeof acc);
+    int64_t stack[256];
+    int top = 0;
+    stack[top++] = 0;
+    while (top > 0) {
+      const or_tnode* nd = &t.v[stack[--top]];
+      int open = 0;
+      for (int k = 0; k < nm && !open; ++k) {
+        int64_t i = ord[q0 + k];
+        open = or_tree_opens(&u[3 * i], hu[i], nd, Lu, th2);
+      }
+      if (open && nd->nchild > 0) {
+        for (int k = 0; k < nd->nchild; ++k) stack[top++] = nd->child0 + k;
+        continue;
+      }
+      for (int k = 0; k < nm; ++k) {
+        int64_t i = ord[q0 + k];
+        double f[3];
+        if (!open) {
+          or_tree_pair(x[i] - nd->com[0], y[i] - nd->com[1], z[i] - nd->com[2], h[i] + nd->hmax, L, n_cut, tab, tc,
+                       f);
+          for (int a = 0; a < 3; ++a) or_add(&acc[k][a], G * nd->M * f[a]);
+          ++inter;
+        } else {
+          for (int64_t p = nd->begin; p < nd->end; ++p) {
+            int64_t j = ord[p];
+            ++inter; /* member x entry, the member's own entry included */
+            if (j == i) continue;
+            or_tree_pair(x[i] - x[j], y[i] - y[j], z[i] - z[j], h[i] + h[j], L, n_cut, tab, tc, f);
+            for (int a = 0; a < 3; ++a) or_add(&acc[k][a], G * m[j] * f[a]);
+          }
+        }
+      }
+    }
+    for (int k = 0; k < nm; ++k) {
+      int64_t o = slot[ord[q0 + k]];
+      if (o < 0) continue;
+      gx[o] = acc[k][0].s + acc[k][0].c;
+      gy[o] = acc[k][1].s + acc[k][1].c;
+      gz[o] = acc[k][2].s + acc[k][2].c;
+    }
+  }
+  if (stats) {
+    int64_t leaves = 0, depth = 0;
+    for (int64_t k = 0; k < t.n; ++k) {
+      if (t.v[k].nchild == 0) ++leaves;
+      if (t.v[k].level > depth) depth = t.v[k].level;
+    }
+    stats[0] = t.n;
+    stats[1] = leaves;
+    stats[2] = depth;
+    stats[3] = inter;
+  }
+done:
+  free(u); free(hu); free(zt); free(ki); free(key); free(ord); free(slot); free(want); free(t.v);
+  return rc;
+}
+
+/* Sorted order of the tree frame (for checks of the sort): ord[q] = particle at
+ * key position q, key[q] its key. */
+int or_tree_order(int64_t n, const double* x, const double* y, const double* z, double L, double R_sim,
+                  double zeta, double phi, uint64_t* key, int64_t* ord) {
+  double S = 2.0 * fmax(L, 2.0 * R_sim), invS = 1.0 / S, c = cos(phi), s = sin(phi), halfL = 0.5 * L;
+  or_keyidx* ki = (or_keyidx*)malloc(sizeof(or_keyidx) * (size_t)n);
+  if (!ki) return -2;
+  for (int64_t i = 0; i < n; ++i) {
+    double xr = fma(c, x[i], -(s * y[i])), yr = fma(s, x[i], c * y[i]), zr = z[i] + zeta;
+    if (zr >= L) zr = zr - L;
+    float v[3] = {(float)fma(xr, invS, 0.5), (float)fma(yr, invS, 0.5), (float)fma(zr - halfL, invS, 0.5)};
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+      if (!(v[a] >= 0.0f && v[a] < 1.0f)) { free(ki); return -1; }
+      q[a] = (uint32_t)(v[a] * 2097152.0f);
+    }
+    ki[i].key = (or_spread3(q[0]) << 2) | (or_spread3(q[1]) << 1) | or_spread3(q[2]);
+    ki[i].idx = i;
+  }
+  qsort(ki, (size_t)n, sizeof(or_keyidx), or_keyidx_cmp);
+  for (int64_t q = 0; q < n; ++q) {
+    key[q] = ki[q].key;
+    ord[q] = ki[q].idx;
+  }
+  free(ki);
+  return 0;
+}

@@ -101,6 +101,21 @@ void or_tail_table(double dR, double dz, double h, const double* tab, const or_t
 void or_pair_field_table(int64_t n, const double* x, const double* y, const double* z, const double* m,
                          const double* h, double G, double L, const double* tab, const or_table_cfg* c,
                          int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz);
+/* Octree (Sect. 2.4): Barnes-Hut group walk in a shifted and rotated frame
+ * (zeta, phi), opening angle theta, leaves of <= leaf particles; each
+ * interaction is the pair term of the direct form (tab == NULL: the plain
+ * window of n_cut; else near images plus the correction table tc). idx ==
+ * NULL gives every particle (ni = n); else the ni listed ones, walking only
+ * their groups. Returns 0, -1 when a particle lies outside the root cube, -2 on
+ * allocation failure, -3 for a bad index. stats (may be NULL): nodes, leaves,
+ * depth, interactions (member x list entry over the groups walked, a member's
+ * own entry in its leaf included). */
+int or_tree_field(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
+                  double G, double L, double R_sim, int32_t n_cut, const double* tab, const or_table_cfg* tc,
+                  double theta, int32_t leaf, double zeta, double phi, int64_t ni, const int64_t* idx, double* gx,
+                  double* gy, double* gz, int64_t* stats);
+int or_tree_order(int64_t n, const double* x, const double* y, const double* z, double L, double R_sim,
+                  double zeta, double phi, uint64_t* key, int64_t* ord);
 double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t, double* grad);
 void or_adam_step(int64_t nw, double* w, const double* g, double* m1, double* m2, double lr,
                   double beta1, double beta2, double eps, int64_t step);

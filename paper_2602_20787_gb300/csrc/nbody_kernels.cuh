@@ -12,6 +12,8 @@ namespace steps {
 constexpr int kErrNonFinite = 1;     // a force, position or momentum is not finite
 constexpr int kErrBgRange = 2;       // a particle lies beyond the background table
 constexpr int kErrZRange = 4;        // z left [0, L) by more than rounding
+constexpr int kErrTreeRange = 8;     // a particle lies outside the octree's root cube
+constexpr int kErrTreeStack = 16;    // an octree walk outgrew its stack
 
 // FP64 positions -> FP32 hi/lo words in units of L (see pair_fp32.cuh).
 __device__ __forceinline__ void pack_one(double x, double y, double z, double m, double h, int i, double invL,
@@ -91,13 +93,40 @@ __device__ __forceinline__ void add_background(const BgParams& bg, double xi, do
 // NT == 0), scale to the comoving field
 // g = a^3 (pair + background), store it, optionally kick p += g K and optionally
 // write a = g / a^3 to an output.
+// Radial correction of Sect. 2.4: g -= D(rho) rho_hat, D interpolated
+// linearly between bin centres (k + 1/2) rmax / nb and held outside them.
+struct RadialCorr {
+  const double* tab;  // nb bin means; null: no correction
+  int nb;
+  double rmax;
+};
+
+__device__ __forceinline__ void radial_correct(const RadialCorr& R, double x, double y, double& g0, double& g1) {
+  if (!R.tab) return;
+  const double rho = sqrt(x * x + y * y);
+  if (!(rho > 0.0)) return;
+  const double s = rho / R.rmax * R.nb - 0.5;
+  double D;
+  if (s <= 0.0) D = R.tab[0];
+  else if (s >= R.nb - 1) D = R.tab[R.nb - 1];
+  else {
+    const int k = (int)s;
+    const double t = s - k;
+    D = (1.0 - t) * R.tab[k] + t * R.tab[k + 1];
+  }
+  g0 -= D * x / rho;
+  g1 -= D * y / rho;
+}
+
+
 static __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
                                 double pair_scale, BgParams bg, const double* __restrict__ x,
                                 const double* __restrict__ y, const double* __restrict__ z, double* __restrict__ gx,
                                 double* __restrict__ gy, double* __restrict__ gz, double K,
                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
                                 double inv_a3, double* __restrict__ ox, double* __restrict__ oy,
-                                double* __restrict__ oz, int* __restrict__ err) {
+                                double* __restrict__ oz, int* __restrict__ err,
+                                RadialCorr rc = RadialCorr{nullptr, 0, 0.0}) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -118,6 +147,7 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
     }
   }
   double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
+  radial_correct(rc, x[i], y[i], g0, g1);
   add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
   if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
   gx[i] = g0; gy[i] = g1; gz[i] = g2;

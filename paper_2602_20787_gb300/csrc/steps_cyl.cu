@@ -31,6 +31,7 @@
 #include "surrogate_pair.cuh"
 #include "surrogate_train.cuh"
 #include "tail_table.cuh"
+#include "octree.cuh"
 
 using namespace steps;
 
@@ -245,6 +246,37 @@ struct steps_cyl_ctx {
   int TC = 0;                      // CTAs of the table pair kernel
   double* chk = nullptr;           // check buffers (grown on demand)
   size_t chk_elems = 0;
+  // octree (force == STEPS_FORCE_OCTREE)
+  struct Tree {
+    uint64_t* key[2] = {nullptr, nullptr};  // radix-sort ping-pong: keys and internal indices
+    int* val[2] = {nullptr, nullptr};
+    unsigned *hist = nullptr, *offs = nullptr;
+    float4 *u4 = nullptr, *u4s = nullptr;   // tree-frame coordinates (internal / key order)
+    double* zt = nullptr;                   // z in the tree frame (internal order)
+    float4 *sA = nullptr, *sB = nullptr;    // packed particles in key order
+    int node_cap = 0, slot_cap = 0;
+    int4* link = nullptr;
+    float4* geo = nullptr;
+    float* hmf = nullptr;
+    uint64_t* pre = nullptr;
+    double4_32a* mom = nullptr;
+    double* hmx = nullptr;
+    float4 *nA = nullptr, *nB = nullptr;
+    int *active[2] = {nullptr, nullptr};
+    int *cnt = nullptr, *beg = nullptr, *pos = nullptr, *totals = nullptr;
+    int* totals_h = nullptr;                // pinned
+    unsigned long long* inter = nullptr;
+    int nodes = 0, depth = 0;
+    double interactions = 0.0, build_ms = 0.0, walk_ms = 0.0;
+    bool fixed = false;
+    double fzeta = 0.0, fphi = 0.0;
+    uint64_t evals = 0;
+    double* rad = nullptr;                  // radial correction table (device)
+    int rad_nb = 0;
+    double rad_rmax = 0.0;
+    std::vector<double> rad_h;
+    cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;
+  } tr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double last_images = 0.0;
   bool timed = false;
@@ -297,6 +329,15 @@ int check_params(const steps_cyl_params* p) {
     if (p->n0 < 1) return fail(STEPS_EINVAL, "n0 must be >= 1");
   }
   if (p->precision < STEPS_FP64 || p->precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
+  if (p->force != STEPS_FORCE_DIRECT && p->force != STEPS_FORCE_OCTREE) return fail(STEPS_EINVAL, "bad force method");
+  if (p->force == STEPS_FORCE_OCTREE) {
+    // the octree's node interactions are smooth only for the infinite window: with a finite
+    // window the image set of a pair jumps at the window's edge, which no node moment follows
+    if (p->n_cut != 0 || p->tail != STEPS_TAIL_TABLE)
+      return fail(STEPS_EINVAL, "the octree needs the infinite window (n_cut = 0) with STEPS_TAIL_TABLE");
+    if (p->leaf_size < 1 || p->leaf_size > 64) return fail(STEPS_EINVAL, "leaf_size must be in [1, 64]");
+    if (!(p->theta > 0.0 && p->theta <= 1.0)) return fail(STEPS_EINVAL, "theta must be in (0, 1]");
+  }
   if (p->tail != STEPS_TAIL_FULL && p->tail != STEPS_TAIL_SURROGATE && p->tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
   if (p->tail != STEPS_TAIL_FULL && p->n_cut > 0 && (p->n0 < 1 || p->n0 >= p->n_cut))
@@ -400,8 +441,10 @@ int read_and_clear_err(steps_cyl_ctx* c, int* out) {
 }
 
 int device_error(int e) {
-  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
-              (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range" : "");
+  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
+              (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range " : "",
+              (e & kErrTreeRange) ? "particle outside the octree root " : "",
+              (e & kErrTreeStack) ? "octree walk stack overflow" : "");
 }
 
 // Morton (Z-order) rank of (x, y): stable sort of 2 x 16-bit interleaved cell
@@ -527,6 +570,247 @@ int launch_fp64(steps_cyl_ctx* c, const int64_t* idx, int ni, double* out) {
   return STEPS_OK;
 }
 
+struct SplitMix {
+  uint64_t s;
+  explicit SplitMix(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }  // [0, 1)
+};
+
+// ---------------------------------------------------------------------------
+// Octree (Sect. 2.4): buffers, build, walk (kernels in octree.cuh).
+// ---------------------------------------------------------------------------
+#define CKT(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? STEPS_ENOMEM : STEPS_ECUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                     \
+  } while (0)
+
+bool is_tree(const steps_cyl_ctx* c) { return c->p.force == STEPS_FORCE_OCTREE; }
+
+int tree_alloc(steps_cyl_ctx* c) {
+  auto& T = c->tr;
+  if (T.key[0]) return STEPS_OK;
+  const size_t n = (size_t)c->n;
+  const int ntiles = (c->n + kSortTile - 1) / kSortTile;
+  for (int k = 0; k < 2; ++k) {
+    CKT(cudaMalloc(&T.key[k], sizeof(uint64_t) * n));
+    CKT(cudaMalloc(&T.val[k], sizeof(int) * n));
+  }
+  CKT(cudaMalloc(&T.hist, sizeof(unsigned) * 256 * (size_t)ntiles));
+  CKT(cudaMalloc(&T.offs, sizeof(unsigned) * 256 * (size_t)ntiles));
+  CKT(cudaMalloc(&T.u4, sizeof(float4) * n));
+  CKT(cudaMalloc(&T.u4s, sizeof(float4) * n));
+  CKT(cudaMalloc(&T.zt, sizeof(double) * n));
+  CKT(cudaMalloc(&T.sA, sizeof(float4) * n));
+  CKT(cudaMalloc(&T.sB, sizeof(float4) * n));
+  CKT(cudaMalloc(&T.totals, sizeof(int) * 2));
+  CKT(cudaMallocHost(&T.totals_h, sizeof(int) * 2));
+  CKT(cudaMalloc(&T.inter, sizeof(unsigned long long)));
+  CKT(cudaEventCreate(&T.t0));
+  CKT(cudaEventCreate(&T.t1));
+  CKT(cudaEventCreate(&T.t2));
+  return STEPS_OK;
+}
+
+// Grow the node arrays to hold `need` nodes, keeping the first `keep`.
+int tree_grow_nodes(steps_cyl_ctx* c, int need, int keep) {
+  auto& T = c->tr;
+  if (need <= T.node_cap) return STEPS_OK;
+  const int cap = std::max(need, T.node_cap * 2);
+  auto grow = [&](auto*& ptr, size_t elem) -> int {
+    void* q = nullptr;
+    CKT(cudaMalloc(&q, elem * (size_t)cap));
+    if (ptr && keep > 0) CKT(cudaMemcpyAsync(q, ptr, elem * (size_t)keep, cudaMemcpyDeviceToDevice, c->st));
+    CKT(cudaStreamSynchronize(c->st));
+    cudaFree(ptr);
+    ptr = static_cast<std::remove_reference_t<decltype(ptr)>>(q);
+    return STEPS_OK;
+  };
+  int rc;
+  if ((rc = grow(T.link, sizeof(int4))) || (rc = grow(T.geo, sizeof(float4))) || (rc = grow(T.hmf, sizeof(float))) ||
+      (rc = grow(T.pre, sizeof(uint64_t))) || (rc = grow(T.mom, sizeof(double4_32a))) ||
+      (rc = grow(T.hmx, sizeof(double))) || (rc = grow(T.nA, sizeof(float4))) || (rc = grow(T.nB, sizeof(float4))))
+    return rc;
+  T.node_cap = cap;
+  return STEPS_OK;
+}
+
+int tree_grow_slots(steps_cyl_ctx* c, int need) {
+  auto& T = c->tr;
+  if (need <= T.slot_cap) return STEPS_OK;
+  const int cap = std::max(need, 2 * T.slot_cap);
+  int* ptrs[5] = {T.active[0], T.active[1], T.cnt, T.beg, T.pos};
+  for (int* q : ptrs) cudaFree(q);
+  // active lists hold node ids (<= cap / 8 per level), the others one entry per child slot
+  CKT(cudaMalloc(&T.active[0], sizeof(int) * (size_t)cap));
+  CKT(cudaMalloc(&T.active[1], sizeof(int) * (size_t)cap));
+  CKT(cudaMalloc(&T.cnt, sizeof(int) * (size_t)cap));
+  CKT(cudaMalloc(&T.beg, sizeof(int) * (size_t)cap));
+  CKT(cudaMalloc(&T.pos, sizeof(int) * (size_t)cap));
+  T.slot_cap = cap;
+  return STEPS_OK;
+}
+
+TreeFrame tree_frame_of(const steps_cyl_ctx* c, double zeta, double phi) {
+  TreeFrame F;
+  const double S = 2.0 * std::max(c->p.L, 2.0 * c->p.R_sim);
+  F.c = std::cos(phi);
+  F.s = std::sin(phi);
+  F.zeta = zeta;
+  F.L = c->p.L;
+  F.halfL = 0.5 * c->p.L;
+  F.invS = 1.0 / S;
+  return F;
+}
+
+// Sort, build and moments of the tree in frame (zeta, phi).
+int tree_build(steps_cyl_ctx* c, double zeta, double phi) {
+  auto& T = c->tr;
+  int rc;
+  if ((rc = tree_alloc(c))) return rc;
+  const int n = c->n;
+  const TreeFrame F = tree_frame_of(c, zeta, phi);
+  tree_frame_kernel<<<grid_for(n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->h, c->perm, n, F, T.u4, T.zt,
+                                                         T.key[0], T.val[0], c->err);
+  CKLAUNCH("tree_frame");
+  const int ntiles = (n + kSortTile - 1) / kSortTile;
+  for (int pass = 0; pass < 8; ++pass) {  // 8 digits of 8 bits; the result returns to buffer 0
+    const int a = pass & 1, b = a ^ 1;
+    radix_hist_kernel<<<ntiles, kSortThreads, 0, c->st>>>(T.key[a], n, 8 * pass, ntiles, T.hist);
+    scan_exclusive_kernel<<<1, 1024, 0, c->st>>>(T.hist, T.offs, 256 * ntiles, nullptr);
+    radix_scatter_kernel<<<ntiles, kSortThreads, 0, c->st>>>(T.key[a], T.val[a], n, 8 * pass, ntiles, T.offs,
+                                                             T.key[b], T.val[b]);
+  }
+  CKLAUNCH("tree_sort");
+  const uint64_t* key = T.key[0];
+  const int* sidx = T.val[0];
+  tree_gather_kernel<<<grid_for(n, 256), 256, 0, c->st>>>(c->jA, c->jB, T.u4, sidx, n, T.sA, T.sB, T.u4s);
+  CKLAUNCH("tree_gather");
+  // root
+  const int leaf = c->p.leaf_size;
+  if ((rc = tree_grow_nodes(c, std::max(1024, 2 * n / std::max(leaf, 1) + 64), 0))) return rc;
+  if ((rc = tree_grow_slots(c, std::max(1024, 8 * (n / (leaf + 1) + 8))))) return rc;
+  {
+    const int4 l0 = make_int4(-1, 0, 0, n);
+    const float4 g0 = make_float4(0.5f, 0.5f, 0.5f, 1.0f);
+    const uint64_t p0 = 0;
+    const int a0 = 0;
+    CKT(cudaMemcpyAsync(T.link, &l0, sizeof l0, cudaMemcpyHostToDevice, c->st));
+    CKT(cudaMemcpyAsync(T.geo, &g0, sizeof g0, cudaMemcpyHostToDevice, c->st));
+    CKT(cudaMemcpyAsync(T.pre, &p0, sizeof p0, cudaMemcpyHostToDevice, c->st));
+    CKT(cudaMemcpyAsync(T.active[0], &a0, sizeof a0, cudaMemcpyHostToDevice, c->st));
+  }
+  std::vector<int> lstart = {0, 1};
+  int nn = 1, n_active = n > leaf ? 1 : 0, cur = 0;
+  for (int level = 0; n_active > 0 && level < kTreeDepth; ++level) {
+    if ((rc = tree_grow_nodes(c, nn + 8 * n_active, nn))) return rc;
+    // active nodes hold > leaf particles each, so 8 n_active <= 8 (n / (leaf + 1)), the size taken above
+    if (8 * n_active > T.slot_cap) return fail(STEPS_ECUDA, "octree build: child slots exceed their bound");
+    tree_children_kernel<<<(8 * n_active + 255) / 256, 256, 0, c->st>>>(T.active[cur], n_active, level, key, T.link,
+                                                                       T.pre, T.cnt, T.beg);
+    tree_link_kernel<<<1, 1024, 0, c->st>>>(T.active[cur], n_active, level, leaf, nn, T.cnt, T.beg, T.pos, T.link,
+                                            T.geo, T.pre, T.active[cur ^ 1], T.totals);
+    CKLAUNCH("tree_level");
+    CKT(cudaMemcpyAsync(T.totals_h, T.totals, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->st));
+    CKT(cudaStreamSynchronize(c->st));
+    nn += T.totals_h[0];
+    lstart.push_back(nn);
+    n_active = T.totals_h[1];
+    cur ^= 1;
+  }
+  T.nodes = nn;
+  T.depth = (int)lstart.size() - 2;
+  for (int l = (int)lstart.size() - 2; l >= 0; --l) {
+    const int a = lstart[l], b = lstart[l + 1];
+    if (b <= a) continue;
+    tree_moments_kernel<<<(b - a + 255) / 256, 256, 0, c->st>>>(a, b, T.link, sidx, c->x, c->y, T.zt, c->m, c->h,
+                                                               T.u4, T.mom, T.hmx, T.hmf);
+  }
+  tree_pack_kernel<<<grid_for(nn, 256), 256, 0, c->st>>>(nn, T.mom, T.hmx, zeta, c->p.L, c->invL, T.nA, T.nB);
+  CKLAUNCH("tree_moments");
+  return STEPS_OK;
+}
+
+// The walk: pair sums [3][n] (internal order) into out.
+int tree_walk(steps_cyl_ctx* c, double* out) {
+  auto& T = c->tr;
+  TreeCrit C;
+  const double S = 2.0 * std::max(c->p.L, 2.0 * c->p.R_sim);
+  C.Lu = (float)(c->p.L / S);
+  C.hLu = 0.5f * C.Lu;
+  C.th2 = (float)(c->p.theta * c->p.theta);
+  const int groups = (c->n + 31) / 32;
+  const int blocks = (groups + kWalkWarps - 1) / kWalkWarps;
+  CKT(cudaMemsetAsync(T.inter, 0, sizeof(unsigned long long), c->st));
+  if (c->p.precision == STEPS_FP32_KAHAN)
+    tree_walk_kernel<true><<<blocks, kWalkWarps * 32, 0, c->st>>>(T.sA, T.sB, T.u4s, T.val[0], c->n, T.link, T.geo,
+                                                                  T.hmf, T.nA, T.nB, C, c->tab, c->tab_const, out,
+                                                                  T.inter, c->err);
+  else
+    tree_walk_kernel<false><<<blocks, kWalkWarps * 32, 0, c->st>>>(T.sA, T.sB, T.u4s, T.val[0], c->n, T.link, T.geo,
+                                                                   T.hmf, T.nA, T.nB, C, c->tab, c->tab_const, out,
+                                                                   T.inter, c->err);
+  CKLAUNCH("tree_walk");
+  return STEPS_OK;
+}
+
+// The frame of the next evaluation: the fixed one, or drawn from the seed and
+// the evaluation counter.
+void tree_next_frame(steps_cyl_ctx* c, double* zeta, double* phi) {
+  auto& T = c->tr;
+  if (T.fixed) {
+    *zeta = T.fzeta;
+    *phi = T.fphi;
+  } else {
+    SplitMix r(c->p.tree_seed * 0x9E3779B97F4A7C15ull + T.evals);
+    *zeta = r.uniform() * c->p.L;
+    *phi = 2.0 * M_PI * r.uniform();
+  }
+  ++T.evals;
+}
+
+// One octree pair evaluation into c->part ([3][n]), timed in phases.
+int tree_forces(steps_cyl_ctx* c, double* out) {
+  auto& T = c->tr;
+  double zeta, phi;
+  tree_next_frame(c, &zeta, &phi);
+  int rc;
+  if ((rc = tree_alloc(c))) return rc;
+  CKT(cudaEventRecord(T.t0, c->st));
+  if ((rc = tree_build(c, zeta, phi))) return rc;
+  CKT(cudaEventRecord(T.t1, c->st));
+  if ((rc = tree_walk(c, out))) return rc;
+  CKT(cudaEventRecord(T.t2, c->st));
+  unsigned long long inter = 0;
+  CKT(cudaMemcpyAsync(&inter, T.inter, sizeof inter, cudaMemcpyDeviceToHost, c->st));
+  CKT(cudaStreamSynchronize(c->st));
+  float b = 0.f, w = 0.f;
+  CKT(cudaEventElapsedTime(&b, T.t0, T.t1));
+  CKT(cudaEventElapsedTime(&w, T.t1, T.t2));
+  T.build_ms = b;
+  T.walk_ms = w;
+  T.interactions = (double)inter;
+  return STEPS_OK;
+}
+
+RadialCorr radial_corr(const steps_cyl_ctx* c) {
+  RadialCorr r{nullptr, 0, 0.0};
+  if (is_tree(c) && c->tr.rad && c->tr.rad_nb > 0) {
+    r.tab = c->tr.rad;
+    r.nb = c->tr.rad_nb;
+    r.rmax = c->tr.rad_rmax;
+  }
+  return r;
+}
+
 // The pair form of the next force evaluation: FP64, the selected modelled tail
 // when it is accepted, else the plain image sum (for the infinite window, which
 // has none, the correction table built at init).
@@ -543,6 +827,20 @@ Form force_form(const steps_cyl_ctx* c) {
 int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   const double pair_scale = -c->p.G * c->invL * c->invL;
   c->forces_stale = false;
+  if (is_tree(c)) {  // the octree: its own build and walk, then the common finalize
+    CK(cudaEventRecord(c->e0, c->st));
+    int rc = tree_forces(c, c->part);
+    if (rc) return rc;
+    CK(cudaEventRecord(c->e1, c->st));
+    c->timed = true;
+    c->last_images = c->tr.interactions;
+    finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
+        c->part, c->n, 0, c->U, c->C, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
+        kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr,
+        c->err, radial_corr(c));
+    CKLAUNCH("finalize");
+    return STEPS_OK;
+  }
   const Form form = force_form(c);
   if (form == Form::PLAIN && is_inf(c)) return fail(STEPS_ENOSURROGATE, "the infinite window has no correction table");
   CK(cudaEventRecord(c->e0, c->st));
@@ -711,6 +1009,17 @@ void release(steps_cyl_ctx* c) {
   if (c->tab.tex) cudaDestroyTextureObject(c->tab.tex);
   if (c->tab_arr) cudaFreeArray(c->tab_arr);
   cudaFree(c->chk);
+  {
+    auto& T = c->tr;
+    void* ptrs[] = {T.key[0], T.key[1], T.val[0], T.val[1], T.hist, T.offs, T.u4, T.u4s, T.zt, T.sA, T.sB,
+                    T.link, T.geo, T.hmf, T.pre, T.mom, T.hmx, T.nA, T.nB, T.active[0], T.active[1], T.cnt,
+                    T.beg, T.pos, T.totals, T.inter, T.rad};
+    for (void* q : ptrs) cudaFree(q);
+    if (T.totals_h) cudaFreeHost(T.totals_h);
+    if (T.t0) cudaEventDestroy(T.t0);
+    if (T.t1) cudaEventDestroy(T.t1);
+    if (T.t2) cudaEventDestroy(T.t2);
+  }
   if (c->e0) cudaEventDestroy(c->e0);
   if (c->e1) cudaEventDestroy(c->e1);
   cudaSetDevice(prev);
@@ -754,17 +1063,6 @@ int scatter_out(steps_cyl_ctx* c, const double* const src[3], double* const dst[
 // Learned far-image surrogate: host side (see surrogate_train.cuh and
 // surrogate_pair.cuh for the definition and the kernels).
 // ---------------------------------------------------------------------------
-struct SplitMix {
-  uint64_t s;
-  explicit SplitMix(uint64_t seed) : s(seed) {}
-  uint64_t next() {
-    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-  }
-  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }  // [0, 1)
-};
 
 uint32_t half_bits(float v) {
   __half_raw r = __float2half_rn(v);
@@ -929,6 +1227,128 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
   *p999 = quant(0.999);
   if (ms_plain) *ms_plain = ms[0];
   if (ms_surr) *ms_surr = ms[1];
+  return STEPS_OK;
+}
+
+// Install a radial correction table (nb bin means over [0, rmax]).
+int set_radial(steps_cyl_ctx* c, const std::vector<double>& tab, double rmax) {
+  auto& T = c->tr;
+  cudaFree(T.rad);
+  T.rad = nullptr;
+  T.rad_nb = 0;
+  CK(cudaMalloc(&T.rad, sizeof(double) * tab.size()));
+  CK(cudaMemcpyAsync(T.rad, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  T.rad_nb = (int)tab.size();
+  T.rad_rmax = rmax;
+  T.rad_h = tab;
+  return STEPS_OK;
+}
+
+// Radial calibration of the octree (Sect. 2.4): the mean radial component of
+// (octree - direct) pair force over a particle sample and several frames, in
+// bins of rho. The direct reference is the same pair form (infinite window,
+// correction table) summed over all j.
+int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frames, const int64_t* sample,
+                   std::vector<double>& table, double* rmax_out) {
+  const int n = c->n;
+  const int ni = std::min(ns, n);
+  std::vector<int> inv(n);
+  for (int k = 0; k < n; ++k) inv[c->perm_h[k]] = k;
+  std::vector<int64_t> pick(ni);
+  if (sample) {
+    for (int q = 0; q < ni; ++q) {
+      if (sample[q] < 0 || sample[q] >= n) return fail(STEPS_EINVAL, "sample index out of range");
+      pick[q] = inv[sample[q]];
+    }
+  } else {
+    std::vector<int> all(n);
+    for (int k = 0; k < n; ++k) all[k] = k;
+    SplitMix rng(0xca1b0000ull ^ c->p.tree_seed);
+    for (int q = 0; q < ni; ++q) {
+      const int r = q + (int)(rng.next() % (uint64_t)(n - q));
+      std::swap(all[q], all[r]);
+      pick[q] = all[q];
+    }
+  }
+  std::vector<double> hx(n), hy(n);
+  CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double rmax = 0.0;
+  for (int k = 0; k < n; ++k) rmax = std::max(rmax, std::hypot(hx[k], hy[k]));
+  if (!(rmax > 0)) return fail(STEPS_EINVAL, "every particle sits on the axis");
+  // direct pair sums of the sample
+  if (ni > c->idx_cap) {
+    cudaFree(c->idx);
+    cudaFree(c->sub);
+    c->idx = nullptr;
+    c->sub = nullptr;
+    c->idx_cap = 0;
+    CK(cudaMalloc(&c->idx, sizeof(int64_t) * ni));
+    CK(cudaMalloc(&c->sub, sizeof(double) * ni * 3));
+    c->idx_cap = ni;
+  }
+  CK(cudaMemcpyAsync(c->idx, pick.data(), sizeof(int64_t) * ni, cudaMemcpyHostToDevice, c->st));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  const int gx = (ni + kBI - 1) / kBI;
+  const int want = std::max(1, std::min(c->NT, (sms * 8 + gx - 1) / gx));
+  const int tpc = (c->NT + want - 1) / want;
+  const int JC = (c->NT + tpc - 1) / tpc;
+  int rc;
+  if ((rc = grow(c, (size_t)JC * 3 * ni + 3 * (size_t)ni))) return rc;
+  double* part = c->chk;
+  double* sums = part + (size_t)JC * 3 * ni;
+  pair_fp32_table_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, n, 0, c->idx, ni, tpc,
+                                                                             c->tab, c->tab_const, part);
+  chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
+  CKLAUNCH("calibration_direct");
+  std::vector<double> D(3 * (size_t)ni), Tq(3 * (size_t)ni);
+  CK(cudaMemcpyAsync(D.data(), sums, sizeof(double) * 3 * ni, cudaMemcpyDeviceToHost, c->st));
+  // octree pair sums of the sample in each frame (all particles walk: groups are fixed by the key order)
+  int* dpick = nullptr;
+  std::vector<int> pick32(pick.begin(), pick.end());
+  CK(cudaMalloc(&dpick, sizeof(int) * ni));
+  CK(cudaMemcpyAsync(dpick, pick32.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, c->st));
+  const double pair_scale = -c->p.G * c->invL * c->invL;
+  std::vector<double> sum(nb, 0.0);
+  std::vector<long long> cnt(nb, 0);
+  SplitMix fr(0xf4a3e000ull ^ c->p.tree_seed);
+  for (int f = 0; f < nf && rc == STEPS_OK; ++f) {
+    const double zeta = frames ? frames[2 * f] : fr.uniform() * c->p.L;
+    const double phi = frames ? frames[2 * f + 1] : 2.0 * M_PI * fr.uniform();
+    if (!(zeta >= 0.0 && zeta < c->p.L) || !std::isfinite(phi)) {
+      rc = fail(STEPS_EINVAL, "frame %d: zeta must lie in [0, L) and phi be finite", f);
+      break;
+    }
+    if ((rc = tree_build(c, zeta, phi)) || (rc = tree_walk(c, c->part))) break;
+    for (int a = 0; a < 3; ++a)
+      gather_kernel<<<grid_for(ni, 256), 256, 0, c->st>>>(c->part + (size_t)a * n, dpick, ni, 1.0,
+                                                         c->sub + (size_t)a * ni);
+    if (cudaMemcpyAsync(Tq.data(), c->sub, sizeof(double) * 3 * ni, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+      rc = fail(STEPS_ECUDA, "calibration read-back failed");
+      break;
+    }
+    for (int q = 0; q < ni; ++q) {
+      const int i = (int)pick[q];
+      const double rho = std::hypot(hx[i], hy[i]);
+      if (!(rho > 0)) continue;
+      const double ex = pair_scale * (Tq[q] - D[q]), ey = pair_scale * (Tq[(size_t)ni + q] - D[(size_t)ni + q]);
+      const int k = std::min(nb - 1, (int)(rho / rmax * nb));
+      sum[k] += (ex * hx[i] + ey * hy[i]) / rho;
+      ++cnt[k];
+    }
+  }
+  cudaFree(dpick);
+  if (rc) return rc;
+  int e = 0;
+  if ((rc = read_and_clear_err(c, &e))) return rc;
+  if (e) return device_error(e);
+  table.assign(nb, 0.0);
+  for (int k = 0; k < nb; ++k) table[k] = cnt[k] ? sum[k] / (double)cnt[k] : 0.0;
+  *rmax_out = rmax;
   return STEPS_OK;
 }
 
@@ -1296,6 +1716,10 @@ int steps_cyl_params_default(steps_cyl_params* p) {
   p->check_every = 50;
   p->check_particles = 1024;
   p->stream = nullptr;
+  p->force = STEPS_FORCE_DIRECT;
+  p->leaf_size = 16;
+  p->theta = 0.5;
+  p->tree_seed = 1;
   return STEPS_OK;
 }
 
@@ -1632,8 +2056,11 @@ struct CkptHeader {
   float surr[STEPS_SURR_NPARAM];
   int32_t tab_ok, tab_nx, tab_ny, pad;  // correction table: rebuilt on resume from its grid
   double tab_dR_max, tab_bound_med, tab_bound_p999;
+  uint64_t tree_evals;                  // octree: frame counter, fixed frame, radial table (after the header)
+  int32_t tree_fixed, rad_nb;
+  double tree_zeta, tree_phi, rad_rmax;
 };
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   g_last_error.clear();
@@ -1664,6 +2091,12 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   hd.tab_dR_max = c->tab_dR_max;
   hd.tab_bound_med = c->tab_bound_med;
   hd.tab_bound_p999 = c->tab_bound_p999;
+  hd.tree_evals = c->tr.evals;
+  hd.tree_fixed = c->tr.fixed ? 1 : 0;
+  hd.tree_zeta = c->tr.fzeta;
+  hd.tree_phi = c->tr.fphi;
+  hd.rad_nb = c->tr.rad ? c->tr.rad_nb : 0;
+  hd.rad_rmax = c->tr.rad_rmax;
   if (c->forces_stale) {
     int rc = eval_forces(c, false, 0.0);
     if (rc) return rc;
@@ -1677,6 +2110,7 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   if (!f) return fail(STEPS_EINVAL, "cannot open %s for writing", path);
   bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
   if (ok && hd.bgK) ok = std::fwrite(tab.data(), sizeof(double), tab.size(), f) == tab.size();
+  if (ok && hd.rad_nb) ok = std::fwrite(c->tr.rad_h.data(), sizeof(double), hd.rad_nb, f) == (size_t)hd.rad_nb;
   if (ok) ok = std::fwrite(arr.data(), sizeof(double), arr.size(), f) == arr.size();
   if (ok) ok = std::fwrite(c->perm_h.data(), sizeof(int), c->n, f) == (size_t)c->n;
   ok = (std::fclose(f) == 0) && ok;
@@ -1693,13 +2127,14 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
   CkptHeader hd;
   if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "STEPSCYL", 8) != 0 ||
       hd.version != kCkptVersion || hd.header_bytes != sizeof hd || hd.n < 2 || hd.n > 0x7fffffffLL - kBI ||
-      hd.bgK < 0 || hd.bgK > (1 << 20)) {
+      hd.bgK < 0 || hd.bgK > (1 << 20) || hd.rad_nb < 0 || hd.rad_nb > 4096) {
     std::fclose(f);
     return fail(STEPS_EINVAL, "%s is not a checkpoint of this library version", path);
   }
-  std::vector<double> tab(hd.bgK ? hd.bgK + 4 : 0), arr((size_t)hd.n * 11);
+  std::vector<double> tab(hd.bgK ? hd.bgK + 4 : 0), arr((size_t)hd.n * 11), rad(hd.rad_nb);
   std::vector<int> perm(hd.n);
   bool ok = !hd.bgK || std::fread(tab.data(), sizeof(double), tab.size(), f) == tab.size();
+  ok = ok && (!hd.rad_nb || std::fread(rad.data(), sizeof(double), rad.size(), f) == rad.size());
   ok = ok && std::fread(arr.data(), sizeof(double), arr.size(), f) == arr.size();
   ok = ok && std::fread(perm.data(), sizeof(int), perm.size(), f) == perm.size();
   std::fclose(f);
@@ -1724,6 +2159,10 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
   c->invL = 1.0 / hd.p.L;
   c->steps_since_order = hd.steps_since_order;
   c->steps_since_check = hd.steps_since_check;
+  c->tr.evals = hd.tree_evals;
+  c->tr.fixed = hd.tree_fixed != 0;
+  c->tr.fzeta = hd.tree_zeta;
+  c->tr.fphi = hd.tree_phi;
   c->surr_bound_med = hd.bound_med;
   c->surr_bound_p999 = hd.bound_p999;
   c->perm_h = perm;
@@ -1757,6 +2196,10 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
     c->tab_ok = true;
     c->tab_bound_med = hd.tab_bound_med;
     c->tab_bound_p999 = hd.tab_bound_p999;
+  }
+  if (hd.rad_nb) {
+    if (!(hd.rad_rmax > 0)) return bail(fail(STEPS_EINVAL, "corrupt checkpoint (radial table)"));
+    if ((rc = set_radial(c, rad, hd.rad_rmax))) return bail(rc);
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(fail(STEPS_ECUDA, "synchronise failed"));
   *out = c;
@@ -1880,6 +2323,7 @@ int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
   if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE && tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
   if (is_inf(c) && tail == STEPS_TAIL_FULL) return fail(STEPS_EINVAL, "the infinite window has no plain image sum");
+  if (is_tree(c) && tail != STEPS_TAIL_TABLE) return fail(STEPS_EINVAL, "the octree evaluates the correction-table form");
   if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
   if (tail == STEPS_TAIL_TABLE && !c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
   if (tail != STEPS_TAIL_FULL && c->p.precision == STEPS_FP64)
@@ -1953,6 +2397,62 @@ int steps_cyl_check_tail(steps_cyl_ctx* c, int32_t tail, int32_t check_particles
   DeviceGuard guard(c->dev);
   return run_check(c, STEPS_TAIL_TABLE, check_particles, 0xc4ec0000ull + (uint64_t)c->steps_since_check,
                    &report[0], &report[1], &report[2], &report[3]);
+}
+
+
+int steps_cyl_tree_frame(steps_cyl_ctx* c, double zeta, double phi) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!is_tree(c)) return fail(STEPS_EINVAL, "the context does not use the octree");
+  if (zeta < 0.0) {
+    c->tr.fixed = false;
+  } else {
+    if (!(zeta < c->p.L) || !std::isfinite(phi)) return fail(STEPS_EINVAL, "zeta must lie in [0, L), phi be finite");
+    c->tr.fixed = true;
+    c->tr.fzeta = zeta;
+    c->tr.fphi = phi;
+  }
+  c->forces_stale = true;
+  return STEPS_OK;
+}
+
+int steps_cyl_tree_stats(steps_cyl_ctx* c, double* out) {
+  g_last_error.clear();
+  if (!c || !out) return fail(STEPS_EINVAL, "NULL argument");
+  if (!is_tree(c)) return fail(STEPS_EINVAL, "the context does not use the octree");
+  out[0] = c->tr.nodes;
+  out[1] = c->tr.depth;
+  out[2] = c->tr.interactions;
+  out[3] = c->tr.build_ms;
+  out[4] = c->tr.walk_ms;
+  out[5] = (double)c->tr.evals;
+  return STEPS_OK;
+}
+
+int steps_cyl_tree_calibrate(steps_cyl_ctx* c, int32_t n_frames, int32_t n_bins, int32_t n_sample,
+                             const double* frames, const int64_t* sample, double* table, double* rmax) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!is_tree(c)) return fail(STEPS_EINVAL, "the context does not use the octree");
+  if (n_frames < 0 || n_frames > 4096) return fail(STEPS_EINVAL, "n_frames must be in [0, 4096]");
+  DeviceGuard guard(c->dev);
+  c->forces_stale = true;
+  if (n_frames == 0) {
+    cudaFree(c->tr.rad);
+    c->tr.rad = nullptr;
+    c->tr.rad_nb = 0;
+    c->tr.rad_h.clear();
+    return STEPS_OK;
+  }
+  if (n_bins < 1 || n_bins > 4096 || n_sample < 1) return fail(STEPS_EINVAL, "bad bins or sample size");
+  std::vector<double> tab;
+  double rm = 0.0;
+  int rc = tree_calibrate(c, n_frames, n_bins, n_sample, frames, sample, tab, &rm);
+  if (rc) return rc;
+  if ((rc = set_radial(c, tab, rm))) return rc;
+  if (table) std::memcpy(table, tab.data(), sizeof(double) * n_bins);
+  if (rmax) *rmax = rm;
+  return STEPS_OK;
 }
 
 

@@ -30,6 +30,7 @@ STEPS_FP64, STEPS_FP32_KAHAN, STEPS_FP32_PLAIN = 0, 1, 2
 STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE, STEPS_TAIL_TABLE = 0, 1, 2
 STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE, STEPS_BG_SPHERE = 0, 1, 2, 3
 STEPS_TOPO_S1R2, STEPS_TOPO_R3 = 0, 1
+STEPS_FORCE_DIRECT, STEPS_FORCE_OCTREE = 0, 1
 
 _EXPORTS = [
     "steps_cyl_params_default", "steps_cyl_init", "steps_cyl_forces", "steps_cyl_forces_subset",
@@ -39,6 +40,7 @@ _EXPORTS = [
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
+    "steps_cyl_tree_frame", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
 ]
 
 STEPS_SURR_NW = 1250
@@ -66,6 +68,8 @@ class Params(ctypes.Structure):
         ("device", ctypes.c_int32), ("reorder_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
         ("check_particles", ctypes.c_int32), ("topology", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("force", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("theta", ctypes.c_double),
+        ("tree_seed", ctypes.c_uint64),
     ]
 
 
@@ -126,6 +130,9 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_check_tail.argtypes = [p, i32, i32, p]
     L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
     L.steps_cyl_resume.argtypes = [ctypes.POINTER(p), ctypes.c_char_p, i32, p]
+    L.steps_cyl_tree_frame.argtypes = [p, d, d]
+    L.steps_cyl_tree_stats.argtypes = [p, p]
+    L.steps_cyl_tree_calibrate.argtypes = [p, i32, i32, i32, p, p, p, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -190,6 +197,10 @@ class Config:
     check_every: int = 50
     check_particles: int = 1024
     topology: int = STEPS_TOPO_S1R2
+    force: int = STEPS_FORCE_DIRECT
+    leaf_size: int = 16
+    theta: float = 0.5
+    tree_seed: int = 1
     stream: int = 0  # cudaStream_t as an integer (torch.cuda.Stream.cuda_stream), 0 = default
 
     def to_c(self) -> Params:
@@ -377,6 +388,31 @@ def steps_cyl_check_tail(ctx, tail: int, check_particles: int = 1024) -> np.ndar
     rep = np.zeros(4)
     _check(load().steps_cyl_check_tail(ctx, int(tail), int(check_particles), _ptr(rep)))
     return rep
+
+
+def steps_cyl_tree_frame(ctx, zeta: float, phi: float):
+    """Fix the octree frame (shift zeta along the axis, rotation phi); zeta < 0: random per evaluation."""
+    _check(load().steps_cyl_tree_frame(ctx, float(zeta), float(phi)))
+
+
+def steps_cyl_tree_stats(ctx) -> dict:
+    out = np.zeros(6)
+    _check(load().steps_cyl_tree_stats(ctx, _ptr(out)))
+    return {"nodes": int(out[0]), "depth": int(out[1]), "interactions": float(out[2]), "build_ms": float(out[3]),
+            "walk_ms": float(out[4]), "evaluations": int(out[5])}
+
+
+def steps_cyl_tree_calibrate(ctx, n_frames: int, n_bins: int = 64, n_sample: int = 4096, frames=None, sample=None):
+    """Radial calibration of the octree; returns (table of n_bins means, rmax)."""
+    fr = None if frames is None else np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
+    sm = None if sample is None else np.ascontiguousarray(sample, dtype=np.int64)
+    if sm is not None and sm.shape[0] < n_sample:
+        raise ValueError("sample holds fewer than n_sample indices")
+    tab = np.zeros(max(int(n_bins), 1))
+    rmax = ctypes.c_double()
+    _check(load().steps_cyl_tree_calibrate(ctx, int(n_frames), int(n_bins), int(n_sample), _ptr(fr), _ptr(sm),
+                                           _ptr(tab), ctypes.byref(rmax)))
+    return tab, rmax.value
 
 
 def steps_cyl_checkpoint(ctx, path: str):

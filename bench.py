@@ -584,6 +584,16 @@ def run_workload(args):
         ap, msp = _timed_forces(sc, torch, sim, reps)
         line["fp32_plain"] = {"pair_ms": msp, "pair_images_per_s": pairs * 2 * w.n_cut / (msp * 1e-3),
                               "error_vs_fp64": _err(ap[idx], a64)}
+        # pair-only errors: the same differences over the FP64 pair term alone (a context without the
+        # background, whose FP64 subset gives the pair term; the background itself is FP64 in every form)
+        nobg = _ctx_for(sc, torch, w, d, sc.STEPS_FP32_PLAIN, background=sc.STEPS_BG_OFF)
+        sc.steps_cyl_set_precision(nobg.ctx, sc.STEPS_FP64)
+        p64 = nobg.forces_subset(idx)
+        nobg.close()
+        for key, a in (("fp32_kahan", a32), ("fp32_plain", ap)):
+            r = np.linalg.norm(a[idx] - a64, axis=1) / np.linalg.norm(p64, axis=1)
+            line[key]["error_vs_fp64_pair_only"] = {"median": float(np.median(r)),
+                                                    "p999": float(np.quantile(r, 0.999)), "max": float(r.max())}
     if w.name.startswith("surrogate") or w.name.startswith("production"):
         sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
         rep = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())

@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 
+import oracle
 from paper_2602_20787_gb300 import ics
 from tests.gpu_helpers import oracle_accel, rel_err, stats
 
@@ -202,3 +203,32 @@ def test_invalid_inputs_are_rejected(sc):
     with pytest.raises(sc.StepsError):
         sim.step(-1.0)
     sim.close()
+
+
+def test_coincident_particles(sc):
+    # duplicated positions (r = 0 between distinct particles; their softenings differ) in every pair form
+    d = ics.particle_load(300, 21, 1.0)
+    d["pos"][10] = d["pos"][11]
+    d["pos"][200] = d["pos"][201] = d["pos"][202]
+    ref = oracle_accel(d["pos"], d["m"], d["h"], 8)
+    for precision in (0, 1, 2):
+        sim = make_sim(sc, d, 8, precision)
+        a = sim.forces()
+        assert np.all(np.isfinite(a))
+        assert stats(a, ref)[2] < (1e-10 if precision == 0 else 1e-3)
+        sim.close()
+    # the infinite window (table form) and the octree on the same load
+    dR_max = max(2.2 * float(np.hypot(d["pos"][:, 0], d["pos"][:, 1]).max()), 1.0)
+    cfg = oracle.make_table_cfg(0, 4, 257, 33, dR_max)
+    tab = oracle.tail_table_build(cfg)
+    rho = d["m"].sum() / (np.pi * ics.R_SIM ** 2)
+    ref_inf = oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, tab, cfg)
+    ref_inf += oracle.background_field(d["pos"], ics.R_SIM, 0.0, 1.0, rho, mode=2)
+    for force in (sc.STEPS_FORCE_DIRECT, sc.STEPS_FORCE_OCTREE):
+        cfg_c = sc.Config(n_cut=0, n0=4, tail=sc.STEPS_TAIL_TABLE, background=sc.STEPS_BG_INFINITE, rho_bar=rho,
+                          force=force, theta=1e-3)
+        sim = sc.Simulation(cfg_c, d["pos"], d["vel"], d["m"], d["h"])
+        a = sim.forces()
+        assert np.all(np.isfinite(a))
+        assert stats(a, ref_inf)[2] < 1e-3
+        sim.close()

@@ -151,3 +151,16 @@ def test_tail_plus_near_is_the_window(orc, rz):
     near_z = sum((dzw + k) * orc.spline_F_over_r(math.hypot(dR, dzw + k), h) for k in range(-n0, n0 + 1))
     assert SRt + near_R == pytest.approx(SR, rel=1e-14)
     assert Szt + near_z == pytest.approx(Sz, rel=1e-12, abs=1e-15)
+
+
+def test_coincident_particles_exert_no_force_on_each_other(orc):
+    # two particles at one point: r = 0 in the centre image, the spline centre is finite
+    # and the separation vector is zero, so the pair adds nothing; the other images pull
+    # symmetrically in +-z and cancel
+    pos = np.array([[0.4, -0.2, 0.3], [0.4, -0.2, 0.3]])
+    g = orc.pair_field(pos, np.array([1.0, 2.0]), np.array([0.05, 0.07]), 1.0, 1.0, 8)
+    assert np.abs(g).max() <= 1e-15     # the +-z images cancel up to rounding
+    # with a third particle the coincident pair feels the same pull per unit mass
+    pos3 = np.vstack([pos, [[1.1, 0.5, 0.8]]])
+    g3 = orc.pair_field(pos3, np.array([1.0, 2.0, 0.5]), np.array([0.05, 0.05, 0.05]), 1.0, 1.0, 8)
+    np.testing.assert_allclose(g3[0], g3[1], rtol=1e-14, atol=1e-14 * np.abs(g3).max())

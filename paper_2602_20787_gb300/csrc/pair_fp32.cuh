@@ -149,21 +149,18 @@ constexpr int kTwo23Bits = 0x4B000000;
 // can be inside only if dR < hh and |k| < hh + 1/2; rn(hh) is an upper bound
 // of that largest |k|, and kw is its maximum over the warp (-1: no lane's pair
 // is softened). Both roundings are exact integer-valued FP32 additions.
-// WRAP = false (R^3 topology): dz is the plain difference, no period.
-template <bool WRAP = true>
 __device__ __forceinline__ void pair_separation(const IParticle& I, const float4& A, const float4& B, float& dx,
                                                 float& dy, float& dz, float& dR2, float& hh) {
   const u64 D = add2(sub2(I.xyh, pk(A.x, A.y)), sub2(I.xyl, pk(B.x, B.y)));
   upk(D, dx, dy);
   dR2 = fmaf(dx, dx, dy * dy);
   const float d = I.zh - A.z;
-  dz = (WRAP ? d - __fsub_rn(__fadd_rn(d, kRound23), kRound23) : d) + (I.zl - B.z);
+  dz = (d - __fsub_rn(__fadd_rn(d, kRound23), kRound23)) + (I.zl - B.z);
   hh = I.h + B.w;
 }
-template <bool WRAP = true>
 __device__ __forceinline__ void pair_geometry(const IParticle& I, const float4& A, const float4& B, float& dx, float& dy,
                                               float& dz, float& dR2, float& hh, int& kw) {
-  pair_separation<WRAP>(I, A, B, dx, dy, dz, dR2, hh);
+  pair_separation(I, A, B, dx, dy, dz, dR2, hh);
   const int kl = dR2 < hh * hh ? __float_as_int(__fadd_rn(hh, kTwo23)) : kTwo23Bits - 1;
   kw = __reduce_max_sync(0xffffffffu, kl) - kTwo23Bits;
 }
@@ -191,12 +188,9 @@ __device__ __forceinline__ u64 spline_outer_value(u64 RR, u64 N3, u64 NIH) {
 // All branches, for images that may have u < 1/2 on some lane. The inner
 // branch is h^-3 (32/3 - 38.4 u^2 + 32 u^3), selected per lane. r^2 is floored
 // at 1e-30 so that a coincident pair gives a finite inner value.
-__device__ __forceinline__ u64 spline_over_r2(u64 O, u64 DR2, u64 IH, u64 NIH, u64 IH3) {
-  const u64 R2 = fma2(O, O, DR2);
-  float a, b;
-  upk(R2, a, b);
-  const u64 RI = pk(rsq(fmaxf(a, 1e-30f)), rsq(fmaxf(b, 1e-30f)));
-  const u64 N3 = mul2(mul2(RI, RI), RI);
+// The select itself, from r^2, its floored rsqrt RI and r^-3 = RI^3 (also the
+// R^3 kernel's softened branch).
+__device__ __forceinline__ u64 spline_value_r2(u64 R2, u64 RI, u64 N3, u64 IH, u64 NIH, u64 IH3) {
   const u64 RR = mul2(R2, RI);
   const u64 U = mul2(RR, IH);
   const u64 inner = mul2(fma2(mul2(U, U), fma2(U, pk(32.0f, 32.0f), pk(-38.4f, -38.4f)),
@@ -207,6 +201,14 @@ __device__ __forceinline__ u64 spline_over_r2(u64 O, u64 DR2, u64 IH, u64 NIH, u
   upk(inner, ia, ib);
   upk(outer, oa, ob);
   return pk(ua < 0.5f ? ia : oa, ub < 0.5f ? ib : ob);
+}
+
+__device__ __forceinline__ u64 spline_over_r2(u64 O, u64 DR2, u64 IH, u64 NIH, u64 IH3) {
+  const u64 R2 = fma2(O, O, DR2);
+  float a, b;
+  upk(R2, a, b);
+  const u64 RI = pk(rsq(fmaxf(a, 1e-30f)), rsq(fmaxf(b, 1e-30f)));
+  return spline_value_r2(R2, RI, mul2(mul2(RI, RI), RI), IH, NIH, IH3);
 }
 
 // Images with u >= 1/2 on every lane (outer shell or beyond): no select.
@@ -345,9 +347,8 @@ static_assert(kBJ % STEPS_KAHAN_GROUP == 0, "a j-tile holds whole Kahan groups")
 
 // All pairs of i with the kBJ j of a (padded) shared-memory tile: pair forces
 // are summed plainly over groups of STEPS_KAHAN_GROUP j, and each group sum
-// enters the compensated per-i sum. R3: the R^3 topology of eq. NewtonianForce
-// (no wrap, the centre image alone).
-template <bool KAHAN, bool R3 = false>
+// enters the compensated per-i sum.
+template <bool KAHAN>
 __device__ __forceinline__ void pair_tile_fp32(const IParticle& I, const float4* sA, const float4* sB, int n_cut,
                                                float fnc, float& sx, float& sy, float& sz, float& cx, float& cy,
                                                float& cz) {
@@ -360,12 +361,9 @@ __device__ __forceinline__ void pair_tile_fp32(const IParticle& I, const float4*
       const float4 B = sB[k];
       float dx, dy, dz, dR2, hh;
       int kw;
-      pair_geometry<!R3>(I, A, B, dx, dy, dz, dR2, hh, kw);
+      pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
       float sr, szz;
-      if (R3)
-        pair_images_fp32<false>(dR2, dz, hh, 1, 1.0f, kw, sr, szz);
-      else
-        pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
+      pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
       const float msr = A.w * sr;
       gx = fmaf(dx, msr, gx);
       gy = fmaf(dy, msr, gy);
@@ -378,7 +376,7 @@ __device__ __forceinline__ void pair_tile_fp32(const IParticle& I, const float4*
 }
 
 // part layout: [slot][3][kBI] doubles, slot = i-block + CTA.
-template <bool KAHAN, bool R3 = false>
+template <bool KAHAN>
 __global__ void __launch_bounds__(kBI, 8)
 pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut,
                  long long U, int NT, int C, double* __restrict__ part) {
@@ -401,7 +399,7 @@ pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, i
       __syncthreads();
       load_tile(jA, jB, n, t, sA, sB);
       __syncthreads();
-      pair_tile_fp32<KAHAN, R3>(I, sA, sB, n_cut, fnc, sx, sy, sz, cx, cy, cz);
+      pair_tile_fp32<KAHAN>(I, sA, sB, n_cut, fnc, sx, sy, sz, cx, cy, cz);
     }
     const long long slot = (long long)b + c;
     double* dst = part + slot * 3 * kBI;

@@ -32,6 +32,7 @@
 #include "surrogate_train.cuh"
 #include "tail_table.cuh"
 #include "octree.cuh"
+#include "r3_pair.cuh"
 
 using namespace steps;
 
@@ -879,9 +880,9 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
     CKLAUNCH("pair_fp32_table");
   } else if (is_r3(c)) {
     if (c->p.precision == STEPS_FP32_KAHAN)
-      pair_fp32_kernel<true, true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 1, c->U, c->NT, c->C, c->part);
+      pair_r3_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part);
     else
-      pair_fp32_kernel<false, true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 1, c->U, c->NT, c->C, c->part);
+      pair_r3_kernel<false><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part);
     CKLAUNCH("pair_fp32_r3");
   } else if (c->p.precision == STEPS_FP32_KAHAN) {
     pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);

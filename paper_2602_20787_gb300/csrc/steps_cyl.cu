@@ -269,6 +269,7 @@ struct steps_cyl_ctx {
     unsigned long long* inter = nullptr;
     int nodes = 0, depth = 0;
     double interactions = 0.0, build_ms = 0.0, walk_ms = 0.0;
+    bool ready = false;                     // every per-particle buffer above is allocated
     bool fixed = false;
     double fzeta = 0.0, fphi = 0.0;
     uint64_t evals = 0;
@@ -598,9 +599,30 @@ bool is_tree(const steps_cyl_ctx* c) { return c->p.force == STEPS_FORCE_OCTREE; 
 
 int tree_alloc(steps_cyl_ctx* c) {
   auto& T = c->tr;
-  if (T.key[0]) return STEPS_OK;
+  if (T.ready) return STEPS_OK;
+  // a failure part-way leaves ready false; the buffers already made are freed with the context
+  // or replaced on the next attempt
   const size_t n = (size_t)c->n;
   const int ntiles = (c->n + kSortTile - 1) / kSortTile;
+  {
+    void* old[] = {T.key[0], T.key[1], T.val[0], T.val[1], T.hist, T.offs, T.u4, T.u4s, T.zt, T.sA, T.sB,
+                   T.totals, T.inter};
+    for (void* q : old) cudaFree(q);
+    T.key[0] = T.key[1] = nullptr;
+    T.val[0] = T.val[1] = nullptr;
+    T.hist = T.offs = nullptr;
+    T.u4 = T.u4s = T.sA = T.sB = nullptr;
+    T.zt = nullptr;
+    T.totals = nullptr;
+    T.inter = nullptr;
+    if (T.totals_h) cudaFreeHost(T.totals_h);
+    T.totals_h = nullptr;
+    for (cudaEvent_t* e : {&T.t0, &T.t1, &T.t2})
+      if (*e) {
+        cudaEventDestroy(*e);
+        *e = nullptr;
+      }
+  }
   for (int k = 0; k < 2; ++k) {
     CKT(cudaMalloc(&T.key[k], sizeof(uint64_t) * n));
     CKT(cudaMalloc(&T.val[k], sizeof(int) * n));
@@ -618,6 +640,7 @@ int tree_alloc(steps_cyl_ctx* c) {
   CKT(cudaEventCreate(&T.t0));
   CKT(cudaEventCreate(&T.t1));
   CKT(cudaEventCreate(&T.t2));
+  T.ready = true;
   return STEPS_OK;
 }
 
@@ -650,6 +673,8 @@ int tree_grow_slots(steps_cyl_ctx* c, int need) {
   const int cap = std::max(need, 2 * T.slot_cap);
   int* ptrs[5] = {T.active[0], T.active[1], T.cnt, T.beg, T.pos};
   for (int* q : ptrs) cudaFree(q);
+  T.active[0] = T.active[1] = T.cnt = T.beg = T.pos = nullptr;
+  T.slot_cap = 0;  // set again only once every array exists
   // active lists hold node ids (<= cap / 8 per level), the others one entry per child slot
   CKT(cudaMalloc(&T.active[0], sizeof(int) * (size_t)cap));
   CKT(cudaMalloc(&T.active[1], sizeof(int) * (size_t)cap));

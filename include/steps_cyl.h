@@ -40,7 +40,8 @@ extern "C" {
 #define STEPS_EINVAL (-1)               /* bad argument (N < 2, h <= 0, L <= 0, z outside [0,L), non-finite input) */
 #define STEPS_ECUDA (-2)                /* a CUDA runtime call failed */
 #define STEPS_ENOMEM (-3)               /* device allocation failed */
-#define STEPS_EDEVICE (-4)              /* the device error word was set (non-finite force, particle beyond the background table) */
+#define STEPS_EDEVICE (-4)              /* the device error word was set (non-finite force, particle beyond the background
+                                         * table, particle outside the octree's root cube, octree walk stack overflow) */
 #define STEPS_ESURROGATE_REJECTED (-5)  /* surrogate error above its bound: the plain image sum was used instead */
 #define STEPS_ENOSURROGATE (-6)         /* modelled tail requested but no accepted network / correction table is loaded */
 

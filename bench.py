@@ -153,6 +153,30 @@ def cpu_baseline(w, d, target_s: float = 12.0):
             "sample": f"{k} i-particles x all {n} j x {2 * w.n_cut} images (FP64 pair field + background), {el:.1f} s"}
 
 
+def oracle_rate(call, n_all, units_per_i, unit, what, target_s=4.0, seed=779):
+    """The FP64 oracle (as it stands) timed beside a form on a bounded i-sample:
+    call(idx) evaluates the sampled particles; one i stands for units_per_i
+    work units (pairs, or 1 for a force per particle)."""
+    import oracle
+    from paper_2602_20787_gb300 import ics
+    probe = ics.subsample(n_all, 4, seed=seed)
+    t0 = time.perf_counter()
+    call(probe)
+    dt_probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(n_all, max(4, 4 * target_s / dt_probe)))
+    for attempt in range(2):  # the probe carries start-up costs: rescale once from a real run
+        idx = ics.subsample(n_all, k, seed=seed + 1)
+        t0 = time.perf_counter()
+        call(idx)
+        el = time.perf_counter() - t0
+        if attempt == 0 and el < 0.5 * target_s and k < n_all:
+            k = int(min(n_all, max(k + 1, k * target_s / max(el, 1e-3))))
+        else:
+            break
+    return {"value": k * units_per_i / el, "unit": unit, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} i-particles: {what}, {el:.1f} s"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -384,7 +408,10 @@ def run_r3_or_glass(args):
         sim.step(dt, 10)
         ev1.record()
         torch.cuda.synchronize()
-        line = {"workload": args.workload, "n": n, "topology": "R3", "images_per_pair": 1,
+        import oracle
+        cpu = oracle_rate(lambda ix: oracle.pair_field_r3(d["pos"], d["m"], d["h"], 1.0, idx=ix), n, n - 1.0,
+                          "pair interactions/s", f"FP64 R3 pair field, all {n} j")
+        line = {"workload": args.workload, "n": n, "topology": "R3", "images_per_pair": 1, "cpu_baseline": cpu,
                 "fp32_kahan": {"pair_ms": ms, "pair_interactions_per_s": pairs / (ms * 1e-3),
                                "fraction_of_mufu_bound": pairs / (ms * 1e-3) / peak,
                                "error_vs_fp64": _err(a32[idx], a64)},
@@ -453,6 +480,14 @@ def run_inf(args):
                       "roofline": {"bound": "mufu", "mufu_ops_per_pair": mufu, "peak_pairs_per_s": peak,
                                    "achieved_pairs_per_s": pairs / (ms * 1e-3), "frac": pairs / (ms * 1e-3) / peak},
                       "kdk_step_ms": ev0.elapsed_time(ev1) / 10}}
+    import oracle
+    tab, dR_max = sc.steps_cyl_get_tail_table(sim.ctx)
+    ocfg = oracle.make_table_cfg(0, w.n0, tab.shape[1], tab.shape[0],
+                                 max(2.2 * float(np.hypot(d["pos"][:, 0], d["pos"][:, 1]).max()), 1.0))
+    otab = oracle.tail_table_build(ocfg)
+    line["cpu_baseline"] = oracle_rate(
+        lambda ix: oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, otab, ocfg, idx=ix), n, n - 1.0,
+        "pair interactions/s", f"FP64 infinite-window table form, all {n} j")
     # the learned tail trained to infinity, checked against the table form
     rep = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
     sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
@@ -545,6 +580,14 @@ def run_octree(args):
     torch.cuda.synchronize()
     line["octree"]["kdk_step_ms"] = ev0.elapsed_time(ev1) / 5
     sim.close()
+    import oracle
+    ocfg = oracle.make_table_cfg(0, w.n0, 257, 33, max(2.2 * float(np.hypot(d["pos"][:, 0], d["pos"][:, 1]).max()), 1.0))
+    otab = oracle.tail_table_build(ocfg)
+    line["octree"]["forces_per_s"] = n / ((st["build_ms"] + st["walk_ms"]) * 1e-3)
+    line["octree"]["cpu_baseline"] = oracle_rate(
+        lambda ix: oracle.tree_field(d["pos"], d["m"], d["h"], 1.0, 1.0, ics.R_SIM, 0, 0.5, 16, 0.3, 0.7, otab, ocfg,
+                                     idx=ix), n, 1.0, "particle forces/s",
+        f"FP64 octree (sort, build, group walks of the sampled particles) of all {n}")
     print(json.dumps(line), flush=True)
     return 0
 
@@ -623,6 +666,19 @@ def run_workload(args):
         atb, mst = _timed_forces(sc, torch, sim, reps + 1)
         mufu_t = (2 * w.n0 + 1) + 4 + 2 + 1   # near images, base rsqrt/rcp, the dR rsqrt
         peak_t = props.multi_processor_count * 2070e6 * MUFU_RSQRT_PER_SM_CLK / mufu_t
+        import oracle
+        dR_t = max(2.2 * float(np.hypot(d["pos"][:, 0], d["pos"][:, 1]).max()), 1.0)
+        tcfg = oracle.make_table_cfg(w.n_cut, w.n0, nx, ny, dR_t)
+        ttab = oracle.tail_table_build(tcfg)
+        line["table_cpu_baseline"] = oracle_rate(
+            lambda ix: oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, ttab, tcfg, idx=ix), n, n - 1.0,
+            "pair interactions/s", f"FP64 table form, all {n} j")
+        sp = ics.random_surrogate_params(5, dR_t)
+        scfg = oracle.make_surr_cfg(w.n_cut, w.n0, dR_t, (0.0, 0.0), (0.05, 0.05))
+        w16 = sp[:1250].astype(np.float16).astype(np.float64)
+        line["surrogate_cpu_baseline"] = oracle_rate(
+            lambda ix: oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, scfg, idx=ix), n,
+            n - 1.0, "pair interactions/s", f"FP64 surrogate form (seeded network), all {n} j")
         line["table"] = {
             "nx": nx, "ny": ny, "build_ms": rt[3], "check_median": rt[0], "check_p999": rt[1], "pair_ms": mst,
             "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (mst * 1e-3),

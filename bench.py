@@ -592,9 +592,82 @@ def run_octree(args):
     return 0
 
 
+def run_octree_accuracy(args):
+    """The octree's accuracy in the manner of the paper's Fig. 3, on an evolved
+    snapshot: the production-shaped load (softening 1:8, N = 65,536) is run
+    with the direct sum of the infinite window from a = 0.02 to a = 1 in 1000
+    comoving KDK steps. At a = 0.1, 0.3 and 1 the octree force (Theta = 0.3 ..
+    0.8, with and without the radial correction calibrated at the start) is
+    compared with the direct force on a particle sample: median relative error
+    and mean radial and tangential force ratios."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    w = ics.WORKLOADS["production_n524288"]
+    n = 65536
+    d = ics.workload_ics(w, n=n)
+    t0, _ = ics.run_schedule(w)
+    t1 = ics.lcdm_time_of_a(1.0, w.Omega_m, w.Omega_L)
+    common = dict(n_cut=0, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_TABLE,
+                  background=sc.STEPS_BG_INFINITE, rho_bar=w.rho_bar, comoving=True, a_start=w.a_start, t_start=t0,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    sim = sc.Simulation(sc.Config(**common), d["pos"], d["vel"], d["m"], d["h"])
+    # radial tables from the initial load, one per opening angle
+    thetas = (0.3, 0.5, 0.8)
+    tables = {}
+    for th in thetas:
+        tr = sc.Simulation(sc.Config(force=sc.STEPS_FORCE_OCTREE, theta=th, **common), d["pos"], d["vel"], d["m"],
+                           d["h"])
+        tables[th] = sc.steps_cyl_tree_calibrate(tr.ctx, 8, 32, 8192)
+        tr.close()
+    idx = ics.subsample(n, 4096, seed=12345)
+    steps, out, done, ev0, ev1 = 1000, {}, 0, torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dt = (t1 - t0) / steps
+    ms = 0.0
+    for a_target in (0.1, 0.3, 1.0):
+        t_target = ics.lcdm_time_of_a(a_target, w.Omega_m, w.Omega_L)
+        k = int(round((t_target - t0) / dt)) - done
+        ev0.record()
+        sim.step(dt, k)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+        done += k
+        x, v, a, t = sim.state()
+        ad = sim.forces_subset(idx)
+        rho = np.hypot(x[idx, 0], x[idx, 1])
+        er = np.stack([x[idx, 0] / rho, x[idx, 1] / rho], 1)
+        et = np.stack([-er[:, 1], er[:, 0]], 1)
+        fr_d = (ad[:, :2] * er).sum(1)
+        ft_d = (ad[:, :2] * et).sum(1)
+        rows = {}
+        for th in thetas:
+            for corr in (False, True):
+                cfg = sc.Config(force=sc.STEPS_FORCE_OCTREE, theta=th, **dict(common, a_start=a, t_start=t))
+                tr = sc.Simulation(cfg, x, v, d["m"], d["h"])
+                if corr:   # the table calibrated on the initial load, as the paper does
+                    sc.steps_cyl_tree_set_radial(tr.ctx, *tables[th])
+                at = tr.forces_subset(idx)
+                tr.close()
+                r = np.linalg.norm(at - ad, axis=1) / np.linalg.norm(ad, axis=1)
+                rows[f"theta_{th}" + ("_corrected" if corr else "")] = {
+                    "median_rel_err": float(np.median(r)), "mean_rel_err": float(np.mean(r)),
+                    "median_radial_ratio": float(np.median((at[:, :2] * er).sum(1) / fr_d)),
+                    "median_tangential_ratio": float(np.median((at[:, :2] * et).sum(1) / ft_d)),
+                    "mean_radial_error_over_mean_force": float(np.mean(((at - ad)[:, :2] * er).sum(1))
+                                                               / np.mean(np.linalg.norm(ad, axis=1)))}
+        out[f"a_{a_target}"] = {"a": a, "rms_net_force": float(np.sqrt((ad ** 2).sum(1).mean())), **rows}
+    line = {"workload": "octree_accuracy_n65536", "n": n, "evolution": {"steps": done, "kdk_ms_total": ms,
+            "form": "direct, infinite window, correction table"}, "snapshots": out}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    if args.workload == "octree_accuracy_n65536":
+        return run_octree_accuracy(args)
     if args.workload in ("r3_n65536", "glass_n65536"):
         return run_r3_or_glass(args)
     if args.workload in ("octree_n65536", "octree_n524288"):

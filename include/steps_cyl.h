@@ -316,6 +316,11 @@ int steps_cyl_tree_stats(steps_cyl_ctx* ctx, double* out);
 int steps_cyl_tree_calibrate(steps_cyl_ctx* ctx, int32_t n_frames, int32_t n_bins, int32_t n_sample,
                              const double* frames, const int64_t* sample, double* table, double* rmax);
 
+/* Install a radial correction table measured elsewhere (n_bins doubles, host, in the
+ * units steps_cyl_tree_calibrate returns: comoving a^3 g; bins over [0, rmax]), e.g.
+ * the initial load's calibration in a later context. n_bins in [1, 4096], rmax > 0. */
+int steps_cyl_tree_set_radial(steps_cyl_ctx* ctx, const double* table, int32_t n_bins, double rmax);
+
 /* As steps_cyl_check_surrogate for a modelled tail (STEPS_TAIL_SURROGATE or
  * STEPS_TAIL_TABLE), which must be loaded and accepted. STEPS_EINVAL for the
  * infinite window (no plain image sum exists). */

@@ -2455,6 +2455,19 @@ int steps_cyl_tree_stats(steps_cyl_ctx* c, double* out) {
   return STEPS_OK;
 }
 
+int steps_cyl_tree_set_radial(steps_cyl_ctx* c, const double* table, int32_t n_bins, double rmax) {
+  g_last_error.clear();
+  if (!c || !table) return fail(STEPS_EINVAL, "NULL argument");
+  if (!is_tree(c)) return fail(STEPS_EINVAL, "the context does not use the octree");
+  if (n_bins < 1 || n_bins > 4096 || !(rmax > 0) || !std::isfinite(rmax)) return fail(STEPS_EINVAL, "bad table shape");
+  std::vector<double> tab(table, table + n_bins);
+  for (double v : tab)
+    if (!std::isfinite(v)) return fail(STEPS_EINVAL, "non-finite table entry");
+  DeviceGuard guard(c->dev);
+  c->forces_stale = true;
+  return set_radial(c, tab, rmax);
+}
+
 int steps_cyl_tree_calibrate(steps_cyl_ctx* c, int32_t n_frames, int32_t n_bins, int32_t n_sample,
                              const double* frames, const int64_t* sample, double* table, double* rmax) {
   g_last_error.clear();

@@ -40,7 +40,7 @@ _EXPORTS = [
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
-    "steps_cyl_tree_frame", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
+    "steps_cyl_tree_frame", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate", "steps_cyl_tree_set_radial",
 ]
 
 STEPS_SURR_NW = 1250
@@ -133,6 +133,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_tree_frame.argtypes = [p, d, d]
     L.steps_cyl_tree_stats.argtypes = [p, p]
     L.steps_cyl_tree_calibrate.argtypes = [p, i32, i32, i32, p, p, p, p]
+    L.steps_cyl_tree_set_radial.argtypes = [p, p, i32, d]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -413,6 +414,12 @@ def steps_cyl_tree_calibrate(ctx, n_frames: int, n_bins: int = 64, n_sample: int
     _check(load().steps_cyl_tree_calibrate(ctx, int(n_frames), int(n_bins), int(n_sample), _ptr(fr), _ptr(sm),
                                            _ptr(tab), ctypes.byref(rmax)))
     return tab, rmax.value
+
+
+def steps_cyl_tree_set_radial(ctx, table, rmax: float):
+    """Install a radial correction table (from steps_cyl_tree_calibrate, possibly of another context)."""
+    tab = np.ascontiguousarray(table, dtype=np.float64).reshape(-1)
+    _check(load().steps_cyl_tree_set_radial(ctx, _ptr(tab), int(tab.shape[0]), float(rmax)))
 
 
 def steps_cyl_checkpoint(ctx, path: str):

@@ -166,6 +166,13 @@ def test_radial_calibration_matches_oracle(sc):
     ref_g[:, 1] -= D * d["pos"][:, 1] / r
     med, _, mx = stats(a, ref_g)
     assert med <= 1e-6 and mx <= 1e-4    # relative to the corrected force, smaller near the axis
+    # the same table installed in another context gives the same corrected forces
+    other = tree_sim(sc, w, d, 0.1, 0.2)
+    sc.steps_cyl_tree_set_radial(other.ctx, tab, rmax)
+    np.testing.assert_array_equal(other.forces(), a)
+    with pytest.raises(sc.StepsError):
+        sc.steps_cyl_tree_set_radial(other.ctx, np.array([np.nan]), rmax)
+    other.close()
     # removing it restores the plain tree force
     sc.steps_cyl_tree_calibrate(sim.ctx, 0)
     med, _, _ = stats(sim.forces(), oracle_tree(d, w.rho_bar, 0.1, 0.2)[0])

@@ -592,6 +592,54 @@ def run_octree(args):
     return 0
 
 
+def run_octree_r3(args):
+    """The R^3 octree (Sect. 2.4) on a uniform ball of 2^20 particles
+    (softenings 0.02 .. 0.2, Theta = 0.5, leaves of 16): build and walk time,
+    interactions, against the direct R^3 kernel on the same load (time and
+    errors on a sample), and the FP64 oracle's octree timed beside it."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    n = 1 << 20
+    d = ics.ball_load(n, 41)
+    stream = torch.cuda.current_stream().cuda_stream
+    # the pair force alone: in a uniform ball the radial background term cancels it down to Poisson noise,
+    # which would turn any tree error into a large relative error of the net force
+    common = dict(topology=sc.STEPS_TOPO_R3, n_cut=1, precision=sc.STEPS_FP32_KAHAN, background=sc.STEPS_BG_OFF,
+                  rho_bar=d["rho_bar"], R_sim=2.0, stream=stream)
+    sim = sc.Simulation(sc.Config(force=sc.STEPS_FORCE_OCTREE, theta=0.5, leaf_size=16, **common), d["pos"], d["vel"],
+                        d["m"], d["h"])
+    runs = []
+    for _ in range(3):
+        _timed_forces(sc, torch, sim, 1)
+        runs.append(sc.steps_cyl_tree_stats(sim.ctx))
+    st = min(runs, key=lambda r: r["build_ms"] + r["walk_ms"])
+    idx = ics.subsample(n, 2048, seed=12345)
+    at = sim.forces_subset(idx)
+    sim.close()
+    direct = sc.Simulation(sc.Config(**common), d["pos"], d["vel"], d["m"], d["h"])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    ad = direct.forces_subset(idx)
+    ev1.record()
+    torch.cuda.synchronize()
+    direct.close()
+    r = np.linalg.norm(at - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    import oracle
+    cpu = oracle_rate(lambda ix: oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, 0.5, 16, [0.1, 0.2, -0.1],
+                                                      [0.0, 0.6, 0.8], 1.0, idx=ix), n, 1.0, "particle forces/s",
+                      f"FP64 R3 octree (sort, build, group walks of the sampled particles) of all {n}")
+    force_ms = st["build_ms"] + st["walk_ms"]
+    line = {"workload": "octree_r3_n1048576", "n": n, "theta": 0.5, "leaf_size": 16,
+            "octree": {"build_ms": st["build_ms"], "walk_ms": st["walk_ms"], "force_ms": force_ms,
+                       "nodes": st["nodes"], "depth": st["depth"], "interactions_per_particle": st["interactions"] / n,
+                       "forces_per_s": n / (force_ms * 1e-3),
+                       "pair_error_vs_direct": {"median": float(np.median(r)), "p99": float(np.quantile(r, 0.99))},
+                       "cpu_baseline": cpu},
+            "direct_force_ms": ev0.elapsed_time(ev1), "speedup_vs_direct": ev0.elapsed_time(ev1) / force_ms}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_octree_accuracy(args):
     """The octree's accuracy in the manner of the paper's Fig. 3, on an evolved
     snapshot: the production-shaped load (softening 1:8, N = 65,536) is run
@@ -668,6 +716,8 @@ def run_workload(args):
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
     if args.workload == "octree_accuracy_n65536":
         return run_octree_accuracy(args)
+    if args.workload == "octree_r3_n1048576":
+        return run_octree_r3(args)
     if args.workload in ("r3_n65536", "glass_n65536"):
         return run_r3_or_glass(args)
     if args.workload in ("octree_n65536", "octree_n524288"):

@@ -99,8 +99,8 @@ typedef struct {
   int32_t topology; /* STEPS_TOPO_S1R2 | STEPS_TOPO_R3 (R^3: n_cut is not used, tail must be STEPS_TAIL_FULL) */
   int32_t reserved; /* 0 */
   void* stream;     /* cudaStream_t to order work on; NULL = legacy default stream */
-  int32_t force;    /* STEPS_FORCE_DIRECT | STEPS_FORCE_OCTREE. The octree (Sect. 2.4) needs the infinite
-                     * window (n_cut = 0, STEPS_TAIL_TABLE), an FP32 precision and the S1xR2 topology */
+  int32_t force;    /* STEPS_FORCE_DIRECT | STEPS_FORCE_OCTREE. The octree (Sect. 2.4) needs an FP32
+                     * precision and, in S1xR2, the infinite window (n_cut = 0, STEPS_TAIL_TABLE) */
   int32_t leaf_size;  /* octree: a node of at most this many particles is a leaf (1 .. 64) */
   double theta;       /* octree: opening angle Theta, 0 < theta <= 1 */
   uint64_t tree_seed; /* octree: seed of the random shift and rotation drawn at every force evaluation */
@@ -284,20 +284,27 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, doubl
 int steps_cyl_get_tail_table(steps_cyl_ctx* ctx, float* out, int32_t* nx, int32_t* ny, double* dR_max);
 
 /* ---- octree (Sect. 2.4) ------------------------------------------------------
- * A Barnes-Hut tree over a cube of side S = 2 max(L, 2 R_sim), drawn at every
- * force evaluation in a random frame: shifted by zeta along the axis and
+ * A Barnes-Hut tree drawn at every force evaluation in a random frame. S1xR2: a
+ * cube of side S = 2 max(L, 2 R_sim), shifted by zeta along the axis and
  * rotated by phi about it (x' = cos phi x - sin phi y, y' = sin phi x +
- * cos phi y, z' = z + zeta mod L). Particles are grouped by 32 in Morton order
+ * cos phi y, z' = z + zeta mod L). R^3: a cube of side 4 R_sim centred at a
+ * point within R_sim / 2 of the origin, rotated by an angle about a unit axis
+ * (Rodrigues), no period. Particles are grouped by 32 in Morton order
  * of the frame; a group opens a node when any member sees it under an angle
  * s / d >= theta or closer than the softening allows; accepted nodes act as
  * point masses at their centre of mass. Every interaction is the pair force of
- * the infinite window (near images exact, the rest from the correction table).
- * An optional radial correction (Sect. 2.4) subtracts the mean radial force
- * error measured by steps_cyl_tree_calibrate. */
+ * the direct form: in S1xR2 the infinite window (near images exact, the rest from
+ * the correction table), in R^3 eq. NewtonianForce. An optional radial correction
+ * (Sect. 2.4) subtracts the mean radial force error measured by
+ * steps_cyl_tree_calibrate (radius: cylindrical in S1xR2, spherical in R^3). */
 
-/* Fix the frame of the following force evaluations (zeta in [0, L), phi in
+/* Fix the frame of the following force evaluations (S1xR2: zeta in [0, L), phi in
  * radians); zeta < 0 returns to a random frame per evaluation. */
 int steps_cyl_tree_frame(steps_cyl_ctx* ctx, double zeta, double phi);
+
+/* R^3: fix the frame to frame[7] = (centre x, y, z within R_sim / 2 of the origin,
+ * unit rotation axis x, y, z, angle in radians); NULL returns to random frames. */
+int steps_cyl_tree_frame_r3(steps_cyl_ctx* ctx, const double* frame);
 
 /* Statistics of the last octree evaluation: out[0] nodes, out[1] depth,
  * out[2] pair interactions (member x entry), out[3] build ms, out[4] walk ms,
@@ -305,10 +312,12 @@ int steps_cyl_tree_frame(steps_cyl_ctx* ctx, double zeta, double phi);
 int steps_cyl_tree_stats(steps_cyl_ctx* ctx, double* out);
 
 /* Radial calibration of Sect. 2.4: for n_frames frames (frames: 2 n_frames
- * doubles (zeta, phi), or NULL to draw them) compare the octree's pair force
- * with the direct pair force on n_sample particles (sample: caller indices, or
- * NULL to draw them) and average the radial component of the difference in
- * n_bins bins of rho over [0, rmax], rmax the largest particle radius now.
+ * doubles (zeta, phi) in S1xR2, 7 n_frames doubles (centre, axis, angle) in R^3,
+ * or NULL to draw them) compare the octree's pair force with the direct pair
+ * force (S1xR2: the table form in FP32; R^3: FP64) on n_sample particles
+ * (sample: caller indices, or NULL to draw them) and average the radial
+ * component of the difference in n_bins bins of the radius over [0, rmax], rmax
+ * the largest particle radius now.
  * Empty bins hold 0. The table is then subtracted from the octree force at
  * every evaluation (interpolated linearly between bin centres, held beyond
  * them). n_frames = 0 removes the correction. table (n_bins doubles, may be

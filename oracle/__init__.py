@@ -104,6 +104,8 @@ def lib():
         L.or_kdk.restype = ctypes.c_int
         L.or_tree_field.argtypes = [i64, p, p, p, p, p, d, d, d, i32, p, p, d, i32, d, d, i64, p, p, p, p, p]
         L.or_tree_field.restype = ctypes.c_int
+        L.or_tree_field_r3.argtypes = [i64, p, p, p, p, p, d, d, d, i32, p, p, d, i64, p, p, p, p, p]
+        L.or_tree_field_r3.restype = ctypes.c_int
         L.or_tree_order.argtypes = [i64, p, p, p, d, d, d, d, p, p]
         L.or_tree_order.restype = ctypes.c_int
         L.or_tail_sums.argtypes = [d, d, d, d, i32, i32, p, p]; L.or_tail_sums.restype = None
@@ -462,3 +464,25 @@ def tree_order(pos, L, R_sim, zeta, phi):
     if rc != 0:
         raise ValueError(f"or_tree_order failed ({rc})")
     return key, ordv
+
+
+def tree_field_r3(pos, m, h, G, R_sim, theta, leaf, cen, axis, angle, idx=None):
+    """The R^3 octree (Sect. 2.4) in the frame (domain centre cen, rotation by
+    angle about the unit axis): (g, stats) as tree_field."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    m = _f64(m); h = _f64(h)
+    n = x.shape[0]
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ni, ip = idx.shape[0], idx.ctypes.data_as(ctypes.c_void_p)
+    gx, gy, gz = np.zeros(ni), np.zeros(ni), np.zeros(ni)
+    stats = np.zeros(4, dtype=np.int64)
+    c = _f64(cen); a = _f64(axis)
+    rc = lib().or_tree_field_r3(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(R_sim), float(theta),
+                                int(leaf), _ptr(c), _ptr(a), float(angle), ni, ip, _ptr(gx), _ptr(gy), _ptr(gz),
+                                stats.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError(f"or_tree_field_r3 failed ({rc})")
+    return np.stack([gx, gy, gz], axis=1), stats

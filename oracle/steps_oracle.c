@@ -965,12 +965,42 @@ static void or_tree_pair(double rx, double ry, double rz, double hh, double L, i
   out[2] = -sz / (L * L);
 }
 
-int or_tree_field(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
-                  double G, double L, double R_sim, int32_t n_cut, const double* tab, const or_table_cfg* tc,
-                  double theta, int32_t leaf, double zeta, double phi, int64_t ni, const int64_t* idx, double* gx,
-                  double* gy, double* gz, int64_t* stats) {
-  double S = 2.0 * fmax(L, 2.0 * R_sim), invS = 1.0 / S, c = cos(phi), s = sin(phi), halfL = 0.5 * L;
-  float Lu = (float)(L * invS), th2 = (float)(theta * theta);
+/* The tree's frame: S1xR2 (shift zeta along the axis, rotation phi about it, root
+ * side S = 2 max(L, 2 R_sim) centred at (0, 0, L/2)), or R^3 (the domain centre
+ * moved to cen, a rotation R about a random axis, root side S = 4 R_sim centred
+ * at cen; no period). */
+typedef struct {
+  int32_t r3;
+  double S, zeta, c, s;   /* S1xR2 */
+  double cen[3], R[9];    /* R^3 */
+} or_tframe;
+
+/* Rotation by angle about the unit axis (Rodrigues' formula), each entry with
+ * the explicit fma/mul sequence written here. */
+static void or_rotation(const double ax[3], double angle, double R[9]) {
+  double cs = cos(angle), sn = sin(angle), t = 1.0 - cs;
+  double tx = t * ax[0], ty = t * ax[1], tz = t * ax[2];
+  double sx = sn * ax[0], sy = sn * ax[1], sz = sn * ax[2];
+  R[0] = fma(tx, ax[0], cs);  R[1] = fma(tx, ax[1], -sz); R[2] = fma(tx, ax[2], sy);
+  R[3] = fma(ty, ax[0], sz);  R[4] = fma(ty, ax[1], cs);  R[5] = fma(ty, ax[2], -sx);
+  R[6] = fma(tz, ax[0], -sy); R[7] = fma(tz, ax[1], sx);  R[8] = fma(tz, ax[2], cs);
+}
+
+/* R^3 pair term per unit G m_j (eq. NewtonianForce): -F(r, hh)/r r. */
+static void or_r3_pair(double rx, double ry, double rz, double hh, double out[3]) {
+  double f = or_spline_F_over_r(sqrt(rx * rx + ry * ry + rz * rz), hh);
+  out[0] = -f * rx;
+  out[1] = -f * ry;
+  out[2] = -f * rz;
+}
+
+static int or_tree_core(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                        const double* h, double G, double L, int32_t n_cut, const double* tab, const or_table_cfg* tc,
+                        double theta, int32_t leaf, const or_tframe* F, int64_t ni, const int64_t* idx, double* gx,
+                        double* gy, double* gz, int64_t* stats) {
+  double S = F->S, invS = 1.0 / S, c = F->c, s = F->s, halfL = 0.5 * L, zeta = F->r3 ? 0.0 : F->zeta;
+  /* R^3 has no period: an infinite period never wraps */
+  float Lu = F->r3 ? (float)INFINITY : (float)(L * invS), th2 = (float)(theta * theta);
   float* u = (float*)malloc(sizeof(float) * 3 * (size_t)n);
   float* hu = (float*)malloc(sizeof(float) * (size_t)n);
   double* zt = (double*)malloc(sizeof(double) * (size_t)n);
@@ -983,14 +1013,26 @@ int or_tree_field(int64_t n, const double* x, const double* y, const double* z, 
   int rc = 0;
   if (!u || !hu || !zt || !ki || !key || !ord || !slot || !want) { rc = -2; goto done; }
   for (int64_t i = 0; i < n; ++i) {
-    double xr = fma(c, x[i], -(s * y[i]));
-    double yr = fma(s, x[i], c * y[i]);
-    double zr = z[i] + zeta;
-    if (zr >= L) zr = zr - L;
-    zt[i] = zr;
-    u[3 * i] = (float)fma(xr, invS, 0.5);
-    u[3 * i + 1] = (float)fma(yr, invS, 0.5);
-    u[3 * i + 2] = (float)fma(zr - halfL, invS, 0.5);
+    if (F->r3) {
+      const double* R = F->R;
+      double dx = x[i] - F->cen[0], dy = y[i] - F->cen[1], dz = z[i] - F->cen[2];
+      double xr = fma(R[0], dx, fma(R[1], dy, R[2] * dz));
+      double yr = fma(R[3], dx, fma(R[4], dy, R[5] * dz));
+      double zr = fma(R[6], dx, fma(R[7], dy, R[8] * dz));
+      zt[i] = z[i]; /* centres of mass in the particles' own frame */
+      u[3 * i] = (float)fma(xr, invS, 0.5);
+      u[3 * i + 1] = (float)fma(yr, invS, 0.5);
+      u[3 * i + 2] = (float)fma(zr, invS, 0.5);
+    } else {
+      double xr = fma(c, x[i], -(s * y[i]));
+      double yr = fma(s, x[i], c * y[i]);
+      double zr = z[i] + zeta;
+      if (zr >= L) zr = zr - L;
+      zt[i] = zr;
+      u[3 * i] = (float)fma(xr, invS, 0.5);
+      u[3 * i + 1] = (float)fma(yr, invS, 0.5);
+      u[3 * i + 2] = (float)fma(zr - halfL, invS, 0.5);
+    }
     hu[i] = (float)(h[i] * invS);
     uint32_t q[3];
     for (int a = 0; a < 3; ++a) {
@@ -1047,8 +1089,11 @@ int or_tree_field(int64_t n, const double* x, const double* y, const double* z, 
         int64_t i = ord[q0 + k];
         double f[3];
         if (!open) {
-          or_tree_pair(x[i] - nd->com[0], y[i] - nd->com[1], z[i] - nd->com[2], h[i] + nd->hmax, L, n_cut, tab, tc,
-                       f);
+          if (F->r3)
+            or_r3_pair(x[i] - nd->com[0], y[i] - nd->com[1], z[i] - nd->com[2], h[i] + nd->hmax, f);
+          else
+            or_tree_pair(x[i] - nd->com[0], y[i] - nd->com[1], z[i] - nd->com[2], h[i] + nd->hmax, L, n_cut, tab,
+                         tc, f);
           for (int a = 0; a < 3; ++a) or_add(&acc[k][a], G * nd->M * f[a]);
           ++inter;
         } else {
@@ -1056,7 +1101,10 @@ int or_tree_field(int64_t n, const double* x, const double* y, const double* z, 
             int64_t j = ord[p];
             ++inter; /* member x entry, the member's own entry included */
             if (j == i) continue;
-            or_tree_pair(x[i] - x[j], y[i] - y[j], z[i] - z[j], h[i] + h[j], L, n_cut, tab, tc, f);
+            if (F->r3)
+              or_r3_pair(x[i] - x[j], y[i] - y[j], z[i] - z[j], h[i] + h[j], f);
+            else
+              or_tree_pair(x[i] - x[j], y[i] - y[j], z[i] - z[j], h[i] + h[j], L, n_cut, tab, tc, f);
             for (int a = 0; a < 3; ++a) or_add(&acc[k][a], G * m[j] * f[a]);
           }
         }
@@ -1084,6 +1132,32 @@ int or_tree_field(int64_t n, const double* x, const double* y, const double* z, 
 done:
   free(u); free(hu); free(zt); free(ki); free(key); free(ord); free(slot); free(want); free(t.v);
   return rc;
+}
+
+int or_tree_field(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
+                  double G, double L, double R_sim, int32_t n_cut, const double* tab, const or_table_cfg* tc,
+                  double theta, int32_t leaf, double zeta, double phi, int64_t ni, const int64_t* idx, double* gx,
+                  double* gy, double* gz, int64_t* stats) {
+  or_tframe F;
+  memset(&F, 0, sizeof F);
+  F.S = 2.0 * fmax(L, 2.0 * R_sim);
+  F.zeta = zeta;
+  F.c = cos(phi);
+  F.s = sin(phi);
+  return or_tree_core(n, x, y, z, m, h, G, L, n_cut, tab, tc, theta, leaf, &F, ni, idx, gx, gy, gz, stats);
+}
+
+int or_tree_field_r3(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
+                     double G, double R_sim, double theta, int32_t leaf, const double cen[3], const double axis[3],
+                     double angle, int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz,
+                     int64_t* stats) {
+  or_tframe F;
+  memset(&F, 0, sizeof F);
+  F.r3 = 1;
+  F.S = 4.0 * R_sim;
+  for (int a = 0; a < 3; ++a) F.cen[a] = cen[a];
+  or_rotation(axis, angle, F.R);
+  return or_tree_core(n, x, y, z, m, h, G, 1.0, 0, NULL, NULL, theta, leaf, &F, ni, idx, gx, gy, gz, stats);
 }
 
 /* Sorted order of the tree frame (for checks of the sort): ord[q] = particle at

@@ -114,6 +114,14 @@ int or_tree_field(int64_t n, const double* x, const double* y, const double* z, 
                   double G, double L, double R_sim, int32_t n_cut, const double* tab, const or_table_cfg* tc,
                   double theta, int32_t leaf, double zeta, double phi, int64_t ni, const int64_t* idx, double* gx,
                   double* gy, double* gz, int64_t* stats);
+/* The R^3 octree (Sect. 2.4): the domain centre moved to cen, the frame rotated
+ * by angle about the unit axis, root side 4 R_sim centred there, no period; the
+ * interactions are the pair force of eq. NewtonianForce. Otherwise as
+ * or_tree_field. */
+int or_tree_field_r3(int64_t n, const double* x, const double* y, const double* z, const double* m, const double* h,
+                     double G, double R_sim, double theta, int32_t leaf, const double cen[3], const double axis[3],
+                     double angle, int64_t ni, const int64_t* idx, double* gx, double* gy, double* gz,
+                     int64_t* stats);
 int or_tree_order(int64_t n, const double* x, const double* y, const double* z, double L, double R_sim,
                   double zeta, double phi, uint64_t* key, int64_t* ord);
 double or_mlp_loss_grad(const double* w, int64_t ns, const double* u, const double* t, double* grad);

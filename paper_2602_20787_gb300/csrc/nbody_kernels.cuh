@@ -95,15 +95,20 @@ __device__ __forceinline__ void add_background(const BgParams& bg, double xi, do
 // write a = g / a^3 to an output.
 // Radial correction of Sect. 2.4: g -= D(rho) rho_hat, D interpolated
 // linearly between bin centres (k + 1/2) rmax / nb and held outside them.
+// Radial correction of Sect. 2.4: g -= D(r) r_hat, D interpolated linearly
+// between bin centres (k + 1/2) rmax / nb and held outside them; r is the
+// cylindrical radius (S1xR2) or the distance from the origin (sph, R^3).
 struct RadialCorr {
   const double* tab;  // nb bin means; null: no correction
   int nb;
   double rmax;
+  int sph;
 };
 
-__device__ __forceinline__ void radial_correct(const RadialCorr& R, double x, double y, double& g0, double& g1) {
+__device__ __forceinline__ void radial_correct(const RadialCorr& R, double x, double y, double z, double& g0,
+                                               double& g1, double& g2) {
   if (!R.tab) return;
-  const double rho = sqrt(x * x + y * y);
+  const double rho = R.sph ? sqrt(x * x + y * y + z * z) : sqrt(x * x + y * y);
   if (!(rho > 0.0)) return;
   const double s = rho / R.rmax * R.nb - 0.5;
   double D;
@@ -116,8 +121,8 @@ __device__ __forceinline__ void radial_correct(const RadialCorr& R, double x, do
   }
   g0 -= D * x / rho;
   g1 -= D * y / rho;
+  if (R.sph) g2 -= D * z / rho;
 }
-
 
 static __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
                                 double pair_scale, BgParams bg, const double* __restrict__ x,
@@ -126,7 +131,7 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
                                 double inv_a3, double* __restrict__ ox, double* __restrict__ oy,
                                 double* __restrict__ oz, int* __restrict__ err,
-                                RadialCorr rc = RadialCorr{nullptr, 0, 0.0}) {
+                                RadialCorr rc = RadialCorr{nullptr, 0, 0.0, 0}) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -147,7 +152,7 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
     }
   }
   double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
-  radial_correct(rc, x[i], y[i], g0, g1);
+  radial_correct(rc, x[i], y[i], z[i], g0, g1, g2);
   add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
   if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
   gx[i] = g0; gy[i] = g1; gz[i] = g2;

@@ -56,7 +56,13 @@ struct TreeFrame {
 };
 
 struct TreeCrit {
-  float Lu, hLu, th2;  // period and half period in root units, theta^2
+  float Lu, hLu, th2;  // period and half period in root units (infinite for R^3), theta^2
+};
+
+// The R^3 frame (Sect. 2.4): the domain centre moved to cen, the frame rotated
+// by the matrix R (row-major), root side S = 4 R_sim centred at cen.
+struct TreeFrame3 {
+  double cen[3], R[9], invS;
 };
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
@@ -103,6 +109,35 @@ static __global__ void tree_frame_kernel(const double* __restrict__ x, const dou
                    qz = (uint32_t)__fmul_rn(cz, 2097152.0f);
     u4[i] = make_float4(ux, uy, uz, hu);
     zt[i] = zr;
+    const int c = perm[i];
+    key[c] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    val[c] = i;
+  }
+}
+
+// The same for the R^3 frame: u = R (x - cen) / S + 1/2, with the explicit
+// fma/mul sequence; zt[i] = z[i] (no period).
+static __global__ void tree_frame_r3_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                            const double* __restrict__ z, const double* __restrict__ h,
+                                            const int* __restrict__ perm, int n, TreeFrame3 F,
+                                            float4* __restrict__ u4, double* __restrict__ zt,
+                                            uint64_t* __restrict__ key, int* __restrict__ val, int* __restrict__ err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double dx = __dsub_rn(x[i], F.cen[0]), dy = __dsub_rn(y[i], F.cen[1]), dz = __dsub_rn(z[i], F.cen[2]);
+    const double xr = __fma_rn(F.R[0], dx, __fma_rn(F.R[1], dy, __dmul_rn(F.R[2], dz)));
+    const double yr = __fma_rn(F.R[3], dx, __fma_rn(F.R[4], dy, __dmul_rn(F.R[5], dz)));
+    const double zr = __fma_rn(F.R[6], dx, __fma_rn(F.R[7], dy, __dmul_rn(F.R[8], dz)));
+    const float ux = __double2float_rn(__fma_rn(xr, F.invS, 0.5));
+    const float uy = __double2float_rn(__fma_rn(yr, F.invS, 0.5));
+    const float uz = __double2float_rn(__fma_rn(zr, F.invS, 0.5));
+    const float hu = __double2float_rn(__dmul_rn(h[i], F.invS));
+    const bool inside = ux >= 0.0f && ux < 1.0f && uy >= 0.0f && uy < 1.0f && uz >= 0.0f && uz < 1.0f;
+    if (!inside) atomicOr(err, kErrTreeRange);
+    const float cx = inside ? ux : 0.0f, cy = inside ? uy : 0.0f, cz = inside ? uz : 0.0f;
+    const uint32_t qx = (uint32_t)__fmul_rn(cx, 2097152.0f), qy = (uint32_t)__fmul_rn(cy, 2097152.0f),
+                   qz = (uint32_t)__fmul_rn(cz, 2097152.0f);
+    u4[i] = make_float4(ux, uy, uz, hu);
+    zt[i] = z[i];
     const int c = perm[i];
     key[c] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     val[c] = i;
@@ -327,14 +362,15 @@ static __global__ void tree_moments_kernel(int n0, int n1, const int4* __restric
   hmf[id] = hu;
 }
 
-// Pseudo-particles of all nodes in the pair kernels' layout.
+// Pseudo-particles of all nodes in the pair kernels' layout (periodic: z of
+// the centre of mass shifted back by zeta into [0, L)).
 static __global__ void tree_pack_kernel(int nn, const double4_32a* __restrict__ mom, const double* __restrict__ hmax,
-                                        double zeta, double L, double invL, float4* __restrict__ nA,
+                                        double zeta, double L, double invL, int periodic, float4* __restrict__ nA,
                                         float4* __restrict__ nB) {
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
     const double4_32a c = mom[id];
     double zc = c.w / c.x - zeta;
-    if (zc < 0.0) zc += L;
+    if (periodic && zc < 0.0) zc += L;
     pack_one(c.y / c.x, c.z / c.x, zc, c.x, hmax[id], id, invL, nA, nB);
   }
 }
@@ -403,13 +439,65 @@ __device__ __forceinline__ void tree_eval(const IParticle& I, int me, const floa
   }
 }
 
+// The R^3 form of the list evaluation (eq. NewtonianForce, one image): two
+// entries per packed FP32x2 op, the spline only when some lane is softened.
+template <bool KAHAN>
+__device__ __forceinline__ void tree_eval_r3(const IParticle& I, int me, const float4* __restrict__ A_,
+                                             const float4* __restrict__ B_, const int* __restrict__ id_, int nl,
+                                             float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
+  float xh, yh, xl, yl;
+  upk(I.xyh, xh, yh);
+  upk(I.xyl, xl, yl);
+  const u64 XH = pk(xh, xh), YH = pk(yh, yh), ZH = pk(I.zh, I.zh);
+  const u64 XL = pk(xl, xl), YL = pk(yl, yl), ZL = pk(I.zl, I.zl);
+  const u64 HI = pk(I.h, I.h);
+#pragma unroll 1
+  for (int k0 = 0; k0 < nl; k0 += 8) {
+    u64 GX = pk(0.f, 0.f), GY = pk(0.f, 0.f), GZ = pk(0.f, 0.f);
+#pragma unroll 1
+    for (int k = k0; k < k0 + 8; k += 2) {
+      const int ka = min(k, nl - 1), kb = min(k + 1, nl - 1);
+      const float4 A0 = A_[ka], A1 = A_[kb], B0 = B_[ka], B1 = B_[kb];
+      const float m0 = (k < nl && id_[ka] != me) ? A0.w : 0.0f;
+      const float m1 = (k + 1 < nl && id_[kb] != me) ? A1.w : 0.0f;
+      const u64 DX = add2(sub2(XH, pk(A0.x, A1.x)), sub2(XL, pk(B0.x, B1.x)));
+      const u64 DY = add2(sub2(YH, pk(A0.y, A1.y)), sub2(YL, pk(B0.y, B1.y)));
+      const u64 DZ = add2(sub2(ZH, pk(A0.z, A1.z)), sub2(ZL, pk(B0.z, B1.z)));
+      const u64 R2 = fma2(DX, DX, fma2(DY, DY, mul2(DZ, DZ)));
+      const u64 HH = add2(HI, pk(B0.w, B1.w));
+      float ra, rb, ha, hb;
+      upk(R2, ra, rb);
+      upk(HH, ha, hb);
+      const u64 RI = pk(rsq(fmaxf(ra, 1e-30f)), rsq(fmaxf(rb, 1e-30f)));
+      u64 F = mul2(mul2(RI, RI), RI);
+      if (__any_sync(0xffffffffu, ra < ha * ha || rb < hb * hb)) {
+        const float iha = rcp_approx(ha), ihb = rcp_approx(hb);
+        const u64 IH = pk(iha, ihb);
+        F = spline_value_r2(R2, RI, F, IH, pk(-iha, -ihb), mul2(mul2(IH, IH), IH));
+      }
+      const u64 MF = mul2(pk(m0, m1), F);
+      GX = fma2(DX, MF, GX);
+      GY = fma2(DY, MF, GY);
+      GZ = fma2(DZ, MF, GZ);
+    }
+    float a, b;
+    upk(GX, a, b);
+    acc<KAHAN>(sx, cx, a + b);
+    upk(GY, a, b);
+    acc<KAHAN>(sy, cy, a + b);
+    upk(GZ, a, b);
+    acc<KAHAN>(sz, cz, a + b);
+  }
+}
+
 #ifndef STEPS_TREE_MIN_BLOCKS
 #define STEPS_TREE_MIN_BLOCKS 4  // co-resident CTAs per SM asked of the register allocator
 #endif
 
 // One warp per group of 32 particles in key order (sA/sB, u4s: key order);
 // out = [3][n] pair sums in internal order (sidx maps key order to internal).
-template <bool KAHAN>
+// R3: the R^3 pair force (no images, no table).
+template <bool KAHAN, bool R3 = false>
 __global__ void __launch_bounds__(kWalkWarps * 32, STEPS_TREE_MIN_BLOCKS)
 tree_walk_kernel(const float4* __restrict__ sA, const float4* __restrict__ sB, const float4* __restrict__ u4s,
                  const int* __restrict__ sidx, int n, const int4* __restrict__ link, const float4* __restrict__ geo,
@@ -469,7 +557,10 @@ tree_walk_kernel(const float4* __restrict__ sA, const float4* __restrict__ sB, c
         const int c = min(32, lk.w - b0);
         if (nl + c > kWalkList) {
           __syncwarp();
-          tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
+          if (R3)
+            tree_eval_r3<KAHAN>(I, me, A_, B_, id_, nl, sx, sy, sz, cx, cy, cz);
+          else
+            tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
           count += (unsigned long long)nl * nvalid;
           nl = 0;
           __syncwarp();
@@ -484,7 +575,10 @@ tree_walk_kernel(const float4* __restrict__ sA, const float4* __restrict__ sB, c
     }
     if (nl > kWalkList - 33) {
       __syncwarp();
-      tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
+      if (R3)
+        tree_eval_r3<KAHAN>(I, me, A_, B_, id_, nl, sx, sy, sz, cx, cy, cz);
+      else
+        tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
       count += (unsigned long long)nl * nvalid;
       nl = 0;
       __syncwarp();
@@ -492,7 +586,10 @@ tree_walk_kernel(const float4* __restrict__ sA, const float4* __restrict__ sB, c
   }
   __syncwarp();
   if (nl > 0) {
-    tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
+    if (R3)
+      tree_eval_r3<KAHAN>(I, me, A_, B_, id_, nl, sx, sy, sz, cx, cy, cz);
+    else
+      tree_eval<KAHAN>(I, me, A_, B_, id_, nl, S, T, sx, sy, sz, cx, cy, cz);
     count += (unsigned long long)nl * nvalid;
   }
   if (lane == 0) {

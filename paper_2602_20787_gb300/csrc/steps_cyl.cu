@@ -197,6 +197,13 @@ int grid_for(int n, int threads) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// One octree frame (Sect. 2.4): S1xR2 uses (zeta, phi); R^3 the domain centre,
+// the rotation axis (unit) and angle.
+struct TreeDraw {
+  double zeta, phi;
+  double cen[3], axis[3], angle;
+};
+
 struct steps_cyl_ctx {
   steps_cyl_params p{};
   int n = 0;
@@ -271,7 +278,7 @@ struct steps_cyl_ctx {
     double interactions = 0.0, build_ms = 0.0, walk_ms = 0.0;
     bool ready = false;                     // every per-particle buffer above is allocated
     bool fixed = false;
-    double fzeta = 0.0, fphi = 0.0;
+    TreeDraw fd{};                          // the fixed frame
     uint64_t evals = 0;
     double* rad = nullptr;                  // radial correction table (device)
     int rad_nb = 0;
@@ -335,8 +342,9 @@ int check_params(const steps_cyl_params* p) {
   if (p->force == STEPS_FORCE_OCTREE) {
     // the octree's node interactions are smooth only for the infinite window: with a finite
     // window the image set of a pair jumps at the window's edge, which no node moment follows
-    if (p->n_cut != 0 || p->tail != STEPS_TAIL_TABLE)
+    if (p->topology == STEPS_TOPO_S1R2 && (p->n_cut != 0 || p->tail != STEPS_TAIL_TABLE))
       return fail(STEPS_EINVAL, "the octree needs the infinite window (n_cut = 0) with STEPS_TAIL_TABLE");
+    if (p->precision == STEPS_FP64) return fail(STEPS_EINVAL, "the octree needs an FP32 precision");
     if (p->leaf_size < 1 || p->leaf_size > 64) return fail(STEPS_EINVAL, "leaf_size must be in [1, 64]");
     if (!(p->theta > 0.0 && p->theta <= 1.0)) return fail(STEPS_EINVAL, "theta must be in (0, 1]");
   }
@@ -697,15 +705,43 @@ TreeFrame tree_frame_of(const steps_cyl_ctx* c, double zeta, double phi) {
   return F;
 }
 
-// Sort, build and moments of the tree in frame (zeta, phi).
-int tree_build(steps_cyl_ctx* c, double zeta, double phi) {
+// Rotation by angle about the unit axis (Rodrigues), each entry with the
+// explicit fma/mul sequence written here, so that any reproduction of the frame
+// gets the same bits.
+void tree_rotation(const double ax[3], double angle, double R[9]) {
+  const double cs = std::cos(angle), sn = std::sin(angle), t = 1.0 - cs;
+  const double tx = t * ax[0], ty = t * ax[1], tz = t * ax[2];
+  const double sx = sn * ax[0], sy = sn * ax[1], sz = sn * ax[2];
+  R[0] = std::fma(tx, ax[0], cs);
+  R[1] = std::fma(tx, ax[1], -sz);
+  R[2] = std::fma(tx, ax[2], sy);
+  R[3] = std::fma(ty, ax[0], sz);
+  R[4] = std::fma(ty, ax[1], cs);
+  R[5] = std::fma(ty, ax[2], -sx);
+  R[6] = std::fma(tz, ax[0], -sy);
+  R[7] = std::fma(tz, ax[1], sx);
+  R[8] = std::fma(tz, ax[2], cs);
+}
+
+// Sort, build and moments of the tree in frame f.
+int tree_build(steps_cyl_ctx* c, const TreeDraw& f) {
   auto& T = c->tr;
   int rc;
   if ((rc = tree_alloc(c))) return rc;
   const int n = c->n;
-  const TreeFrame F = tree_frame_of(c, zeta, phi);
-  tree_frame_kernel<<<grid_for(n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->h, c->perm, n, F, T.u4, T.zt,
-                                                         T.key[0], T.val[0], c->err);
+  const double zeta = is_r3(c) ? 0.0 : f.zeta;
+  if (is_r3(c)) {
+    TreeFrame3 F;
+    for (int a = 0; a < 3; ++a) F.cen[a] = f.cen[a];
+    tree_rotation(f.axis, f.angle, F.R);
+    F.invS = 1.0 / (4.0 * c->p.R_sim);
+    tree_frame_r3_kernel<<<grid_for(n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->h, c->perm, n, F, T.u4, T.zt,
+                                                              T.key[0], T.val[0], c->err);
+  } else {
+    const TreeFrame F = tree_frame_of(c, f.zeta, f.phi);
+    tree_frame_kernel<<<grid_for(n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->h, c->perm, n, F, T.u4, T.zt,
+                                                           T.key[0], T.val[0], c->err);
+  }
   CKLAUNCH("tree_frame");
   const int ntiles = (n + kSortTile - 1) / kSortTile;
   for (int pass = 0; pass < 8; ++pass) {  // 8 digits of 8 bits; the result returns to buffer 0
@@ -760,7 +796,8 @@ int tree_build(steps_cyl_ctx* c, double zeta, double phi) {
     tree_moments_kernel<<<(b - a + 255) / 256, 256, 0, c->st>>>(a, b, T.link, sidx, c->x, c->y, T.zt, c->m, c->h,
                                                                T.u4, T.mom, T.hmx, T.hmf);
   }
-  tree_pack_kernel<<<grid_for(nn, 256), 256, 0, c->st>>>(nn, T.mom, T.hmx, zeta, c->p.L, c->invL, T.nA, T.nB);
+  tree_pack_kernel<<<grid_for(nn, 256), 256, 0, c->st>>>(nn, T.mom, T.hmx, zeta, c->p.L, c->invL, is_r3(c) ? 0 : 1,
+                                                         T.nA, T.nB);
   CKLAUNCH("tree_moments");
   return STEPS_OK;
 }
@@ -770,13 +807,22 @@ int tree_walk(steps_cyl_ctx* c, double* out) {
   auto& T = c->tr;
   TreeCrit C;
   const double S = 2.0 * std::max(c->p.L, 2.0 * c->p.R_sim);
-  C.Lu = (float)(c->p.L / S);
+  C.Lu = is_r3(c) ? INFINITY : (float)(c->p.L / S);  // R^3: no period, the wrap never applies
   C.hLu = 0.5f * C.Lu;
   C.th2 = (float)(c->p.theta * c->p.theta);
   const int groups = (c->n + 31) / 32;
   const int blocks = (groups + kWalkWarps - 1) / kWalkWarps;
   CKT(cudaMemsetAsync(T.inter, 0, sizeof(unsigned long long), c->st));
-  if (c->p.precision == STEPS_FP32_KAHAN)
+  const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+  if (is_r3(c) && kahan)
+    tree_walk_kernel<true, true><<<blocks, kWalkWarps * 32, 0, c->st>>>(T.sA, T.sB, T.u4s, T.val[0], c->n, T.link,
+                                                                        T.geo, T.hmf, T.nA, T.nB, C, c->tab,
+                                                                        c->tab_const, out, T.inter, c->err);
+  else if (is_r3(c))
+    tree_walk_kernel<false, true><<<blocks, kWalkWarps * 32, 0, c->st>>>(T.sA, T.sB, T.u4s, T.val[0], c->n, T.link,
+                                                                         T.geo, T.hmf, T.nA, T.nB, C, c->tab,
+                                                                         c->tab_const, out, T.inter, c->err);
+  else if (kahan)
     tree_walk_kernel<true><<<blocks, kWalkWarps * 32, 0, c->st>>>(T.sA, T.sB, T.u4s, T.val[0], c->n, T.link, T.geo,
                                                                   T.hmf, T.nA, T.nB, C, c->tab, c->tab_const, out,
                                                                   T.inter, c->err);
@@ -788,30 +834,52 @@ int tree_walk(steps_cyl_ctx* c, double* out) {
   return STEPS_OK;
 }
 
+// A frame drawn from a generator: S1xR2, a shift uniform in [0, L) and an angle
+// uniform in [0, 2 pi); R^3, a rotation axis uniform on the sphere, an angle
+// uniform in [0, 2 pi) and a domain centre uniform in the ball of radius R_sim / 2.
+TreeDraw tree_draw(const steps_cyl_ctx* c, SplitMix& r) {
+  TreeDraw f{};
+  if (!is_r3(c)) {
+    f.zeta = r.uniform() * c->p.L;
+    f.phi = 2.0 * M_PI * r.uniform();
+    return f;
+  }
+  const double za = 2.0 * r.uniform() - 1.0, pa = 2.0 * M_PI * r.uniform(), sa = std::sqrt(std::max(0.0, 1.0 - za * za));
+  f.axis[0] = sa * std::cos(pa);
+  f.axis[1] = sa * std::sin(pa);
+  f.axis[2] = za;
+  f.angle = 2.0 * M_PI * r.uniform();
+  const double rc = 0.5 * c->p.R_sim * std::cbrt(r.uniform());
+  const double zc = 2.0 * r.uniform() - 1.0, pc = 2.0 * M_PI * r.uniform(), sc = std::sqrt(std::max(0.0, 1.0 - zc * zc));
+  f.cen[0] = rc * sc * std::cos(pc);
+  f.cen[1] = rc * sc * std::sin(pc);
+  f.cen[2] = rc * zc;
+  return f;
+}
+
 // The frame of the next evaluation: the fixed one, or drawn from the seed and
 // the evaluation counter.
-void tree_next_frame(steps_cyl_ctx* c, double* zeta, double* phi) {
+TreeDraw tree_next_frame(steps_cyl_ctx* c) {
   auto& T = c->tr;
+  TreeDraw f;
   if (T.fixed) {
-    *zeta = T.fzeta;
-    *phi = T.fphi;
+    f = T.fd;
   } else {
     SplitMix r(c->p.tree_seed * 0x9E3779B97F4A7C15ull + T.evals);
-    *zeta = r.uniform() * c->p.L;
-    *phi = 2.0 * M_PI * r.uniform();
+    f = tree_draw(c, r);
   }
   ++T.evals;
+  return f;
 }
 
 // One octree pair evaluation into c->part ([3][n]), timed in phases.
 int tree_forces(steps_cyl_ctx* c, double* out) {
   auto& T = c->tr;
-  double zeta, phi;
-  tree_next_frame(c, &zeta, &phi);
+  const TreeDraw f = tree_next_frame(c);
   int rc;
   if ((rc = tree_alloc(c))) return rc;
   CKT(cudaEventRecord(T.t0, c->st));
-  if ((rc = tree_build(c, zeta, phi))) return rc;
+  if ((rc = tree_build(c, f))) return rc;
   CKT(cudaEventRecord(T.t1, c->st));
   if ((rc = tree_walk(c, out))) return rc;
   CKT(cudaEventRecord(T.t2, c->st));
@@ -828,11 +896,12 @@ int tree_forces(steps_cyl_ctx* c, double* out) {
 }
 
 RadialCorr radial_corr(const steps_cyl_ctx* c) {
-  RadialCorr r{nullptr, 0, 0.0};
+  RadialCorr r{nullptr, 0, 0.0, 0};
   if (is_tree(c) && c->tr.rad && c->tr.rad_nb > 0) {
     r.tab = c->tr.rad;
     r.nb = c->tr.rad_nb;
     r.rmax = c->tr.rad_rmax;
+    r.sph = is_r3(c) ? 1 : 0;
   }
   return r;
 }
@@ -1256,6 +1325,21 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
   return STEPS_OK;
 }
 
+// A frame's arguments: S1xR2 zeta in [0, L), phi finite; R^3 a finite centre
+// inside R_sim / 2 of the origin, a unit axis (to 1e-12) and a finite angle.
+int check_frame(const steps_cyl_ctx* c, const TreeDraw& f) {
+  if (!is_r3(c)) {
+    if (!(f.zeta >= 0.0 && f.zeta < c->p.L) || !std::isfinite(f.phi))
+      return fail(STEPS_EINVAL, "zeta must lie in [0, L) and phi be finite");
+    return STEPS_OK;
+  }
+  const double r2 = f.cen[0] * f.cen[0] + f.cen[1] * f.cen[1] + f.cen[2] * f.cen[2];
+  const double a2 = f.axis[0] * f.axis[0] + f.axis[1] * f.axis[1] + f.axis[2] * f.axis[2];
+  if (!(r2 <= 0.25 * c->p.R_sim * c->p.R_sim) || !(std::fabs(a2 - 1.0) <= 1e-12) || !std::isfinite(f.angle))
+    return fail(STEPS_EINVAL, "the frame needs a centre within R_sim / 2, a unit axis and a finite angle");
+  return STEPS_OK;
+}
+
 // Install a radial correction table (nb bin means over [0, rmax]).
 int set_radial(steps_cyl_ctx* c, const std::vector<double>& tab, double rmax) {
   auto& T = c->tr;
@@ -1273,8 +1357,9 @@ int set_radial(steps_cyl_ctx* c, const std::vector<double>& tab, double rmax) {
 
 // Radial calibration of the octree (Sect. 2.4): the mean radial component of
 // (octree - direct) pair force over a particle sample and several frames, in
-// bins of rho. The direct reference is the same pair form (infinite window,
-// correction table) summed over all j.
+// bins of the radius (the cylindrical rho in S1xR2, the distance from the
+// origin in R^3). The direct reference is the same pair form summed over all j:
+// the infinite window's table form, or in R^3 the FP64 pair force.
 int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frames, const int64_t* sample,
                    std::vector<double>& table, double* rmax_out) {
   const int n = c->n;
@@ -1297,13 +1382,16 @@ int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frame
       pick[q] = all[q];
     }
   }
-  std::vector<double> hx(n), hy(n);
+  const bool sph = is_r3(c);
+  std::vector<double> hx(n), hy(n), hz(n, 0.0);
   CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  if (sph) CK(cudaMemcpyAsync(hz.data(), c->z, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  auto radius = [&](int k) { return sph ? std::sqrt(hx[k] * hx[k] + hy[k] * hy[k] + hz[k] * hz[k]) : std::hypot(hx[k], hy[k]); };
   double rmax = 0.0;
-  for (int k = 0; k < n; ++k) rmax = std::max(rmax, std::hypot(hx[k], hy[k]));
-  if (!(rmax > 0)) return fail(STEPS_EINVAL, "every particle sits on the axis");
+  for (int k = 0; k < n; ++k) rmax = std::max(rmax, radius(k));
+  if (!(rmax > 0)) return fail(STEPS_EINVAL, "every particle sits at the centre");
   // direct pair sums of the sample
   if (ni > c->idx_cap) {
     cudaFree(c->idx);
@@ -1324,14 +1412,26 @@ int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frame
   const int JC = (c->NT + tpc - 1) / tpc;
   int rc;
   if ((rc = grow(c, (size_t)JC * 3 * ni + 3 * (size_t)ni))) return rc;
-  double* part = c->chk;
-  double* sums = part + (size_t)JC * 3 * ni;
-  pair_fp32_table_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, n, 0, c->idx, ni, tpc,
-                                                                             c->tab, c->tab_const, part);
-  chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
-  CKLAUNCH("calibration_direct");
+  double* sums = nullptr;  // [3][ni]
+  CK(cudaMalloc(&sums, sizeof(double) * 3 * ni));
+  if (sph) {
+    rc = launch_fp64(c, c->idx, ni, sums);
+  } else {
+    double* part = c->chk;
+    pair_fp32_table_subset_kernel<true, true><<<dim3(gx, JC), kBI, 0, c->st>>>(c->jA, c->jB, n, 0, c->idx, ni, tpc,
+                                                                               c->tab, c->tab_const, part);
+    chunk_sum_kernel<<<(ni + 255) / 256, 256, 0, c->st>>>(part, ni, JC, sums);
+  }
+  if (!rc && cudaGetLastError() != cudaSuccess) rc = fail(STEPS_ECUDA, "calibration direct launch failed");
+  if (rc) {
+    cudaFree(sums);
+    return rc;
+  }
   std::vector<double> D(3 * (size_t)ni), Tq(3 * (size_t)ni);
-  CK(cudaMemcpyAsync(D.data(), sums, sizeof(double) * 3 * ni, cudaMemcpyDeviceToHost, c->st));
+  const cudaError_t ce = cudaMemcpyAsync(D.data(), sums, sizeof(double) * 3 * ni, cudaMemcpyDeviceToHost, c->st);
+  const cudaError_t cs = cudaStreamSynchronize(c->st);
+  cudaFree(sums);
+  if (ce != cudaSuccess || cs != cudaSuccess) return fail(STEPS_ECUDA, "calibration direct read-back failed");
   // octree pair sums of the sample in each frame (all particles walk: groups are fixed by the key order)
   int* dpick = nullptr;
   std::vector<int> pick32(pick.begin(), pick.end());
@@ -1342,13 +1442,22 @@ int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frame
   std::vector<long long> cnt(nb, 0);
   SplitMix fr(0xf4a3e000ull ^ c->p.tree_seed);
   for (int f = 0; f < nf && rc == STEPS_OK; ++f) {
-    const double zeta = frames ? frames[2 * f] : fr.uniform() * c->p.L;
-    const double phi = frames ? frames[2 * f + 1] : 2.0 * M_PI * fr.uniform();
-    if (!(zeta >= 0.0 && zeta < c->p.L) || !std::isfinite(phi)) {
-      rc = fail(STEPS_EINVAL, "frame %d: zeta must lie in [0, L) and phi be finite", f);
-      break;
+    TreeDraw fd{};
+    if (!frames) {
+      fd = tree_draw(c, fr);
+    } else if (sph) {  // 7 doubles per frame: centre, unit axis, angle
+      const double* q = frames + 7 * (size_t)f;
+      for (int a = 0; a < 3; ++a) {
+        fd.cen[a] = q[a];
+        fd.axis[a] = q[3 + a];
+      }
+      fd.angle = q[6];
+    } else {
+      fd.zeta = frames[2 * f];
+      fd.phi = frames[2 * f + 1];
     }
-    if ((rc = tree_build(c, zeta, phi)) || (rc = tree_walk(c, c->part))) break;
+    if ((rc = check_frame(c, fd))) break;
+    if ((rc = tree_build(c, fd)) || (rc = tree_walk(c, c->part))) break;
     for (int a = 0; a < 3; ++a)
       gather_kernel<<<grid_for(ni, 256), 256, 0, c->st>>>(c->part + (size_t)a * n, dpick, ni, 1.0,
                                                          c->sub + (size_t)a * ni);
@@ -1359,11 +1468,12 @@ int tree_calibrate(steps_cyl_ctx* c, int nf, int nb, int ns, const double* frame
     }
     for (int q = 0; q < ni; ++q) {
       const int i = (int)pick[q];
-      const double rho = std::hypot(hx[i], hy[i]);
+      const double rho = radius(i);
       if (!(rho > 0)) continue;
       const double ex = pair_scale * (Tq[q] - D[q]), ey = pair_scale * (Tq[(size_t)ni + q] - D[(size_t)ni + q]);
+      const double ez = sph ? pair_scale * (Tq[2 * (size_t)ni + q] - D[2 * (size_t)ni + q]) : 0.0;
       const int k = std::min(nb - 1, (int)(rho / rmax * nb));
-      sum[k] += (ex * hx[i] + ey * hy[i]) / rho;
+      sum[k] += (ex * hx[i] + ey * hy[i] + ez * hz[i]) / rho;
       ++cnt[k];
     }
   }
@@ -2003,6 +2113,7 @@ int steps_cyl_set_precision(steps_cyl_ctx* c, int32_t precision) {
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (precision < STEPS_FP64 || precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   if (precision == STEPS_FP64 && is_inf(c)) return fail(STEPS_EINVAL, "the infinite window needs an FP32 precision");
+  if (precision == STEPS_FP64 && is_tree(c)) return fail(STEPS_EINVAL, "the octree needs an FP32 precision");
   DeviceGuard guard(c->dev);
   c->p.precision = precision;
   if (precision == STEPS_FP64) c->p.tail = STEPS_TAIL_FULL;
@@ -2084,9 +2195,9 @@ struct CkptHeader {
   double tab_dR_max, tab_bound_med, tab_bound_p999;
   uint64_t tree_evals;                  // octree: frame counter, fixed frame, radial table (after the header)
   int32_t tree_fixed, rad_nb;
-  double tree_zeta, tree_phi, rad_rmax;
+  double tree_frame[9], rad_rmax;       // zeta, phi, centre, axis, angle
 };
-constexpr uint32_t kCkptVersion = 3;
+constexpr uint32_t kCkptVersion = 4;
 
 int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   g_last_error.clear();
@@ -2119,8 +2230,11 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   hd.tab_bound_p999 = c->tab_bound_p999;
   hd.tree_evals = c->tr.evals;
   hd.tree_fixed = c->tr.fixed ? 1 : 0;
-  hd.tree_zeta = c->tr.fzeta;
-  hd.tree_phi = c->tr.fphi;
+  {
+    const TreeDraw& f = c->tr.fd;
+    const double v[9] = {f.zeta, f.phi, f.cen[0], f.cen[1], f.cen[2], f.axis[0], f.axis[1], f.axis[2], f.angle};
+    std::memcpy(hd.tree_frame, v, sizeof v);
+  }
   hd.rad_nb = c->tr.rad ? c->tr.rad_nb : 0;
   hd.rad_rmax = c->tr.rad_rmax;
   if (c->forces_stale) {
@@ -2187,8 +2301,17 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
   c->steps_since_check = hd.steps_since_check;
   c->tr.evals = hd.tree_evals;
   c->tr.fixed = hd.tree_fixed != 0;
-  c->tr.fzeta = hd.tree_zeta;
-  c->tr.fphi = hd.tree_phi;
+  {
+    TreeDraw& f = c->tr.fd;
+    const double* v = hd.tree_frame;
+    f.zeta = v[0];
+    f.phi = v[1];
+    for (int a = 0; a < 3; ++a) {
+      f.cen[a] = v[2 + a];
+      f.axis[a] = v[5 + a];
+    }
+    f.angle = v[8];
+  }
   c->surr_bound_med = hd.bound_med;
   c->surr_bound_p999 = hd.bound_p999;
   c->perm_h = perm;
@@ -2349,7 +2472,8 @@ int steps_cyl_set_tail(steps_cyl_ctx* c, int32_t tail) {
   if (tail != STEPS_TAIL_FULL && tail != STEPS_TAIL_SURROGATE && tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
   if (is_inf(c) && tail == STEPS_TAIL_FULL) return fail(STEPS_EINVAL, "the infinite window has no plain image sum");
-  if (is_tree(c) && tail != STEPS_TAIL_TABLE) return fail(STEPS_EINVAL, "the octree evaluates the correction-table form");
+  if (is_tree(c) && tail != (is_r3(c) ? STEPS_TAIL_FULL : STEPS_TAIL_TABLE))
+    return fail(STEPS_EINVAL, "the octree evaluates one pair form (S1xR2: the correction table; R^3: the plain force)");
   if (tail == STEPS_TAIL_SURROGATE && !c->surr_ok) return fail(STEPS_ENOSURROGATE, "no accepted surrogate is loaded");
   if (tail == STEPS_TAIL_TABLE && !c->tab_ok) return fail(STEPS_ENOSURROGATE, "no accepted correction table is built");
   if (tail != STEPS_TAIL_FULL && c->p.precision == STEPS_FP64)
@@ -2430,13 +2554,39 @@ int steps_cyl_tree_frame(steps_cyl_ctx* c, double zeta, double phi) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (!is_tree(c)) return fail(STEPS_EINVAL, "the context does not use the octree");
+  if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 octree takes steps_cyl_tree_frame_r3");
   if (zeta < 0.0) {
     c->tr.fixed = false;
   } else {
-    if (!(zeta < c->p.L) || !std::isfinite(phi)) return fail(STEPS_EINVAL, "zeta must lie in [0, L), phi be finite");
+    TreeDraw f{};
+    f.zeta = zeta;
+    f.phi = phi;
+    int rc = check_frame(c, f);
+    if (rc) return rc;
     c->tr.fixed = true;
-    c->tr.fzeta = zeta;
-    c->tr.fphi = phi;
+    c->tr.fd = f;
+  }
+  c->forces_stale = true;
+  return STEPS_OK;
+}
+
+int steps_cyl_tree_frame_r3(steps_cyl_ctx* c, const double* frame) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!is_tree(c) || !is_r3(c)) return fail(STEPS_EINVAL, "the context does not use the R^3 octree");
+  if (!frame) {
+    c->tr.fixed = false;
+  } else {
+    TreeDraw f{};
+    for (int a = 0; a < 3; ++a) {
+      f.cen[a] = frame[a];
+      f.axis[a] = frame[3 + a];
+    }
+    f.angle = frame[6];
+    int rc = check_frame(c, f);
+    if (rc) return rc;
+    c->tr.fixed = true;
+    c->tr.fd = f;
   }
   c->forces_stale = true;
   return STEPS_OK;

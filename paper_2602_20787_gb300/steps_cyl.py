@@ -40,7 +40,8 @@ _EXPORTS = [
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
-    "steps_cyl_tree_frame", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate", "steps_cyl_tree_set_radial",
+    "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
+    "steps_cyl_tree_set_radial",
 ]
 
 STEPS_SURR_NW = 1250
@@ -131,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
     L.steps_cyl_resume.argtypes = [ctypes.POINTER(p), ctypes.c_char_p, i32, p]
     L.steps_cyl_tree_frame.argtypes = [p, d, d]
+    L.steps_cyl_tree_frame_r3.argtypes = [p, p]
     L.steps_cyl_tree_stats.argtypes = [p, p]
     L.steps_cyl_tree_calibrate.argtypes = [p, i32, i32, i32, p, p, p, p]
     L.steps_cyl_tree_set_radial.argtypes = [p, p, i32, d]
@@ -394,6 +396,15 @@ def steps_cyl_check_tail(ctx, tail: int, check_particles: int = 1024) -> np.ndar
 def steps_cyl_tree_frame(ctx, zeta: float, phi: float):
     """Fix the octree frame (shift zeta along the axis, rotation phi); zeta < 0: random per evaluation."""
     _check(load().steps_cyl_tree_frame(ctx, float(zeta), float(phi)))
+
+
+def steps_cyl_tree_frame_r3(ctx, centre=None, axis=None, angle: float = 0.0):
+    """R^3: fix the octree frame (domain centre, unit rotation axis, angle); no centre: random per evaluation."""
+    if centre is None:
+        _check(load().steps_cyl_tree_frame_r3(ctx, None))
+        return
+    f = np.ascontiguousarray(list(centre) + list(axis) + [angle], dtype=np.float64)
+    _check(load().steps_cyl_tree_frame_r3(ctx, _ptr(f)))
 
 
 def steps_cyl_tree_stats(ctx) -> dict:

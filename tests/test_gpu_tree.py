@@ -271,3 +271,120 @@ def test_tree_full_size_sampled(sc):
     # this load's net forces are small residuals: its FP32 forms sit near 2e-6 at the median
     assert med <= 1e-5 and mx <= 1e-3
     sim.close()
+
+
+# ---- the R^3 octree ------------------------------------------------------------
+
+def r3_tree_config(sc, rho_bar, **kw):
+    base = dict(topology=sc.STEPS_TOPO_R3, n_cut=1, precision=sc.STEPS_FP32_KAHAN, background=sc.STEPS_BG_SPHERE,
+                rho_bar=rho_bar, R_sim=2.0, force=sc.STEPS_FORCE_OCTREE, theta=0.5, leaf_size=16)
+    base.update(kw)
+    return sc.Config(**base)
+
+
+def unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v)
+
+
+def oracle_tree_r3(d, cen, axis, angle, theta=0.5, leaf=16, idx=None):
+    g, st = oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, theta, leaf, cen, axis, angle, idx=idx)
+    sel = d["pos"] if idx is None else d["pos"][idx]
+    return g + oracle.background_sphere(sel, 1.0, d["rho_bar"]), st
+
+
+@pytest.mark.parametrize("theta,leaf", [(0.5, 16), (0.3, 8), (0.8, 32)])
+def test_r3_tree_matches_oracle(sc, theta, leaf):
+    d = ics.ball_load(3000, 31)
+    cen, axis, angle = [0.2, -0.3, 0.1], unit([0.3, -0.5, 0.8]), 1.3
+    sim = sc.Simulation(r3_tree_config(sc, d["rho_bar"], theta=theta, leaf_size=leaf), d["pos"], d["vel"], d["m"],
+                        d["h"])
+    sc.steps_cyl_tree_frame_r3(sim.ctx, cen, axis, angle)
+    a = sim.forces()
+    st = sc.steps_cyl_tree_stats(sim.ctx)
+    ref, ost = oracle_tree_r3(d, cen, axis, angle, theta, leaf)
+    med, _, mx = stats(a, ref)
+    print(f"R3 octree theta {theta}: median {med:.2e} max {mx:.2e}; nodes {st['nodes']} (oracle {ost[0]}), "
+          f"interactions {st['interactions']:.0f} (oracle {ost[3]})")
+    assert st["nodes"] == ost[0] and st["depth"] == ost[2] and st["interactions"] == ost[3]
+    assert med <= 1e-6 and mx <= 2e-5
+    sim.close()
+
+
+def splitmix_frames_r3(seed, first, count, R_sim):
+    # the library's R^3 frame draw: axis uniform on the sphere, angle, centre uniform in the ball of radius R_sim / 2
+    M = (1 << 64) - 1
+    out = []
+    for e in range(first, first + count):
+        s = (seed * 0x9E3779B97F4A7C15 + e) & M
+        u = []
+        for _ in range(6):
+            s = (s + 0x9E3779B97F4A7C15) & M
+            z = s
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+            z ^= z >> 31
+            u.append((z >> 11) * 2.0 ** -53)
+        za, pa = 2.0 * u[0] - 1.0, 2.0 * math.pi * u[1]
+        sa = math.sqrt(max(0.0, 1.0 - za * za))
+        axis = [sa * math.cos(pa), sa * math.sin(pa), za]
+        angle = 2.0 * math.pi * u[2]
+        rc = 0.5 * R_sim * math.cbrt(u[3])
+        zc, pc = 2.0 * u[4] - 1.0, 2.0 * math.pi * u[5]
+        sc_ = math.sqrt(max(0.0, 1.0 - zc * zc))
+        out.append(([rc * sc_ * math.cos(pc), rc * sc_ * math.sin(pc), rc * zc], axis, angle))
+    return out
+
+
+def test_r3_random_frames_per_evaluation(sc):
+    d = ics.ball_load(2000, 32)
+    sim = sc.Simulation(r3_tree_config(sc, d["rho_bar"], tree_seed=9), d["pos"], d["vel"], d["m"], d["h"])
+    idx = ics.subsample(2000, 200, seed=4)
+    for cen, axis, angle in splitmix_frames_r3(9, 1, 2, 2.0):
+        a = sim.forces()
+        ref, _ = oracle_tree_r3(d, cen, axis, angle, idx=idx)
+        med, _, mx = stats(a[idx], ref)
+        assert med <= 1e-6 and mx <= 2e-5
+    sim.close()
+
+
+def test_r3_radial_calibration_matches_oracle(sc):
+    d = ics.ball_load(2500, 33)
+    sim = sc.Simulation(r3_tree_config(sc, d["rho_bar"]), d["pos"], d["vel"], d["m"], d["h"])
+    frames = [([0.1, 0.2, -0.3], unit([1, 1, 0.5]), 0.7), ([-0.4, 0.1, 0.2], unit([0.2, -1, 0.3]), 2.5)]
+    flat = np.array([list(c) + list(a) + [g] for c, a, g in frames])
+    sample = ics.subsample(2500, 500, seed=7)
+    nb = 10
+    tab, rmax = sc.steps_cyl_tree_calibrate(sim.ctx, 2, nb, 500, frames=flat, sample=sample)
+    direct = oracle.pair_field_r3(d["pos"], d["m"], d["h"], 1.0, idx=sample)
+    r = np.linalg.norm(d["pos"][sample], axis=1)
+    assert rmax == pytest.approx(np.linalg.norm(d["pos"], axis=1).max(), rel=1e-15)
+    k = np.minimum(nb - 1, (r / rmax * nb).astype(int))
+    sums, cnt = np.zeros(nb), np.zeros(nb)
+    for cen, axis, angle in frames:
+        g, _ = oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, 0.5, 16, cen, axis, angle, idx=sample)
+        e = ((g - direct) * d["pos"][sample]).sum(1) / r
+        np.add.at(sums, k, e)
+        np.add.at(cnt, k, 1)
+    ref = np.where(cnt > 0, sums / np.maximum(cnt, 1), 0.0)
+    scale = np.median(np.linalg.norm(direct, axis=1))
+    print("R3 radial table", tab, "oracle", ref)
+    assert np.abs(tab - ref).max() <= 1e-5 * scale
+    sim.close()
+
+
+def test_r3_tree_configurations_are_checked(sc):
+    d = ics.ball_load(300, 34)
+    with pytest.raises(sc.StepsError) as e:
+        sc.Simulation(r3_tree_config(sc, d["rho_bar"], precision=sc.STEPS_FP64), d["pos"], d["vel"], d["m"], d["h"])
+    assert e.value.code == sc.STEPS_EINVAL
+    sim = sc.Simulation(r3_tree_config(sc, d["rho_bar"]), d["pos"], d["vel"], d["m"], d["h"])
+    for call in (lambda: sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE),
+                 lambda: sc.steps_cyl_tree_frame(sim.ctx, 0.1, 0.2),
+                 lambda: sc.steps_cyl_tree_frame_r3(sim.ctx, [0.0, 0.0, 0.0], [1.0, 1.0, 0.0], 0.3),
+                 lambda: sc.steps_cyl_tree_frame_r3(sim.ctx, [2.0, 0.0, 0.0], [1.0, 0.0, 0.0], 0.3),
+                 lambda: sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)):
+        with pytest.raises(sc.StepsError) as e:
+            call()
+        assert e.value.code in (sc.STEPS_EINVAL, sc.STEPS_ENOSURROGATE)
+    sim.close()

@@ -118,3 +118,49 @@ def test_particle_outside_the_root_is_refused(orc):
     pos[7, 0] = 2.0 * max(1.0, 2.0 * ics.R_SIM)       # beyond half the root side
     with pytest.raises(ValueError):
         oracle.tree_field(pos, d["m"], d["h"], 1.0, 1.0, ics.R_SIM, 8, 0.5, 16, 0.0, 0.0)
+
+
+# ---- the R^3 octree (Sect. 2.4: domain centre shifted inside R_sim / 2, rotation about a random axis) ----
+
+def unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v)
+
+
+def test_r3_vanishing_angle_is_the_direct_sum(orc):
+    d = ics.ball_load(800, 11)
+    g, st = oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, 1e-7, 8, [0.2, -0.3, 0.1], unit([1, 2, -1]), 0.9)
+    ref = oracle.pair_field_r3(d["pos"], d["m"], d["h"], 1.0)
+    assert np.abs(g - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert st[3] == 800 * 800
+
+
+def test_r3_error_falls_with_the_opening_angle(orc):
+    d = ics.ball_load(3000, 12)
+    ref = oracle.pair_field_r3(d["pos"], d["m"], d["h"], 1.0)
+    med = []
+    for th in (0.2, 0.4, 0.7):
+        g, _ = oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, th, 16, [0.1, 0.4, -0.2], unit([0.3, -0.5, 0.8]),
+                                    1.3)
+        med.append(np.median(rel(g, ref)))
+    print("R3 median errors", med)
+    assert med[0] < 2e-4 and med[0] < med[1] < med[2] < 3e-2
+
+
+def test_r3_field_turns_with_the_load(orc):
+    # the load turned by Q, with the domain centre turned by Q and the frame rotation composed with Q^T,
+    # sees the same tree: its field is the turned field
+    d = ics.ball_load(1500, 13)
+    ax, ang, cen = unit([0.3, -0.5, 0.8]), 1.3, np.array([0.1, 0.4, -0.2])
+    g, _ = oracle.tree_field_r3(d["pos"], d["m"], d["h"], 1.0, 2.0, 0.5, 16, cen, ax, ang)
+    # a quarter turn about the frame's own axis commutes with the frame rotation
+    Q = rotation(ax, 0.5 * math.pi)
+    g2, _ = oracle.tree_field_r3(d["pos"] @ Q.T, d["m"], d["h"], 1.0, 2.0, 0.5, 16, Q @ cen, ax, ang - 0.5 * math.pi)
+    r = rel(g2, g @ Q.T)
+    assert np.median(r) < 1e-9
+    assert np.mean(r < 1e-6) > 0.98
+
+
+def rotation(ax, ang):
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)

@@ -388,3 +388,26 @@ def test_r3_tree_configurations_are_checked(sc):
             call()
         assert e.value.code in (sc.STEPS_EINVAL, sc.STEPS_ENOSURROGATE)
     sim.close()
+
+
+def test_r3_tree_kdk_resume_keeps_the_frame_sequence(sc, tmp_path):
+    # random R^3 frames drawn by evaluation count, so a resumed run continues the sequence
+    d = ics.ball_load(600, 35)
+    d["vel"] = np.random.default_rng(5).normal(0.0, 0.01, d["pos"].shape)
+    cfg = r3_tree_config(sc, d["rho_bar"], tree_seed=3)
+    ref = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    ref.step(0.02, 4)
+    xr, vr, _, _ = ref.state()
+    ref.close()
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    sim.step(0.02, 2)
+    path = str(tmp_path / "r3tree.ckpt")
+    sim.checkpoint(path)
+    sim.close()
+    sim = sc.Simulation.resume(path)
+    sim.step(0.02, 2)
+    x, v, _, _ = sim.state()
+    np.testing.assert_array_equal(x, xr)
+    np.testing.assert_array_equal(v, vr)
+    assert sc.steps_cyl_tree_stats(sim.ctx)["evaluations"] == 5
+    sim.close()

@@ -104,10 +104,13 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """The pair kernel's source and its launch shape (the stream-K CTA multiplier)."""
     h = hashlib.sha256()
-    for f in ("pair_fp32.cuh",):
-        with open(os.path.join(ROOT, "paper_2602_20787_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2602_20787_gb300", "csrc")
+    with open(os.path.join(csrc, "pair_fp32.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "steps_cyl.cu")) as fh:
+        h.update("".join(ln for ln in fh if ln.startswith("#define STEPS_CTA_MULT")).encode())
     return h.hexdigest()[:16]
 
 

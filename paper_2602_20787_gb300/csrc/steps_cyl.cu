@@ -39,7 +39,7 @@ using namespace steps;
 // CTAs of the pair kernel per resident slot (build-time tuning knob): more CTAs
 // than slots lets the block scheduler even out CTAs whose work differs.
 #ifndef STEPS_CTA_MULT
-#define STEPS_CTA_MULT 8
+#define STEPS_CTA_MULT 32
 #endif
 
 namespace {

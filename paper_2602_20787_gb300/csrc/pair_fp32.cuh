@@ -52,7 +52,7 @@ constexpr int kBJ = 128;  // j per shared-memory tile
 
 // Tuning knobs (build-time; the defaults are the measured best on GB300).
 #ifndef STEPS_KAHAN_GROUP
-#define STEPS_KAHAN_GROUP 4   // pair forces summed plainly in groups of this many j before the Kahan update
+#define STEPS_KAHAN_GROUP 8   // pair forces summed plainly in groups of this many j before the Kahan update
 #endif
 #ifndef STEPS_SPLINE_UNROLL
 #define STEPS_SPLINE_UNROLL 2 // unroll of the spline-capable image loop

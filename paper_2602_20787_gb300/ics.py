@@ -196,3 +196,108 @@ def random_surrogate_params(seed: int, dR_max: float, mu=(0.0, 0.0), sc=(0.05, 0
         parts.append(rng.uniform(-b, b, cnt))
     parts.append(np.array([mu[0], mu[1], sc[0], sc[1], dR_max]))
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# The paper's tessellated particle load (Sect. 3.1, eqs. inversestereographic
+# and omegatovarrho, Fig. 4).
+#
+# The compact radius w = 2 arctan(rho / D_s) runs over [0, w_max) with
+# w_max = 2 arctan(R_sim / D_s). The region w >= w_c is cut into n_out rings of
+# equal width dw in w, each ring into n_phi equal azimuth sectors and n_z equal
+# z slabs: a uniform grid in (w, phi, z). Inside the core w < w_c the mass
+# resolution is held constant. The core is cut into n_in rings of equal area
+# (equal width in rho^2), with the same n_phi x n_z cells per ring. n_in is
+# chosen so that a core cell has the volume of a cell of the first outer ring,
+# rounded to a whole number of rings, so the resolution is continuous at
+# rho_c = D_s tan(w_c / 2).
+#
+# Each cell holds one particle at a uniformly random point of its volume, with
+# mass m_i = rho_bar V_i, where V_i = (rho_hi^2 - rho_lo^2) / 2 * dphi * dz is
+# the cell's exact comoving volume. The cells tile the cylinder rho < R_sim,
+# 0 <= z < L exactly, so the masses sum to rho_bar pi R_sim^2 L.
+#
+# The paper only says "random location in each compact cell". This generator
+# draws uniformly in volume, so the expected density is exactly rho_bar. A draw
+# uniform in w would differ only at second order in dw.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class CompactRings:
+    """Ring structure of the tessellated load. s_edges are the ring edges in
+    s = rho^2 (n_in + n_out + 1 values, s_edges[-1] = R_sim^2). cell_volume
+    holds one value per ring; the cells of a ring share it."""
+    s_edges: np.ndarray
+    n_in: int
+    n_out: int
+    n_phi: int
+    n_z: int
+    omega_c: float
+    rho_c: float
+    omega_max: float
+    L: float
+
+    @property
+    def cell_volume(self) -> np.ndarray:
+        ds = np.diff(self.s_edges)
+        ds[: self.n_in] = self.s_edges[self.n_in] / max(self.n_in, 1)  # one exact core volume
+        return 0.5 * ds * (2.0 * math.pi / self.n_phi) * (self.L / self.n_z)
+
+    @property
+    def n(self) -> int:
+        return (self.n_in + self.n_out) * self.n_phi * self.n_z
+
+
+def compact_rings(n_out: int, n_phi: int, n_z: int, *, D_s: float = D_S, R_sim: float = R_SIM,
+                  omega_c: float = 0.0, L: float = L_BOX) -> CompactRings:
+    """Ring edges and cell volumes of the tessellated load (no particles drawn).
+    omega_c = 0 gives the plain uniform grid in w with no constant-mass core."""
+    if n_out < 1 or n_phi < 1 or n_z < 1:
+        raise ValueError("n_out, n_phi and n_z must be >= 1")
+    if not (D_s > 0.0 and R_sim > 0.0 and L > 0.0):
+        raise ValueError("D_s, R_sim and L must be positive")
+    w_max = 2.0 * math.atan(R_sim / D_s)
+    if not (0.0 <= omega_c < w_max):
+        raise ValueError("omega_c must lie in [0, 2 arctan(R_sim / D_s))")
+    dw = (w_max - omega_c) / n_out
+    w_edges = omega_c + dw * np.arange(n_out + 1)
+    rho_out = D_s * np.tan(0.5 * w_edges)
+    rho_out[0] = D_s * math.tan(0.5 * omega_c)
+    rho_out[-1] = R_sim
+    s_out = rho_out * rho_out
+    rho_c = float(rho_out[0])
+    if omega_c > 0.0:
+        a1 = s_out[1] - s_out[0]
+        n_in = max(1, int(round(s_out[0] / a1)))
+        s_in = s_out[0] * np.arange(n_in) / n_in
+    else:
+        n_in = 0
+        s_in = np.zeros(0)
+    return CompactRings(np.concatenate([s_in, s_out]), n_in, n_out, n_phi, n_z, float(omega_c), rho_c,
+                        w_max, float(L))
+
+
+def compact_load(n_out: int, n_phi: int, n_z: int, seed: int, *, D_s: float = D_S, R_sim: float = R_SIM,
+                 omega_c: float = 0.0, L: float = L_BOX, rho_bar: float = 1.0, eps0: float = 0.01):
+    """One particle per cell of compact_rings(...), uniform in the cell's volume,
+    with m_i = rho_bar V_i and softening eps0 (m_i / m_min)^(1/3).
+
+    Returns dict(pos (n,3), vel (n,3), m (n,), h (n,), rings), particles in
+    ring-major order (ring, then azimuth sector, then z slab); z in [0, L)."""
+    rings = compact_rings(n_out, n_phi, n_z, D_s=D_s, R_sim=R_sim, omega_c=omega_c, L=L)
+    nr = rings.n_in + rings.n_out
+    ring = np.repeat(np.arange(nr), n_phi * n_z)
+    sec = np.tile(np.repeat(np.arange(n_phi), n_z), nr)
+    slab = np.tile(np.arange(n_z), nr * n_phi)
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0.0, 1.0, (rings.n, 3))
+    s_lo, s_hi = rings.s_edges[ring], rings.s_edges[ring + 1]
+    rho = np.sqrt(s_lo + u[:, 0] * (s_hi - s_lo))
+    rho = np.minimum(rho, np.nextafter(R_sim, 0.0))
+    phi = (sec + u[:, 1]) * (2.0 * math.pi / n_phi)
+    z = (slab + u[:, 2]) * (L / n_z)
+    z[z >= L] -= L
+    m = rho_bar * rings.cell_volume[ring]
+    h = eps0 * (m / m.min()) ** (1.0 / 3.0)
+    pos = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+    return {"pos": pos, "vel": np.zeros((rings.n, 3)), "m": m, "h": h, "rings": rings}

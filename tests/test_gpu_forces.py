@@ -123,6 +123,21 @@ def test_full_size_lcdm_sampled(sc):
     sim.close()
 
 
+def test_compact_load_table1_geometry(sc):
+    """The paper's tessellated load with its constant-mass core (Sect. 3.1), in
+    Table 1's geometry in units of L_z: R_sim = 0.5, D_S = 0.07, omega_c = 1.63973."""
+    R = 0.5
+    d = ics.compact_load(10, 12, 8, 31, D_s=0.07, R_sim=R, omega_c=1.63973, L=1.0, eps0=0.005)
+    assert d["rings"].n_in > 1
+    ref = oracle_accel(d["pos"], d["m"], d["h"], 16, R=R)
+    for precision, med_gate, p999_gate in ((0, 1e-11, 1e-9), (1, 1e-5, 1e-3)):
+        sim = make_sim(sc, d, 16, precision, R_sim=R)
+        med, p999, mx = stats(sim.forces(), ref)
+        print(f"compact load, precision {precision}: median {med:.3e} p99.9 {p999:.3e} max {mx:.3e}")
+        assert med <= med_gate and p999 <= p999_gate, (precision, med, p999)
+        sim.close()
+
+
 def test_deterministic(sc):
     d = ics.particle_load(3000, 5, 1.0)
     sim = make_sim(sc, d, 16, 1)

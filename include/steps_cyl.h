@@ -383,7 +383,12 @@ int steps_cyl_checkpoint(steps_cyl_ctx* ctx, const char* path);
 
 /* Create a context from a checkpoint file on the given device and stream. The
  * resumed context continues bit-identically to the one that wrote the file.
- * STEPS_EINVAL for a missing, foreign or truncated file. */
+ * STEPS_EINVAL for a missing, foreign or truncated file, and for a corrupt one.
+ * That covers a file whose size differs from what its header implies, a
+ * permutation that is not one of [0, n), and a finite-cylinder background
+ * without its table. It also covers a non-finite or non-positive a, a
+ * non-finite t or rho0, and a fixed octree frame that steps_cyl_tree_frame
+ * would refuse. These checks, except the frame's, run before any CUDA call. */
 int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void* stream);
 
 /* Release the context and its device memory. NULL is accepted. */

@@ -2271,6 +2271,14 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
     std::fclose(f);
     return fail(STEPS_EINVAL, "%s is not a checkpoint of this library version", path);
   }
+  // The header fixes the file's exact size; checking it first keeps a corrupt
+  // particle count from sizing the buffers below.
+  const long long need = (long long)sizeof hd + (hd.bgK ? (hd.bgK + 4LL) * 8 : 0) + hd.rad_nb * 8LL +
+                         hd.n * (11LL * 8 + 4);
+  if (std::fseek(f, 0, SEEK_END) != 0 || std::ftell(f) != need || std::fseek(f, (long)sizeof hd, SEEK_SET) != 0) {
+    std::fclose(f);
+    return fail(STEPS_EINVAL, "%s is truncated or has trailing bytes", path);
+  }
   std::vector<double> tab(hd.bgK ? hd.bgK + 4 : 0), arr((size_t)hd.n * 11), rad(hd.rad_nb);
   std::vector<int> perm(hd.n);
   bool ok = !hd.bgK || std::fread(tab.data(), sizeof(double), tab.size(), f) == tab.size();
@@ -2283,6 +2291,22 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
   hd.p.device = device;
   int rc = check_params(&hd.p);
   if (rc) return rc;
+  // Everything read from the file that indexes device memory or sizes a table
+  // is checked before the first CUDA call: the permutation must be one of
+  // [0, n), and a finite-cylinder background needs its table.
+  {
+    std::vector<char> seen(hd.n, 0);
+    for (int64_t k = 0; k < hd.n; ++k) {
+      const int v = perm[k];
+      if (v < 0 || v >= hd.n || seen[v]) return fail(STEPS_EINVAL, "corrupt checkpoint (permutation)");
+      seen[v] = 1;
+    }
+  }
+  if (hd.p.background == STEPS_BG_FINITE && (hd.bgK < 1 || !(hd.bg_dr > 0.0) || !std::isfinite(hd.bg_dr)))
+    return fail(STEPS_EINVAL, "corrupt checkpoint (background table)");
+  if (!(hd.a > 0.0) || !std::isfinite(hd.a) || !std::isfinite(hd.t) || !(hd.rho0 >= 0.0) ||
+      !std::isfinite(hd.rho0))
+    return fail(STEPS_EINVAL, "corrupt checkpoint (a, t or rho0)");
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(STEPS_EINVAL, "device %d out of range", device);
@@ -2319,6 +2343,7 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
     release(c);
     return code;
   };
+  if (c->tr.fixed && (rc = check_frame(c, c->tr.fd))) return bail(rc);
   if ((rc = allocate_context(c))) return bail(rc);
   if (cudaMemcpyAsync(c->state, arr.data(), sizeof(double) * arr.size(), cudaMemcpyHostToDevice, c->st) !=
       cudaSuccess)

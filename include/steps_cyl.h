@@ -80,7 +80,7 @@ typedef struct {
                      * surrogate trained to infinity may be selected later), an FP32 precision
                      * and STEPS_BG_INFINITE or STEPS_BG_OFF */
   int32_t n0;       /* near range of a modelled tail: images |k| <= n0 summed directly,
-                     * 1 <= n0 < n_cut (n0 >= 1 for the infinite window) */
+                     * 1 <= n0 < n_cut (1 <= n0 < 512 for the infinite window) */
   int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
   int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE | STEPS_TAIL_TABLE */
   int32_t background; /* STEPS_BG_OFF | STEPS_BG_FINITE | STEPS_BG_INFINITE */
@@ -208,6 +208,8 @@ int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg);
  * |k| > n0, SR = sum F(r,h)/r and SZ = sum (dz + k) F(r,h)/r (eq. Force_spline_kernel).
  * n_cut = 0: the infinite line, images |k| <= 512 one by one and the continuum
  * cells beyond with their near end's Euler-Maclaurin term.
+ * Requires 0 <= n0 < n_cut <= 4096, or n_cut = 0 and 0 <= n0 < 512; STEPS_EINVAL
+ * otherwise, before any CUDA call.
  * out: host or device, ns x 2. Synchronises the stream. */
 int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out,
                         void* stream);

@@ -335,7 +335,9 @@ int check_params(const steps_cyl_params* p) {
     if (p->precision == STEPS_FP64) return fail(STEPS_EINVAL, "the infinite window needs an FP32 precision");
     if (p->background != STEPS_BG_OFF && p->background != STEPS_BG_INFINITE)
       return fail(STEPS_EINVAL, "the infinite window takes STEPS_BG_INFINITE or STEPS_BG_OFF");
-    if (p->n0 < 1) return fail(STEPS_EINVAL, "n0 must be >= 1");
+    // the tail sums images |k| <= kKInf one by one and the line ends beyond, so the
+    // near range must end inside that range
+    if (p->n0 < 1 || p->n0 >= kKInf) return fail(STEPS_EINVAL, "n0 must be in [1, %d) for the infinite window", kKInf);
   }
   if (p->precision < STEPS_FP64 || p->precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   if (p->force != STEPS_FORCE_DIRECT && p->force != STEPS_FORCE_OCTREE) return fail(STEPS_EINVAL, "bad force method");
@@ -2398,7 +2400,8 @@ int steps_cyl_train_cfg_default(steps_cyl_train_cfg* cfg) {
 int steps_cyl_tail_sums(int64_t ns, const double* samples, int32_t n_cut, int32_t n0, double* out, void* stream) {
   g_last_error.clear();
   if (ns < 0 || !samples || !out) return fail(STEPS_EINVAL, "bad arguments");
-  if (n_cut < 0 || n0 < 0 || (n_cut > 0 && n0 >= n_cut)) return fail(STEPS_EINVAL, "need 0 <= n0 < n_cut or n_cut = 0");
+  if (n_cut < 0 || n_cut > 4096 || n0 < 0 || (n_cut > 0 && n0 >= n_cut) || (n_cut == 0 && n0 >= kKInf))
+    return fail(STEPS_EINVAL, "need 0 <= n0 < n_cut <= 4096, or n_cut = 0 and 0 <= n0 < %d", kKInf);
   if (ns == 0) return STEPS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   double *ds = nullptr, *dout = nullptr;

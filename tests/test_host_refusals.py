@@ -1,7 +1,13 @@
-"""Checkpoint validation on the host: steps_cyl_resume refuses corrupt files
-before its first CUDA call, so these run without a GPU. The files are written
-here from a ctypes mirror of the library's checkpoint header. A layout mismatch
-would show up as "not a checkpoint" in place of the specific refusal."""
+"""Refusals that the C ABI makes on the host, before its first CUDA call, so
+these run without a GPU.
+
+- Checkpoints: steps_cyl_resume refuses corrupt files. The files are written
+  here from a ctypes mirror of the library's checkpoint header. A layout
+  mismatch would show up as "not a checkpoint" in place of the specific refusal.
+- Parameters: steps_cyl_init and steps_cyl_tail_sums refuse window and
+  near-range settings outside their domain (eq. ForceCylindrical's window, and
+  the infinite window of Sect. 2.2, whose tail sums the images to |k| = 512 one
+  by one)."""
 import ctypes
 import math
 
@@ -111,3 +117,38 @@ def test_a_background_table_is_optional_without_the_finite_background(lib, tmp_p
     path = write_ckpt(tmp_path / "c", bgK=0, background=sc.STEPS_BG_OFF)
     size = ctypes.sizeof(CkptHeader) + N * (11 * 8 + 4)
     assert path.stat().st_size == size
+
+
+def init_refused(cfg, what, n=4):
+    d = np.zeros(n)
+    arrs = [np.linspace(0.1, 0.4, n), np.zeros(n), np.linspace(0.1, 0.7, n), d, d, d, np.ones(n), np.ones(n)]
+    with pytest.raises(sc.StepsError) as e:
+        sc.steps_cyl_init(cfg, n, *arrs)
+    assert e.value.code == sc.STEPS_EINVAL
+    assert what in str(e.value), str(e.value)
+
+
+@pytest.mark.parametrize("n0", [0, 512, 4000])
+def test_infinite_window_near_range(lib, n0):
+    cfg = sc.Config(n_cut=0, n0=n0, tail=sc.STEPS_TAIL_TABLE, background=sc.STEPS_BG_INFINITE)
+    init_refused(cfg, "n0 must be in [1, 512)")
+
+
+@pytest.mark.parametrize("kw,what", [(dict(n_cut=4097), "n_cut must be in"), (dict(n_cut=-1), "n_cut must be in"),
+                                     (dict(n_cut=8, n0=8, tail=sc.STEPS_TAIL_TABLE), "n0 must be in [1, n_cut)"),
+                                     (dict(theta=0.5, force=sc.STEPS_FORCE_OCTREE), "octree needs the infinite"),
+                                     (dict(topology=sc.STEPS_TOPO_R3, background=sc.STEPS_BG_FINITE), "R^3 topology")])
+def test_init_parameters(lib, kw, what):
+    init_refused(sc.Config(**kw), what)
+
+
+def test_init_particle_count(lib):
+    init_refused(sc.Config(), "n must be in", n=1)
+
+
+@pytest.mark.parametrize("n_cut,n0", [(4097, 4), (-1, 0), (8, 8), (8, -1), (0, 512), (0, 1000)])
+def test_tail_sums_domain(lib, n_cut, n0):
+    smp = np.array([[0.5, 0.1, 0.01]])
+    with pytest.raises(sc.StepsError) as e:
+        sc.steps_cyl_tail_sums(smp, n_cut, n0)
+    assert e.value.code == sc.STEPS_EINVAL

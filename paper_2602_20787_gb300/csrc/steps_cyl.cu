@@ -2374,7 +2374,9 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
     c->tab_bound_p999 = hd.tab_bound_p999;
   }
   if (hd.rad_nb) {
-    if (!(hd.rad_rmax > 0)) return bail(fail(STEPS_EINVAL, "corrupt checkpoint (radial table)"));
+    bool good = hd.rad_rmax > 0 && std::isfinite(hd.rad_rmax);
+    for (double v : rad) good = good && std::isfinite(v);
+    if (!good) return bail(fail(STEPS_EINVAL, "corrupt checkpoint (radial table)"));
     if ((rc = set_radial(c, rad, hd.rad_rmax))) return bail(rc);
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(fail(STEPS_ECUDA, "synchronise failed"));

@@ -503,6 +503,55 @@ def run_inf(args):
     return 0
 
 
+def run_table1(args):
+    """The paper's tessellated particle load (Sect. 3.1, Fig. 4) in Table 1's
+    geometry in units of L_z (R_sim = 0.5, D_S = 0.07, omega_c = 1.63973; N =
+    65,536: 4 equal-mass core rings and 12 outer rings of 64 x 64 cells),
+    comoving at Table 1's initial redshift (a = 0.02) and cosmology, Ncut = 16:
+    the FP32-Kahan force and KDK-step times, the pair kernel's MUFU roofline,
+    the error against the GPU FP64 form on a sample, and the oracle beside it."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    d = ics.table1_load()
+    n, n_cut = d["pos"].shape[0], 16
+    pairs = n * (n - 1.0)
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * 2070e6
+    a0 = ics.TABLE1_A_INIT
+    t0 = ics.lcdm_time_of_a(a0, ics.TABLE1_OMEGA_M, ics.TABLE1_OMEGA_L)
+    R = ics.TABLE1_GEOMETRY["R_sim"]
+    cfg = sc.Config(n_cut=n_cut, precision=sc.STEPS_FP32_KAHAN, R_sim=R, rho_bar=d["rho_bar"], comoving=True,
+                    Omega_m=ics.TABLE1_OMEGA_M, Omega_L=ics.TABLE1_OMEGA_L, a_start=a0, t_start=t0,
+                    stream=torch.cuda.current_stream().cuda_stream)
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    a32, ms = _timed_forces(sc, torch, sim, 3)
+    idx = ics.subsample(n, 256, seed=12345)
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)
+    a64 = sim.forces_subset(idx)
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    sim.step(0.01 * t0, 10)
+    ev1.record()
+    torch.cuda.synchronize()
+    rate = pairs * 2 * n_cut / (ms * 1e-3)
+    line = {"workload": "table1_n65536", "n": n, "n_cut": n_cut, "core_rings": d["rings"].n_in,
+            "outer_rings": d["rings"].n_out, "cells_per_ring": [64, 64],
+            "mass_range": float(d["m"].max() / d["m"].min()),
+            "fp32_kahan": {"pair_ms": ms, "pair_images_per_s": rate, "roofline_frac": rate / peak,
+                           "kdk_step_ms": ev0.elapsed_time(ev1) / 10, "error_vs_fp64": _err(a32[idx], a64)}}
+    sim.close()
+    import oracle
+
+    def ref(ix):
+        return (oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, n_cut, idx=ix)
+                + oracle.background_field(d["pos"][ix], R, n_cut * 1.0, 1.0, d["rho_bar"], mode=1))
+    line["cpu_baseline"] = oracle_rate(ref, n, (n - 1.0) * 2 * n_cut, "pair-images/s",
+                                       f"FP64 oracle pair field + background, all {n} j x {2 * n_cut} images")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_octree(args):
     """Octree (Sect. 2.4) on the production-shaped load (softening ratio 1:8;
     N = 524,288, or 65,536 with the same law), infinite window with the
@@ -727,6 +776,8 @@ def run_workload(args):
         return run_octree(args)
     if args.workload == "inf_n65536":
         return run_inf(args)
+    if args.workload == "table1_n65536":
+        return run_table1(args)
     w = ics.WORKLOADS[args.workload]
     d = ics.workload_ics(w)
     n = w.n

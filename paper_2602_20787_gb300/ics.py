@@ -301,3 +301,21 @@ def compact_load(n_out: int, n_phi: int, n_z: int, seed: int, *, D_s: float = D_
     h = eps0 * (m / m.min()) ** (1.0 / 3.0)
     pos = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
     return {"pos": pos, "vel": np.zeros((rings.n, 3)), "m": m, "h": h, "rings": rings}
+
+
+# Table 1's geometry in units of L_z = 1 Gpc: R_sim = 500 Mpc, D_S = 70 Mpc,
+# omega_c = 1.63973 rad; its cosmology (Omega_m = 0.3111, Omega_L = 0.6889)
+# and initial redshift z = 49 (a = 0.02).
+TABLE1_GEOMETRY = dict(D_s=0.07, R_sim=0.5, omega_c=1.63973)
+TABLE1_OMEGA_M, TABLE1_OMEGA_L, TABLE1_A_INIT = 0.3111, 0.6889, 1.0 / 50.0
+
+
+def table1_load(n_out: int = 12, n_phi: int = 64, n_z: int = 64, seed: int = 6):
+    """The tessellated load in Table 1's geometry with comoving masses
+    (rho_bar = 3 Omega_m / (8 pi), G = H0 = L = 1) and the literal softening law
+    eps_i = 0.01 L (m_i / m_min)^(1/3). The defaults give N = 65,536: 4 core
+    rings and 12 outer rings of 64 x 64 cells."""
+    rho_bar = comoving_rho_bar(TABLE1_OMEGA_M)
+    d = compact_load(n_out, n_phi, n_z, seed, L=L_BOX, rho_bar=rho_bar, eps0=0.01 * L_BOX, **TABLE1_GEOMETRY)
+    d["rho_bar"] = rho_bar
+    return d

@@ -11,8 +11,17 @@ Each rank's rows are evaluated with the same per-i sum order as on one rank, so
 the sharded result equals the unsharded one bit for bit. This module holds the
 partition, the exchange and the rank reductions; they run with any
 torch.distributed backend (NCCL between GPUs, gloo on the host).
+
+Rank loss is detected on the host, between steps. A Heartbeat posts each step
+to a key-value store before the step's launches. A rank that crashed, hung or
+left posts nothing more, so the others raise RankLost before their next launch
+instead of entering a collective that would never complete. A process group
+created with a short timeout is the second line: a collective whose peer died
+ends with an error.
 """
 from __future__ import annotations
+
+import time
 
 import numpy as np
 
@@ -62,3 +71,61 @@ def sum_over_ranks(values, group=None, device=None) -> np.ndarray:
     t = torch.tensor(np.asarray(values, dtype=np.float64), device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.cpu().numpy()
+
+
+class RankLost(RuntimeError):
+    """A peer did not reach a step: `ranks` are the ranks that failed to post
+    `step` (crashed, hung or left)."""
+
+    def __init__(self, ranks, step: int):
+        super().__init__(f"rank(s) {list(ranks)} did not reach step {step}")
+        self.ranks = list(ranks)
+        self.step = int(step)
+
+
+class Heartbeat:
+    """Liveness of the ranks between steps, through a key-value store: a
+    torch.distributed store, or anything with set(key, value) and
+    check([key]) -> bool.
+
+    beat(step) posts this rank's step. It returns once every rank has posted
+    the same step. It raises RankLost naming the ranks that did not post it
+    within `timeout` seconds; a rank that called leave() is named at once. Call
+    beat before a step's launches, so that no kernel or collective is in flight
+    when a loss is found."""
+
+    def __init__(self, store, rank: int, world: int, timeout: float = 2.0, poll: float = 0.005,
+                 prefix: str = "heartbeat"):
+        if world < 1 or not (0 <= rank < world) or not timeout > 0:
+            raise ValueError("need 0 <= rank < world and timeout > 0")
+        self.store, self.rank, self.world = store, rank, world
+        self.timeout, self.poll, self.prefix = float(timeout), float(poll), prefix
+
+    def _key(self, step: int, r: int) -> str:
+        return f"{self.prefix}/step/{step}/{r}"
+
+    def _left(self, r: int) -> str:
+        return f"{self.prefix}/left/{r}"
+
+    def beat(self, step: int) -> None:
+        self.store.set(self._key(step, self.rank), b"1")
+        deadline = time.monotonic() + self.timeout
+        pending = [r for r in range(self.world) if r != self.rank]
+        while True:
+            pending = [r for r in pending if not self.store.check([self._key(step, r)])]
+            if not pending:
+                break
+            left = [r for r in pending if self.store.check([self._left(r)])]
+            if left:
+                raise RankLost(left, step)
+            if time.monotonic() >= deadline:
+                raise RankLost(pending, step)
+            time.sleep(self.poll)
+        # every rank has posted `step`, so none still waits on this rank's previous key
+        delete = getattr(self.store, "delete_key", None)
+        if delete is not None and step > 0:
+            delete(self._key(step - 1, self.rank))
+
+    def leave(self, step: int) -> None:
+        """Announce that this rank stops after `step` (call it between steps)."""
+        self.store.set(self._left(self.rank), str(int(step)).encode())

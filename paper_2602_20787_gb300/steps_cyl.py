@@ -11,8 +11,10 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import json
 import math
 import os
+import time
 
 import numpy as np
 
@@ -451,6 +453,41 @@ def steps_cyl_resume(path: str, device: int = 0, stream: int = 0):
     return ctx
 
 
+class StepLog:
+    """Per-step metrics as JSON lines appended to a file. Each line holds:
+    - step, t and a;
+    - wall_ms_per_step, the host wall time of the chunk's KDK steps and the
+      diagnostics read-back, per step;
+    - pair_images_per_s of the last force evaluation's pair kernel;
+    - P (sum m p), L_z, the kinetic energy and the total mass, as
+      steps_cyl_diagnostics returns them."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.fh = open(path, "a")
+
+    def write(self, step: int, diag, timing, wall_ms: float) -> dict:
+        images, pair_ms = timing
+        rec = {"step": int(step), "t": float(diag[6]), "a": float(diag[5]), "wall_ms_per_step": float(wall_ms),
+               "pair_images_per_s": float(images / (pair_ms * 1e-3)) if pair_ms > 0 else None,
+               "P": [float(x) for x in diag[0:3]], "L_z": float(diag[3]), "kinetic": float(diag[4]),
+               "mass": float(diag[7])}
+        self.fh.write(json.dumps(rec) + "\n")
+        self.fh.flush()
+        return rec
+
+    def close(self):
+        if self.fh:
+            self.fh.close()
+            self.fh = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Simulation:
     """Convenience owner of one context (numpy/torch arrays in, numpy out)."""
 
@@ -476,6 +513,24 @@ class Simulation:
 
     def step(self, dt: float, nsteps: int = 1):
         steps_cyl_kdk_step(self.ctx, dt, nsteps)
+
+    def run(self, dt: float, nsteps: int, log: str | None = None, every: int = 1):
+        """nsteps KDK steps of dt. With a log path, the steps run in chunks of
+        `every` and one JSON line per chunk is appended to the file (StepLog)."""
+        if log is None:
+            return self.step(dt, nsteps)
+        if every < 1:
+            raise ValueError("every must be >= 1")
+        with StepLog(log) as lg:
+            done = 0
+            while done < nsteps:
+                k = min(every, nsteps - done)
+                t0 = time.perf_counter()
+                self.step(dt, k)
+                diag = self.diagnostics()  # reads back to the host: the chunk has finished
+                wall_ms = (time.perf_counter() - t0) * 1e3 / k
+                done += k
+                lg.write(done, diag, self.last_timing(), wall_ms)
 
     def state(self):
         out = [np.zeros(self.n) for _ in range(6)]

@@ -17,6 +17,7 @@
 // set_state moves particles, and every reorder_every KDK steps.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -45,6 +46,15 @@ using namespace steps;
 namespace {
 
 thread_local std::string g_last_error;
+
+// A named host range around one phase of an evaluation or a step, for profilers
+// that record NVTX ranges; without one attached the calls do nothing.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -727,6 +737,7 @@ void tree_rotation(const double ax[3], double angle, double R[9]) {
 
 // Sort, build and moments of the tree in frame f.
 int tree_build(steps_cyl_ctx* c, const TreeDraw& f) {
+  Range range("steps_cyl.tree_build");
   auto& T = c->tr;
   int rc;
   if ((rc = tree_alloc(c))) return rc;
@@ -806,6 +817,7 @@ int tree_build(steps_cyl_ctx* c, const TreeDraw& f) {
 
 // The walk: pair sums [3][n] (internal order) into out.
 int tree_walk(steps_cyl_ctx* c, double* out) {
+  Range range("steps_cyl.tree_walk");
   auto& T = c->tr;
   TreeCrit C;
   const double S = 2.0 * std::max(c->p.L, 2.0 * c->p.R_sim);
@@ -922,6 +934,7 @@ Form force_form(const steps_cyl_ctx* c) {
 // One force evaluation at the current packed positions. Stores g = a^3 (pair +
 // background) in gx/gy/gz (internal order); kicks p by K when kick is set.
 int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
+  Range range("steps_cyl.forces");
   const double pair_scale = -c->p.G * c->invL * c->invL;
   c->forces_stale = false;
   if (is_tree(c)) {  // the octree: its own build and walk, then the common finalize
@@ -1050,6 +1063,7 @@ int validate_state(steps_cyl_ctx* c) {
 }
 
 int pack_positions(steps_cyl_ctx* c) {
+  Range range("steps_cyl.pack");
   pack_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(c->x, c->y, c->z, c->m, c->h, c->n, c->invL, c->jA, c->jB);
   CKLAUNCH("pack");
   return STEPS_OK;
@@ -1522,6 +1536,7 @@ int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999
 // float2 array and read through a texture with bilinear filtering (the
 // cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius.
 int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
+  Range range("steps_cyl.build_table");
   if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
   if (c->p.n0 < 1 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
     return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
@@ -1615,6 +1630,7 @@ int read_loss(cudaStream_t st, const float* lpart, int nblocks, float* dev_out, 
 }
 
 int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* report) {
+  Range range("steps_cyl.train_surrogate");
   const int64_t ns = cfg->n_samples;
   if (ns < 1024 || cfg->epochs < 1 || cfg->batch < 64 || cfg->batch % kTrainThreads != 0 || !(cfg->lr > 0) ||
       cfg->dR_max < 0 || cfg->reserved != 0 || cfg->check_particles < 1)
@@ -2023,6 +2039,7 @@ int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
   char reject_msg[160] = "";
   if (nsteps > 0 && c->forces_stale && (rc = eval_forces(c, false, 0.0))) return rc;
   for (int s = 0; s < nsteps; ++s) {
+    Range range("steps_cyl.kdk_step");
     const Factors f = kdk_factors(c->cosmo, c->a, dt);
     if (!std::isfinite(f.K1) || !std::isfinite(f.D) || !std::isfinite(f.a_next) || !(f.a_next > 0))
       return fail(STEPS_EINVAL, "the Friedmann integration left the valid range (a = %g)", f.a_next);

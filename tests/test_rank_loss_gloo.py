@@ -123,7 +123,7 @@ def test_rank_that_leaves_is_named_at_once(tmp_path):
     assert res[1] == {"left": 1}
     for r in (0, 2):
         assert res[r]["lost"] == [1] and res[r]["step"] == 2
-        assert res[r]["elapsed"] < 0.5 * HB_TIMEOUT
+        assert res[r]["elapsed"] < HB_TIMEOUT      # named by the leave() key, not by the timeout
 
 
 def test_collective_with_a_dead_peer_errors_instead_of_hanging(tmp_path):

@@ -152,3 +152,19 @@ def test_tail_sums_domain(lib, n_cut, n0):
     with pytest.raises(sc.StepsError) as e:
         sc.steps_cyl_tail_sums(smp, n_cut, n0)
     assert e.value.code == sc.STEPS_EINVAL
+
+
+def test_binding_checks_dtype_and_layout(lib):
+    n = 4
+    good = [np.linspace(0.1, 0.4, n), np.zeros(n), np.linspace(0.1, 0.7, n)] + [np.zeros(n)] * 3 + [np.ones(n)] * 2
+    bad_dtype = list(good)
+    bad_dtype[6] = np.ones(n, dtype=np.float32)
+    with pytest.raises(TypeError):
+        sc.steps_cyl_init(sc.Config(), n, *bad_dtype)
+    strided = list(good)
+    strided[0] = np.linspace(0.1, 0.8, 2 * n)[::2]
+    with pytest.raises(ValueError):
+        sc.steps_cyl_init(sc.Config(), n, *strided)
+    with pytest.raises(TypeError):
+        sc._ptr([1.0, 2.0])
+    assert sc._ptr(None) is None

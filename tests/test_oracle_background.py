@@ -2,6 +2,7 @@
 because the printed form is garbled) and of the homogeneous-load balance
 (Sect. 2.1: the net comoving force of a homogeneous load vanishes)."""
 import math
+import warnings
 
 import numpy as np
 import pytest
@@ -32,7 +33,13 @@ def field_point_polar(rho, R, Lw, G=1.0, rho0=1.0):
     if rho > R:
         a = math.asin(R / rho)
         pts = [math.pi - a, math.pi + a]
-    val, _ = integrate.quad(integrand, 0.0, 2 * math.pi, points=pts, epsabs=0, epsrel=1e-13, limit=400)
+    # Near the axis the integrand cancels over the circle (the field is O(rho)), and
+    # quad reports that roundoff keeps it from the requested 1e-13. The error it does
+    # reach is checked instead, well inside the 2e-11 that the pins compare to.
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", integrate.IntegrationWarning)
+        val, err = integrate.quad(integrand, 0.0, 2 * math.pi, points=pts, epsabs=0, epsrel=1e-13, limit=400)
+    assert err <= 5e-12 * abs(val)
     return 2.0 * G * rho0 * Lw * val
 
 

@@ -285,6 +285,12 @@ void or_background_sphere(int64_t ni, const double* x, const double* y, const do
   }
 }
 
+/* A field that could not be computed (out of memory) is NaN, which every
+ * comparison rejects. */
+static void or_fill_nan(int64_t n, double* gx, double* gy, double* gz) {
+  for (int64_t i = 0; i < n; ++i) gx[i] = gy[i] = gz[i] = NAN;
+}
+
 /* Total comoving field g = a^3 (pair + background) at the current positions. */
 static void or_total_field(int64_t n, const double* x, const double* y, const double* z,
                            const double* m, const double* h, double G, double L, int32_t n_cut,
@@ -294,6 +300,7 @@ static void or_total_field(int64_t n, const double* x, const double* y, const do
     or_pair_field_r3(n, x, y, z, m, h, G, n, NULL, gx, gy, gz);
     if (background != 3) return;
     double* b = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!b) { or_fill_nan(n, gx, gy, gz); return; }
     or_background_sphere(n, x, y, z, G, rho0, b, b + n, b + 2 * n);
     for (int64_t i = 0; i < n; ++i) { gx[i] += b[i]; gy[i] += b[n + i]; gz[i] += b[2 * n + i]; }
     free(b);
@@ -303,6 +310,7 @@ static void or_total_field(int64_t n, const double* x, const double* y, const do
   if (background == 0) return;
   double* bx = (double*)malloc(sizeof(double) * (size_t)n);
   double* by = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!bx || !by) { free(bx); free(by); or_fill_nan(n, gx, gy, gz); return; }
   if (background == 1) {
     or_background_field(n, x, y, R_bg, (double)n_cut * L, G, rho0, bx, by);
   } else {

@@ -109,6 +109,7 @@ def lib():
         L.or_tree_order.argtypes = [i64, p, p, p, d, d, d, d, p, p]
         L.or_tree_order.restype = ctypes.c_int
         L.or_tail_sums.argtypes = [d, d, d, d, i32, i32, p, p]; L.or_tail_sums.restype = None
+        L.or_diagnostics.argtypes = [i64, p, p, p, p, p, p, d, p]; L.or_diagnostics.restype = None
         L.or_mlp_forward.argtypes = [p, p, p]; L.or_mlp_forward.restype = None
         L.or_mlp_loss_grad.argtypes = [p, i64, p, p, p]; L.or_mlp_loss_grad.restype = d
         L.or_adam_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]; L.or_adam_step.restype = None
@@ -245,6 +246,17 @@ def kdk(pos, vel_p, m, h, G, L, n_cut, R_bg, rho0, background, c: Cosmo, a, t, d
     if rc != 0:
         raise MemoryError("oracle KDK allocation failed")
     return np.stack([x, y, z], 1), np.stack([px, py, pz], 1), a_.value, t_.value
+
+
+def diagnostics(pos, p, m, a):
+    """Sect. 1 conserved quantities of a state: (P[3] = sum m p, L_z = sum m (x p_y - y p_x),
+    kinetic energy sum m |dx/dt|^2 / 2 with dx/dt = p / a^2, total mass). p: canonical momenta."""
+    x, y = _f64(pos[:, 0]), _f64(pos[:, 1])
+    px, py, pz = (_f64(p[:, k]) for k in range(3))
+    m = _f64(m)
+    out = np.zeros(6)
+    lib().or_diagnostics(x.shape[0], _ptr(x), _ptr(y), _ptr(px), _ptr(py), _ptr(pz), _ptr(m), float(a), _ptr(out))
+    return out
 
 
 def tail_sums(dR, dzw, h, L, n_cut, n0):

@@ -367,6 +367,39 @@ int or_kdk(int64_t n, double* x, double* y, double* z, double* px, double* py, d
 }
 
 /* ---------------------------------------------------------------------------
+ * Diagnostics of a state (Sect. 1: in S1xR2 the axial momentum P_z and the
+ * angular momentum L_z about the axis are conserved, by invariance under
+ * translations along the axis and rotations about it). Given positions and
+ * canonical momenta p = a^2 dx/dt at expansion factor a, plain sums over the
+ * particles in index order with long double accumulators:
+ *   out[0..2] = sum m p,  out[3] = L_z = sum m (x p_y - y p_x),
+ *   out[4] = kinetic energy sum m |dx/dt|^2 / 2 = sum m |p|^2 / (2 a^4),
+ *   out[5] = total mass sum m.
+ * ------------------------------------------------------------------------- */
+void or_diagnostics(int64_t n, const double* x, const double* y, const double* px, const double* py,
+                    const double* pz, const double* m, double a, double out[6]) {
+  long double P0 = 0.0L, P1 = 0.0L, P2 = 0.0L, Lz = 0.0L, K = 0.0L, M = 0.0L;
+  for (int64_t i = 0; i < n; ++i) {
+    const long double mi = m[i];
+    P0 += mi * px[i];
+    P1 += mi * py[i];
+    P2 += mi * pz[i];
+    Lz += mi * ((long double)x[i] * py[i] - (long double)y[i] * px[i]);
+    const long double vx = (long double)px[i] / ((long double)a * a);
+    const long double vy = (long double)py[i] / ((long double)a * a);
+    const long double vz = (long double)pz[i] / ((long double)a * a);
+    K += 0.5L * mi * (vx * vx + vy * vy + vz * vz);
+    M += mi;
+  }
+  out[0] = (double)P0;
+  out[1] = (double)P1;
+  out[2] = (double)P2;
+  out[3] = (double)Lz;
+  out[4] = (double)K;
+  out[5] = (double)M;
+}
+
+/* ---------------------------------------------------------------------------
  * Far-image tail of eq. ForceCylindrical for the learned surrogate.
  * In the wrapped frame dzw in [-L/2, L/2) the window of eq. ForceCylindrical
  * is the set of offsets o_k = dzw + k L with |o_k| < Ncut L. The near set is

@@ -60,6 +60,10 @@ int or_kdk_topo(int64_t n, double* x, double* y, double* z, double* px, double* 
                 const double* m, const double* h, double G, double L, int32_t n_cut, double R_bg,
                 double rho0, int32_t background, int32_t topology, const or_cosmo* c, double* a, double* t,
                 double dt, int32_t nsteps);
+/* Sect. 1 diagnostics of a state at expansion factor a (p canonical, a^2 dx/dt):
+ * out = (sum m p [3], L_z = sum m (x p_y - y p_x), sum m |dx/dt|^2 / 2, sum m). */
+void or_diagnostics(int64_t n, const double* x, const double* y, const double* px, const double* py,
+                    const double* pz, const double* m, double a, double out[6]);
 void or_tail_sums(double dR, double dzw, double h, double L, int32_t n_cut, int32_t n0, double* SR,
                   double* Sz);
 void or_mlp_forward(const double* w, const double* u, double* y);

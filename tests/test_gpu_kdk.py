@@ -163,3 +163,42 @@ def test_checkpoint_resume_is_bit_identical(sc, tmp_path):
         sc.Simulation.resume(path)
     s1.close()
     s2.close()
+
+
+def test_diagnostics_match_oracle(sc):
+    # Sect. 1 diagnostics of a state on the oracle's own comoving trajectory:
+    # a context is given the oracle's state after a few KDK steps, and its
+    # diagnostics must equal the oracle's sums of that state; then a context
+    # stepped by the library from the start must reach the oracle's values to
+    # the KDK parity tolerance.
+    w = ics.WORKLOADS["lcdm_n65536"]
+    n, steps = 384, 6
+    d = ics.particle_load(n, 7, w.M_tot, displaced=True, rho_bar=w.rho_bar)
+    vel = np.random.default_rng(17).normal(0.0, 0.05, (n, 3))
+    t0, dt = ics.run_schedule(w)
+    c = oracle.make_cosmo()
+    xo, po, ao, to = oracle.kdk(d["pos"], vel * w.a_start ** 2, d["m"], d["h"], 1.0, 1.0, w.n_cut, ics.R_SIM,
+                                w.rho_bar, 1, c, w.a_start, t0, dt, steps)
+    do = oracle.diagnostics(xo, po, d["m"], ao)
+    pscale = np.sum(d["m"][:, None] * np.abs(po))
+    lscale = np.sum(d["m"] * np.hypot(xo[:, 0], xo[:, 1]) * np.linalg.norm(po, axis=1))
+
+    cfg = sc.Config(n_cut=w.n_cut, precision=0, comoving=True, a_start=ao, t_start=to, rho_bar=w.rho_bar)
+    held = sc.Simulation(cfg, xo, po / ao ** 2, d["m"], d["h"])
+    dg = held.diagnostics()
+    held.close()
+    assert dg[5] == ao and dg[6] == to
+    np.testing.assert_allclose(dg[0:3], do[0:3], rtol=0, atol=1e-12 * pscale)
+    assert abs(dg[3] - do[3]) <= 1e-12 * lscale
+    assert dg[4] == pytest.approx(do[4], rel=1e-12)
+    assert dg[7] == pytest.approx(do[5], rel=1e-14)
+
+    cfg = sc.Config(n_cut=w.n_cut, precision=0, comoving=True, a_start=w.a_start, t_start=t0, rho_bar=w.rho_bar)
+    sim = sc.Simulation(cfg, d["pos"], vel, d["m"], d["h"])
+    sim.step(dt, steps)
+    ds = sim.diagnostics()
+    sim.close()
+    np.testing.assert_allclose(ds[0:3], do[0:3], rtol=0, atol=1e-10 * pscale)
+    assert abs(ds[3] - do[3]) <= 1e-10 * lscale
+    assert ds[4] == pytest.approx(do[4], rel=1e-9)
+    assert ds[5] == pytest.approx(ao, rel=1e-14)

@@ -344,25 +344,30 @@ int steps_cyl_check_tail(steps_cyl_ctx* ctx, int32_t tail, int32_t check_particl
 int steps_cyl_check_surrogate(steps_cyl_ctx* ctx, int32_t check_particles, double* report);
 
 /* ---- allocation-free pair accelerations ----------------------------------
- * This entry point has no counterpart in the paper; it serves callers that may
+ * This entry point has no counterpart in the paper. It serves callers that may
  * not allocate device memory: a host whose device memory is owned and budgeted
  * by another allocator (a caching allocator or an arena reserved at start-up), a
  * loop that must not take cudaMalloc's implicit device-wide synchronisation, or
- * a plug-in that may allocate only while it initialises. It computes the pair
- * term of eq. ComovingEquationsOfMotionCylindrical in static space,
- *   a_i = G sum_{j != i} m_j F_S1R2(x_i - x_j, h_i + h_j),
- * i.e. what steps_cyl_forces returns for a context with STEPS_BG_OFF and a = 1,
- * with the same kernels, and calls no cudaMalloc, cudaFree or allocating library
- * routine. Its scratch (packed positions, work-split partial sums, error word)
- * is one file-scope device array of STEPS_NOALLOC_SCRATCH_BYTES bytes that every
- * device loading this library holds until the process exits.
+ * a plug-in that may allocate only while it initialises. Its result is what
+ * steps_cyl_forces returns for a context with background STEPS_BG_OFF in static
+ * space (a = 1), computed with the same kernels, and it calls no cudaMalloc,
+ * cudaFree or allocating library routine. Its scratch (packed positions and the
+ * work split's partial sums) is one file-scope device array of
+ * STEPS_NOALLOC_SCRATCH_BYTES bytes that every device loading this library
+ * holds until the process exits.
  *   - n: 2 <= n <= STEPS_NOALLOC_MAX_N, else STEPS_EINVAL (nothing is launched).
- *   - x, y, z, m, h (inputs) and ax, ay, az (outputs): device memory of the
- *     calling thread's current device, length n, doubles; z in [0, L); m, h > 0.
+ *   - x, y, z, m, h (inputs) and ax, ay, az (outputs): device (or managed)
+ *     memory of the calling thread's current device, n doubles each; z in
+ *     [0, L); m, h > 0. A host pointer, pinned or not, or another device's
+ *     memory gives STEPS_EINVAL before anything is launched (checked with
+ *     cudaPointerGetAttributes; the lengths cannot be checked here).
  *   - precision: STEPS_FP32_KAHAN or STEPS_FP32_PLAIN; n_cut in [1, 4096];
  *     G, L > 0. stream: cudaStream_t to enqueue on (NULL = legacy default).
- *   - The call returns once the work is enqueued; non-finite results are not
- *     reported (check the outputs).
+ *   - The call returns once the work is enqueued and never synchronises, so it
+ *     keeps no device error word: non-finite results are not reported (check
+ *     the outputs). STEPS_ECUDA when a runtime call or a launch of this call
+ *     fails; an error left pending by the caller's earlier work is neither
+ *     cleared nor reported as this call's.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
  *     before any stream capture.
@@ -371,7 +376,7 @@ int steps_cyl_check_surrogate(steps_cyl_ctx* ctx, int32_t check_particles, doubl
  *     results, so serialise them. */
 #define STEPS_NOALLOC_MAX_N 65536
 #define STEPS_NOALLOC_MAX_CTAS 2048
-#define STEPS_NOALLOC_SCRATCH_BYTES 9961728
+#define STEPS_NOALLOC_SCRATCH_BYTES 9961472
 int steps_cyl_pair_accel_noalloc(int64_t n, const double* x, const double* y, const double* z,
                                  const double* m, const double* h, double G, double L,
                                  int32_t n_cut, int32_t precision, double* ax, double* ay,

@@ -154,7 +154,7 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
   double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
   radial_correct(rc, x[i], y[i], z[i], g0, g1, g2);
   add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
-  if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(err, kErrNonFinite);
+  if (err && (!isfinite(g0) || !isfinite(g1) || !isfinite(g2))) atomicOr(err, kErrNonFinite);
   gx[i] = g0; gy[i] = g1; gz[i] = g2;
   if (px) {
     px[i] += g0 * K;

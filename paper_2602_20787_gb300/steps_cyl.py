@@ -285,12 +285,25 @@ def steps_cyl_free(ctx):
 
 
 def steps_cyl_pair_accel_noalloc(x, y, z, m, h, G, L, n_cut, precision, ax, ay, az, stream=0):
-    """Pair accelerations with no device allocation (CUDA float64 tensors of the
-    current device; outputs written in place). For callers that may not allocate
-    device memory: see include/steps_cyl.h for the contract, its scratch limit
-    and why concurrent calls must be serialised."""
-    _check_f64(x, y, z, m, h, ax, ay, az)
-    n = int(x.numel() if hasattr(x, "numel") else len(x))
+    """Pair accelerations with no device allocation, for callers that may not
+    allocate device memory (see include/steps_cyl.h for the contract, its
+    scratch limit and why concurrent calls must be serialised). Every array is a
+    contiguous float64 CUDA tensor of the current device with the same length n;
+    the outputs ax, ay, az are written in place. Anything else raises before the
+    library is called."""
+    import torch
+    arrs = (x, y, z, m, h, ax, ay, az)
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for a in arrs:
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise StepsError(STEPS_EINVAL, "every array must be a CUDA tensor")
+        if a.device.index != dev:
+            raise StepsError(STEPS_EINVAL, f"arrays must live on the current device cuda:{dev}")
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise StepsError(STEPS_EINVAL, "arrays must be contiguous float64")
+    n = int(x.numel())
+    if any(int(a.numel()) != n for a in arrs):
+        raise StepsError(STEPS_EINVAL, "all eight arrays must have the same length")
     if n > STEPS_NOALLOC_MAX_N:
         raise StepsError(STEPS_EINVAL, f"n = {n} exceeds STEPS_NOALLOC_MAX_N = {STEPS_NOALLOC_MAX_N}")
     rc = load().steps_cyl_pair_accel_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L),

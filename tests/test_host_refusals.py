@@ -168,3 +168,13 @@ def test_binding_checks_dtype_and_layout(lib):
     with pytest.raises(TypeError):
         sc._ptr([1.0, 2.0])
     assert sc._ptr(None) is None
+
+
+def test_noalloc_binding_refuses_host_arrays_before_the_library():
+    # the allocation-free entry point takes device memory only; the binding
+    # refuses numpy arrays (host memory) before it calls the library
+    pytest.importorskip("torch")
+    x = np.zeros(16)
+    with pytest.raises(sc.StepsError) as e:
+        sc.steps_cyl_pair_accel_noalloc(x, x, x, x, x, 1.0, 1.0, 4, sc.STEPS_FP32_KAHAN, x, x, x)
+    assert e.value.code == sc.STEPS_EINVAL

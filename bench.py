@@ -1,15 +1,21 @@
 """Benchmark of the S1xR2 StePS hot path on GB300.
 
 One step = one comoving KDK step (kick, drift + z wrap + repack, pair-force
-kernel over every pair and 2 Ncut images, background, kick) of the LCDM
-workload: N = 65,536 particles, Ncut = 16, FP32 pair math with Kahan-compensated
-sums on FP64 positions/momenta, a from 0.02 upward (the configuration the
-pair-interactions/s metric is quoted on). The metric is pair-images per second
-(images counted, N (N-1) 2 Ncut per step) over the whole job.
+kernel over every pair, background, kick) of the production-shaped workload:
+N = 524,288 particles, Ncut = 64 (128 images per pair), softening ratio 1:8,
+LCDM from a = 0.02, positions and momenta in FP64. The headline form is the
+learned far-image tail: the near images |k| <= 4 summed exactly in FP32 with
+Kahan-compensated sums, the tail beyond them from the network (trained on the
+GPU first, accepted only within its error bound, re-checked against the plain
+sum every 50 steps). The metric is equivalent pair-images per second: N (N-1)
+128 per step, the work of the plain window sum the form stands in for, over
+the whole job. The same line carries the plain FP32-Kahan 128-image sum timed
+on the same run, both forms' errors against FP64, and the speedup.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank advances its own independent cylinder
-(weak scaling, no collective on the data path).
+       python bench.py --workload NAME   (the other workloads, one JSON line each)
+Under torchrun (N > 1) the ranks share one cylinder (strong scaling): each owns
+a contiguous range of rows, and each step all-gathers the packed rows once.
 
 --impl reference times the FP64 CPU oracle (the deliberately plain reference of
 this project) on a bounded sample of the same workload on the host cores.
@@ -33,7 +39,9 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "lcdm_n65536"
+WORKLOAD = "production_n524288"
+CHECK_EVERY = 50     # the plain sum re-checks the learned tail every 50 KDK steps
+REORDER_EVERY = 32   # the library's default Morton re-order interval
 METRIC = "pair-interactions/s (images counted)"
 UNIT = "pair-images/s"
 MUFU_RSQRT_PER_SM_CLK = 16  # MUFU rsqrt lanes per SM per clock, measured on GB300 (one rsqrt per pair-image)
@@ -103,21 +111,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
-    """The pair kernel's source and its launch shape (the stream-K CTA multiplier)."""
+PROFILED = {  # the committed ncu summary of each timed kernel, and the sources that define it
+    "plain": ("pair_fp32_kahan_lcdm_n65536.md", ["pair_fp32.cuh"]),
+    "surrogate": ("pair_fp32_surr_kahan_surrogate_n65536.md", ["pair_fp32.cuh", "surrogate_pair.cuh"]),
+}
+
+
+def kernel_source_hash(kind: str = "plain") -> str:
+    """A pair kernel's sources and its launch shape (the stream-K CTA multiplier)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_20787_gb300", "csrc")
-    with open(os.path.join(csrc, "pair_fp32.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for f in PROFILED[kind][1]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(csrc, "steps_cyl.cu")) as fh:
         h.update("".join(ln for ln in fh if ln.startswith("#define STEPS_CTA_MULT")).encode())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(kind: str = "plain"):
     """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "pair_fp32_kahan_lcdm_n65536.md")
+    path = os.path.join(ROOT, "profiles", PROFILED[kind][0])
     if not os.path.exists(path):
         return None
     src_hash, traffic = None, None
@@ -130,7 +145,7 @@ def recorded_traffic():
                     traffic = float(ln.split(":", 1)[1].strip())
                 except ValueError:
                     traffic = None
-    if src_hash != kernel_source_hash():
+    if src_hash != kernel_source_hash(kind):
         return None
     return traffic
 
@@ -210,13 +225,165 @@ def run_reference(args, rank, world):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "n_cut": w.n_cut, "i_sample_per_step": k},
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (FP64 oracle, plain window sum)", "n": n, "n_cut": w.n_cut,
+                   "i_sample_per_step": k},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def measured_peaks():
+    """The measured peaks of the GB300s (MEASURED_PEAKS.json), or None."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def surrogate_roofline(n_sm, sm_mhz, n0, pairs, kernel_s):
+    """Roofline of the learned-tail pair kernel per pair (one i, one j):
+    - MUFU: 2 n0 + 1 near-image rsqrt, 4 rsqrt + 2 rcp of the two-sided
+      continuum base and 1 rsqrt of dR, at 16 MUFU ops/SM/clk;
+    - tensor: the network's own 2 (3 x 32 + 32 x 32 + 32 x 2) = 2368 flops at
+      the measured sustained dense f16/bf16 rate (the kernel runs inside a
+      seconds-long step).
+    The larger time per pair binds."""
+    mufu_ops = (2 * n0 + 1) + 4 + 2 + 1
+    mlp_flops = 2 * (3 * 32 + 32 * 32 + 32 * 2)
+    pk = measured_peaks()
+    if pk and pk.get("bf16_tflops_sustained"):
+        tensor_flops, tensor_src = pk["bf16_tflops_sustained"] * 1e12, "of measured (bf16 sustained, same rate as f16)"
+    else:
+        tensor_flops, tensor_src = 1.7e15, "of fallback (sustained bf16)"
+    mufu_pairs = n_sm * sm_mhz * 1e6 * MUFU_RSQRT_PER_SM_CLK / mufu_ops
+    tensor_pairs = tensor_flops / mlp_flops
+    peak = min(mufu_pairs, tensor_pairs)
+    achieved = pairs / kernel_s
+    return {"bound": "alu" if mufu_pairs <= tensor_pairs else "tensor", "achieved": achieved, "peak": peak,
+            "unit": "pair interactions/s", "frac": achieved / peak, "traffic": recorded_traffic("surrogate"),
+            "peak_basis": f"min(MUFU: {n_sm} SMs x {MUFU_RSQRT_PER_SM_CLK}/SM/clk x {sm_mhz:.0f} MHz / {mufu_ops} "
+                          f"ops per pair = {mufu_pairs:.3e}; tensor: {tensor_flops:.3e} flop/s {tensor_src} / "
+                          f"{mlp_flops} network flops per pair = {tensor_pairs:.3e})"}
+
+
+def force_errors(sim, sc, idx, forms):
+    """Relative force errors of the FP32 forms against the library's FP64 form
+    (which the test-suite pins to the FP64 oracle at <= 1.4e-13) on the sampled
+    particles, all at the same state. forms: {name: tail}."""
+    out = {}
+    for name, tail in forms.items():
+        sc.steps_cyl_set_tail(sim.ctx, tail)
+        out[name] = sim.forces_subset(idx)
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)
+    a64 = sim.forces_subset(idx)
+    sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP32_KAHAN)
+    return {k: _err(v, a64) for k, v in out.items()}
+
+
+def run_sharded(args, rank, world, local):
+    """N > 1 GPUs: one cylinder of the headline workload strong-scaled across
+    the ranks. Every rank builds the same context from the same load, trains
+    the same network (deterministic), and then owns a contiguous range of rows
+    (steps_cyl_shard); each KDK step is drift, one NCCL all-gather of the packed
+    rows, kick (shard.ShardedSimulation). value = the whole cylinder's
+    equivalent pair-images per second over the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    from paper_2602_20787_gb300 import ics, shard, steps_cyl as sc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    w = ics.WORKLOADS[WORKLOAD]
+    d = ics.workload_ics(w)
+    n = w.n
+    t0, dt = ics.run_schedule(w)
+    cfg = sc.Config(n_cut=w.n_cut, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_FULL,
+                    background=sc.STEPS_BG_FINITE, comoving=True, a_start=w.a_start, t_start=t0, rho_bar=w.rho_bar,
+                    check_particles=1024, device=local, stream=stream.cuda_stream)
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    try:
+        sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
+        accepted = True
+    except sc.StepsError as e:
+        if e.code != sc.STEPS_ESURROGATE_REJECTED:
+            raise
+        accepted = False
+    tail = sc.STEPS_TAIL_SURROGATE if accepted else sc.STEPS_TAIL_FULL
+    sc.steps_cyl_set_tail(sim.ctx, tail)
+    rows = shard.GpuRows(sim, rank, world)
+    ssim = shard.ShardedSimulation(rows, tail=tail if accepted else 0, check_every=CHECK_EVERY)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    ssim.step(dt, args.warmup)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    if rank == 0:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_ms = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        ssim.step(dt, 1)
+        ev[s][1].record(stream)
+        pair_ms.append(sc.steps_cyl_last_timing(sim.ctx)[1])
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    t_local = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_max = shard.max_over_ranks(t_local, device=dev)
+    kernel_max = shard.max_over_ranks(statistics.mean(pair_ms) / 1e3, device=dev)
+    pairs = n * (n - 1.0)
+    images_per_step = pairs * 2.0 * w.n_cut
+    value = images_per_step * args.steps / t_max
+
+    # end to end through the public API: per step the sharded KDK step and the
+    # whole cylinder's diagnostics read back to the host (inputs stay resident;
+    # the only per-step traffic is the device-side all-gather)
+    te0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ssim.step(dt, 1)
+        ssim.diagnostics()
+    torch.cuda.synchronize(dev)
+    te = shard.max_over_ranks(time.perf_counter() - te0, device=dev)
+    diag = ssim.diagnostics()
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        sm_mhz = clk["sm_max_mhz"] or 2070.0
+        roof = surrogate_roofline(props.multi_processor_count, sm_mhz, w.n0, rows.chunk * (n - 1.0), kernel_max)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + (" (learned tail, n0 = 4)" if accepted else
+                                               " (plain sum: network rejected)"),
+                       "n": n, "n_cut": w.n_cut, "n0": w.n0, "parallelism": f"row shards x {world}",
+                       "exchange": "one NCCL all-gather of the packed rows (32 B per particle) per step",
+                       "rows_per_rank": rows.chunk, "a_after": float(diag[6]),
+                       "l2": "256 MiB buffer written between timed steps (inputs 16 MB < L2)"},
+            "kdk_step_ms": 1e3 * t_max / args.steps,
+            "pair_kernel_ms": 1e3 * kernel_max,
+            "roofline": roof,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "e2e": {"value": images_per_step * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 8 * 8 * world, "steps": args.e2e_steps} if args.e2e_steps > 0 else None,
+            "gpu_launches": 5 * args.steps * world,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    sim.close()
+    dist.destroy_process_group()
     return 0
 
 
@@ -226,78 +393,99 @@ def run(args):
     local = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if world > 1:
+        return run_sharded(args, rank, world, local)
 
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_mod
-        dist = dist_mod
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    w = ics.WORKLOADS[WORKLOAD]
-    # each rank an independent cylinder (different seed), same law and size
-    d = ics.particle_load(w.n, w.seed + 1000 * rank, w.M_tot, displaced=True, rho_bar=w.rho_bar,
-                          filament_frac=w.filament_frac, eps_law=w.eps_law)
-    t0, dt = ics.run_schedule(w)
     stream = torch.cuda.current_stream(dev)
-    cfg = sc.Config(n_cut=w.n_cut, precision=sc.STEPS_FP32_KAHAN, background=sc.STEPS_BG_FINITE, comoving=True,
-                    a_start=w.a_start, t_start=t0, rho_bar=w.rho_bar, device=local, stream=stream.cuda_stream)
+    w = ics.WORKLOADS[WORKLOAD]
+    d = ics.workload_ics(w)
     n = w.n
-    cols = [torch.tensor(np.ascontiguousarray(d["pos"][:, k]), device=dev) for k in range(3)]
-    vel = [torch.zeros(n, dtype=torch.float64, device=dev) for _ in range(3)]
-    m_t = torch.tensor(d["m"], device=dev)
-    h_t = torch.tensor(d["h"], device=dev)
-    ctx = sc.steps_cyl_init(cfg, n, *cols, *vel, m_t, h_t)
+    t0, dt = ics.run_schedule(w)
+    cfg = sc.Config(n_cut=w.n_cut, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_FULL,
+                    background=sc.STEPS_BG_FINITE, comoving=True, a_start=w.a_start, t_start=t0, rho_bar=w.rho_bar,
+                    check_every=CHECK_EVERY, check_particles=1024, device=local, stream=stream.cuda_stream)
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    ctx = sim.ctx
+
+    # the learned tail: trained by the library's own GPU kernels on its FP64 tail
+    # sums, then accepted only if it meets the error bound against the plain sum
+    tr0 = time.perf_counter()
+    try:
+        rep = sc.steps_cyl_train_surrogate(ctx, sc.steps_cyl_train_cfg_default())
+        accepted = True
+    except sc.StepsError as e:
+        if e.code != sc.STEPS_ESURROGATE_REJECTED:
+            raise
+        rep, accepted = e.report, False
+    train_wall_s = time.perf_counter() - tr0
+    sc.steps_cyl_set_tail(ctx, sc.STEPS_TAIL_SURROGATE if accepted else sc.STEPS_TAIL_FULL)
 
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    def timed_steps(k):
+        """k KDK steps, each bracketed by CUDA events on the context stream with
+        an L2 flush between them; returns (per-step ms, pair-kernel ms)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        pair = []
+        for s in range(k):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            sc.steps_cyl_kdk_step(ctx, dt, 1)  # synchronises to read the device error word
+            ev[s][1].record(stream)
+            pair.append(sc.steps_cyl_last_timing(ctx)[1])
         torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in ev], pair
 
     for _ in range(args.warmup):
         sc.steps_cyl_kdk_step(ctx, dt, 1)
-    barrier()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pair_ms = []
+    torch.cuda.synchronize(dev)
+    steps_before = args.warmup
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     clocks.start()
-    barrier()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        ev[s][0].record(stream)
-        sc.steps_cyl_kdk_step(ctx, dt, 1)  # synchronises to read the device error word
-        ev[s][1].record(stream)
-        pair_ms.append(sc.steps_cyl_last_timing(ctx)[1])
+    step_ms, pair_ms = timed_steps(args.steps)
     g1.record(stream)
-    barrier()
+    torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     region_ms = g0.elapsed_time(g1)
-    t_local = sum(step_ms) / 1e3
-    t_max = t_local
-    if dist is not None:
-        from paper_2602_20787_gb300 import shard
-        t_max = shard.max_over_ranks(t_local, device=dev)
-    images_per_step = n * (n - 1) * 2.0 * w.n_cut
-    value = images_per_step * args.steps * world / t_max
-
-    # roofline of the dominant kernel (the pair kernel): one MUFU rsqrt per pair-image
+    t_steps = sum(step_ms) / 1e3
+    pairs = n * (n - 1.0)
+    images_per_step = pairs * 2.0 * w.n_cut   # the window's equivalent images
+    value = images_per_step * args.steps / t_steps
+    kernel_s = statistics.mean(pair_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
-    sm_max = clk["sm_max_mhz"] or 2070.0
-    peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_max * 1e6
-    pair_avg_s = statistics.mean(pair_ms) / 1e3
-    achieved = images_per_step / pair_avg_s
+    sm_mhz = clk["sm_max_mhz"] or 2070.0
+    roof = surrogate_roofline(props.multi_processor_count, sm_mhz, w.n0, pairs, kernel_s)
+    if not accepted:  # the plain sum ran: its own roofline
+        peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_mhz * 1e6
+        roof = {"bound": "alu", "achieved": images_per_step / kernel_s, "peak": peak, "unit": UNIT,
+                "frac": images_per_step / kernel_s / peak, "traffic": None}
+    # reorders and surrogate checks that fell in the timed region add launches
+    timed = range(steps_before + 1, steps_before + args.steps + 1)
+    reorders = sum(1 for s in timed if s % REORDER_EVERY == 0)
+    checks = sum(1 for s in timed if s % CHECK_EVERY == 0) if accepted else 0
+    launches = 3 * args.steps + 12 * reorders + 6 * checks
+    steps_before += args.steps
+
+    # the plain FP32-Kahan image sum on the same run, for the speedup
+    plain_steps = max(2, args.steps // 5)
+    sc.steps_cyl_set_tail(ctx, sc.STEPS_TAIL_FULL)
+    sc.steps_cyl_kdk_step(ctx, dt, 1)
+    plain_ms, plain_pair_ms = timed_steps(plain_steps)
+    steps_before += 1 + plain_steps
+    plain_kernel_s = statistics.mean(plain_pair_ms) / 1e3
+    plain_step_s = statistics.mean(plain_ms) / 1e3
+    peak_plain = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_mhz * 1e6
+    sc.steps_cyl_set_tail(ctx, sc.STEPS_TAIL_SURROGATE if accepted else sc.STEPS_TAIL_FULL)
+    sc.steps_cyl_kdk_step(ctx, dt, 1)  # the switch marks the forces stale: refresh them untimed
 
     # end to end through the public API with pinned host buffers: per step the
     # state goes host -> device (set_state), one KDK step runs, the state comes back
@@ -306,7 +494,6 @@ def run(args):
         host = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(6)]
         sc.steps_cyl_get_state(ctx, *host)
         torch.cuda.synchronize(dev)
-        barrier()
         te0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             sc.steps_cyl_set_state(ctx, *host)
@@ -314,44 +501,53 @@ def run(args):
             sc.steps_cyl_get_state(ctx, *host)
         torch.cuda.synchronize(dev)
         te = time.perf_counter() - te0
-        if dist is not None:
-            from paper_2602_20787_gb300 import shard
-            te = shard.max_over_ranks(te, device=dev)
-        e2e = {"value": images_per_step * args.e2e_steps * world / te, "unit": UNIT,
-               "h2d_bytes_per_step": 6 * 8 * n, "d2h_bytes_per_step": 6 * 8 * n, "steps": args.e2e_steps}
+        e2e = {"value": images_per_step * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
+               "d2h_bytes_per_step": 6 * 8 * n, "steps": args.e2e_steps}
 
-    diag = sc.steps_cyl_diagnostics(ctx)
-    sc.steps_cyl_free(ctx)
+    # force errors of both forms against FP64 at the same state, on the seeded sample
+    idx = ics.subsample(n, 4096, seed=12345)
+    forms = {"surrogate": sc.STEPS_TAIL_SURROGATE, "plain": sc.STEPS_TAIL_FULL} if accepted else \
+        {"plain": sc.STEPS_TAIL_FULL}
+    errs = force_errors(sim, sc, idx, forms)
+    diag = sim.diagnostics()
+    sim.close()
 
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(w, d)
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "n_cut": w.n_cut, "images_per_pair": 2 * w.n_cut,
-                       "precision": "fp32 pair math, Kahan j-sum, fp64 state", "background": "finite cylinder",
-                       "cosmology": "LCDM 0.3/0.7", "a_after": diag[5],
-                       "l2": "256 MiB buffer written between timed steps (inputs 4 MB < L2)",
-                       "per_rank": "independent cylinder per rank" if world > 1 else None,
-                       "timed_region_ms": region_ms},
-            "kdk_step_ms": 1e3 * t_max / args.steps,
-            "pair_kernel_ms": 1e3 * pair_avg_s,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
-                         "frac": achieved / peak, "traffic": recorded_traffic(),
-                         "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_RSQRT_PER_SM_CLK} MUFU rsqrt/SM/clk "
-                                       f"x {sm_max:.0f} MHz (max SM clock); 1 rsqrt per pair-image"},
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-            "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    cpu = None if args.no_cpu_baseline else cpu_baseline(w, d)
+    ms_step = 1e3 * t_steps / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + (" (learned tail, n0 = 4)" if accepted else " (plain sum: network rejected)"),
+                   "n": n, "n_cut": w.n_cut, "n0": w.n0, "images_per_pair_equivalent": 2 * w.n_cut,
+                   "executed_near_images_per_pair": 2 * w.n0 + 1 if accepted else 2 * w.n_cut,
+                   "form": "learned far-image tail + FP32-Kahan near images" if accepted else "plain FP32-Kahan",
+                   "precision": "fp32 pair math, Kahan j-sum, fp64 state", "softening": "1:8 ratio law",
+                   "background": "finite cylinder", "cosmology": "LCDM 0.3/0.7", "a_after": diag[5],
+                   "check_every": CHECK_EVERY,
+                   "l2": "256 MiB buffer written between timed steps (inputs 16 MB < L2)",
+                   "timed_region_ms": region_ms},
+        "kdk_step_ms": ms_step,
+        "pair_kernel_ms": 1e3 * kernel_s,
+        "surrogate": {"accepted": accepted, "train_ms": float(rep[5]), "train_wall_s": train_wall_s,
+                      "check_vs_plain_median": float(rep[2]), "check_vs_plain_p999": float(rep[3]),
+                      "error_vs_fp64": errs.get("surrogate"),
+                      "speedup_vs_plain_kdk_step": plain_step_s / (ms_step / 1e3),
+                      "speedup_vs_plain_pair_kernel": plain_kernel_s / kernel_s},
+        "plain": {"steps": plain_steps, "kdk_step_ms": 1e3 * plain_step_s, "pair_kernel_ms": 1e3 * plain_kernel_s,
+                  "pair_images_per_s": images_per_step / plain_step_s,
+                  "error_vs_fp64": errs["plain"],
+                  "roofline": {"bound": "alu", "achieved": images_per_step / plain_kernel_s, "peak": peak_plain,
+                               "unit": UNIT, "frac": images_per_step / plain_kernel_s / peak_plain,
+                               "traffic": None}},
+        "error_reference": "library FP64 form on 4096 particles (seed 12345), pinned to the FP64 oracle in the tests",
+        "roofline": roof,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 

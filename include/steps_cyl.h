@@ -168,6 +168,58 @@ int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
  * its pair kernel in milliseconds (CUDA events on the context stream). */
 int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
 
+/* ---- row sharding (one rank per GPU) ---------------------------------------
+ * Sect. 2.4 runs the direct force on many GPUs with MPI. Here the rows i of the
+ * pair sum are split across ranks: each rank's context holds the whole particle
+ * set, evaluates the pair force of its own rows against every j, and kicks and
+ * drifts only those rows. The one exchange per step is an all-gather of the
+ * packed positions of every rank's rows, made by the caller (NCCL, gloo, ...)
+ * between steps_cyl_shard_drift and steps_cyl_shard_kick.
+ *
+ * steps_cyl_shard makes a context (created by steps_cyl_init from the same full
+ * state on every rank, with the same parameters) the shard `rank` of `world`.
+ * The internal particle order, which every rank computed identically at init,
+ * is frozen from then on. The rows are split into world balanced contiguous
+ * ranges of 128-row blocks (world <= ceil(n / 128)). rows (3 int64, host)
+ * receives the owned internal range [k0, k1) and chunk, the largest share: an
+ * exchange buffer holds chunk rows of 8 floats (32 bytes) per rank.
+ * Afterwards:
+ *   - steps_cyl_forces, steps_cyl_get_state and steps_cyl_diagnostics cover the
+ *     owned rows only: outputs in caller order hold zeros for the other rows
+ *     (so a sum over ranks assembles the whole), and diagnostics sum the owned
+ *     rows (sum them over ranks; out[5], out[6] are a and t);
+ *   - steps_cyl_kdk_step, steps_cyl_forces_subset, steps_cyl_set_state,
+ *     steps_cyl_checkpoint, steps_cyl_train_surrogate, steps_cyl_set_surrogate
+ *     and steps_cyl_build_tail_table give STEPS_EINVAL: train or install a
+ *     modelled tail before sharding; steps_cyl_set_tail and
+ *     steps_cyl_set_precision still switch forms;
+ *   - steps_cyl_check_surrogate checks a sample of the owned rows, and the
+ *     periodic checks of steps_cyl_kdk_step do not run: the caller combines
+ *     the ranks' checks (e.g. the largest error) and switches every rank alike.
+ * STEPS_EINVAL for a context sharded already, an octree context, the FP64
+ * precision (its kernel reads the FP64 positions of every j, and only the
+ * packed FP32 words are exchanged; steps_cyl_set_precision refuses it later
+ * too), or a bad rank/world; STEPS_ENOMEM/ECUDA leave the context whole and
+ * unsharded. */
+int steps_cyl_shard(steps_cyl_ctx* ctx, int32_t rank, int32_t world, int64_t* rows);
+
+/* First half of a sharded KDK step of dt (the order of steps_cyl_kdk_step): the
+ * kick and drift factors of the Friedmann integration, then on the owned rows
+ * p += g K1, x += p D, z wrapped into [0, L), the FP32 positions repacked. The
+ * owned packed rows are written to send (device memory of the context's
+ * device, 16-byte aligned, chunk x 8 floats; rows past the share are zeros).
+ * The caller then gathers every rank's send buffer, in rank order, into one
+ * buffer of world x chunk x 8 floats. Stream-ordered; returns without waiting. */
+int steps_cyl_shard_drift(steps_cyl_ctx* ctx, double dt, float* send);
+
+/* Second half of the step: the gathered packed rows of every rank (recv,
+ * device memory, 16-byte aligned, world x chunk x 8 floats, rank order) become
+ * the j-set; the pair force of the owned rows against all n particles, the
+ * background and the second kick p += g K2 follow, and a and t advance.
+ * STEPS_EINVAL unless steps_cyl_shard_drift came first. Synchronises the stream
+ * to read the device error word (STEPS_EDEVICE). */
+int steps_cyl_shard_kick(steps_cyl_ctx* ctx, const float* recv);
+
 /* ---- learned far-image surrogate ------------------------------------------
  * The paper sums every image of the window (eq. ForceCylindrical). The
  * surrogate tail form (STEPS_TAIL_SURROGATE) sums the near images |k| <= n0

@@ -131,17 +131,20 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
                                 double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
                                 double inv_a3, double* __restrict__ ox, double* __restrict__ oy,
                                 double* __restrict__ oz, int* __restrict__ err,
-                                RadialCorr rc = RadialCorr{nullptr, 0, 0.0, 0}) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+                                RadialCorr rc = RadialCorr{nullptr, 0, 0.0, 0}, int i0 = 0) {
+  // rows [i0, n), i0 a multiple of kBI (all rows unless they are sharded); the
+  // partials and direct sums are indexed from i0
+  const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double sx = 0.0, sy = 0.0, sz = 0.0;
   if (NT == 0) {
-    // direct sums (FP64 pair kernel): part = [3][n]
-    sx = part[i];
-    sy = part[(long long)n + i];
-    sz = part[2 * (long long)n + i];
+    // direct sums (FP64 pair kernel): part = [3][n - i0]
+    const long long q = i - i0, m = n - i0;
+    sx = part[q];
+    sy = part[m + q];
+    sz = part[2 * m + q];
   } else {
-    const int b = i / kBI, l = i % kBI;
+    const int b = (i - i0) / kBI, l = (i - i0) % kBI;
     const long long p_lo = (long long)b * NT, p_hi = p_lo + NT - 1;
     const int c_lo = cta_of_unit(p_lo, U, C), c_hi = cta_of_unit(p_hi, U, C);
     for (int c = c_lo; c <= c_hi; ++c) {
@@ -368,6 +371,35 @@ static __global__ void subset_finalize_kernel(const double* __restrict__ pairsum
   ox[q] = g0 * inv_a3;
   oy[q] = g1 * inv_a3;
   oz[q] = g2 * inv_a3;
+}
+
+// ---------------------------------------------------------------------------
+// Row sharding (Sect. 2.4's distributed direct engine, one rank per GPU). Each
+// rank owns a contiguous range of internal rows; the only exchange of a step is
+// the packed positions of every rank's rows, gathered between the drift and the
+// force evaluation.
+// The owned packed rows [k0, k0 + rows) -> send[chunk][2] = (jA, jB) per row,
+// zero rows past the share, so every rank sends chunk rows.
+static __global__ void shard_send_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int k0,
+                                         int rows, int chunk, float4* __restrict__ send) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < chunk; q += gridDim.x * blockDim.x) {
+    const bool own = q < rows;
+    send[2 * q] = own ? jA[k0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    send[2 * q + 1] = own ? jB[k0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// The gathered recv[world][chunk][2] -> the packed arrays: rank r's rows are
+// [off[r], off[r + 1]) (blockIdx.y = r).
+static __global__ void shard_recv_kernel(const float4* __restrict__ recv, const int* __restrict__ off, int chunk,
+                                         float4* __restrict__ jA, float4* __restrict__ jB) {
+  const int r = blockIdx.y;
+  const int o = off[r], rows = off[r + 1] - o;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rows; q += gridDim.x * blockDim.x) {
+    const long long src = 2 * ((long long)r * chunk + q);
+    jA[o + q] = recv[src];
+    jB[o + q] = recv[src + 1];
+  }
 }
 
 }  // namespace steps

@@ -375,11 +375,13 @@ __device__ __forceinline__ void pair_tile_fp32(const IParticle& I, const float4*
   }
 }
 
-// part layout: [slot][3][kBI] doubles, slot = i-block + CTA.
+// part layout: [slot][3][kBI] doubles, slot = i-block + CTA. The units cover
+// the i-blocks [b0, b0 + U / NT) (all of them unless the rows are sharded), and
+// slots count i-blocks from b0.
 template <bool KAHAN>
 __global__ void __launch_bounds__(kBI, 8)
 pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut,
-                 long long U, int NT, int C, double* __restrict__ part) {
+                 long long U, int NT, int C, double* __restrict__ part, int b0 = 0) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   const int c = blockIdx.x;
@@ -388,7 +390,8 @@ pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, i
   const float fnc = (float)n_cut;
   long long u = u0;
   while (u < u1) {
-    const int b = (int)(u / NT);
+    const int lb = (int)(u / NT);  // i-block of the evaluated range [b0, b0 + U / NT)
+    const int b = b0 + lb;
     const int t0 = (int)(u % NT);
     const long long rem = u1 - u;
     const int t1 = (int)min((long long)NT, (long long)t0 + rem);
@@ -401,7 +404,7 @@ pair_fp32_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, i
       __syncthreads();
       pair_tile_fp32<KAHAN>(I, sA, sB, n_cut, fnc, sx, sy, sz, cx, cy, cz);
     }
-    const long long slot = (long long)b + c;
+    const long long slot = (long long)lb + c;
     double* dst = part + slot * 3 * kBI;
     dst[threadIdx.x] = (double)sx + (double)cx * (KAHAN ? -1.0 : 0.0);
     dst[kBI + threadIdx.x] = (double)sy + (double)cy * (KAHAN ? -1.0 : 0.0);

@@ -102,14 +102,15 @@ __device__ __forceinline__ void pair_tile_r3(const IParticle& I, const R3Tile& T
 template <bool KAHAN>
 __global__ void __launch_bounds__(kBI, 8)
 pair_r3_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, long long U, int NT, int C,
-               double* __restrict__ part) {
+               double* __restrict__ part, int b0 = 0) {
   __shared__ R3Tile T;
   const int c = blockIdx.x;
   const long long u0 = (long long)c * U / C;
   const long long u1 = (long long)(c + 1) * U / C;
   long long u = u0;
   while (u < u1) {
-    const int b = (int)(u / NT);
+    const int lb = (int)(u / NT);
+    const int b = b0 + lb;
     const int t0 = (int)(u % NT);
     const int t1 = (int)min((long long)NT, (long long)t0 + (u1 - u));
     const int i = b * kBI + threadIdx.x;
@@ -121,7 +122,7 @@ pair_r3_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int
       __syncthreads();
       pair_tile_r3<KAHAN>(I, T, sx, sy, sz, cx, cy, cz);
     }
-    double* dst = part + ((long long)b + c) * 3 * kBI;
+    double* dst = part + ((long long)lb + c) * 3 * kBI;
     dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
     dst[kBI + threadIdx.x] = (double)sy - (KAHAN ? (double)cy : 0.0);
     dst[2 * kBI + threadIdx.x] = (double)sz - (KAHAN ? (double)cz : 0.0);

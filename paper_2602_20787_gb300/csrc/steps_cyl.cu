@@ -243,6 +243,17 @@ struct steps_cyl_ctx {
   double bg_dr = 0.0;
   int C = 0, NT = 0, NB = 0;
   long long U = 0;
+  // Rows evaluated by the pair kernels: i-blocks [b0, b0 + nbo), internal rows
+  // [k0, k1). All of them unless the rows are sharded (steps_cyl_shard); U and
+  // the CTA counts C, SC, TC are those of this range, capped at Ccap etc.
+  int b0 = 0, nbo = 0, k0 = 0, k1 = 0;
+  int Ccap = 0, SCcap = 0, TCcap = 0;
+  // row sharding
+  bool shard = false;
+  int shard_rank = 0, shard_world = 1, chunk = 0;
+  int* shard_off = nullptr;       // device: world + 1 row offsets
+  bool drifted = false;           // steps_cyl_shard_drift done, steps_cyl_shard_kick pending
+  double pend_K2 = 0.0, pend_a = 0.0, pend_dt = 0.0;
   int steps_since_order = 0;
   bool forces_stale = false;       // g must be recomputed before the next kick
   // learned far-image surrogate
@@ -428,6 +439,13 @@ __global__ void scatter_kernel(const double* __restrict__ src, const int* __rest
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[map[k]] = s * src[k];
 }
 
+// dst[map[k]] = s * src[k] for k in [k0, k1), 0 for the other k
+__global__ void scatter_rows_kernel(const double* __restrict__ src, const int* __restrict__ map, int n, double s,
+                                    int k0, int k1, double* __restrict__ dst) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    dst[map[k]] = (k >= k0 && k < k1) ? s * src[k] : 0.0;
+}
+
 __global__ void gather3_kernel(const double* __restrict__ ax, const double* __restrict__ ay,
                                const double* __restrict__ az, const int64_t* __restrict__ idx, int ni, double s,
                                double* __restrict__ ox, double* __restrict__ oy, double* __restrict__ oz) {
@@ -467,6 +485,12 @@ int device_error(int e) {
               (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range " : "",
               (e & kErrTreeRange) ? "particle outside the octree root " : "",
               (e & kErrTreeStack) ? "octree walk stack overflow" : "");
+}
+
+// Calls that need every row of the context current refuse a sharded context.
+int refuse_sharded(const steps_cyl_ctx* c, const char* what) {
+  return fail(STEPS_EINVAL, "%s: the context's rows are sharded (use steps_cyl_shard_drift / steps_cyl_shard_kick)",
+              what);
 }
 
 // Morton (Z-order) rank of (x, y): stable sort of 2 x 16-bit interleaved cell
@@ -955,59 +979,63 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   if (form == Form::PLAIN && is_inf(c)) return fail(STEPS_ENOSURROGATE, "the infinite window has no correction table");
   CK(cudaEventRecord(c->e0, c->st));
   if (form == Form::FP64) {
-    int rc = launch_fp64(c, nullptr, c->n, c->part);
+    int rc = launch_fp64(c, nullptr, c->n, c->part);  // never sharded
     if (rc) return rc;
   } else if (form == Form::SURROGATE) {
     const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
     if (is_inf(c) && kahan)
       pair_fp32_surr_kernel<true, true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->SC,
-                                                                  c->surr_lanes, c->surr, c->part);
+                                                                  c->surr_lanes, c->surr, c->part, c->b0);
     else if (is_inf(c))
       pair_fp32_surr_kernel<false, true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->SC,
-                                                                   c->surr_lanes, c->surr, c->part);
+                                                                   c->surr_lanes, c->surr, c->part, c->b0);
     else if (kahan)
       pair_fp32_surr_kernel<true><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
-                                                             c->surr_lanes, c->surr, c->part);
+                                                             c->surr_lanes, c->surr, c->part, c->b0);
     else
       pair_fp32_surr_kernel<false><<<c->SC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->SC,
-                                                              c->surr_lanes, c->surr, c->part);
+                                                              c->surr_lanes, c->surr, c->part, c->b0);
     CKLAUNCH("pair_fp32_surrogate");
   } else if (form == Form::TABLE) {
     const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
     if (is_inf(c) && kahan)
       pair_fp32_table_kernel<true, true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->TC, c->tab,
-                                                                   c->tab_const, c->part);
+                                                                   c->tab_const, c->part, c->b0);
     else if (is_inf(c))
       pair_fp32_table_kernel<false, true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->U, c->NT, c->TC, c->tab,
-                                                                    c->tab_const, c->part);
+                                                                    c->tab_const, c->part, c->b0);
     else if (kahan)
       pair_fp32_table_kernel<true><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
-                                                              c->tab, c->tab_const, c->part);
+                                                              c->tab, c->tab_const, c->part, c->b0);
     else
       pair_fp32_table_kernel<false><<<c->TC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->TC,
-                                                               c->tab, c->tab_const, c->part);
+                                                               c->tab, c->tab_const, c->part, c->b0);
     CKLAUNCH("pair_fp32_table");
   } else if (is_r3(c)) {
     if (c->p.precision == STEPS_FP32_KAHAN)
-      pair_r3_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part);
+      pair_r3_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part, c->b0);
     else
-      pair_r3_kernel<false><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part);
+      pair_r3_kernel<false><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->U, c->NT, c->C, c->part, c->b0);
     CKLAUNCH("pair_fp32_r3");
   } else if (c->p.precision == STEPS_FP32_KAHAN) {
-    pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);
+    pair_fp32_kernel<true><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part,
+                                                    c->b0);
     CKLAUNCH("pair_fp32_kahan");
   } else {
-    pair_fp32_kernel<false><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part);
+    pair_fp32_kernel<false><<<c->C, kBI, 0, c->st>>>(c->jA, c->jB, c->n, c->p.n_cut, c->U, c->NT, c->C, c->part,
+                                                     c->b0);
     CKLAUNCH("pair_fp32_plain");
   }
   CK(cudaEventRecord(c->e1, c->st));
   c->timed = true;
-  c->last_images = (double)c->n * (double)(c->n - 1) * images_per_pair(c);
+  c->last_images = (double)(c->k1 - c->k0) * (double)(c->n - 1) * images_per_pair(c);
   const int NT = form == Form::FP64 ? 0 : c->NT;
   const int ctas = form == Form::SURROGATE ? c->SC : form == Form::TABLE ? c->TC : c->C;
-  finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
-      c->part, c->n, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
-      kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err);
+  // rows [k0, k1): every row, or the rows this context owns when they are sharded
+  finalize_kernel<<<(c->k1 - c->k0 + 255) / 256, 256, 0, c->st>>>(
+      c->part, c->k1, NT, c->U, ctas, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
+      kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr, c->err,
+      RadialCorr{nullptr, 0, 0.0, 0}, c->k0);
   CKLAUNCH("finalize");
   return STEPS_OK;
 }
@@ -1120,6 +1148,7 @@ void release(steps_cyl_ctx* c) {
   if (c->tab.tex) cudaDestroyTextureObject(c->tab.tex);
   if (c->tab_arr) cudaFreeArray(c->tab_arr);
   cudaFree(c->chk);
+  cudaFree(c->shard_off);
   {
     auto& T = c->tr;
     void* ptrs[] = {T.key[0], T.key[1], T.val[0], T.val[1], T.hist, T.offs, T.u4, T.u4s, T.zt, T.sA, T.sB,
@@ -1151,19 +1180,21 @@ struct DeviceGuard {
 
 // Internal-order arrays -> caller-order outputs (any memory), scaled. Device
 // outputs receive the scatter directly; host outputs go through stage.
+// Internal arrays -> caller order, scaled. A sharded context writes its own
+// rows and zeros elsewhere, so a sum over the ranks assembles the whole.
 int scatter_out(steps_cyl_ctx* c, const double* const src[3], double* const dst[3], double scale) {
   bool host = false;
   for (int q = 0; q < 3; ++q) {
     if (!dst[q]) continue;
-    if (is_host_ptr(dst[q])) {
-      double* s = c->stage + (size_t)q * c->n;
-      scatter_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, s);
-      CKLAUNCH("scatter");
-      CK(cudaMemcpyAsync(dst[q], s, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    double* d = is_host_ptr(dst[q]) ? c->stage + (size_t)q * c->n : dst[q];
+    if (c->shard)
+      scatter_rows_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, c->k0, c->k1, d);
+    else
+      scatter_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, d);
+    CKLAUNCH("scatter");
+    if (d != dst[q]) {
+      CK(cudaMemcpyAsync(dst[q], d, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
       host = true;
-    } else {
-      scatter_kernel<<<grid_for(c->n, 256), 256, 0, c->st>>>(src[q], c->perm, c->n, scale, dst[q]);
-      CKLAUNCH("scatter");
     }
   }
   if (host) CK(cudaStreamSynchronize(c->st));
@@ -1250,14 +1281,16 @@ int run_check(steps_cyl_ctx* c, int model, int ncheck, uint64_t seed, double* me
   // none) its correction table, exact to well below the FP32 arithmetic
   if (is_inf(c) && (model != STEPS_TAIL_SURROGATE || !c->tab_ok))
     return fail(STEPS_EINVAL, "the infinite window checks only a surrogate, against its correction table");
-  const int ni = std::max(1, std::min(ncheck, c->n));
+  // the sample is drawn from the rows this context evaluates (all, or its shard)
+  const int nrows = c->k1 - c->k0;
+  const int ni = std::max(1, std::min(ncheck, nrows));
   std::vector<int64_t> pick(ni);
   {
-    std::vector<int> all(c->n);
-    for (int k = 0; k < c->n; ++k) all[k] = k;
+    std::vector<int> all(nrows);
+    for (int k = 0; k < nrows; ++k) all[k] = c->k0 + k;
     SplitMix rng(seed);
     for (int q = 0; q < ni; ++q) {  // partial Fisher-Yates: distinct internal indices
-      const int r = q + (int)(rng.next() % (uint64_t)(c->n - q));
+      const int r = q + (int)(rng.next() % (uint64_t)(nrows - q));
       std::swap(all[q], all[r]);
       pick[q] = all[q];
     }
@@ -1791,6 +1824,19 @@ int train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* re
 
 // Device buffers and the work split of a context whose n, device and stream
 // are set (init and resume).
+// The pair kernels evaluate the i-blocks [b0, b0 + nbo): their stream-K units
+// and CTA counts for that range.
+void set_rows(steps_cyl_ctx* c, int b0, int nbo) {
+  c->b0 = b0;
+  c->nbo = nbo;
+  c->k0 = b0 * kBI;
+  c->k1 = std::min(c->n, (b0 + nbo) * kBI);
+  c->U = (long long)nbo * c->NT;
+  c->C = (int)std::min<long long>(c->U, c->Ccap);
+  c->SC = (int)std::min<long long>(c->U, c->SCcap);
+  c->TC = (int)std::min<long long>(c->U, c->TCcap);
+}
+
 int allocate_context(steps_cyl_ctx* c) {
 #define CKA(call)                                                                            \
   do {                                                                                       \
@@ -1823,13 +1869,14 @@ int allocate_context(steps_cyl_ctx* c) {
   c->NB = (c->n + kBI - 1) / kBI;
   c->NT = (c->n + kBJ - 1) / kBJ;
   c->U = (long long)c->NB * c->NT;
-  c->C = (int)std::min<long long>(c->U, (long long)sms * std::max(occ, 1) * STEPS_CTA_MULT);
+  c->Ccap = sms * std::max(occ, 1) * STEPS_CTA_MULT;
   int socc = 0;
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, pair_fp32_surr_kernel<true>, kBI, 0));
-  c->SC = (int)std::min<long long>(c->U, (long long)sms * std::max(socc, 1) * STEPS_CTA_MULT);
+  c->SCcap = sms * std::max(socc, 1) * STEPS_CTA_MULT;
   int tocc = 0;
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tocc, pair_fp32_table_kernel<true>, kBI, 0));
-  c->TC = (int)std::min<long long>(c->U, (long long)sms * std::max(tocc, 1) * STEPS_CTA_MULT);
+  c->TCcap = sms * std::max(tocc, 1) * STEPS_CTA_MULT;
+  set_rows(c, 0, c->NB);
   c->part_elems = std::max((size_t)(c->NB + std::max({c->C, c->SC, c->TC})) * 3 * kBI, nb * 3);
   CKA(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
 
@@ -1962,6 +2009,7 @@ int steps_cyl_forces(steps_cyl_ctx* c, double* ax, double* ay, double* az) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (!ax || !ay || !az) return fail(STEPS_EINVAL, "NULL output");
+  if (c->drifted) return fail(STEPS_EINVAL, "a sharded step is half done: steps_cyl_shard_kick must come first");
   DeviceGuard guard(c->dev);
   int rc;
   if ((rc = eval_forces(c, false, 0.0))) return rc;
@@ -1979,6 +2027,7 @@ int steps_cyl_forces(steps_cyl_ctx* c, double* ax, double* ay, double* az) {
 int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, double* ax, double* ay, double* az) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_forces_subset");
   if (ni < 0 || ni > c->n) return fail(STEPS_EINVAL, "ni must be in [0, n]");
   if (ni == 0) return STEPS_OK;
   if (!idx || !ax || !ay || !az) return fail(STEPS_EINVAL, "NULL argument");
@@ -2031,6 +2080,7 @@ int steps_cyl_forces_subset(steps_cyl_ctx* c, int64_t ni, const int64_t* idx, do
 int steps_cyl_kdk_step(steps_cyl_ctx* c, double dt, int32_t nsteps) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_kdk_step");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(STEPS_EINVAL, "dt must be finite and > 0");
   if (nsteps < 0) return fail(STEPS_EINVAL, "nsteps must be >= 0");
   DeviceGuard guard(c->dev);
@@ -2105,6 +2155,7 @@ int steps_cyl_set_state(steps_cyl_ctx* c, const double* x, const double* y, cons
                         const double* vy, const double* vz) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_set_state");
   if (!x || !y || !z || !vx || !vy || !vz) return fail(STEPS_EINVAL, "NULL input array");
   DeviceGuard guard(c->dev);
   int rc;
@@ -2133,6 +2184,7 @@ int steps_cyl_set_precision(steps_cyl_ctx* c, int32_t precision) {
   if (precision < STEPS_FP64 || precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   if (precision == STEPS_FP64 && is_inf(c)) return fail(STEPS_EINVAL, "the infinite window needs an FP32 precision");
   if (precision == STEPS_FP64 && is_tree(c)) return fail(STEPS_EINVAL, "the octree needs an FP32 precision");
+  if (precision == STEPS_FP64 && c->shard) return fail(STEPS_EINVAL, "a sharded context needs an FP32 precision");
   DeviceGuard guard(c->dev);
   c->p.precision = precision;
   if (precision == STEPS_FP64) c->p.tail = STEPS_TAIL_FULL;
@@ -2144,7 +2196,9 @@ int steps_cyl_diagnostics(steps_cyl_ctx* c, double out[8]) {
   g_last_error.clear();
   if (!c || !out) return fail(STEPS_EINVAL, "NULL argument");
   DeviceGuard guard(c->dev);
-  diag_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->st>>>(c->x, c->y, c->px, c->py, c->pz, c->m, c->n, c->red);
+  const int k0 = c->k0;  // sharded: the rows this context owns
+  diag_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->st>>>(c->x + k0, c->y + k0, c->px + k0, c->py + k0, c->pz + k0,
+                                                             c->m + k0, c->k1 - k0, c->red);
   CKLAUNCH("diag_partial");
   diag_final_kernel<<<1, 32, 0, c->st>>>(c->red, kRedBlocks, c->red + kRedBlocks * 6);
   CKLAUNCH("diag_final");
@@ -2160,6 +2214,101 @@ int steps_cyl_diagnostics(steps_cyl_ctx* c, double out[8]) {
   out[5] = c->a;
   out[6] = c->t;
   out[7] = r[5];
+  return STEPS_OK;
+}
+
+int steps_cyl_shard(steps_cyl_ctx* c, int32_t rank, int32_t world, int64_t* rows) {
+  g_last_error.clear();
+  if (!c || !rows) return fail(STEPS_EINVAL, "NULL argument");
+  if (c->shard) return fail(STEPS_EINVAL, "the context is sharded already");
+  if (world < 1 || rank < 0 || rank >= world) return fail(STEPS_EINVAL, "need 0 <= rank < world");
+  if (world > c->NB) return fail(STEPS_EINVAL, "world = %d exceeds the %d blocks of %d rows", world, c->NB, kBI);
+  if (is_tree(c)) return fail(STEPS_EINVAL, "the octree is not row-sharded");
+  // the FP64 pair kernel reads the FP64 positions of every j, and only the
+  // packed FP32 words of the other ranks' rows are exchanged
+  if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "a sharded context needs an FP32 precision");
+  DeviceGuard guard(c->dev);
+  // balanced contiguous ranges of i-blocks, the same on every rank
+  const int base = c->NB / world, extra = c->NB % world;
+  std::vector<int> off(world + 1);
+  for (int r = 0; r <= world; ++r) off[r] = std::min(c->n, (r * base + std::min(r, extra)) * kBI);
+  int chunk = 0;
+  for (int r = 0; r < world; ++r) chunk = std::max(chunk, off[r + 1] - off[r]);
+  const int b0 = rank * base + std::min(rank, extra), nbo = base + (rank < extra ? 1 : 0);
+  const int k0 = off[rank], k1 = off[rank + 1];
+  int* d_off = nullptr;
+  cudaError_t e = cudaMalloc(&d_off, sizeof(int) * (world + 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (world + 1), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) {  // the context stays whole and unsharded
+    cudaFree(d_off);
+    return fail(e == cudaErrorMemoryAllocation ? STEPS_ENOMEM : STEPS_ECUDA, "steps_cyl_shard: %s",
+                cudaGetErrorString(e));
+  }
+  c->shard_off = d_off;
+  set_rows(c, b0, nbo);
+  c->shard = true;
+  c->shard_rank = rank;
+  c->shard_world = world;
+  c->chunk = chunk;
+  c->p.reorder_every = -1;  // the internal order stays the one every rank holds
+  rows[0] = k0;
+  rows[1] = k1;
+  rows[2] = chunk;
+  return STEPS_OK;
+}
+
+// A caller's exchange buffer: device memory, 16-byte aligned (float4 rows).
+static bool exchange_buffer_ok(const void* p) { return p && !is_host_ptr(p) && ((uintptr_t)p & 15u) == 0; }
+
+int steps_cyl_shard_drift(steps_cyl_ctx* c, double dt, float* send) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!c->shard) return fail(STEPS_EINVAL, "the context is not sharded (steps_cyl_shard)");
+  if (c->drifted) return fail(STEPS_EINVAL, "steps_cyl_shard_kick must follow the last steps_cyl_shard_drift");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(STEPS_EINVAL, "dt must be finite and > 0");
+  if (!exchange_buffer_ok(send)) return fail(STEPS_EINVAL, "send must be 16-byte aligned device memory");
+  DeviceGuard guard(c->dev);
+  Range range("steps_cyl.shard_drift");
+  int rc;
+  if (c->forces_stale && (rc = eval_forces(c, false, 0.0))) return rc;
+  const Factors f = kdk_factors(c->cosmo, c->a, dt);
+  if (!std::isfinite(f.K1) || !std::isfinite(f.D) || !std::isfinite(f.a_next) || !(f.a_next > 0))
+    return fail(STEPS_EINVAL, "the Friedmann integration left the valid range (a = %g)", f.a_next);
+  const int k0 = c->k0, rows = c->k1 - c->k0;
+  kick_drift_pack_kernel<<<grid_for(rows, 256), 256, 0, c->st>>>(
+      c->x + k0, c->y + k0, c->z + k0, c->px + k0, c->py + k0, c->pz + k0, c->gx + k0, c->gy + k0, c->gz + k0,
+      c->m + k0, c->h + k0, rows, f.K1, f.D, c->p.L, c->invL, c->jA + k0, c->jB + k0, c->err, is_r3(c) ? 0 : 1);
+  CKLAUNCH("kick_drift_pack");
+  shard_send_kernel<<<grid_for(c->chunk, 256), 256, 0, c->st>>>(c->jA, c->jB, k0, rows, c->chunk,
+                                                                 reinterpret_cast<float4*>(send));
+  CKLAUNCH("shard_send");
+  c->pend_K2 = f.K2;
+  c->pend_a = f.a_next;
+  c->pend_dt = dt;
+  c->drifted = true;
+  return STEPS_OK;
+}
+
+int steps_cyl_shard_kick(steps_cyl_ctx* c, const float* recv) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!c->shard) return fail(STEPS_EINVAL, "the context is not sharded (steps_cyl_shard)");
+  if (!c->drifted) return fail(STEPS_EINVAL, "steps_cyl_shard_drift must come first");
+  if (!exchange_buffer_ok(recv)) return fail(STEPS_EINVAL, "recv must be 16-byte aligned device memory");
+  DeviceGuard guard(c->dev);
+  Range range("steps_cyl.shard_kick");
+  shard_recv_kernel<<<dim3(grid_for(c->chunk, 256), c->shard_world), 256, 0, c->st>>>(
+      reinterpret_cast<const float4*>(recv), c->shard_off, c->chunk, c->jA, c->jB);
+  CKLAUNCH("shard_recv");
+  int rc;
+  if ((rc = eval_forces(c, true, c->pend_K2))) return rc;
+  c->a = c->pend_a;
+  c->t += c->pend_dt;
+  c->drifted = false;
+  int e = 0;
+  if ((rc = read_and_clear_err(c, &e))) return rc;
+  if (e) return device_error(e);
   return STEPS_OK;
 }
 
@@ -2221,6 +2370,7 @@ constexpr uint32_t kCkptVersion = 4;
 int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   g_last_error.clear();
   if (!c || !path) return fail(STEPS_EINVAL, "NULL argument");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_checkpoint");
   DeviceGuard guard(c->dev);
   CkptHeader hd;
   std::memset(&hd, 0, sizeof hd);
@@ -2468,6 +2618,7 @@ int steps_cyl_mlp_loss_grad(int64_t ns, const float* w, const float* u, const fl
 int steps_cyl_train_surrogate(steps_cyl_ctx* c, const steps_cyl_train_cfg* cfg, double* report) {
   g_last_error.clear();
   if (!c || !cfg) return fail(STEPS_EINVAL, "NULL argument");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_train_surrogate (train before sharding)");
   DeviceGuard guard(c->dev);
   if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the surrogate needs an FP32 precision");
   const int32_t tail = c->p.tail;
@@ -2481,6 +2632,7 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* c, const float* params, double err_me
                             double* report) {
   g_last_error.clear();
   if (!c || !params) return fail(STEPS_EINVAL, "NULL argument");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_set_surrogate (install before sharding)");
   if (!(err_median > 0) || !(err_p999 > 0)) return fail(STEPS_EINVAL, "bounds must be > 0");
   DeviceGuard guard(c->dev);
   std::vector<float> P(STEPS_SURR_NPARAM);
@@ -2544,6 +2696,7 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* c, int32_t nx, int32_t ny, double 
                                double err_p999, int32_t check_particles, double* report) {
   g_last_error.clear();
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_build_tail_table (build before sharding)");
   if (nx < 2 || nx > 4096 || ny < 2 || ny > 1024) return fail(STEPS_EINVAL, "nx must be in [2, 4096], ny in [2, 1024]");
   if (!(dR_max >= 0) || !std::isfinite(dR_max)) return fail(STEPS_EINVAL, "dR_max must be finite and >= 0");
   if (!(err_median > 0) || !(err_p999 > 0) || check_particles < 1) return fail(STEPS_EINVAL, "bad check bounds");

@@ -428,7 +428,8 @@ __device__ __forceinline__ void pair_tile(const IParticle& I, const float4* sA, 
 template <bool KAHAN, bool INF = false>
 __global__ void __launch_bounds__(kBI, STEPS_SURR_MIN_BLOCKS)
 pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
-                      int NT, int C, const SurrLane* __restrict__ wl, SurrConst S, double* __restrict__ part) {
+                      int NT, int C, const SurrLane* __restrict__ wl, SurrConst S, double* __restrict__ part,
+                      int b0 = 0) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   // weight fragments stay in shared memory (word-major, conflict-free) and are
@@ -445,7 +446,8 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
   const float fnc = (float)n_cut;
   long long u = u0;
   while (u < u1) {
-    const int b = (int)(u / NT);
+    const int lb = (int)(u / NT);
+    const int b = b0 + lb;
     const int t0 = (int)(u % NT);
     const int t1 = (int)min((long long)NT, (long long)t0 + (u1 - u));
     const int i = b * kBI + threadIdx.x;
@@ -458,7 +460,7 @@ pair_fp32_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
       pair_tile<KAHAN, true, INF>(I, sA, sB, kBJ, i - t * kBJ, n_cut, fnc, W, ibuf, S, sx, sy, sz, cx, cy,
                                   cz);
     }
-    double* dst = part + ((long long)b + c) * 3 * kBI;
+    double* dst = part + ((long long)lb + c) * 3 * kBI;
     dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
     dst[kBI + threadIdx.x] = (double)sy - (KAHAN ? (double)cy : 0.0);
     dst[2 * kBI + threadIdx.x] = (double)sz - (KAHAN ? (double)cz : 0.0);

@@ -122,7 +122,7 @@ __device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4
 template <bool KAHAN, bool INF = false>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, long long U,
-                       int NT, int C, TableTail T, SurrConst S, double* __restrict__ part) {
+                       int NT, int C, TableTail T, SurrConst S, double* __restrict__ part, int b0 = 0) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   const int c = blockIdx.x;
@@ -130,7 +130,8 @@ pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__
   const long long u1 = (long long)(c + 1) * U / C;
   long long u = u0;
   while (u < u1) {
-    const int b = (int)(u / NT);
+    const int lb = (int)(u / NT);
+    const int b = b0 + lb;
     const int t0 = (int)(u % NT);
     const int t1 = (int)min((long long)NT, (long long)t0 + (u1 - u));
     const int i = b * kBI + threadIdx.x;
@@ -142,7 +143,7 @@ pair_fp32_table_kernel(const float4* __restrict__ jA, const float4* __restrict__
       __syncthreads();
       pair_tile_table<KAHAN, INF>(I, sA, sB, i - t * kBJ, n_cut, S, T, sx, sy, sz, cx, cy, cz);
     }
-    double* dst = part + ((long long)b + c) * 3 * kBI;
+    double* dst = part + ((long long)lb + c) * 3 * kBI;
     dst[threadIdx.x] = (double)sx - (KAHAN ? (double)cx : 0.0);
     dst[kBI + threadIdx.x] = (double)sy - (KAHAN ? (double)cy : 0.0);
     dst[2 * kBI + threadIdx.x] = (double)sz - (KAHAN ? (double)cz : 0.0);

@@ -7,10 +7,13 @@ one all-gather of the positions, after which every rank holds the full j-set and
 computes its own rows; the KDK kick and drift are local to each rank's rows, and
 the conserved quantities need one all-reduce of a few sums.
 
-Each rank's rows are evaluated with the same per-i sum order as on one rank, so
-the sharded result equals the unsharded one bit for bit. This module holds the
-partition, the exchange and the rank reductions; they run with any
-torch.distributed backend (NCCL between GPUs, gloo on the host).
+This module holds the partition, the exchange and the rank reductions, and
+ShardedSimulation, which drives one cylinder's KDK steps across the ranks with
+one all-gather per step; they run with any torch.distributed backend (NCCL
+between GPUs, gloo on the host). The rank's compute is pluggable: GpuRows runs
+it through the C ABI (steps_cyl_shard, steps_cyl_shard_drift and
+steps_cyl_shard_kick); a backend whose per-row sums keep the unsharded order
+reproduces the unsharded run bit for bit.
 
 Rank loss is detected on the host, between steps. A Heartbeat posts each step
 to a key-value store before the step's launches. A rank that crashed, hung or
@@ -71,6 +74,131 @@ def sum_over_ranks(values, group=None, device=None) -> np.ndarray:
     t = torch.tensor(np.asarray(values, dtype=np.float64), device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.cpu().numpy()
+
+
+def all_gather_rows(send, group=None):
+    """All-gather of equal-sized per-rank tensors (chunk, c) into (world * chunk, c)
+    in rank order: NCCL's gather into one tensor for CUDA tensors, the list form
+    otherwise (gloo)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    if send.is_cuda:
+        out = torch.empty((world * send.shape[0],) + tuple(send.shape[1:]), dtype=send.dtype, device=send.device)
+        dist.all_gather_into_tensor(out, send.contiguous(), group=group)
+        return out
+    parts = [torch.empty_like(send) for _ in range(world)]
+    dist.all_gather(parts, send.contiguous(), group=group)
+    return torch.cat(parts, 0)
+
+
+class GpuRows:
+    """A rank's rows on its GPU: a steps_cyl context made from the full state
+    (the same on every rank) and then sharded with steps_cyl_shard. Train or
+    install a modelled tail on the context before handing it over.
+
+    drift(dt) runs steps_cyl_shard_drift and returns the send buffer (chunk, 8)
+    float32; kick(recv) runs steps_cyl_shard_kick on the gathered rows. The
+    context's stream must be the current torch stream, so that the collective
+    between them is ordered after the drift and before the kick."""
+
+    def __init__(self, sim, rank: int, world: int):
+        import torch
+        from . import steps_cyl as sc
+        self.sc, self.sim, self.rank, self.world = sc, sim, rank, world
+        self.k0, self.k1, self.chunk = sc.steps_cyl_shard(sim.ctx, rank, world)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.send = torch.zeros((self.chunk, 8), dtype=torch.float32, device=self.device)
+
+    def drift(self, dt: float):
+        self.sc.steps_cyl_shard_drift(self.sim.ctx, dt, self.send)
+        return self.send
+
+    def kick(self, recv):
+        self.sc.steps_cyl_shard_kick(self.sim.ctx, recv)
+
+    def sums(self):
+        """(P[3], L_z, kinetic energy, mass) of the owned rows, and (a, t)."""
+        d = self.sim.diagnostics()
+        return np.array([d[0], d[1], d[2], d[3], d[4], d[7]]), (float(d[5]), float(d[6]))
+
+    def state(self):
+        """Positions and velocities in caller order, zeros outside the owned rows."""
+        x, v, _, _ = self.sim.state()
+        return np.concatenate([x, v], 1)
+
+    def check(self, tail: int, particles: int = 1024):
+        """(median, p99.9) of the modelled tail's error on a sample of the owned rows."""
+        rep = self.sc.steps_cyl_check_tail(self.sim.ctx, tail, particles)
+        return float(rep[0]), float(rep[1])
+
+    def set_tail(self, tail: int):
+        self.sc.steps_cyl_set_tail(self.sim.ctx, tail)
+
+
+class ShardedSimulation:
+    """One cylinder whose rows are split across the ranks of a process group
+    (Sect. 2.4's distributed direct engine, one rank per GPU). Each KDK step is
+    compute.drift(dt) on the rank's rows, one all-gather of the packed rows of
+    every rank, and compute.kick(gathered) on the rank's rows: the pair force of
+    its rows against every particle, the background and the second kick. There
+    is no other exchange. `compute` is the rank's backend (GpuRows, or any
+    object with the same drift / kick / sums / state / check / set_tail
+    methods and a `device` attribute for the collectives' tensors).
+
+    With a modelled tail (tail = STEPS_TAIL_SURROGATE or STEPS_TAIL_TABLE) and
+    check_every > 0, every check_every steps each rank checks a sample of its
+    rows against the plain image sum; the largest median and p99.9 over the
+    ranks decide, and a failed check switches every rank to the plain sum
+    together (returned by step() as False)."""
+
+    def __init__(self, compute, group=None, tail: int = 0, check_every: int = 0, bounds=(1e-5, 1e-3),
+                 check_particles: int = 1024):
+        self.compute, self.group = compute, group
+        self.tail, self.check_every, self.bounds = int(tail), int(check_every), bounds
+        self.check_particles = int(check_particles)
+        self.steps = 0
+        self.last_check = None
+
+    def step(self, dt: float, nsteps: int = 1) -> bool:
+        ok = True
+        for _ in range(nsteps):
+            send = self.compute.drift(dt)
+            self.compute.kick(all_gather_rows(send, self.group))
+            self.steps += 1
+            if self.tail and self.check_every > 0 and self.steps % self.check_every == 0:
+                ok = self._check() and ok
+        return ok
+
+    def _check(self) -> bool:
+        import torch
+        import torch.distributed as dist
+        med, p999 = self.compute.check(self.tail, self.check_particles)
+        t = torch.tensor([med, p999], dtype=torch.float64, device=getattr(self.compute, "device", None))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=self.group)
+        med, p999 = float(t[0]), float(t[1])
+        self.last_check = (med, p999)
+        if med <= self.bounds[0] and p999 <= self.bounds[1]:
+            return True
+        self.tail = 0
+        self.compute.set_tail(0)
+        return False
+
+    def diagnostics(self) -> np.ndarray:
+        """P[3], L_z, kinetic energy, mass of the whole cylinder, then a and t."""
+        sums, (a, t) = self.compute.sums()
+        tot = sum_over_ranks(sums, group=self.group, device=getattr(self.compute, "device", None))
+        return np.concatenate([tot, [a, t]])
+
+    def state(self) -> np.ndarray:
+        """(n, 6) positions and velocities of every particle in caller order,
+        assembled from the ranks' rows (every rank receives it)."""
+        import torch
+        import torch.distributed as dist
+        own = self.compute.state()
+        t = torch.tensor(own, dtype=torch.float64, device=getattr(self.compute, "device", None))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+        return t.cpu().numpy()
 
 
 class RankLost(RuntimeError):

@@ -43,7 +43,7 @@ _EXPORTS = [
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
-    "steps_cyl_tree_set_radial",
+    "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
 ]
 
 STEPS_SURR_NW = 1250
@@ -138,6 +138,9 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_tree_stats.argtypes = [p, p]
     L.steps_cyl_tree_calibrate.argtypes = [p, i32, i32, i32, p, p, p, p]
     L.steps_cyl_tree_set_radial.argtypes = [p, p, i32, d]
+    L.steps_cyl_shard.argtypes = [p, i32, i32, p]
+    L.steps_cyl_shard_drift.argtypes = [p, d, p]
+    L.steps_cyl_shard_kick.argtypes = [p, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -311,6 +314,32 @@ def steps_cyl_pair_accel_noalloc(x, y, z, m, h, G, L, n_cut, precision, ax, ay, 
                                              ctypes.c_void_p(stream or None))
     if rc != STEPS_OK:
         raise StepsError(rc, "steps_cyl_pair_accel_noalloc rejected its arguments or failed to launch")
+
+
+def steps_cyl_shard(ctx, rank: int, world: int):
+    """Make the context shard `rank` of `world` (row sharding): returns the
+    owned internal rows (k0, k1) and chunk, the rows per rank of an exchange."""
+    rows = np.zeros(3, dtype=np.int64)
+    _check(load().steps_cyl_shard(ctx, int(rank), int(world), _ptr(rows)))
+    return int(rows[0]), int(rows[1]), int(rows[2])
+
+
+def _exchange_buffer(buf, what):
+    if not hasattr(buf, "is_cuda") or not buf.is_cuda or str(buf.dtype) != "torch.float32":
+        raise StepsError(STEPS_EINVAL, f"{what} must be a float32 CUDA tensor")
+    return _ptr(buf)
+
+
+def steps_cyl_shard_drift(ctx, dt: float, send):
+    """First half of a sharded KDK step; the owned packed rows go to send
+    (float32 CUDA tensor of chunk x 8)."""
+    _check(load().steps_cyl_shard_drift(ctx, float(dt), _exchange_buffer(send, "send")))
+
+
+def steps_cyl_shard_kick(ctx, recv):
+    """Second half of a sharded KDK step from the gathered rows (float32 CUDA
+    tensor of world x chunk x 8, rank order)."""
+    _check(load().steps_cyl_shard_kick(ctx, _exchange_buffer(recv, "recv")))
 
 
 def steps_cyl_train_cfg_default(**overrides) -> TrainCfg:

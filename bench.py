@@ -45,7 +45,6 @@ REORDER_EVERY = 32   # the library's default Morton re-order interval
 METRIC = "pair-interactions/s (images counted)"
 UNIT = "pair-images/s"
 MUFU_RSQRT_PER_SM_CLK = 16  # MUFU rsqrt lanes per SM per clock, measured on GB300 (one rsqrt per pair-image)
-MMA_SYNC_FLOP_PER_SM_CLK = 1913.0  # mma.sync m16n8k16 f16->f32 flops per SM per clock, measured on GB300
 
 
 def env_int(name, default):
@@ -150,22 +149,28 @@ def recorded_traffic(kind: str = "plain"):
     return traffic
 
 
-def cpu_baseline(w, d, target_s: float = 12.0):
+def cpu_baseline(w, d, target_s: float = 15.0):
     """FP64 oracle (as it stands) on a bounded i-sample of the same workload:
-    pair field of the sampled i against all N particles plus the background."""
+    pair field of the sampled i against all N particles plus the background.
+    The sample is sized from a small probe and rescaled once from a real run,
+    so that it takes about target_s seconds."""
     import oracle
     from paper_2602_20787_gb300 import ics
     n = w.n
-    probe = ics.subsample(n, 8, seed=777)
-    t0 = time.perf_counter()
-    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=probe)
-    dt_probe = max(time.perf_counter() - t0, 1e-3)
-    k = int(min(n, max(8, 8 * target_s / dt_probe)))
-    idx = ics.subsample(n, k, seed=778)
-    t0 = time.perf_counter()
-    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
-    oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
-    el = time.perf_counter() - t0
+
+    def run(k, seed):
+        idx = ics.subsample(n, k, seed=seed)
+        t0 = time.perf_counter()
+        oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+        oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
+        return time.perf_counter() - t0
+
+    dt_probe = max(run(16, 777), 1e-3)
+    k = int(min(n, max(16, 16 * target_s / dt_probe)))
+    el = run(k, 778)
+    if el < 0.5 * target_s and k < n:
+        k = int(min(n, max(k + 1, k * target_s / max(el, 1e-3))))
+        el = run(k, 779)
     images = k * (n - 1) * 2.0 * w.n_cut
     return {"value": images / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{k} i-particles x all {n} j x {2 * w.n_cut} images (FP64 pair field + background), {el:.1f} s"}
@@ -246,14 +251,15 @@ def measured_peaks():
         return None
 
 
-def surrogate_roofline(n_sm, sm_mhz, n0, pairs, kernel_s):
+def surrogate_roofline(n_sm, sm_mhz, n0, pairs, kernel_s, symmetric=False):
     """Roofline of the learned-tail pair kernel per pair (one i, one j):
     - MUFU: 2 n0 + 1 near-image rsqrt, 4 rsqrt + 2 rcp of the two-sided
       continuum base and 1 rsqrt of dR, at 16 MUFU ops/SM/clk;
     - tensor: the network's own 2 (3 x 32 + 32 x 32 + 32 x 2) = 2368 flops at
       the measured sustained dense f16/bf16 rate (the kernel runs inside a
       seconds-long step).
-    The larger time per pair binds."""
+    The larger time per pair binds. pairs: the pairs the kernel evaluated (each
+    unordered pair once for the symmetric kernels)."""
     mufu_ops = (2 * n0 + 1) + 4 + 2 + 1
     mlp_flops = 2 * (3 * 32 + 32 * 32 + 32 * 2)
     pk = measured_peaks()
@@ -266,7 +272,8 @@ def surrogate_roofline(n_sm, sm_mhz, n0, pairs, kernel_s):
     peak = min(mufu_pairs, tensor_pairs)
     achieved = pairs / kernel_s
     return {"bound": "alu" if mufu_pairs <= tensor_pairs else "tensor", "achieved": achieved, "peak": peak,
-            "unit": "pair interactions/s", "frac": achieved / peak, "traffic": recorded_traffic("surrogate"),
+            "unit": "pair interactions evaluated/s", "frac": achieved / peak,
+            "traffic": recorded_traffic("surrogate"), "symmetric": symmetric,
             "peak_basis": f"min(MUFU: {n_sm} SMs x {MUFU_RSQRT_PER_SM_CLK}/SM/clk x {sm_mhz:.0f} MHz / {mufu_ops} "
                           f"ops per pair = {mufu_pairs:.3e}; tensor: {tensor_flops:.3e} flop/s {tensor_src} / "
                           f"{mlp_flops} network flops per pair = {tensor_pairs:.3e})"}
@@ -463,11 +470,15 @@ def run(args):
     kernel_s = statistics.mean(pair_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk["sm_max_mhz"] or 2070.0
-    roof = surrogate_roofline(props.multi_processor_count, sm_mhz, w.n0, pairs, kernel_s)
+    ev_s = sc.steps_cyl_last_eval(ctx)  # the pairs the kernel evaluated (each unordered pair once if symmetric)
+    roof = surrogate_roofline(props.multi_processor_count, sm_mhz, w.n0, ev_s["pairs_evaluated"], kernel_s,
+                              ev_s["symmetric"])
+    peak_plain = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_mhz * 1e6
     if not accepted:  # the plain sum ran: its own roofline
-        peak = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_mhz * 1e6
-        roof = {"bound": "alu", "achieved": images_per_step / kernel_s, "peak": peak, "unit": UNIT,
-                "frac": images_per_step / kernel_s / peak, "traffic": None}
+        done = ev_s["pairs_evaluated"] * 2.0 * w.n_cut
+        roof = {"bound": "alu", "achieved": done / kernel_s, "peak": peak_plain, "unit": "pair-images evaluated/s",
+                "frac": done / kernel_s / peak_plain, "traffic": recorded_traffic("plain"),
+                "symmetric": ev_s["symmetric"]}
     # reorders and surrogate checks that fell in the timed region add launches
     timed = range(steps_before + 1, steps_before + args.steps + 1)
     reorders = sum(1 for s in timed if s % REORDER_EVERY == 0)
@@ -483,7 +494,8 @@ def run(args):
     steps_before += 1 + plain_steps
     plain_kernel_s = statistics.mean(plain_pair_ms) / 1e3
     plain_step_s = statistics.mean(plain_ms) / 1e3
-    peak_plain = props.multi_processor_count * MUFU_RSQRT_PER_SM_CLK * sm_mhz * 1e6
+    ev_p = sc.steps_cyl_last_eval(ctx)
+    plain_done = ev_p["pairs_evaluated"] * 2.0 * w.n_cut
     sc.steps_cyl_set_tail(ctx, sc.STEPS_TAIL_SURROGATE if accepted else sc.STEPS_TAIL_FULL)
     sc.steps_cyl_kdk_step(ctx, dt, 1)  # the switch marks the forces stale: refresh them untimed
 
@@ -537,9 +549,11 @@ def run(args):
         "plain": {"steps": plain_steps, "kdk_step_ms": 1e3 * plain_step_s, "pair_kernel_ms": 1e3 * plain_kernel_s,
                   "pair_images_per_s": images_per_step / plain_step_s,
                   "error_vs_fp64": errs["plain"],
-                  "roofline": {"bound": "alu", "achieved": images_per_step / plain_kernel_s, "peak": peak_plain,
-                               "unit": UNIT, "frac": images_per_step / plain_kernel_s / peak_plain,
-                               "traffic": None}},
+                  "roofline": {"bound": "alu", "achieved": plain_done / plain_kernel_s, "peak": peak_plain,
+                               "unit": "pair-images evaluated/s", "frac": plain_done / plain_kernel_s / peak_plain,
+                               "traffic": recorded_traffic("plain"), "symmetric": ev_p["symmetric"],
+                               "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_RSQRT_PER_SM_CLK} MUFU "
+                                             f"rsqrt/SM/clk x {sm_mhz:.0f} MHz; 1 rsqrt per pair-image"}},
         "error_reference": "library FP64 form on 4096 particles (seed 12345), pinned to the FP64 oracle in the tests",
         "roofline": roof,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
@@ -959,9 +973,112 @@ def run_octree_accuracy(args):
     return 0
 
 
+def run_production(args):
+    """The production-shaped run as the workload states it: N = 524,288,
+    softening 1:8, LCDM from a = 0.02 to a = 1 in 1000 KDK steps, the learned
+    tail with FP32-Kahan near images, and the plain image sum re-checking it
+    every 50 steps (a failed check falls back to the plain sum). Per chunk of 50
+    steps one JSON line goes to --log (a, t, step time, the momentum drift, the
+    check's errors, the form in use); a checkpoint is written every
+    --ckpt-every steps to --ckpt, and --resume continues from one. At the end
+    the forces of both forms are compared with the FP64 oracle on 4,096
+    particles (seed 12345) at the final state."""
+    import torch
+    from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    w = ics.WORKLOADS["production_n524288"]
+    d = ics.workload_ics(w)
+    n = w.n
+    t0, dt = ics.run_schedule(w)
+    stream = torch.cuda.current_stream().cuda_stream
+    log = open(args.log, "a") if args.log else None
+    if args.resume:
+        sim = sc.Simulation.resume(args.resume, 0, stream)
+        rec = json.load(open(args.resume + ".json"))
+    else:
+        cfg = sc.Config(n_cut=w.n_cut, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, rho_bar=w.rho_bar, comoving=True,
+                        a_start=w.a_start, t_start=t0, check_every=CHECK_EVERY, check_particles=1024, stream=stream)
+        sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+        rep = sc.steps_cyl_train_surrogate(sim.ctx, sc.steps_cyl_train_cfg_default())
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+        d0 = sim.diagnostics()
+        rec = {"done": 0, "fallbacks": 0, "step_ms_total": 0.0, "P0": [float(v) for v in d0[:3]], "Lz0": float(d0[3]),
+               "train": {"ms": float(rep[5]), "check_median": float(rep[2]), "check_p999": float(rep[3])},
+               "form": "surrogate"}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stop = min(w.nsteps, rec["done"] + (args.steps_limit or w.nsteps))
+    while rec["done"] < stop:
+        k = min(CHECK_EVERY - rec["done"] % CHECK_EVERY, stop - rec["done"])
+        ev0.record()
+        fell_back = False
+        try:
+            sim.step(dt, k)
+        except sc.StepsError as e:   # a periodic check dropped the network: the plain sum carries on
+            if e.code != sc.STEPS_ESURROGATE_REJECTED:
+                raise
+            fell_back = True
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        rec["done"] += k
+        rec["step_ms_total"] += ms
+        if fell_back:
+            rec["fallbacks"] += 1
+            rec["form"] = "plain"
+        dg = sim.diagnostics()
+        x, v, a, t = sim.state()
+        p = v * a * a
+        pscale = float(np.sum(d["m"][:, None] * np.abs(p)))
+        chunk = {"step": rec["done"], "a": float(dg[5]), "t": float(dg[6]), "step_ms": ms / k,
+                 "pz_drift_over_momentum_scale": abs(float(dg[2]) - rec["P0"][2]) / pscale,
+                 "lz_drift_over_scale": abs(float(dg[3]) - rec["Lz0"]) /
+                 float(np.sum(d["m"] * np.hypot(x[:, 0], x[:, 1]) * np.linalg.norm(p, axis=1))),
+                 "form": rec["form"], "fell_back": fell_back}
+        if rec["done"] % CHECK_EVERY == 0 and rec["form"] == "surrogate":
+            ck = sc.steps_cyl_check_surrogate(sim.ctx, 1024)
+            chunk["check_median"], chunk["check_p999"] = float(ck[0]), float(ck[1])
+        if log:
+            log.write(json.dumps(chunk) + "\n")
+            log.flush()
+        rec["last"] = chunk
+        if args.ckpt and (rec["done"] % args.ckpt_every == 0 or rec["done"] == stop):
+            sim.checkpoint(args.ckpt)
+            with open(args.ckpt + ".json", "w") as fh:
+                json.dump(rec, fh)
+    line = {"workload": "production_run_n524288", "n": n, "n_cut": w.n_cut, "n0": w.n0, "steps_done": rec["done"],
+            "steps_total": w.nsteps, "fallbacks": rec["fallbacks"], "form_at_end": rec["form"],
+            "mean_step_ms": rec["step_ms_total"] / max(rec["done"], 1), "last": rec.get("last"),
+            "train": rec["train"]}
+    if rec["done"] >= w.nsteps:
+        # both forms against the FP64 oracle at the final state
+        import oracle
+        oracle.build()
+        x, v, a, t = sim.state()
+        idx = ics.subsample(n, 4096, seed=12345)
+        forms = {"plain": sc.STEPS_TAIL_FULL}
+        if rec["form"] == "surrogate":
+            forms = {"surrogate": sc.STEPS_TAIL_SURROGATE, "plain": sc.STEPS_TAIL_FULL}
+        got = {}
+        for name, tail in forms.items():
+            sc.steps_cyl_set_tail(sim.ctx, tail)
+            got[name] = sim.forces_subset(idx)
+        to0 = time.perf_counter()
+        ref = (oracle.pair_field(x, d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+               + oracle.background_field(x[idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)) / a ** 3
+        line["oracle_seconds"] = time.perf_counter() - to0
+        line["a_end"] = a
+        line["error_vs_oracle"] = {k: _err(g, ref) for k, g in got.items()}
+    sim.close()
+    if log:
+        log.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     import torch
     from paper_2602_20787_gb300 import ics, steps_cyl as sc
+    if args.workload == "production_run":
+        return run_production(args)
     if args.workload == "octree_accuracy_n65536":
         return run_octree_accuracy(args)
     if args.workload == "octree_r3_n1048576":
@@ -986,7 +1103,10 @@ def run_workload(args):
     sim = _ctx_for(sc, torch, w, d, sc.STEPS_FP32_KAHAN, check_particles=1024,
                    check_every=10 if w.name.startswith("production") else 50)
     a32, ms32 = _timed_forces(sc, torch, sim, reps)
-    line["fp32_kahan"] = {"pair_ms": ms32, "pair_images_per_s": pairs * 2 * w.n_cut / (ms32 * 1e-3)}
+    ev32 = sc.steps_cyl_last_eval(sim.ctx)
+    line["fp32_kahan"] = {"pair_ms": ms32, "pair_images_per_s": pairs * 2 * w.n_cut / (ms32 * 1e-3),
+                          "symmetric": ev32["symmetric"],
+                          "evaluated_roofline_frac": ev32["pairs_evaluated"] * 2 * w.n_cut / (ms32 * 1e-3) / peak}
     sc.steps_cyl_set_precision(sim.ctx, sc.STEPS_FP64)
     a64 = sim.forces_subset(idx)
     ms64 = sc.steps_cyl_last_timing(sim.ctx)[1]
@@ -1000,6 +1120,27 @@ def run_workload(args):
         ap, msp = _timed_forces(sc, torch, sim, reps)
         line["fp32_plain"] = {"pair_ms": msp, "pair_images_per_s": pairs * 2 * w.n_cut / (msp * 1e-3),
                               "error_vs_fp64": _err(ap[idx], a64)}
+        # every form against the FP64 oracle itself on the same 4,096 particles
+        # (pair field of eq. ComovingEquationsOfMotionCylindrical against all j,
+        # plus the background of eq. F_horiz), in the library's units (1 / a^3)
+        import oracle
+        oracle.build()
+        to0 = time.perf_counter()
+        o_pair = oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+        o_bg = oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
+        oracle_s = time.perf_counter() - to0
+        inv_a3 = 1.0 / w.a_start ** 3
+        o_tot, o_pair = (o_pair + o_bg) * inv_a3, o_pair * inv_a3
+        line["oracle_reference"] = {
+            "what": f"FP64 oracle pair field + background of {idx.size} particles (seed 12345) against all {n} j, "
+                    f"{2 * w.n_cut} images per pair", "cores": oracle.num_threads(), "seconds": oracle_s}
+        line["fp64_subset"]["error_vs_oracle"] = _err(a64, o_tot)
+        for key, a in (("fp32_kahan", a32[idx]), ("fp32_plain", ap[idx])):
+            line[key]["error_vs_oracle"] = _err(a, o_tot)
+            r = np.linalg.norm(a - o_tot, axis=1) / np.linalg.norm(o_pair, axis=1)
+            line[key]["error_vs_oracle_over_pair_term"] = {"median": float(np.median(r)),
+                                                           "p999": float(np.quantile(r, 0.999)),
+                                                           "max": float(r.max())}
         # pair-only errors: the same differences over the FP64 pair term alone (a context without the
         # background, whose FP64 subset gives the pair term; the background itself is FP64 in every form)
         nobg = _ctx_for(sc, torch, w, d, sc.STEPS_FP32_PLAIN, background=sc.STEPS_BG_OFF)
@@ -1020,23 +1161,16 @@ def run_workload(args):
             "pair_ms": mss, "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (mss * 1e-3),
             "executed_near_images_per_pair": 2 * w.n0 + 1, "speedup_vs_fp32_plain_sum": ms32 / mss,
             "error_vs_fp64": _err(asg[idx], a64)}
-        # per-pair pipe bound of the surrogate kernel: MUFU ops (near images,
-        # base rsqrt/rcp, the dR rsqrt) against 16/SM/clk, and the padded MLP
-        # flops of its mma.sync calls against the measured mma.sync rate
-        mufu = (2 * w.n0 + 1) + 4 + 2 + 1
-        flops = (8 * 2048 + 20 * 4096) / 32.0
-        clk = {"mufu": mufu / MUFU_RSQRT_PER_SM_CLK, "tensor_mma_sync": flops / MMA_SYNC_FLOP_PER_SM_CLK}
-        bound = max(clk, key=clk.get)
-        peak_pairs = props.multi_processor_count * 2070e6 / clk[bound]
-        line["surrogate"]["roofline"] = {
-            "bound": bound, "clk_per_pair_per_sm": clk, "peak_pairs_per_s": peak_pairs,
-            "achieved_pairs_per_s": pairs / (mss * 1e-3), "frac": pairs / (mss * 1e-3) / peak_pairs}
+        ev = sc.steps_cyl_last_eval(sim.ctx)
+        line["surrogate"]["roofline"] = surrogate_roofline(props.multi_processor_count, 2070.0, w.n0,
+                                                           ev["pairs_evaluated"], mss * 1e-3, ev["symmetric"])
         # correction-table tail: near images exact, tail from the GPU-built table
         sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
         nx, ny = 257, 33
         rt = sc.steps_cyl_build_tail_table(sim.ctx, nx, ny)
         sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
         atb, mst = _timed_forces(sc, torch, sim, reps + 1)
+        ev_t = sc.steps_cyl_last_eval(sim.ctx)
         mufu_t = (2 * w.n0 + 1) + 4 + 2 + 1   # near images, base rsqrt/rcp, the dR rsqrt
         peak_t = props.multi_processor_count * 2070e6 * MUFU_RSQRT_PER_SM_CLK / mufu_t
         import oracle
@@ -1058,7 +1192,8 @@ def run_workload(args):
             "speedup_vs_fp32_plain_sum": ms32 / mst, "speedup_vs_surrogate": mss / mst,
             "error_vs_fp64": _err(atb[idx], a64),
             "roofline": {"bound": "mufu", "mufu_ops_per_pair": mufu_t, "peak_pairs_per_s": peak_t,
-                         "achieved_pairs_per_s": pairs / (mst * 1e-3), "frac": pairs / (mst * 1e-3) / peak_t}}
+                         "achieved_pairs_evaluated_per_s": ev_t["pairs_evaluated"] / (mst * 1e-3),
+                         "frac": ev_t["pairs_evaluated"] / (mst * 1e-3) / peak_t, "symmetric": ev_t["symmetric"]}}
         sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
     if w.name.startswith("production") or w.name.startswith("plain_small") or w.name.startswith("lcdm"):
         steps = min(args.steps, w.nsteps) if w.nsteps else args.steps
@@ -1093,6 +1228,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=None, help="run another workload's measurement (one JSON line)")
+    ap.add_argument("--log", default=None, help="production_run: per-chunk JSON lines")
+    ap.add_argument("--ckpt", default=None, help="production_run: checkpoint path")
+    ap.add_argument("--ckpt-every", type=int, default=250, help="production_run: steps between checkpoints")
+    ap.add_argument("--resume", default=None, help="production_run: continue from this checkpoint")
+    ap.add_argument("--steps-limit", type=int, default=0, help="production_run: stop after this many steps")
     args = ap.parse_args()
     if args.workload:
         sys.exit(run_workload(args))

@@ -168,6 +168,18 @@ int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
  * its pair kernel in milliseconds (CUDA events on the context stream). */
 int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
 
+/* The last direct force evaluation in more detail (out: 4 doubles, host):
+ * out[0] = pair-images delivered (as steps_cyl_last_timing), out[1] = pairs the
+ * pair kernel evaluated, out[2] = its device time in ms, out[3] = 1 when it was
+ * a symmetric kernel. The FP32 direct forms of an S1xR2 context whose rows are
+ * not shared with other ranks evaluate each unordered pair of particles once
+ * and add it to both (Newton's third law; the window of eq. ForceCylindrical is
+ * symmetric in i and j), so out[1] is n (n - 1) / 2 plus the pairs inside each
+ * block of 128 rows, which are taken both ways; the row kernels evaluate
+ * (rows) x (n - 1) ordered pairs. The octree reports its interactions in
+ * steps_cyl_tree_stats instead. */
+int steps_cyl_last_eval(steps_cyl_ctx* ctx, double out[4]);
+
 /* ---- row sharding (one rank per GPU) ---------------------------------------
  * Sect. 2.4 runs the direct force on many GPUs with MPI. Here the rows i of the
  * pair sum are split across ranks: each rank's context holds the whole particle

@@ -124,6 +124,34 @@ __device__ __forceinline__ void radial_correct(const RadialCorr& R, double x, do
   if (R.sph) g2 -= D * z / rho;
 }
 
+// The common end of a finalize: the pair sums (sx, sy, sz) scaled to the
+// comoving field g = a^3 (pair + background), the radial correction, the
+// background; g stored, optionally p += g K, optionally a = g / a^3 written.
+__device__ __forceinline__ void finish_particle(int i, double sx, double sy, double sz, double pair_scale,
+                                                const BgParams& bg, const double* __restrict__ x,
+                                                const double* __restrict__ y, const double* __restrict__ z,
+                                                double* __restrict__ gx, double* __restrict__ gy,
+                                                double* __restrict__ gz, double K, double* __restrict__ px,
+                                                double* __restrict__ py, double* __restrict__ pz, double inv_a3,
+                                                double* __restrict__ ox, double* __restrict__ oy,
+                                                double* __restrict__ oz, int* __restrict__ err, const RadialCorr& rc) {
+  double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
+  radial_correct(rc, x[i], y[i], z[i], g0, g1, g2);
+  add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
+  if (err && (!isfinite(g0) || !isfinite(g1) || !isfinite(g2))) atomicOr(err, kErrNonFinite);
+  gx[i] = g0; gy[i] = g1; gz[i] = g2;
+  if (px) {
+    px[i] += g0 * K;
+    py[i] += g1 * K;
+    pz[i] += g2 * K;
+  }
+  if (ox) {
+    ox[i] = g0 * inv_a3;
+    oy[i] = g1 * inv_a3;
+    oz[i] = g2 * inv_a3;
+  }
+}
+
 static __global__ void finalize_kernel(const double* __restrict__ part, int n, int NT, long long U, int C,
                                 double pair_scale, BgParams bg, const double* __restrict__ x,
                                 const double* __restrict__ y, const double* __restrict__ z, double* __restrict__ gx,
@@ -154,21 +182,24 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
       sz += q[2 * kBI + l];
     }
   }
-  double g0 = pair_scale * sx, g1 = pair_scale * sy, g2 = pair_scale * sz;
-  radial_correct(rc, x[i], y[i], z[i], g0, g1, g2);
-  add_background(bg, x[i], y[i], z[i], g0, g1, g2, err);
-  if (err && (!isfinite(g0) || !isfinite(g1) || !isfinite(g2))) atomicOr(err, kErrNonFinite);
-  gx[i] = g0; gy[i] = g1; gz[i] = g2;
-  if (px) {
-    px[i] += g0 * K;
-    py[i] += g1 * K;
-    pz[i] += g2 * K;
-  }
-  if (ox) {
-    ox[i] = g0 * inv_a3;
-    oy[i] = g1 * inv_a3;
-    oz[i] = g2 * inv_a3;
-  }
+  finish_particle(i, sx, sy, sz, pair_scale, bg, x, y, z, gx, gy, gz, K, px, py, pz, inv_a3, ox, oy, oz, err, rc);
+}
+
+// Finalize from the fixed-point accumulators of the symmetric pair kernels
+// (pair_sym.cuh): acc[3][n] in units of 1 / scale.
+static __global__ void finalize_fix_kernel(const unsigned long long* __restrict__ acc, int n, double inv_scale,
+                                           double pair_scale, BgParams bg, const double* __restrict__ x,
+                                           const double* __restrict__ y, const double* __restrict__ z,
+                                           double* __restrict__ gx, double* __restrict__ gy, double* __restrict__ gz,
+                                           double K, double* __restrict__ px, double* __restrict__ py,
+                                           double* __restrict__ pz, int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double sx = (double)(long long)acc[i] * inv_scale;
+  const double sy = (double)(long long)acc[(long long)n + i] * inv_scale;
+  const double sz = (double)(long long)acc[2 * (long long)n + i] * inv_scale;
+  finish_particle(i, sx, sy, sz, pair_scale, bg, x, y, z, gx, gy, gz, K, px, py, pz, 1.0, nullptr, nullptr, nullptr,
+                  err, RadialCorr{nullptr, 0, 0.0, 0});
 }
 
 // First half of a KDK step: p += g K1; x += p D; z wrapped into [0, L); repack.

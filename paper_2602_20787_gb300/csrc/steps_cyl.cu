@@ -34,6 +34,7 @@
 #include "tail_table.cuh"
 #include "octree.cuh"
 #include "r3_pair.cuh"
+#include "pair_sym.cuh"
 
 using namespace steps;
 
@@ -248,6 +249,12 @@ struct steps_cyl_ctx {
   // the CTA counts C, SC, TC are those of this range, capped at Ccap etc.
   int b0 = 0, nbo = 0, k0 = 0, k1 = 0;
   int Ccap = 0, SCcap = 0, TCcap = 0;
+  // symmetric (Newton's third law) evaluation into fixed-point accumulators
+  unsigned long long* facc = nullptr;  // [3][n]
+  double fix_scale = 0.0;              // 2^S
+  bool fix_ready = false, fix_ok = false;
+  long long Usym = 0;
+  int SYC = 0, SYSC = 0, SYTC = 0;     // CTAs of the symmetric plain / surrogate / table kernels
   // row sharding
   bool shard = false;
   int shard_rank = 0, shard_world = 1, chunk = 0;
@@ -309,6 +316,8 @@ struct steps_cyl_ctx {
   } tr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double last_images = 0.0;
+  double last_pairs = 0.0;   // pairs the last pair kernel evaluated
+  bool last_sym = false;     // ... with the symmetric kernels
   bool timed = false;
 };
 
@@ -481,10 +490,11 @@ int read_and_clear_err(steps_cyl_ctx* c, int* out) {
 }
 
 int device_error(int e) {
-  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
+  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
               (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range " : "",
               (e & kErrTreeRange) ? "particle outside the octree root " : "",
-              (e & kErrTreeStack) ? "octree walk stack overflow" : "");
+              (e & kErrTreeStack) ? "octree walk stack overflow " : "",
+              (e & kErrFixRange) ? "pair sum beyond the fixed-point range" : "");
 }
 
 // Calls that need every row of the context current refuse a sharded context.
@@ -944,6 +954,44 @@ RadialCorr radial_corr(const steps_cyl_ctx* c) {
   return r;
 }
 
+// Scale of the fixed-point accumulators of the symmetric kernels, from a bound
+// on any particle's pair sum |sum_j m_j v_ij| (positions in units of L): one
+// image's softened force is at most 4 / hh^2 <= (L / h_min)^2 (the peak of the
+// spline of eq. Force_spline_kernel with hh >= 2 h_min), the other images of
+// the window add at most 2 sum_k 1 / (k - 1/2)^2 < 10, and the masses add up
+// to M. With a factor 16 to spare, 2^S = 2^61 / (16 B) rounded down to a power
+// of two. Below 2^40 (a softening so small that the unit 2^-S would not be far
+// below FP32 rounding of typical sums) the row kernels are used instead.
+int fix_scale(steps_cyl_ctx* c) {
+  std::vector<double> hm(c->n), hh(c->n);
+  CK(cudaMemcpyAsync(hm.data(), c->m, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hh.data(), c->h, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double M = 0.0, hmin = INFINITY;
+  for (int k = 0; k < c->n; ++k) {
+    M += std::fabs(hm[k]);
+    hmin = std::min(hmin, hh[k]);
+  }
+  const double q = c->p.L / hmin;
+  const double B = M * (q * q + 10.0);
+  const int S = (int)std::floor(57.0 - std::log2(B));
+  c->fix_ok = std::isfinite(B) && B > 0 && S >= 40 && S <= 1000;
+  c->fix_scale = c->fix_ok ? std::ldexp(1.0, S) : 0.0;
+  c->fix_ready = true;
+  return STEPS_OK;
+}
+
+#ifndef STEPS_SYMMETRIC
+#define STEPS_SYMMETRIC 1  // evaluate each unordered pair once (build-time switch)
+#endif
+
+// The FP32 direct forms of an S1xR2 context take the symmetric kernels, unless
+// its rows are shared with other ranks (a rank has no j side for rows it does
+// not own).
+bool use_sym(const steps_cyl_ctx* c) {
+  return STEPS_SYMMETRIC && (!c->shard || c->shard_world == 1) && !is_r3(c) && c->fix_ok;
+}
+
 // The pair form of the next force evaluation: FP64, the selected modelled tail
 // when it is accepted, else the plain image sum (for the infinite window, which
 // has none, the correction table built at init).
@@ -968,6 +1016,8 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
     CK(cudaEventRecord(c->e1, c->st));
     c->timed = true;
     c->last_images = c->tr.interactions;
+    c->last_pairs = c->tr.interactions;
+    c->last_sym = false;
     finalize_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
         c->part, c->n, 0, c->U, c->C, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
         kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, 1.0, nullptr, nullptr, nullptr,
@@ -977,6 +1027,70 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   }
   const Form form = force_form(c);
   if (form == Form::PLAIN && is_inf(c)) return fail(STEPS_ENOSURROGATE, "the infinite window has no correction table");
+  if (!c->fix_ready) {
+    int rc = fix_scale(c);
+    if (rc) return rc;
+  }
+  if (form != Form::FP64 && use_sym(c)) {
+    CK(cudaMemsetAsync(c->facc, 0, sizeof(unsigned long long) * 3 * (size_t)c->n, c->st));
+    CK(cudaEventRecord(c->e0, c->st));
+    const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+    const FixAcc F{c->facc, c->n, c->fix_scale, c->err};
+    const int nc = c->p.n_cut;
+    if (form == Form::SURROGATE) {
+      if (is_inf(c) && kahan)
+        pair_sym_surr_kernel<true, true><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym, c->SYSC,
+                                                                     c->surr_lanes, c->surr, F);
+      else if (is_inf(c))
+        pair_sym_surr_kernel<false, true><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym, c->SYSC,
+                                                                      c->surr_lanes, c->surr, F);
+      else if (kahan)
+        pair_sym_surr_kernel<true, false><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
+                                                                      c->SYSC, c->surr_lanes, c->surr, F);
+      else
+        pair_sym_surr_kernel<false, false><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
+                                                                       c->SYSC, c->surr_lanes, c->surr, F);
+      CKLAUNCH("pair_sym_surrogate");
+    } else if (form == Form::TABLE) {
+      if (is_inf(c) && kahan)
+        pair_sym_table_kernel<true, true><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym,
+                                                                      c->SYTC, c->tab, c->tab_const, F);
+      else if (is_inf(c))
+        pair_sym_table_kernel<false, true><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym,
+                                                                       c->SYTC, c->tab, c->tab_const, F);
+      else if (kahan)
+        pair_sym_table_kernel<true, false><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
+                                                                       c->SYTC, c->tab, c->tab_const, F);
+      else
+        pair_sym_table_kernel<false, false><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
+                                                                        c->SYTC, c->tab, c->tab_const, F);
+      CKLAUNCH("pair_sym_table");
+    } else if (kahan) {
+      pair_sym_kernel<true><<<c->SYC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym, c->SYC, F);
+      CKLAUNCH("pair_sym_kahan");
+    } else {
+      pair_sym_kernel<false><<<c->SYC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym, c->SYC, F);
+      CKLAUNCH("pair_sym_plain");
+    }
+    CK(cudaEventRecord(c->e1, c->st));
+    c->timed = true;
+    c->last_images = (double)c->n * (double)(c->n - 1) * images_per_pair(c);
+    {  // unordered pairs across blocks once, ordered pairs within a block both ways
+      double within = 0.0;
+      for (int b = 0; b < c->NB; ++b) {
+        const double nb = (double)(std::min(c->n, (b + 1) * kBI) - b * kBI);
+        within += nb * (nb - 1.0);
+      }
+      const double all = (double)c->n * (double)(c->n - 1);
+      c->last_pairs = 0.5 * (all - within) + within;
+      c->last_sym = true;
+    }
+    finalize_fix_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
+        c->facc, c->n, 1.0 / c->fix_scale, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
+        kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, c->err);
+    CKLAUNCH("finalize_fix");
+    return STEPS_OK;
+  }
   CK(cudaEventRecord(c->e0, c->st));
   if (form == Form::FP64) {
     int rc = launch_fp64(c, nullptr, c->n, c->part);  // never sharded
@@ -1029,6 +1143,8 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   CK(cudaEventRecord(c->e1, c->st));
   c->timed = true;
   c->last_images = (double)(c->k1 - c->k0) * (double)(c->n - 1) * images_per_pair(c);
+  c->last_pairs = (double)(c->k1 - c->k0) * (double)(c->n - 1);
+  c->last_sym = false;
   const int NT = form == Form::FP64 ? 0 : c->NT;
   const int ctas = form == Form::SURROGATE ? c->SC : form == Form::TABLE ? c->TC : c->C;
   // rows [k0, k1): every row, or the rows this context owns when they are sharded
@@ -1149,6 +1265,7 @@ void release(steps_cyl_ctx* c) {
   if (c->tab_arr) cudaFreeArray(c->tab_arr);
   cudaFree(c->chk);
   cudaFree(c->shard_off);
+  cudaFree(c->facc);
   {
     auto& T = c->tr;
     void* ptrs[] = {T.key[0], T.key[1], T.val[0], T.val[1], T.hist, T.offs, T.u4, T.u4s, T.zt, T.sA, T.sB,
@@ -1877,6 +1994,16 @@ int allocate_context(steps_cyl_ctx* c) {
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tocc, pair_fp32_table_kernel<true>, kBI, 0));
   c->TCcap = sms * std::max(tocc, 1) * STEPS_CTA_MULT;
   set_rows(c, 0, c->NB);
+  // the symmetric kernels share the upper triangle of the block grid
+  c->Usym = (long long)c->NB * (c->NB + 1) / 2;
+  int yocc = 0, ysocc = 0, ytocc = 0;
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&yocc, pair_sym_kernel<true>, kBI, 0));
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ysocc, pair_sym_surr_kernel<true, false>, kBI, 0));
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ytocc, pair_sym_table_kernel<true, false>, kBI, 0));
+  c->SYC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(yocc, 1) * STEPS_CTA_MULT);
+  c->SYSC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ysocc, 1) * STEPS_CTA_MULT);
+  c->SYTC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ytocc, 1) * STEPS_CTA_MULT);
+  CKA(cudaMalloc(&c->facc, sizeof(unsigned long long) * nb * 3));
   c->part_elems = std::max((size_t)(c->NB + std::max({c->C, c->SC, c->TC})) * 3 * kBI, nb * 3);
   CKA(cudaMalloc(&c->part, sizeof(double) * c->part_elems));
 
@@ -2322,6 +2449,21 @@ int steps_cyl_last_timing(steps_cyl_ctx* c, double* pair_images, double* pair_ms
   CK(cudaEventElapsedTime(&ms, c->e0, c->e1));
   if (pair_images) *pair_images = c->last_images;
   if (pair_ms) *pair_ms = ms;
+  return STEPS_OK;
+}
+
+int steps_cyl_last_eval(steps_cyl_ctx* c, double out[4]) {
+  g_last_error.clear();
+  if (!c || !out) return fail(STEPS_EINVAL, "NULL argument");
+  if (!c->timed) return fail(STEPS_EINVAL, "no force evaluation yet");
+  DeviceGuard guard(c->dev);
+  CK(cudaEventSynchronize(c->e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->e0, c->e1));
+  out[0] = c->last_images;
+  out[1] = c->last_pairs;
+  out[2] = ms;
+  out[3] = c->last_sym ? 1.0 : 0.0;
   return STEPS_OK;
 }
 

@@ -83,6 +83,9 @@ WORKLOADS = {
                                  a_start=0.02, a_end=0.02),
     "production_n524288": Workload("production_n524288", 524288, 4, 64, comoving=True, displaced=True,
                                    eps_law="ratio8", a_start=0.02, a_end=1.0, nsteps=1000),
+    # the production-shaped law at a size that profiles quickly
+    "production_n65536": Workload("production_n65536", 65536, 4, 64, comoving=True, displaced=True,
+                                  eps_law="ratio8", a_start=0.02, a_end=1.0, nsteps=1000),
 }
 
 

@@ -44,6 +44,7 @@ _EXPORTS = [
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
     "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
+    "steps_cyl_last_eval",
 ]
 
 STEPS_SURR_NW = 1250
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_set_precision.argtypes = [p, i32]
     L.steps_cyl_diagnostics.argtypes = [p, p]
     L.steps_cyl_last_timing.argtypes = [p, p, p]
+    L.steps_cyl_last_eval.argtypes = [p, p]
     L.steps_cyl_free.argtypes = [p]
     L.steps_cyl_strerror.argtypes = [ctypes.c_int]
     L.steps_cyl_strerror.restype = ctypes.c_char_p
@@ -280,6 +282,15 @@ def steps_cyl_last_timing(ctx):
     imgs, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().steps_cyl_last_timing(ctx, ctypes.byref(imgs), ctypes.byref(ms)))
     return imgs.value, ms.value
+
+
+def steps_cyl_last_eval(ctx) -> dict:
+    """The last direct force evaluation: pair-images delivered, pairs the
+    kernel evaluated, its device ms, and whether it was a symmetric kernel."""
+    out = np.zeros(4)
+    _check(load().steps_cyl_last_eval(ctx, _ptr(out)))
+    return {"pair_images": float(out[0]), "pairs_evaluated": float(out[1]), "pair_ms": float(out[2]),
+            "symmetric": bool(out[3])}
 
 
 def steps_cyl_free(ctx):

@@ -41,7 +41,8 @@ extern "C" {
 #define STEPS_ECUDA (-2)                /* a CUDA runtime call failed */
 #define STEPS_ENOMEM (-3)               /* device allocation failed */
 #define STEPS_EDEVICE (-4)              /* the device error word was set (non-finite force, particle beyond the background
-                                         * table, particle outside the octree's root cube, octree walk stack overflow) */
+                                         * table, particle outside the octree's root cube, octree walk stack overflow,
+                                         * a pair sum beyond the range of the symmetric kernels' fixed-point sums) */
 #define STEPS_ESURROGATE_REJECTED (-5)  /* surrogate error above its bound: the plain image sum was used instead */
 #define STEPS_ENOSURROGATE (-6)         /* modelled tail requested but no accepted network / correction table is loaded */
 
@@ -125,7 +126,7 @@ int steps_cyl_init(steps_cyl_ctx** out, const steps_cyl_params* p, int64_t n, co
 /* Accelerations at the current positions: the pair term of eq.
  * ComovingEquationsOfMotionCylindrical divided by a^3 plus the background term
  * (also divided by a^3), without the Hubble drag. ax, ay, az: length n, host or
- * device, written in full. */
+ * device, written in full (a sharded context writes zeros outside its rows). */
 int steps_cyl_forces(steps_cyl_ctx* ctx, double* ax, double* ay, double* az);
 
 /* Same as steps_cyl_forces for the ni particles listed in idx (host or device
@@ -163,9 +164,11 @@ int steps_cyl_set_precision(steps_cyl_ctx* ctx, int32_t precision);
  * out[7] = total mass. out: 8 doubles of host memory. */
 int steps_cyl_diagnostics(steps_cyl_ctx* ctx, double out[8]);
 
-/* Pair-images evaluated by the last force evaluation, counted as the paper's
- * window (2 Ncut per pair, 2 Ncut - 1 when r_z = 0 mod L), and the device time of
- * its pair kernel in milliseconds (CUDA events on the context stream). */
+/* Pair-images of the last force evaluation, counted as the paper's window
+ * over every ordered pair (2 Ncut per pair, 2 Ncut - 1 when r_z = 0 mod L),
+ * and the device time of its pair kernel in milliseconds (CUDA events on the
+ * context stream). The symmetric kernels deliver these while evaluating each
+ * unordered pair once; steps_cyl_last_eval gives the count they evaluated. */
 int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_ms);
 
 /* The last direct force evaluation in more detail (out: 4 doubles, host):

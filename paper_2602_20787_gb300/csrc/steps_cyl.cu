@@ -1340,10 +1340,11 @@ void build_lanes(const float* P, SurrLane lanes[32]) {
       const int o = 8 * nb + g;
       const float w0 = 2 * t < 3 ? W1[o * 3 + 2 * t] : 0.f, w1 = 2 * t + 1 < 3 ? W1[o * 3 + 2 * t + 1] : 0.f;
       s.w1[nb] = pack_half2(w0, w1);
-      s.b1[2 * nb] = b1[8 * nb + 2 * t];
-      s.b1[2 * nb + 1] = b1[8 * nb + 2 * t + 1];
-      s.b2[2 * nb] = b2[8 * nb + 2 * t];
-      s.b2[2 * nb + 1] = b2[8 * nb + 2 * t + 1];
+      // accumulator seeds: columns 2t, 2t + 1 of rows g and g + 8 of n-block nb
+      for (int q = 0; q < 4; ++q) {
+        s.c1[4 * nb + q] = b1[8 * nb + 2 * t + (q & 1)];
+        s.c2[4 * nb + q] = b2[8 * nb + 2 * t + (q & 1)];
+      }
       for (int kb = 0; kb < 2; ++kb) {
         const int k = 16 * kb + 2 * t;
         s.w2[(kb * 4 + nb) * 2] = pack_half2(W2[o * kH + k], W2[o * kH + k + 1]);
@@ -1357,8 +1358,7 @@ void build_lanes(const float* P, SurrLane lanes[32]) {
       s.w3[kb * 2] = pack_half2(W3[o * kH + k], W3[o * kH + k + 1]);
       s.w3[kb * 2 + 1] = pack_half2(W3[o * kH + k + 8], W3[o * kH + k + 9]);
     }
-    s.b3[0] = b3[0];
-    s.b3[1] = b3[1];
+    for (int q = 0; q < 4; ++q) s.c3[q] = b3[q & 1];
   }
 }
 
@@ -1375,6 +1375,7 @@ int install_surrogate(steps_cyl_ctx* c, const float* P) {
   c->surr.dR_max = P[kNW + 4];
   c->surr.inv_dR_max = 1.0f / P[kNW + 4];
   c->surr.n0 = c->p.n0;
+  surr_const_finish(c->surr, c->p.n_cut);
   c->surr_params.assign(P, P + STEPS_SURR_NPARAM);
   return STEPS_OK;
 }
@@ -1730,7 +1731,8 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
   CK(cudaCreateTextureObject(&c->tab.tex, &res, &td, nullptr));
   c->tab.hx = 0.5f * (nx - 1);
   c->tab.hy = 0.5f * (ny - 1);
-  c->tab_const = SurrConst{0.f, 0.f, 1.f, 1.f, (float)(1.0 / dR_max), (float)dR_max, c->p.n0};
+  c->tab_const = SurrConst{0.f, 0.f, 1.f, 1.f, (float)(1.0 / dR_max), (float)dR_max, c->p.n0, 0.f, 0.f, 0.f, 0.f};
+  surr_const_finish(c->tab_const, c->p.n_cut);
   c->tab_nx = nx;
   c->tab_ny = ny;
   c->tab_dR_max = dR_max;

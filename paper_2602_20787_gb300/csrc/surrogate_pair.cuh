@@ -23,25 +23,29 @@
 namespace steps {
 
 // Per-lane B fragments and accumulator seeds, prepared on the host from the
-// FP32 weights (W1 as m16n8k8 fragments, W2 and W3 as m16n8k16 fragments).
+// FP32 weights (W1 as m16n8k8 fragments, W2 and W3 as m16n8k16 fragments). The
+// seeds are the biases laid out as the mma's C operand (c0..c3 of lane (g, t)
+// hold columns 2t, 2t + 1 of rows g and g + 8), so one 128-bit load yields a C
+// operand with no register moves.
 struct SurrLane {
   uint32_t w1[4];   // n-block nb: {W1[8nb+g][2t], W1[8nb+g][2t+1]} (input 2 at t = 1, zero beyond)
   uint32_t w2[16];  // [kb][nb][2]
   uint32_t w3[4];   // [kb][2], rows 0, 1 of W3 only
-  float b1[8];      // [nb][2]: b1[8nb+2t], b1[8nb+2t+1]
-  float b2[8];
-  float b3[2];
-  float pad[6];
+  float c1[16];     // [nb][4]: b1[8nb+2t], b1[8nb+2t+1], b1[8nb+2t], b1[8nb+2t+1]
+  float c2[16];
+  float c3[4];      // b3[0], b3[1], b3[0], b3[1]
 };
-static_assert(sizeof(SurrLane) == 48 * 4, "SurrLane layout");
+static_assert(sizeof(SurrLane) == 60 * 4, "SurrLane layout");
 
-// Lane L's SurrLane lives at wt[L * kSurrStride ...] in shared memory: rows of
-// 52 words (48 + 4 pad), so the 16-byte loads of a quarter warp (8 lanes, row
-// offsets 20 L mod 32 banks) hit 32 distinct banks. Each layer's fragments are
-// read once per network call with 128-bit volatile shared loads: kept out of
-// the register file across the j loop, they leave room for resident warps.
+// Lane L's SurrLane lives at wt[L * kSurrStride ...] in shared memory. A row
+// stride of 60 words (28 mod 32) puts the 16-byte loads of a quarter warp (8
+// lanes) on 32 distinct banks. Each layer's fragments are read once per
+// network call with 128-bit volatile shared loads: kept out of the register
+// file across the j loop, they leave room for resident warps.
 constexpr int kSurrWords = sizeof(SurrLane) / 4;
-constexpr int kSurrStride = kSurrWords + 4;
+constexpr int kSurrStride = kSurrWords;
+static_assert(kSurrStride % 32 == 4 || kSurrStride % 32 == 12 || kSurrStride % 32 == 20 || kSurrStride % 32 == 28,
+              "conflict-free 16-byte loads");
 struct SurrW {
   const uint32_t* p;  // wt + lane * kSurrStride (16-byte aligned)
   __device__ __forceinline__ uint4 ld4(int w) const {
@@ -51,8 +55,12 @@ struct SurrW {
                  : "r"((uint32_t)__cvta_generic_to_shared(p + w)));
     return v;
   }
+  __device__ __forceinline__ float4 ldc(int w) const {
+    const uint4 v = ld4(w);
+    return make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w));
+  }
 };
-constexpr int kW1 = 0, kW2 = 4, kW3 = 20, kB1 = 24, kB2 = 32, kB3 = 40;
+constexpr int kW1 = 0, kW2 = 4, kW3 = 20, kC1 = 24, kC2 = 40, kC3 = 56;
 
 // Stage the 32 lanes' fragments into shared memory (all threads of the block
 // take part; ends with a barrier).
@@ -69,17 +77,33 @@ struct SurrConst {
   float mu0, mu1, sc0, sc1;
   float inv_dR_max, dR_max;
   int n0;
+  // derived on the host (surr_const_finish): A = n0 + 1/2, 2 / A, 2 / dR_max,
+  // and the far end of the finite window, n_cut - 1/2
+  float A, two_over_A, two_inv_dR_max, fnh;
 };
 
-__device__ __forceinline__ void mma_k8(float d[4], uint32_t a0, uint32_t a1, uint32_t b0, const float c[4]) {
+__host__ __device__ __forceinline__ void surr_const_finish(SurrConst& S, int n_cut) {
+  S.A = (float)S.n0 + 0.5f;
+  S.two_over_A = 2.0f / S.A;
+  S.two_inv_dR_max = 2.0f * S.inv_dR_max;
+  S.fnh = (float)n_cut - 0.5f;
+}
+
+__device__ __forceinline__ void mma_k8(float d[4], uint32_t a0, uint32_t a1, uint32_t b0, const float4& c) {
   asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%9,%10};"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a0), "r"(a1), "r"(b0), "f"(c[0]), "f"(c[1]), "f"(c[2]), "f"(c[3]));
+      : "r"(a0), "r"(a1), "r"(b0), "f"(c.x), "f"(c.y), "f"(c.z), "f"(c.w));
 }
-__device__ __forceinline__ void mma_k16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1, const float c[4]) {
+__device__ __forceinline__ void mma_k16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1, const float4& c) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]), "f"(c[3]));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c.x), "f"(c.y), "f"(c.z), "f"(c.w));
+}
+// d += A B (the accumulator stays in place)
+__device__ __forceinline__ void mma_k16_acc(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 // ReLU and pack two FP32 values as f16x2 (lo in the lower half)
 __device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
@@ -144,17 +168,14 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
   uint32_t a2[NT][2][4];
   {
     const uint4 w1 = W.ld4(kW1);
-    const uint4 ba = W.ld4(kB1), bb = W.ld4(kB1 + 4);
     const uint32_t wv[4] = {w1.x, w1.y, w1.z, w1.w};
-    const float b[8] = {f32(ba.x), f32(ba.y), f32(ba.z), f32(ba.w), f32(bb.x), f32(bb.y), f32(bb.z), f32(bb.w)};
+    const float4 cb[4] = {W.ldc(kC1), W.ldc(kC1 + 4), W.ldc(kC1 + 8), W.ldc(kC1 + 12)};
 #pragma unroll
     for (int tl = 0; tl < NT; ++tl) {
       float d1[4][4];
 #pragma unroll
-      for (int nb = 0; nb < 4; ++nb) {
-        const float c[4] = {b[2 * nb], b[2 * nb + 1], b[2 * nb], b[2 * nb + 1]};
-        mma_k8(d1[nb], in[tl >> 1][2 * (tl & 1)], in[tl >> 1][2 * (tl & 1) + 1], wv[nb], c);
-      }
+      for (int nb = 0; nb < 4; ++nb)
+        mma_k8(d1[nb], in[tl >> 1][2 * (tl & 1)], in[tl >> 1][2 * (tl & 1) + 1], wv[nb], cb[nb]);
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
         a2[tl][kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
@@ -173,16 +194,14 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
       const uint4 v = W.ld4(kW2 + 4 * q);
       w2[4 * q] = v.x; w2[4 * q + 1] = v.y; w2[4 * q + 2] = v.z; w2[4 * q + 3] = v.w;
     }
-    const uint4 ba = W.ld4(kB2), bb = W.ld4(kB2 + 4);
-    const float b[8] = {f32(ba.x), f32(ba.y), f32(ba.z), f32(ba.w), f32(bb.x), f32(bb.y), f32(bb.z), f32(bb.w)};
+    const float4 cb[4] = {W.ldc(kC2), W.ldc(kC2 + 4), W.ldc(kC2 + 8), W.ldc(kC2 + 12)};
 #pragma unroll
     for (int tl = 0; tl < NT; ++tl) {
       float d2[4][4];
 #pragma unroll
       for (int nb = 0; nb < 4; ++nb) {
-        const float c[4] = {b[2 * nb], b[2 * nb + 1], b[2 * nb], b[2 * nb + 1]};
-        mma_k16(d2[nb], a2[tl][0], w2[2 * nb], w2[2 * nb + 1], c);
-        mma_k16(d2[nb], a2[tl][1], w2[2 * (4 + nb)], w2[2 * (4 + nb) + 1], d2[nb]);
+        mma_k16(d2[nb], a2[tl][0], w2[2 * nb], w2[2 * nb + 1], cb[nb]);
+        mma_k16_acc(d2[nb], a2[tl][1], w2[2 * (4 + nb)], w2[2 * (4 + nb) + 1]);
       }
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
@@ -196,12 +215,12 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
   // layer 3: [16 x 32] x [32 x 8] per tile (columns 0, 1 used)
   float out[NT][4];
   {
-    const uint4 w3 = W.ld4(kW3), b3 = W.ld4(kB3);
-    const float c3[4] = {f32(b3.x), f32(b3.y), f32(b3.x), f32(b3.y)};
+    const uint4 w3 = W.ld4(kW3);
+    const float4 c3 = W.ldc(kC3);
 #pragma unroll
     for (int tl = 0; tl < NT; ++tl) {
       mma_k16(out[tl], a3[tl][0], w3.x, w3.y, c3);
-      mma_k16(out[tl], a3[tl][1], w3.z, w3.w, out[tl]);
+      mma_k16_acc(out[tl], a3[tl][1], w3.z, w3.w);
     }
   }
   // output column n carries output (n & 1), so lane (g, t) holds both outputs
@@ -217,47 +236,145 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
   }
 }
 
-// FP32 base of both sides of the tail at once (packed: lane 0 the side beyond
-// +n0, lane 1 the side beyond -n0), each over the cells [lo, hi]: the SR and SZ
-// parts and the near-end reciprocal distance il. Per side, with
-// i(x) = (x^2 + dR^2)^(-1/2): the integrals (hi^2 - lo^2) il^2 ih^2 / (hi ih + lo il)
-// (of i^3, written without cancellation) and il - ih (of x i^3), minus 1/24 of
-// the end-point derivative differences, d/dx i^3 = -3 x i^5 and
-// d/dx (x i^3) = i^3 - 3 x^2 i^5.
-__device__ __forceinline__ void side_base_x2(float R2, u64 LO, u64 HI, u64& SR, u64& SZ, u64& IL) {
-  const u64 R2x = pk(R2, R2);
-  float a, b, c, d;
-  upk(fma2(LO, LO, R2x), a, b);
-  upk(fma2(HI, HI, R2x), c, d);
-  IL = pk(rsq(a), rsq(b));
-  const u64 IH = pk(rsq(c), rsq(d));
+// FP32 base of both sides of the tail at once (lane a: the side beyond +n0,
+// lane b: the side beyond -n0), each over the cells [lo, hi]. With
+// i(x) = (x^2 + dR^2)^(-1/2), per side: the integrals
+// (hi^2 - lo^2) il^2 ih^2 / (hi ih + lo il) (of i^3, written without
+// cancellation) and il - ih (of x i^3), minus 1/24 of the end-point derivative
+// differences, d/dx i^3 = -3 x i^5 and d/dx (x i^3) = i^3 - 3 x^2 i^5. Returns
+// the SR parts of both sides added, the SZ parts subtracted (the z part is odd
+// in dz), and the near-end il of side a. The packed work stays packed; the
+// constants enter through scalar FMAs with immediate operands, so that no
+// constant pair has to be assembled in registers.
+__device__ __forceinline__ void tail_base_fp32(float R2, float lo_a, float lo_b, float hi_a, float hi_b, float& br,
+                                               float& bz, float& il_a) {
+  const u64 LO = pk(lo_a, lo_b), HI = pk(hi_a, hi_b);
+  const u64 IL = pk(rsq(fmaf(lo_a, lo_a, R2)), rsq(fmaf(lo_b, lo_b, R2)));
+  const u64 IH = pk(rsq(fmaf(hi_a, hi_a, R2)), rsq(fmaf(hi_b, hi_b, R2)));
   const u64 IL2 = mul2(IL, IL), IH2 = mul2(IH, IH);
   float e, f;
   upk(fma2(HI, IH, mul2(LO, IL)), e, f);
   const u64 IR = mul2(mul2(mul2(sub2(HI, LO), add2(HI, LO)), mul2(IL2, IH2)), pk(rcp_approx(e), rcp_approx(f)));
   const u64 P = mul2(LO, mul2(mul2(IL2, IL2), IL));  // lo il^5
   const u64 Q = mul2(HI, mul2(mul2(IH2, IH2), IH));  // hi ih^5
-  SR = fma2(sub2(Q, P), pk(0.125f, 0.125f), IR);
   const u64 D3 = sub2(mul2(IH2, IH), mul2(IL2, IL));
   const u64 E = sub2(mul2(HI, Q), mul2(LO, P));
-  SZ = fma2(E, pk(0.125f, 0.125f), fma2(D3, pk(-1.0f / 24.0f, -1.0f / 24.0f), sub2(IL, IH)));
+  float qp_a, qp_b, ir_a, ir_b, d3_a, d3_b, e_a, e_b, d_a, d_b, il_b;
+  upk(sub2(Q, P), qp_a, qp_b);
+  upk(IR, ir_a, ir_b);
+  upk(D3, d3_a, d3_b);
+  upk(E, e_a, e_b);
+  upk(sub2(IL, IH), d_a, d_b);
+  upk(IL, il_a, il_b);
+  br = fmaf(qp_a, 0.125f, ir_a) + fmaf(qp_b, 0.125f, ir_b);
+  bz = fmaf(e_a, 0.125f, fmaf(d3_a, -1.0f / 24.0f, d_a)) - fmaf(e_b, 0.125f, fmaf(d3_b, -1.0f / 24.0f, d_b));
 }
 
 // The same base with both far ends at infinity (the Ncut -> infinity window):
 // per side Int_lo^inf i^3 = 1/(r (r + lo)) = il^2 / (1 + lo il) and
 // Int_lo^inf x i^3 = il, plus the near end's term (-3 lo il^5 and
 // il^3 - 3 lo^2 il^5, over 24).
-__device__ __forceinline__ void side_base_inf_x2(float R2, u64 LO, u64& SR, u64& SZ, u64& IL) {
-  float a, b;
-  upk(fma2(LO, LO, pk(R2, R2)), a, b);
-  IL = pk(rsq(a), rsq(b));
+__device__ __forceinline__ void tail_base_inf_fp32(float R2, float lo_a, float lo_b, float& br, float& bz,
+                                                   float& il_a) {
+  const u64 LO = pk(lo_a, lo_b);
+  const u64 IL = pk(rsq(fmaf(lo_a, lo_a, R2)), rsq(fmaf(lo_b, lo_b, R2)));
   const u64 IL2 = mul2(IL, IL), IL3 = mul2(IL2, IL);
   float e, f;
   upk(fma2(LO, IL, pk(1.0f, 1.0f)), e, f);
   const u64 IR = mul2(IL2, pk(rcp_approx(e), rcp_approx(f)));
   const u64 P = mul2(LO, mul2(IL2, IL3));  // lo il^5
-  SR = fma2(P, pk(-0.125f, -0.125f), IR);
-  SZ = fma2(fma2(mul2(LO, pk(-3.0f, -3.0f)), P, IL3), pk(1.0f / 24.0f, 1.0f / 24.0f), IL);
+  const u64 T = fma2(mul2(LO, P), pk(-3.0f, -3.0f), IL3);  // il^3 - 3 lo^2 il^5
+  float p_a, p_b, ir_a, ir_b, t_a, t_b, il_b;
+  upk(P, p_a, p_b);
+  upk(IR, ir_a, ir_b);
+  upk(T, t_a, t_b);
+  upk(IL, il_a, il_b);
+  br = fmaf(p_a, -0.125f, ir_a) + fmaf(p_b, -0.125f, ir_b);
+  bz = fmaf(t_a, 1.0f / 24.0f, il_a) - fmaf(t_b, 1.0f / 24.0f, il_b);
+}
+
+// F/r of one image from its r^2: the scalar form of spline_value_r2 (all three
+// branches, core selected per lane) or, with FULL false, of the outer-shell
+// form spline_outer_value (exactly r^-3 for u >= 1). ih = 1 / hh.
+template <bool FULL>
+__device__ __forceinline__ float spline_scalar(float r2, float ih, float ih3) {
+  const float ri = rsq(fmaxf(r2, 1e-30f));
+  const float rr = r2 * ri;
+  const float n3 = ri * ri * ri;
+  const float v = fmaxf(fmaf(rr, -ih, 1.0f), 0.0f);
+  const float v2 = v * v;
+  const float nr = fmaf(fmaf(v, -10.6666666667f, 25.6f), v, -16.0f);
+  const float outer = n3 * fmaf(v2 * v2, nr, 1.0f);
+  if (!FULL) return outer;
+  const float u = rr * ih;
+  const float inner = fmaf(u * u, fmaf(u, 32.0f, -38.4f), 10.6666666667f) * ih3;
+  return u < 0.5f ? inner : outer;
+}
+
+// Near images |k| <= n0 of a pair for the modelled-tail forms: the centre
+// image k = 0 on its own (no edge image rides along), then the pairs +-k
+// walked outward packed, with the warp-uniform spline tiers of
+// pair_images_fp32.
+__device__ __forceinline__ void near_images_fp32(float dR2, float dz, float hh, int n0, int kw, float& sr,
+                                                 float& sz) {
+  const u64 DR2 = pk(dR2, dR2);
+  const u64 STEP = pk(1.0f, -1.0f);
+  u64 O = pk(dz, dz);
+  u64 SR = pk(0.0f, 0.0f), SZ = pk(0.0f, 0.0f);
+  float cr;  // the centre image's F/r
+  const float c2 = fmaf(dz, dz, dR2);
+  int k = 1;
+  if (kw >= 0) {
+    const float ih = rcp_approx(hh);
+    const u64 NIH = pk(-ih, -ih);
+    const bool core = 4.0f * dR2 < hh * hh;
+    if (__any_sync(0xffffffffu, core)) {
+      const int kl = core ? __float_as_int(__fadd_rn(0.5f * hh, kTwo23)) : kTwo23Bits;
+      const int k1 = min(__reduce_max_sync(0xffffffffu, kl) - kTwo23Bits, n0);
+      const float ih3 = ih * ih * ih;
+      const u64 IH = pk(ih, ih), IH3 = pk(ih3, ih3);
+      cr = spline_scalar<true>(c2, ih, ih3);
+      for (; k <= k1; ++k) {
+        O = add2(O, STEP);
+        const u64 F = spline_over_r2(O, DR2, IH, NIH, IH3);
+        SR = add2(SR, F);
+        SZ = fma2(O, F, SZ);
+      }
+    } else {
+      cr = spline_scalar<false>(c2, ih, 0.0f);
+    }
+    const int kg = min(kw, n0);
+    for (; k <= kg; ++k) {
+      O = add2(O, STEP);
+      const u64 F = spline_outer_over_r2(O, DR2, NIH);
+      SR = add2(SR, F);
+      SZ = fma2(O, F, SZ);
+    }
+  } else {
+    const float ri = rsq(c2);
+    cr = ri * ri * ri;
+  }
+  // Newtonian pairs k .. n0: the first (count mod 4) enter a straight run
+  // part-way, the rest go in fours
+  const int cnt = n0 + 1 - k;
+  switch (cnt & 3) {
+    case 3: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
+    case 2: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
+    case 1: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
+    default: break;
+  }
+#pragma unroll 1
+  for (int q = cnt >> 2; q > 0; --q) {
+    newton_pair(O, STEP, DR2, SR, SZ);
+    newton_pair(O, STEP, DR2, SR, SZ);
+    newton_pair(O, STEP, DR2, SR, SZ);
+    newton_pair(O, STEP, DR2, SR, SZ);
+  }
+  float s0, s1, z0, z1;
+  upk(SR, s0, s1);
+  upk(SZ, z0, z1);
+  sr = (s0 + s1) + cr;
+  sz = (z0 + z1) + dz * cr;
 }
 
 // Per-pair state carried across the network: the image sums are affine in
@@ -274,35 +391,33 @@ struct SurrPair {
 template <bool INF = false>
 __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int n_cut, int kw, const SurrConst& S,
                                              SurrPair& P) {
-  const int n0 = S.n0;
+  (void)n_cut;  // the finite window's far end comes in S.fnh
   float sr, sz;
-  pair_images_fp32<false>(dR2, dz, hh, n0 + 1, (float)(n0 + 1), kw, sr, sz);
+  near_images_fp32(dR2, dz, hh, S.n0, kw, sr, sz);
   // tail base and envelope (|dz|; z part gets sign(dz))
-  const float adz = fabsf(dz), A = (float)n0 + 0.5f;
-  u64 SRb, SZb, ILb;
+  const float adz = fabsf(dz), A = S.A;
+  float br, bz, il1;
   if (INF) {
-    side_base_inf_x2(dR2, pk(A + adz, A - adz), SRb, SZb, ILb);
+    tail_base_inf_fp32(dR2, A + adz, A - adz, br, bz, il1);
   } else {
-    const float kneg = adz > 0.0f ? (float)n_cut : (float)(n_cut - 1);
-    side_base_x2(dR2, pk(A + adz, A - adz), pk((float)(n_cut - 1) + 0.5f + adz, kneg + 0.5f - adz), SRb, SZb, ILb);
+    // far ends: + side (n_cut - 1) + 1/2 + |dz|; - side at n_cut + 1/2 - |dz| when
+    // dz != 0 (the edge image n_cut belongs to it), else n_cut - 1/2
+    const float hb = (adz > 0.0f ? S.fnh + 1.0f : S.fnh) - adz;
+    tail_base_fp32(dR2, A + adz, A - adz, S.fnh + adz, hb, br, bz, il1);
   }
-  float br1, br2, bz1, bz2, il1, il2;
-  upk(SRb, br1, br2);
-  upk(SZb, bz1, bz2);
-  upk(ILb, il1, il2);
   const float e = il1 * il1;
   const float er = e * e * e;
   const float sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
   const float ez = sg * (e * e * il1);  // sign(dz) E_z: the z part of the tail is odd in dz
   // tail = base + E (y sc + mu)
-  P.a0 = fmaf(er, S.mu0, sr + (br1 + br2));
+  P.a0 = fmaf(er, S.mu0, sr + br);
   P.b0 = er * S.sc0;
-  P.a1 = fmaf(ez, S.mu1, fmaf(sg, bz1 - bz2, sz));
+  P.a1 = fmaf(ez, S.mu1, fmaf(sg, bz, sz));
   P.b1 = ez * S.sc1;
   const float dR = dR2 * rsq(fmaxf(dR2, 1e-30f));
-  P.u[0] = 2.0f * fminf(dR, S.dR_max) * S.inv_dR_max - 1.0f;
-  P.u[1] = 4.0f * adz - 1.0f;
-  P.u[2] = 2.0f * fminf(hh, A) / A - 1.0f;
+  P.u[0] = fmaf(fminf(dR, S.dR_max), S.two_inv_dR_max, -1.0f);
+  P.u[1] = fmaf(adz, 4.0f, -1.0f);
+  P.u[2] = fmaf(fminf(hh, A), S.two_over_A, -1.0f);
 }
 
 // Stage C: tail = base + envelope x network output, plus the exact spline

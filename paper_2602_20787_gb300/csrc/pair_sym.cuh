@@ -179,6 +179,11 @@ __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const fl
   }
 }
 
+#ifndef STEPS_SURR_UNROLL
+#define STEPS_SURR_UNROLL 1  // unroll of the two-j steps of a Kahan group (learned tail)
+#endif
+constexpr int kSurrUnroll = STEPS_SURR_UNROLL;
+
 // Learned tail (surrogate_pair.cuh): STEPS_SURR_NJ j per network call, the
 // j side reduced two j at a time.
 template <bool KAHAN, bool INF>
@@ -190,7 +195,7 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll 1
+#pragma unroll(kSurrUnroll)
     for (int k = k0; k < k0 + STEPS_KAHAN_GROUP; k += 2) {
       float w[2][3];
       if (STEPS_SURR_NJ == 2) {

@@ -315,8 +315,10 @@ __device__ __forceinline__ float spline_scalar(float r2, float ih, float ih3) {
 // image k = 0 on its own (no edge image rides along), then the pairs +-k
 // walked outward packed, with the warp-uniform spline tiers of
 // pair_images_fp32.
-__device__ __forceinline__ void near_images_fp32(float dR2, float dz, float hh, int n0, int kw, float& sr,
+template <int N0 = 0>  // N0 > 0: the near range fixed at compile time (n0 is then N0)
+__device__ __forceinline__ void near_images_fp32(float dR2, float dz, float hh, int n0_rt, int kw, float& sr,
                                                  float& sz) {
+  const int n0 = N0 > 0 ? N0 : n0_rt;
   const u64 DR2 = pk(dR2, dR2);
   const u64 STEP = pk(1.0f, -1.0f);
   u64 O = pk(dz, dz);
@@ -357,6 +359,16 @@ __device__ __forceinline__ void near_images_fp32(float dR2, float dz, float hh, 
   // Newtonian pairs k .. n0: the first (count mod 4) enter a straight run
   // part-way, the rest go in fours
   const int cnt = n0 + 1 - k;
+  if (N0 > 0 && k == 1) {  // no softened pair: the whole fixed range, unrolled
+#pragma unroll
+    for (int q = 0; q < N0; ++q) newton_pair(O, STEP, DR2, SR, SZ);
+    float s0, s1, z0, z1;
+    upk(SR, s0, s1);
+    upk(SZ, z0, z1);
+    sr = (s0 + s1) + cr;
+    sz = (z0 + z1) + dz * cr;
+    return;
+  }
   switch (cnt & 3) {
     case 3: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
     case 2: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
@@ -393,7 +405,12 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
                                              SurrPair& P) {
   (void)n_cut;  // the finite window's far end comes in S.fnh
   float sr, sz;
-  near_images_fp32(dR2, dz, hh, S.n0, kw, sr, sz);
+#if STEPS_SURR_N0_FIXED
+  if (S.n0 == 4)  // the near range of the learned-tail workloads, unrolled
+    near_images_fp32<4>(dR2, dz, hh, 4, kw, sr, sz);
+  else
+#endif
+    near_images_fp32(dR2, dz, hh, S.n0, kw, sr, sz);
   // tail base and envelope (|dz|; z part gets sign(dz))
   const float adz = fabsf(dz), A = S.A;
   float br, bz, il1;
@@ -472,6 +489,9 @@ __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A
   }
 }
 
+#ifndef STEPS_SURR_N0_FIXED
+#define STEPS_SURR_N0_FIXED 1  // compile the n0 = 4 near range unrolled beside the general one
+#endif
 #ifndef STEPS_SURR_NJ
 #define STEPS_SURR_NJ 2  // values of j per network call (independent mma chains per warp)
 #endif

@@ -298,8 +298,10 @@ def run_sharded(args, rank, world, local):
     the ranks. Every rank builds the same context from the same load, trains
     the same network (deterministic), and then owns a contiguous range of rows
     (steps_cyl_shard); each KDK step is drift, one NCCL all-gather of the packed
-    rows, kick (shard.ShardedSimulation). value = the whole cylinder's
-    equivalent pair-images per second over the slowest rank's time."""
+    rows, the rank's share of the unordered pairs, one reduce-scatter of the
+    integer pair sums, and the finish of its rows (shard.ShardedSimulation).
+    value = the whole cylinder's equivalent pair-images per second over the
+    slowest rank's time."""
     import torch
     import torch.distributed as dist
     from paper_2602_20787_gb300 import ics, shard, steps_cyl as sc
@@ -375,7 +377,10 @@ def run_sharded(args, rank, world, local):
             "config": {"workload": WORKLOAD + (" (learned tail, n0 = 4)" if accepted else
                                                " (plain sum: network rejected)"),
                        "n": n, "n_cut": w.n_cut, "n0": w.n0, "parallelism": f"row shards x {world}",
-                       "exchange": "one NCCL all-gather of the packed rows (32 B per particle) per step",
+                       "exchange": ("per step one NCCL all-gather of the packed rows (32 B per particle) and one "
+                                    "reduce-scatter of the int64 pair sums (24 B per particle); each unordered pair "
+                                    "evaluated once across the ranks") if rows.symmetric else
+                                   "one NCCL all-gather of the packed rows (32 B per particle) per step",
                        "rows_per_rank": rows.chunk, "a_after": float(diag[6]),
                        "l2": "256 MiB buffer written between timed steps (inputs 16 MB < L2)"},
             "kdk_step_ms": 1e3 * t_max / args.steps,

@@ -235,6 +235,40 @@ int steps_cyl_shard_drift(steps_cyl_ctx* ctx, double dt, float* send);
  * to read the device error word (STEPS_EDEVICE). */
 int steps_cyl_shard_kick(steps_cyl_ctx* ctx, const float* recv);
 
+/* The symmetric sharded step. The row step above evaluates each of a rank's
+ * rows against every j, one ordered pair at a time. On one GPU the FP32 direct
+ * forms evaluate each unordered pair once instead (steps_cyl_last_eval), and
+ * the symmetric step does the same across ranks, with a second exchange:
+ *   steps_cyl_shard_drift    (as above; then the caller all-gathers send)
+ *   steps_cyl_shard_force    this rank's equal share of the unordered pairs,
+ *                            both particles of each, into sums
+ *   (the caller reduce-scatters sums: 64-bit integer sums over the ranks)
+ *   steps_cyl_shard_finish   this rank's rows from its reduced sums: the
+ *                            background and p += g K2; a and t advance.
+ * Integer sums make the step deterministic for a given world size.
+ *
+ * steps_cyl_shard_mode: *symmetric = 1 when the sharded context offers this step
+ * (world > 1, S1xR2, not FP64, and the fixed-point scale of steps_cyl_last_eval's
+ * symmetric kernels is usable); *sums_len (may be NULL) = world x 3 x chunk, the
+ * int64 length of the sums buffer (0 without the step). */
+int steps_cyl_shard_mode(steps_cyl_ctx* ctx, int32_t* symmetric, int64_t* sums_len);
+
+/* The gathered rows (recv, as for steps_cyl_shard_kick) become the j-set; this
+ * rank's 1/world share of the unordered pairs is evaluated and every pair added
+ * to both its particles in sums: device memory, 16-byte aligned, int64
+ * [world][3][chunk] (rank-major: rank q's rows, component by component), in
+ * units of 2^-S of the fixed-point scale; zeroed and written whole. A NCCL
+ * reduce-scatter of sums with ncclInt64 and ncclSum hands rank q its slice
+ * [3][chunk]. STEPS_EINVAL without a symmetric step or after anything but
+ * steps_cyl_shard_drift. Stream-ordered; returns without waiting. */
+int steps_cyl_shard_force(steps_cyl_ctx* ctx, const float* recv, int64_t* sums);
+
+/* Finish the step from own: device memory, 16-byte aligned, int64 [3][chunk],
+ * the sums of this rank's rows added over every rank. STEPS_EINVAL unless
+ * steps_cyl_shard_force came first. Synchronises the stream to read the device
+ * error word (STEPS_EDEVICE). */
+int steps_cyl_shard_finish(steps_cyl_ctx* ctx, const int64_t* own);
+
 /* ---- learned far-image surrogate ------------------------------------------
  * The paper sums every image of the window (eq. ForceCylindrical). The
  * surrogate tail form (STEPS_TAIL_SURROGATE) sums the near images |k| <= n0

@@ -186,18 +186,22 @@ static __global__ void finalize_kernel(const double* __restrict__ part, int n, i
 }
 
 // Finalize from the fixed-point accumulators of the symmetric pair kernels
-// (pair_sym.cuh): acc[3][n] in units of 1 / scale.
-static __global__ void finalize_fix_kernel(const unsigned long long* __restrict__ acc, int n, double inv_scale,
-                                           double pair_scale, BgParams bg, const double* __restrict__ x,
-                                           const double* __restrict__ y, const double* __restrict__ z,
-                                           double* __restrict__ gx, double* __restrict__ gy, double* __restrict__ gz,
-                                           double K, double* __restrict__ px, double* __restrict__ py,
+// (pair_sym.cuh), in units of 1 / scale, for the rows [i0, n): acc[3][stride]
+// indexed from i0 (stride = n, i0 = 0 for every row; a rank's own rows of a
+// sharded step have i0 = its first row and stride = its exchange chunk).
+static __global__ void finalize_fix_kernel(const unsigned long long* __restrict__ acc, int n, int i0, int stride,
+                                           double inv_scale, double pair_scale, BgParams bg,
+                                           const double* __restrict__ x, const double* __restrict__ y,
+                                           const double* __restrict__ z, double* __restrict__ gx,
+                                           double* __restrict__ gy, double* __restrict__ gz, double K,
+                                           double* __restrict__ px, double* __restrict__ py,
                                            double* __restrict__ pz, int* __restrict__ err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = i0 + q;
   if (i >= n) return;
-  const double sx = (double)(long long)acc[i] * inv_scale;
-  const double sy = (double)(long long)acc[(long long)n + i] * inv_scale;
-  const double sz = (double)(long long)acc[2 * (long long)n + i] * inv_scale;
+  const double sx = (double)(long long)acc[q] * inv_scale;
+  const double sy = (double)(long long)acc[(long long)stride + q] * inv_scale;
+  const double sz = (double)(long long)acc[2 * (long long)stride + q] * inv_scale;
   finish_particle(i, sx, sy, sz, pair_scale, bg, x, y, z, gx, gy, gz, K, px, py, pz, 1.0, nullptr, nullptr, nullptr,
                   err, RadialCorr{nullptr, 0, 0.0, 0});
 }

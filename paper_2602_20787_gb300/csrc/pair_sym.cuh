@@ -41,14 +41,27 @@ namespace steps {
 constexpr int kErrFixRange = 32;  // a pair sum left the range of the fixed-point accumulators
 constexpr int kJRow = 3 * kBJ;    // floats of one warp's j-side row: [kBJ][3]
 
-// Fixed-point accumulators acc[3][n] (two's complement in unsigned words, unit
-// 1 / scale) and the error word.
+// Fixed-point accumulators (two's complement in unsigned words, unit
+// 1 / scale) and the error word. Unsharded (world == 0): acc[3][n]. When the
+// rows are sharded across world ranks (balanced contiguous ranges of 128-row
+// blocks: the first `extra` ranks own base + 1 blocks, the others base),
+// acc[world][3][chunk], rank-major, so that a reduce-scatter over the ranks
+// hands each rank the sums of its own rows.
 struct FixAcc {
   unsigned long long* acc;
   int n;
   double scale;
   int* err;
+  int world, base, extra, chunk;
 };
+
+__device__ __forceinline__ long long fix_index(const FixAcc& F, int c, int i) {
+  if (F.world == 0) return (long long)c * F.n + i;
+  const int b = i / kBI, big = F.extra * (F.base + 1);
+  const int r = b < big ? b / (F.base + 1) : F.extra + (b - big) / F.base;
+  const int first = (r < F.extra ? r * (F.base + 1) : big + (r - F.extra) * F.base) * kBI;
+  return ((long long)r * 3 + c) * F.chunk + (i - first);
+}
 
 __device__ __forceinline__ void fix_add(const FixAcc& F, int c, int i, double v) {
   const double q = v * F.scale;
@@ -56,7 +69,7 @@ __device__ __forceinline__ void fix_add(const FixAcc& F, int c, int i, double v)
     atomicOr(F.err, kErrFixRange);
     return;
   }
-  atomicAdd(F.acc + (long long)c * F.n + i, (unsigned long long)__double2ll_rn(q));
+  atomicAdd(F.acc + fix_index(F, c, i), (unsigned long long)__double2ll_rn(q));
 }
 
 // Offset of row b of the upper triangle (units t = b .. NB - 1 per row).
@@ -256,11 +269,12 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
 // warps' j-side rows, [kBI / 32][kJRow] floats.
 template <bool KAHAN, class Tile>
 __device__ __forceinline__ void sym_stream_k(const float4* __restrict__ jA, const float4* __restrict__ jB, int n,
-                                             int NB, long long U, int C, float4* sA, float4* sB, float* sJ,
-                                             const FixAcc& F, Tile tile) {
+                                             int NB, long long Ua, long long U, int C, float4* sA, float4* sB,
+                                             float* sJ, const FixAcc& F, Tile tile) {
+  // the units [Ua, Ua + U) (all of them, or a rank's share), split over C CTAs
   const int c = blockIdx.x;
-  const long long u0 = (long long)c * U / C;
-  const long long u1 = (long long)(c + 1) * U / C;
+  const long long u0 = Ua + (long long)c * U / C;
+  const long long u1 = Ua + (long long)(c + 1) * U / C;
   float* row = sJ + (threadIdx.x >> 5) * kJRow;
   long long u = u0;
   while (u < u1) {
@@ -307,13 +321,13 @@ __device__ __forceinline__ void sym_stream_k(const float4* __restrict__ jA, cons
 // ---- kernels ---------------------------------------------------------------
 template <bool KAHAN>
 __global__ void __launch_bounds__(kBI, 8)
-pair_sym_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB, long long U,
-                int C, FixAcc F) {
+pair_sym_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB, long long Ua,
+                long long U, int C, FixAcc F) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   __shared__ float sJ[kBI / 32 * kJRow];
   const float fnc = (float)n_cut;
-  sym_stream_k<KAHAN>(jA, jB, n, NB, U, C, sA, sB, sJ, F,
+  sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int /*self*/,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
                         sym_tile_plain<KAHAN>(I, mi, a, bb, sym, row, n_cut, fnc, sx, sy, sz, cx, cy, cz);
@@ -323,7 +337,7 @@ pair_sym_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, in
 template <bool KAHAN, bool INF>
 __global__ void __launch_bounds__(kBI, STEPS_SURR_MIN_BLOCKS)
 pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB,
-                     long long U, int C, const SurrLane* __restrict__ wl, SurrConst S, FixAcc F) {
+                     long long Ua, long long U, int C, const SurrLane* __restrict__ wl, SurrConst S, FixAcc F) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   __shared__ float sJ[kBI / 32 * kJRow];
@@ -333,7 +347,7 @@ pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ j
   mlp_zero_inputs<STEPS_SURR_NJ>(ibuf);
   stage_surr_weights(wl, sWT);
   const SurrW W{sWT + (threadIdx.x & 31) * kSurrStride};
-  sym_stream_k<KAHAN>(jA, jB, n, NB, U, C, sA, sB, sJ, F,
+  sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int self,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
                         sym_tile_surr<KAHAN, INF>(I, mi, a, bb, sym, row, self, n_cut, W, ibuf, S, sx, sy, sz, cx,
@@ -344,11 +358,11 @@ pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ j
 template <bool KAHAN, bool INF>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_sym_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB,
-                      long long U, int C, TableTail T, SurrConst S, FixAcc F) {
+                      long long Ua, long long U, int C, TableTail T, SurrConst S, FixAcc F) {
   __shared__ float4 sA[kBJ];
   __shared__ float4 sB[kBJ];
   __shared__ float sJ[kBI / 32 * kJRow];
-  sym_stream_k<KAHAN>(jA, jB, n, NB, U, C, sA, sB, sJ, F,
+  sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int self,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
                         sym_tile_table<KAHAN, INF>(I, mi, a, bb, sym, row, self, n_cut, S, T, sx, sy, sz, cx, cy,

@@ -260,6 +260,8 @@ struct steps_cyl_ctx {
   int shard_rank = 0, shard_world = 1, chunk = 0;
   int* shard_off = nullptr;       // device: world + 1 row offsets
   bool drifted = false;           // steps_cyl_shard_drift done, steps_cyl_shard_kick pending
+  bool shard_sym = false;         // the symmetric two-exchange step is available
+  bool forced = false;            // steps_cyl_shard_force done, steps_cyl_shard_finish pending
   double pend_K2 = 0.0, pend_a = 0.0, pend_dt = 0.0;
   int steps_since_order = 0;
   bool forces_stale = false;       // g must be recomputed before the next kick
@@ -1003,6 +1005,64 @@ Form force_form(const steps_cyl_ctx* c) {
   return Form::PLAIN;
 }
 
+// Pairs the symmetric kernels evaluate over all units: the unordered pairs
+// across blocks once, the ordered pairs inside each 128-row block both ways.
+double sym_pairs(const steps_cyl_ctx* c) {
+  double within = 0.0;
+  for (int b = 0; b < c->NB; ++b) {
+    const double nb = (double)(std::min(c->n, (b + 1) * kBI) - b * kBI);
+    within += nb * (nb - 1.0);
+  }
+  const double all = (double)c->n * (double)(c->n - 1);
+  return 0.5 * (all - within) + within;
+}
+
+// The symmetric kernel of the form over the units [Ua, Ua + U) into F.
+int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const FixAcc& F) {
+  const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+  const int nc = c->p.n_cut, n = c->n, NB = c->NB;
+  auto ctas = [&](int full) {  // the CTA count of the whole triangle, scaled to a share of it
+    return (int)std::max<long long>(1, std::min<long long>(U, (long long)full * U / std::max<long long>(c->Usym, 1)));
+  };
+  if (form == Form::SURROGATE) {
+    const int C = ctas(c->SYSC);
+    if (is_inf(c) && kahan)
+      pair_sym_surr_kernel<true, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->surr_lanes, c->surr, F);
+    else if (is_inf(c))
+      pair_sym_surr_kernel<false, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->surr_lanes, c->surr,
+                                                              F);
+    else if (kahan)
+      pair_sym_surr_kernel<true, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->surr_lanes, c->surr,
+                                                              F);
+    else
+      pair_sym_surr_kernel<false, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->surr_lanes,
+                                                               c->surr, F);
+    CKLAUNCH("pair_sym_surrogate");
+  } else if (form == Form::TABLE) {
+    const int C = ctas(c->SYTC);
+    if (is_inf(c) && kahan)
+      pair_sym_table_kernel<true, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->tab, c->tab_const, F);
+    else if (is_inf(c))
+      pair_sym_table_kernel<false, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->tab, c->tab_const,
+                                                               F);
+    else if (kahan)
+      pair_sym_table_kernel<true, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab, c->tab_const,
+                                                               F);
+    else
+      pair_sym_table_kernel<false, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
+                                                                c->tab_const, F);
+    CKLAUNCH("pair_sym_table");
+  } else {
+    const int C = ctas(c->SYC);
+    if (kahan)
+      pair_sym_kernel<true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, F);
+    else
+      pair_sym_kernel<false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, F);
+    CKLAUNCH("pair_sym");
+  }
+  return STEPS_OK;
+}
+
 // One force evaluation at the current packed positions. Stores g = a^3 (pair +
 // background) in gx/gy/gz (internal order); kicks p by K when kick is set.
 int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
@@ -1034,60 +1094,16 @@ int eval_forces(steps_cyl_ctx* c, bool kick, double K) {
   if (form != Form::FP64 && use_sym(c)) {
     CK(cudaMemsetAsync(c->facc, 0, sizeof(unsigned long long) * 3 * (size_t)c->n, c->st));
     CK(cudaEventRecord(c->e0, c->st));
-    const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
-    const FixAcc F{c->facc, c->n, c->fix_scale, c->err};
-    const int nc = c->p.n_cut;
-    if (form == Form::SURROGATE) {
-      if (is_inf(c) && kahan)
-        pair_sym_surr_kernel<true, true><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym, c->SYSC,
-                                                                     c->surr_lanes, c->surr, F);
-      else if (is_inf(c))
-        pair_sym_surr_kernel<false, true><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym, c->SYSC,
-                                                                      c->surr_lanes, c->surr, F);
-      else if (kahan)
-        pair_sym_surr_kernel<true, false><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
-                                                                      c->SYSC, c->surr_lanes, c->surr, F);
-      else
-        pair_sym_surr_kernel<false, false><<<c->SYSC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
-                                                                       c->SYSC, c->surr_lanes, c->surr, F);
-      CKLAUNCH("pair_sym_surrogate");
-    } else if (form == Form::TABLE) {
-      if (is_inf(c) && kahan)
-        pair_sym_table_kernel<true, true><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym,
-                                                                      c->SYTC, c->tab, c->tab_const, F);
-      else if (is_inf(c))
-        pair_sym_table_kernel<false, true><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, 0, c->NB, c->Usym,
-                                                                       c->SYTC, c->tab, c->tab_const, F);
-      else if (kahan)
-        pair_sym_table_kernel<true, false><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
-                                                                       c->SYTC, c->tab, c->tab_const, F);
-      else
-        pair_sym_table_kernel<false, false><<<c->SYTC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym,
-                                                                        c->SYTC, c->tab, c->tab_const, F);
-      CKLAUNCH("pair_sym_table");
-    } else if (kahan) {
-      pair_sym_kernel<true><<<c->SYC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym, c->SYC, F);
-      CKLAUNCH("pair_sym_kahan");
-    } else {
-      pair_sym_kernel<false><<<c->SYC, kBI, 0, c->st>>>(c->jA, c->jB, c->n, nc, c->NB, c->Usym, c->SYC, F);
-      CKLAUNCH("pair_sym_plain");
-    }
+    int rc = launch_sym(c, form, 0, c->Usym, FixAcc{c->facc, c->n, c->fix_scale, c->err, 0, 0, 0, 0});
+    if (rc) return rc;
     CK(cudaEventRecord(c->e1, c->st));
     c->timed = true;
     c->last_images = (double)c->n * (double)(c->n - 1) * images_per_pair(c);
-    {  // unordered pairs across blocks once, ordered pairs within a block both ways
-      double within = 0.0;
-      for (int b = 0; b < c->NB; ++b) {
-        const double nb = (double)(std::min(c->n, (b + 1) * kBI) - b * kBI);
-        within += nb * (nb - 1.0);
-      }
-      const double all = (double)c->n * (double)(c->n - 1);
-      c->last_pairs = 0.5 * (all - within) + within;
-      c->last_sym = true;
-    }
+    c->last_pairs = sym_pairs(c);
+    c->last_sym = true;
     finalize_fix_kernel<<<(c->n + 255) / 256, 256, 0, c->st>>>(
-        c->facc, c->n, 1.0 / c->fix_scale, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, K,
-        kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, c->err);
+        c->facc, c->n, 0, c->n, 1.0 / c->fix_scale, pair_scale, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz,
+        K, kick ? c->px : nullptr, kick ? c->py : nullptr, kick ? c->pz : nullptr, c->err);
     CKLAUNCH("finalize_fix");
     return STEPS_OK;
   }
@@ -2365,6 +2381,8 @@ int steps_cyl_shard(steps_cyl_ctx* c, int32_t rank, int32_t world, int64_t* rows
   for (int r = 0; r < world; ++r) chunk = std::max(chunk, off[r + 1] - off[r]);
   const int b0 = rank * base + std::min(rank, extra), nbo = base + (rank < extra ? 1 : 0);
   const int k0 = off[rank], k1 = off[rank + 1];
+  int rc0 = 0;
+  if (!c->fix_ready && (rc0 = fix_scale(c))) return rc0;  // the scale of the symmetric step's sums
   int* d_off = nullptr;
   cudaError_t e = cudaMalloc(&d_off, sizeof(int) * (world + 1));
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (world + 1), cudaMemcpyHostToDevice, c->st);
@@ -2376,6 +2394,7 @@ int steps_cyl_shard(steps_cyl_ctx* c, int32_t rank, int32_t world, int64_t* rows
   }
   c->shard_off = d_off;
   set_rows(c, b0, nbo);
+  c->shard_sym = world > 1 && STEPS_SYMMETRIC && !is_r3(c) && c->fix_ok;
   c->shard = true;
   c->shard_rank = rank;
   c->shard_world = world;
@@ -2424,6 +2443,7 @@ int steps_cyl_shard_kick(steps_cyl_ctx* c, const float* recv) {
   if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
   if (!c->shard) return fail(STEPS_EINVAL, "the context is not sharded (steps_cyl_shard)");
   if (!c->drifted) return fail(STEPS_EINVAL, "steps_cyl_shard_drift must come first");
+  if (c->forced) return fail(STEPS_EINVAL, "steps_cyl_shard_force was called: finish with steps_cyl_shard_finish");
   if (!exchange_buffer_ok(recv)) return fail(STEPS_EINVAL, "recv must be 16-byte aligned device memory");
   DeviceGuard guard(c->dev);
   Range range("steps_cyl.shard_kick");
@@ -2451,6 +2471,73 @@ int steps_cyl_last_timing(steps_cyl_ctx* c, double* pair_images, double* pair_ms
   CK(cudaEventElapsedTime(&ms, c->e0, c->e1));
   if (pair_images) *pair_images = c->last_images;
   if (pair_ms) *pair_ms = ms;
+  return STEPS_OK;
+}
+
+int steps_cyl_shard_mode(steps_cyl_ctx* c, int32_t* symmetric, int64_t* sums_len) {
+  g_last_error.clear();
+  if (!c || !symmetric) return fail(STEPS_EINVAL, "NULL argument");
+  if (!c->shard) return fail(STEPS_EINVAL, "the context is not sharded (steps_cyl_shard)");
+  *symmetric = c->shard_sym ? 1 : 0;
+  if (sums_len) *sums_len = c->shard_sym ? (int64_t)c->shard_world * 3 * c->chunk : 0;
+  return STEPS_OK;
+}
+
+int steps_cyl_shard_force(steps_cyl_ctx* c, const float* recv, int64_t* sums) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!c->shard || !c->shard_sym) return fail(STEPS_EINVAL, "the context has no symmetric sharded step");
+  if (!c->drifted || c->forced) return fail(STEPS_EINVAL, "steps_cyl_shard_force must follow steps_cyl_shard_drift");
+  if (!exchange_buffer_ok(recv) || !exchange_buffer_ok(sums))
+    return fail(STEPS_EINVAL, "recv and sums must be 16-byte aligned device memory");
+  const Form form = force_form(c);
+  if (form == Form::FP64 || (form == Form::PLAIN && is_inf(c)))
+    return fail(STEPS_EINVAL, "the symmetric sharded step needs an FP32 direct form");
+  DeviceGuard guard(c->dev);
+  Range range("steps_cyl.shard_force");
+  shard_recv_kernel<<<dim3(grid_for(c->chunk, 256), c->shard_world), 256, 0, c->st>>>(
+      reinterpret_cast<const float4*>(recv), c->shard_off, c->chunk, c->jA, c->jB);
+  CKLAUNCH("shard_recv");
+  const size_t len = (size_t)c->shard_world * 3 * c->chunk;
+  CK(cudaMemsetAsync(sums, 0, sizeof(int64_t) * len, c->st));
+  // this rank's equal share of the upper-triangle units, both sides of each pair
+  const int W = c->shard_world, r = c->shard_rank;
+  const long long Ua = (long long)r * c->Usym / W, Ub = (long long)(r + 1) * c->Usym / W;
+  const FixAcc F{reinterpret_cast<unsigned long long*>(sums), c->n, c->fix_scale, c->err, W, c->NB / W, c->NB % W,
+                 c->chunk};
+  CK(cudaEventRecord(c->e0, c->st));
+  int rc = launch_sym(c, form, Ua, Ub - Ua, F);
+  if (rc) return rc;
+  CK(cudaEventRecord(c->e1, c->st));
+  c->timed = true;
+  c->last_images = (double)(c->k1 - c->k0) * (double)(c->n - 1) * images_per_pair(c);
+  c->last_pairs = sym_pairs(c) * (double)(Ub - Ua) / (double)c->Usym;
+  c->last_sym = true;
+  c->forced = true;
+  return STEPS_OK;
+}
+
+int steps_cyl_shard_finish(steps_cyl_ctx* c, const int64_t* own) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (!c->forced) return fail(STEPS_EINVAL, "steps_cyl_shard_force must come first");
+  if (!exchange_buffer_ok(own)) return fail(STEPS_EINVAL, "own must be 16-byte aligned device memory");
+  DeviceGuard guard(c->dev);
+  Range range("steps_cyl.shard_finish");
+  const int rows = c->k1 - c->k0;
+  finalize_fix_kernel<<<(rows + 255) / 256, 256, 0, c->st>>>(
+      reinterpret_cast<const unsigned long long*>(own), c->k1, c->k0, c->chunk, 1.0 / c->fix_scale,
+      -c->p.G * c->invL * c->invL, bg_params(c), c->x, c->y, c->z, c->gx, c->gy, c->gz, c->pend_K2, c->px, c->py,
+      c->pz, c->err);
+  CKLAUNCH("finalize_fix");
+  c->forces_stale = false;
+  c->a = c->pend_a;
+  c->t += c->pend_dt;
+  c->drifted = false;
+  c->forced = false;
+  int e = 0, rc;
+  if ((rc = read_and_clear_err(c, &e))) return rc;
+  if (e) return device_error(e);
   return STEPS_OK;
 }
 

@@ -92,23 +92,48 @@ def all_gather_rows(send, group=None):
     return torch.cat(parts, 0)
 
 
+def reduce_scatter_rows(sums, group=None):
+    """Sum over the ranks of a rank-major tensor (world * k, ...) and hand rank r
+    its slice r of k rows: NCCL's reduce-scatter for CUDA tensors, an all-reduce
+    and a slice otherwise (gloo has no reduce-scatter). Integer tensors sum
+    exactly, so the result does not depend on the order of the ranks."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    k = sums.shape[0] // world
+    if sums.is_cuda:
+        import torch
+        out = torch.empty((k,) + tuple(sums.shape[1:]), dtype=sums.dtype, device=sums.device)
+        dist.reduce_scatter_tensor(out, sums.contiguous(), op=dist.ReduceOp.SUM, group=group)
+        return out
+    tot = sums.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM, group=group)
+    return tot[rank * k:(rank + 1) * k].contiguous()
+
+
 class GpuRows:
     """A rank's rows on its GPU: a steps_cyl context made from the full state
     (the same on every rank) and then sharded with steps_cyl_shard. Train or
     install a modelled tail on the context before handing it over.
 
     drift(dt) runs steps_cyl_shard_drift and returns the send buffer (chunk, 8)
-    float32; kick(recv) runs steps_cyl_shard_kick on the gathered rows. The
-    context's stream must be the current torch stream, so that the collective
-    between them is ordered after the drift and before the kick."""
+    float32. Then either kick(recv) runs steps_cyl_shard_kick on the gathered
+    rows (the row step), or, when `symmetric` is set, force(recv) returns the
+    rank's pair sums (steps_cyl_shard_force) and finish(own) completes the step
+    from the reduce-scattered sums of its rows (steps_cyl_shard_finish). The
+    context's stream must be the current torch stream, so that the collectives
+    between the calls are ordered after the one before and before the next."""
 
-    def __init__(self, sim, rank: int, world: int):
+    def __init__(self, sim, rank: int, world: int, symmetric: bool = True):
         import torch
         from . import steps_cyl as sc
         self.sc, self.sim, self.rank, self.world = sc, sim, rank, world
         self.k0, self.k1, self.chunk = sc.steps_cyl_shard(sim.ctx, rank, world)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.send = torch.zeros((self.chunk, 8), dtype=torch.float32, device=self.device)
+        avail, sums_len = sc.steps_cyl_shard_mode(sim.ctx)
+        self.symmetric = bool(symmetric and avail)
+        self.sums = torch.zeros(sums_len, dtype=torch.int64, device=self.device) if self.symmetric else None
 
     def drift(self, dt: float):
         self.sc.steps_cyl_shard_drift(self.sim.ctx, dt, self.send)
@@ -116,6 +141,13 @@ class GpuRows:
 
     def kick(self, recv):
         self.sc.steps_cyl_shard_kick(self.sim.ctx, recv)
+
+    def force(self, recv):
+        self.sc.steps_cyl_shard_force(self.sim.ctx, recv, self.sums)
+        return self.sums
+
+    def finish(self, own):
+        self.sc.steps_cyl_shard_finish(self.sim.ctx, own)
 
     def sums(self):
         """(P[3], L_z, kinetic energy, mass) of the owned rows, and (a, t)."""
@@ -139,12 +171,15 @@ class GpuRows:
 class ShardedSimulation:
     """One cylinder whose rows are split across the ranks of a process group
     (Sect. 2.4's distributed direct engine, one rank per GPU). Each KDK step is
-    compute.drift(dt) on the rank's rows, one all-gather of the packed rows of
-    every rank, and compute.kick(gathered) on the rank's rows: the pair force of
-    its rows against every particle, the background and the second kick. There
-    is no other exchange. `compute` is the rank's backend (GpuRows, or any
-    object with the same drift / kick / sums / state / check / set_tail
-    methods and a `device` attribute for the collectives' tensors).
+    compute.drift(dt) on the rank's rows and one all-gather of the packed rows
+    of every rank. Then, in the row step, compute.kick(gathered): the pair force
+    of the rank's rows against every particle, the background and the second
+    kick, with no other exchange. In the symmetric step (compute.symmetric),
+    compute.force(gathered) evaluates the rank's share of the unordered pairs
+    for both particles of each, one reduce-scatter sums them onto the ranks
+    that own the rows, and compute.finish(own) completes the step. `compute` is the rank's backend (GpuRows, or any
+    object with the same drift / kick (or force / finish) / sums / state / check
+    / set_tail methods and a `device` attribute for the collectives' tensors).
 
     With a modelled tail (tail = STEPS_TAIL_SURROGATE or STEPS_TAIL_TABLE) and
     check_every > 0, every check_every steps each rank checks a sample of its
@@ -164,7 +199,13 @@ class ShardedSimulation:
         ok = True
         for _ in range(nsteps):
             send = self.compute.drift(dt)
-            self.compute.kick(all_gather_rows(send, self.group))
+            recv = all_gather_rows(send, self.group)
+            if getattr(self.compute, "symmetric", False):
+                # each unordered pair once across the ranks, then the sums of every
+                # rank's rows gathered to it (integer sums: exact in any order)
+                self.compute.finish(reduce_scatter_rows(self.compute.force(recv), self.group))
+            else:
+                self.compute.kick(recv)
             self.steps += 1
             if self.tail and self.check_every > 0 and self.steps % self.check_every == 0:
                 ok = self._check() and ok

@@ -44,7 +44,7 @@ _EXPORTS = [
     "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
     "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
-    "steps_cyl_last_eval",
+    "steps_cyl_last_eval", "steps_cyl_shard_mode", "steps_cyl_shard_force", "steps_cyl_shard_finish",
 ]
 
 STEPS_SURR_NW = 1250
@@ -143,6 +143,9 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_shard.argtypes = [p, i32, i32, p]
     L.steps_cyl_shard_drift.argtypes = [p, d, p]
     L.steps_cyl_shard_kick.argtypes = [p, p]
+    L.steps_cyl_shard_mode.argtypes = [p, p, p]
+    L.steps_cyl_shard_force.argtypes = [p, p, p]
+    L.steps_cyl_shard_finish.argtypes = [p, p]
     for name in _EXPORTS:
         fn = getattr(L, name)
         if fn.restype is None or fn.restype is ctypes.c_int:
@@ -351,6 +354,33 @@ def steps_cyl_shard_kick(ctx, recv):
     """Second half of a sharded KDK step from the gathered rows (float32 CUDA
     tensor of world x chunk x 8, rank order)."""
     _check(load().steps_cyl_shard_kick(ctx, _exchange_buffer(recv, "recv")))
+
+
+def steps_cyl_shard_mode(ctx):
+    """(symmetric, sums_len): whether the sharded context offers the symmetric
+    two-exchange step, and the int64 length of its sums buffer."""
+    sym = ctypes.c_int32()
+    ln = ctypes.c_int64()
+    _check(load().steps_cyl_shard_mode(ctx, ctypes.byref(sym), ctypes.byref(ln)))
+    return bool(sym.value), int(ln.value)
+
+
+def _int64_cuda(buf, what):
+    if not hasattr(buf, "is_cuda") or not buf.is_cuda or str(buf.dtype) != "torch.int64":
+        raise StepsError(STEPS_EINVAL, f"{what} must be an int64 CUDA tensor")
+    return _ptr(buf)
+
+
+def steps_cyl_shard_force(ctx, recv, sums):
+    """This rank's share of the unordered pairs into sums (int64 CUDA tensor of
+    world x 3 x chunk), from the gathered rows recv."""
+    _check(load().steps_cyl_shard_force(ctx, _exchange_buffer(recv, "recv"), _int64_cuda(sums, "sums")))
+
+
+def steps_cyl_shard_finish(ctx, own):
+    """Finish the symmetric sharded step from this rank's reduced sums (int64
+    CUDA tensor of 3 x chunk)."""
+    _check(load().steps_cyl_shard_finish(ctx, _int64_cuda(own, "own")))
 
 
 def steps_cyl_train_cfg_default(**overrides) -> TrainCfg:

@@ -187,3 +187,91 @@ def test_sharded_simulation_reproduces_the_unsharded_oracle_kdk(tmp_path, world)
     np.testing.assert_allclose(diag[:3], ref[:3], rtol=0, atol=1e-14 * scale)
     assert diag[4] == pytest.approx(ref[4], rel=1e-13) and diag[5] == pytest.approx(ref[5], rel=1e-14)
     assert diag[6] == a and diag[7] == t
+
+
+class OracleSymRows(OracleRows):
+    """The symmetric step with an FP64 oracle compute (test backend): force()
+    evaluates this rank's 1/world share of the unordered pairs (i < j, in
+    lexicographic order) with the oracle's windowed image sum of eq.
+    ForceCylindrical, adding m_j f to i and -m_i f to j in a rank-major buffer
+    [world][3][chunk]; finish() takes the rank's reduce-scattered rows."""
+
+    symmetric = True
+
+    def force(self, recv):
+        import torch
+        r = recv.numpy()
+        for q, (a_, b) in enumerate(self.parts):
+            self.x[a_:b] = r[q * self.chunk: q * self.chunk + (b - a_)]
+        world = len(self.parts)
+        rank = self.parts.index((self.k0, self.k1))
+        iu, ju = np.triu_indices(self.n, 1)
+        lo, hi = rank * iu.size // world, (rank + 1) * iu.size // world
+        sums = np.zeros((world, 3, self.chunk))
+        owner = np.zeros(self.n, dtype=np.int64)
+        for q, (a_, b) in enumerate(self.parts):
+            owner[a_:b] = q
+        first = np.array([a_ for a_, _ in self.parts])
+        for i, j in zip(iu[lo:hi], ju[lo:hi]):
+            f, _ = self.orc.image_force(self.x[i] - self.x[j], self.h[i] + self.h[j], 1.0, self.n_cut)
+            sums[owner[i], :, i - first[owner[i]]] += self.m[j] * f
+            sums[owner[j], :, j - first[owner[j]]] -= self.m[i] * f
+        return torch.tensor(sums.reshape(world * 3, self.chunk))
+
+    def finish(self, own):
+        g = own.numpy().reshape(3, self.chunk)[:, : self.k1 - self.k0].T.copy()
+        self.g = g + self.orc.background_field(self.x[self.own], self.R, self.n_cut * 1.0, 1.0, self.rho0, mode=1)
+        self.p[self.k0:self.k1] += self.g * self.K2
+        self.a = self.an
+        self.t += self.dt
+
+
+def sym_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    import oracle
+    from paper_2602_20787_gb300 import ics
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = ics.WORKLOADS["lcdm_n65536"]
+        n, n_cut, steps = 131, 4, 3
+        d = ics.particle_load(n, 34, w.M_tot, displaced=True, rho_bar=w.rho_bar)
+        p0 = np.random.default_rng(9).normal(0.0, 0.05, (n, 3)) * w.a_start ** 2
+        t0, dt = ics.run_schedule(w)
+        rows = OracleSymRows(d["pos"], p0, d["m"], d["h"], n_cut, w.rho_bar, oracle.make_cosmo(), w.a_start, t0,
+                             rank, world)
+        sim = shard.ShardedSimulation(rows)
+        sim.step(20 * dt, steps)
+        st = sim.state()
+        if rank == 0:
+            np.save(os.path.join(out_dir, f"symstate{world}.npy"), st)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_symmetric_sharded_step_matches_the_oracle_kdk(tmp_path):
+    # the symmetric step's orchestration: drift, all-gather, each rank's share
+    # of the unordered pairs for both particles, reduce-scatter, finish; against
+    # the oracle's unsharded KDK (the pair sums are added in another order, so
+    # to FP64 rounding, not bit for bit)
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_2602_20787_gb300 import ics
+    oracle.build()
+    world = 3
+    mp.start_processes(sym_worker, args=(world, free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    st = np.load(tmp_path / f"symstate{world}.npy")
+    w = ics.WORKLOADS["lcdm_n65536"]
+    n, n_cut, steps = 131, 4, 3
+    d = ics.particle_load(n, 34, w.M_tot, displaced=True, rho_bar=w.rho_bar)
+    p0 = np.random.default_rng(9).normal(0.0, 0.05, (n, 3)) * w.a_start ** 2
+    t0, dt = ics.run_schedule(w)
+    x, p, a, _ = oracle.kdk(d["pos"], p0, d["m"], d["h"], 1.0, 1.0, n_cut, ics.R_SIM, w.rho_bar, 1,
+                            oracle.make_cosmo(), w.a_start, t0, 20 * dt, steps)
+    disp = np.abs(x - d["pos"]).max()
+    np.testing.assert_allclose(st[:, :3], x, rtol=0, atol=1e-12 * disp)
+    v = p / a ** 2
+    np.testing.assert_allclose(st[:, 3:], v, rtol=0, atol=1e-12 * np.abs(v).max())

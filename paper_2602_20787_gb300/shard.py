@@ -133,7 +133,7 @@ class GpuRows:
         self.send = torch.zeros((self.chunk, 8), dtype=torch.float32, device=self.device)
         avail, sums_len = sc.steps_cyl_shard_mode(sim.ctx)
         self.symmetric = bool(symmetric and avail)
-        self.sums = torch.zeros(sums_len, dtype=torch.int64, device=self.device) if self.symmetric else None
+        self.pair_sums = torch.zeros(sums_len, dtype=torch.int64, device=self.device) if self.symmetric else None
 
     def drift(self, dt: float):
         self.sc.steps_cyl_shard_drift(self.sim.ctx, dt, self.send)
@@ -143,8 +143,8 @@ class GpuRows:
         self.sc.steps_cyl_shard_kick(self.sim.ctx, recv)
 
     def force(self, recv):
-        self.sc.steps_cyl_shard_force(self.sim.ctx, recv, self.sums)
-        return self.sums
+        self.sc.steps_cyl_shard_force(self.sim.ctx, recv, self.pair_sums)
+        return self.pair_sums
 
     def finish(self, own):
         self.sc.steps_cyl_shard_finish(self.sim.ctx, own)

@@ -210,11 +210,15 @@ def run_reference(args, rank, world):
     d = ics.workload_ics(w)
     n = w.n
     per_step_target = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    probe = ics.subsample(n, 4, seed=900)
-    t0 = time.perf_counter()
-    oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=probe)
-    dt_probe = max(time.perf_counter() - t0, 1e-3)
-    k = int(min(n, max(4, 4 * per_step_target / dt_probe)))
+    # size the per-step sample from a real (untimed) calibration run, so that the
+    # thread pool is warm and each step holds enough rows to keep every core busy
+    k = 8 * oracle.num_threads()
+    for _ in range(2):
+        idx = ics.subsample(n, k, seed=900)
+        t0 = time.perf_counter()
+        oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, w.n_cut, idx=idx)
+        el = max(time.perf_counter() - t0, 1e-3)
+        k = int(min(n, max(8 * oracle.num_threads(), k * per_step_target / el)))
     times = []
     for s in range(args.warmup + args.steps):
         idx = ics.subsample(n, k, seed=1000 + s)

@@ -58,6 +58,9 @@ constexpr int kBJ = 128;  // j per shared-memory tile
 #define STEPS_SPLINE_UNROLL 2 // unroll of the spline-capable image loop
 #endif
 constexpr int kSplineUnroll = STEPS_SPLINE_UNROLL;
+#ifndef STEPS_NCUT_FIXED
+#define STEPS_NCUT_FIXED 1    // compile the windows N_cut = 16 and 64 unrolled beside the general one
+#endif
 
 typedef unsigned long long u64;
 
@@ -242,9 +245,10 @@ __device__ __forceinline__ void newton_pair(u64& O, u64 STEP, u64 DR2, u64& SR, 
 //       other pairs up to kw use the outer-shell form; the rest the Newtonian
 //       loop (1/r^3), which is exact there because |dz +- k| >= k - 1/2 > h.
 //   EDGE = false leaves the edge image out (the near part |k| < n_cut only).
-template <bool EDGE = true>
-__device__ __forceinline__ void pair_images_fp32(float dR2, float dz, float hh, int n_cut, float fnc, int kw,
+template <bool EDGE = true, int NC = 0>  // NC > 0: the window fixed at compile time (n_cut is then NC)
+__device__ __forceinline__ void pair_images_fp32(float dR2, float dz, float hh, int n_cut_rt, float fnc, int kw,
                                                  float& sr, float& sz) {
+  const int n_cut = NC > 0 ? NC : n_cut_rt;
   const u64 DR2 = pk(dR2, dR2);
   const u64 STEP = pk(1.0f, -1.0f);
   // centre image (k = 0) and edge image (dz - sign(dz) Ncut, absent at dz == 0)
@@ -302,9 +306,15 @@ __device__ __forceinline__ void pair_images_fp32(float dR2, float dz, float hh, 
     CZ = mul2(O, CR);
     O = pk(dz, dz);
   }
-  // Newtonian image pairs k .. n_cut - 1, outward: the first (count mod 4)
-  // enter a straight run part-way (no remainder loop), the rest go in fours
+  // Newtonian image pairs k .. n_cut - 1, outward. With the window fixed at
+  // compile time and no softened pair beyond the centre (k == 1, the common
+  // case), one straight run; else the first (count mod 4) enter a straight run
+  // part-way (no remainder loop) and the rest go in fours.
   const int cnt = n_cut - k;
+  if (NC > 0 && k == 1) {
+#pragma unroll
+    for (int q = 1; q < NC; ++q) newton_pair(O, STEP, DR2, SR, SZ);
+  } else {
   switch (cnt & 3) {
     case 3: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
     case 2: newton_pair(O, STEP, DR2, SR, SZ);  // fall through
@@ -317,6 +327,7 @@ __device__ __forceinline__ void pair_images_fp32(float dR2, float dz, float hh, 
     newton_pair(O, STEP, DR2, SR, SZ);
     newton_pair(O, STEP, DR2, SR, SZ);
     newton_pair(O, STEP, DR2, SR, SZ);
+  }
   }
   float s0, s1, z0, z1, c0, c1, d0, d1;
   upk(SR, s0, s1);

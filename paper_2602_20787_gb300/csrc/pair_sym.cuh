@@ -143,7 +143,14 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
         int kw;
         pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
         float sr, szz;
-        pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
+#if STEPS_NCUT_FIXED
+        if (n_cut == 16)
+          pair_images_fp32<true, 16>(dR2, dz, hh, 16, fnc, kw, sr, szz);
+        else if (n_cut == 64)
+          pair_images_fp32<true, 64>(dR2, dz, hh, 64, fnc, kw, sr, szz);
+        else
+#endif
+          pair_images_fp32(dR2, dz, hh, n_cut, fnc, kw, sr, szz);
         const float msr = A.w * sr;
         gx = fmaf(dx, msr, gx);
         gy = fmaf(dy, msr, gy);

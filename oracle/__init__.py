@@ -124,6 +124,7 @@ def lib():
         L.or_image_sums_inf.argtypes = [d, d, d, i32, p, p]; L.or_image_sums_inf.restype = None
         L.or_pair_field_inf.argtypes = [i64, p, p, p, p, p, d, d, i64, p, p, p, p]; L.or_pair_field_inf.restype = None
         L.or_tail_base_inf.argtypes = [d, d, i32, p, p]; L.or_tail_base_inf.restype = None
+        L.or_ewald_tail.argtypes = [d, d, i32, d, i32, i32, p, p]; L.or_ewald_tail.restype = None
         T = ctypes.POINTER(TableCfg)
         L.or_tail_residual.argtypes = [d, d, i32, i32, p]; L.or_tail_residual.restype = None
         L.or_tail_table_build.argtypes = [T, p]; L.or_tail_table_build.restype = None
@@ -429,6 +430,14 @@ def pair_field_inf(pos, m, h, G, L, idx=None):
     lib().or_pair_field_inf(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(h), float(G), float(L), ni, ip, _ptr(gx),
                             _ptr(gy), _ptr(gz))
     return np.stack([gx, gy, gz], axis=1)
+
+
+def ewald_tail(dR, dzw, n0, alpha, nmax, mmax):
+    """Sect. 2.3 Ewald sums (SR, SZ) of the infinite line's images |k| > n0, units of L."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_ewald_tail(float(dR), float(dzw), int(n0), float(alpha), int(nmax), int(mmax), ctypes.byref(a),
+                        ctypes.byref(b))
+    return a.value, b.value
 
 
 def tail_base_inf(dR, adz, n0):

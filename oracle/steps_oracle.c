@@ -693,6 +693,90 @@ void or_image_sums_inf(double dR, double dzw, double h, int32_t n0, double* SR, 
   *SZ = sz.s + sz.c;
 }
 
+/* ---------------------------------------------------------------------------
+ * Ewald summation of the infinite periodic line (Sect. 2.3, eqs.
+ * cylindricalEwaldSplit, EwaldRealSum, EwaldRecSum and the m = 0 term), in
+ * units of L (period 1), returning the sums of the images |k| > n0 in the
+ * convention of or_image_sums_inf (point masses: force -G m (dR SR, SZ)).
+ * The split parameter alpha is in units of 1/L.
+ *   Real space (eq. EwaldRealSum): an image at distance r contributes
+ *     [erfc(a r) + (2 a r / sqrt(pi)) exp(-a^2 r^2)] / r^3 = 1/r^3 - a^3 E(a r),
+ *     E(x) = [erf(x) - (2 x / sqrt(pi)) exp(-x^2)] / x^3,
+ *   summed over |n| <= nmax. The images |n| <= n0 are left out of the tail, so
+ *   for them only -a^3 E(a r) remains, which is finite at r = 0 (E(0) =
+ *   4 / (3 sqrt(pi))); E comes from its series below x = 0.25.
+ *   Fourier space (eq. EwaldRecSum): mode k = 2 pi m of the screened line has
+ *   the potential -2 cos(k z) B(k, rho), with the kernel re-derived: writing
+ *   erf(a r)/r = (2/sqrt(pi)) Int_0^a exp(-r^2 s^2) ds and integrating along z,
+ *     B(k, rho) = Int_0^{a^2} exp(-rho^2 t - k^2 / (4t)) dt / t,
+ *   which tends to 2 K0(k rho) as a grows. The printed eq. Bkernel tends to
+ *   2 exp(-k rho) instead, the kernel of a doubly periodic slab. The sums get
+ *     SR += 4 cos(k z) J(k, rho), J = Int_0^{a^2} exp(-rho^2 t - k^2/(4t)) dt,
+ *     SZ += 2 k sin(k z) B(k, rho),
+ *   both integrals taken in s = ln t with composite 8-point Gauss-Legendre.
+ *   m = 0: the line's mean radial field, SR += 2 (1 - exp(-a^2 rho^2)) / rho^2.
+ * ------------------------------------------------------------------------- */
+static double or_ewald_E(double x) {
+  const double sqpi = 1.7724538509055160273;
+  if (x < 0.25) {
+    /* (2/sqrt(pi)) sum_{n>=1} (-1)^(n+1) 2n x^(2n-2) / (n! (2n+1)) */
+    double x2 = x * x, term = 1.0, sum = 0.0, fact = 1.0;
+    for (int n = 1; n <= 12; ++n) {
+      fact *= (double)n;
+      sum += ((n % 2) ? 1.0 : -1.0) * 2.0 * n * term / (fact * (2.0 * n + 1.0));
+      term *= x2;
+    }
+    return 2.0 / sqpi * sum;
+  }
+  return (erf(x) - 2.0 * x / sqpi * exp(-x * x)) / (x * x * x);
+}
+
+/* J (with_t = 0) or B (with_t = 1) of the Fourier kernel: Int over s = ln t from
+ * ln(k^2 / 300) (where exp(-k^2 / (4t)) < e^-75) to ln(a^2) */
+static double or_ewald_mode_integral(double k, double rho, double a, int with_t) {
+  const double s_hi = log(a * a), s_lo = log(k * k / 300.0);
+  if (s_lo >= s_hi) return 0.0;
+  const int panels = 256;
+  const double h = (s_hi - s_lo) / panels;
+  double tot = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    const double mid = s_lo + (p + 0.5) * h, half = 0.5 * h;
+    double acc = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      const double sv = mid + half * or_gl_x[q];
+      const double t = exp(sv);
+      const double g = exp(-rho * rho * t - k * k / (4.0 * t));
+      acc += or_gl_w[q] * (with_t ? g : g * t);
+    }
+    tot += acc * half;
+  }
+  return tot;
+}
+
+void or_ewald_tail(double dR, double dzw, int32_t n0, double alpha, int32_t nmax, int32_t mmax, double* SR,
+                   double* SZ) {
+  const double R2 = dR * dR, a = alpha, a3 = a * a * a;
+  or_sum sr = {0, 0}, sz = {0, 0};
+  for (int k = -nmax; k <= nmax; ++k) {
+    const double o = dzw + (double)k, r = sqrt(R2 + o * o);
+    const double screened = -a3 * or_ewald_E(a * r);
+    const double f = (k >= -n0 && k <= n0) ? screened : 1.0 / (r * r * r) + screened;
+    or_add(&sr, f);
+    or_add(&sz, o * f);
+  }
+  const double two_pi = 6.283185307179586477;
+  for (int m = 1; m <= mmax; ++m) {
+    const double k = two_pi * m;
+    or_add(&sr, 4.0 * cos(k * dzw) * or_ewald_mode_integral(k, dR, a, 0));
+    or_add(&sz, 2.0 * k * sin(k * dzw) * or_ewald_mode_integral(k, dR, a, 1));
+  }
+  const double y = a * a * R2;
+  or_add(&sr, y > 0 ? -2.0 * a * a * expm1(-y) / y : 2.0 * a * a);
+  /* the images |k| > n0 that the real-space sum missed are screened away */
+  *SR = sr.s + sr.c;
+  *SZ = sz.s + sz.c;
+}
+
 /* Pair term with the infinite window: a_i = -G sum_j m_j (dx SR, dy SR, SZ)/L^2 */
 void or_pair_field_inf(int64_t n, const double* x, const double* y, const double* z, const double* m,
                        const double* h, double G, double L, int64_t ni, const int64_t* idx, double* gx,

@@ -90,6 +90,11 @@ void or_pair_field_inf(int64_t n, const double* x, const double* y, const double
                        const double* h, double G, double L, int64_t ni, const int64_t* idx, double* gx,
                        double* gy, double* gz);
 void or_tail_base_inf(double dR, double adz, int32_t n0, double* BR, double* BZ);
+/* Ewald summation of the infinite line (Sect. 2.3) with the re-derived Fourier
+ * kernel: the sums of the images |k| > n0 (units of L, point masses), split
+ * parameter alpha (1/L), real-space images |n| <= nmax, Fourier modes m <= mmax. */
+void or_ewald_tail(double dR, double dzw, int32_t n0, double alpha, int32_t nmax, int32_t mmax, double* SR,
+                   double* SZ);
 /* Correction-table tail (the paper's Sect. 2.3 table restated for the windowed
  * sum beyond |k| <= n0): residual of the point-mass tail over the continuum base
  * in envelope units on a uniform (dR, |dz|) grid, read bilinearly. */

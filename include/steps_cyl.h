@@ -381,6 +381,28 @@ int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
 int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, double dR_max, double err_median,
                                double err_p999, int32_t check_particles, double* report);
 
+/* The infinite window's table (n_cut = 0) from the Ewald summation of the line
+ * (Sect. 2.3, eqs. cylindricalEwaldSplit, EwaldRealSum, EwaldRecSum and the
+ * m = 0 term) instead of the direct sum: in FP64 on the GPU, the real-space
+ * images |k| <= nmax screened by erfc at split parameter alpha (units 1/L; the
+ * near images |k| <= n0 keep only their smooth long-range part, so that they
+ * are left out of the tail), Fourier modes k = 2 pi m, 1 <= m <= mmax, and the
+ * m = 0 line term. The Fourier kernel is the incomplete Bessel integral
+ * Int_0^{alpha^2} exp(-rho^2 t - k^2 / (4 t)) dt / t, which tends to
+ * 2 K0(k rho) as alpha grows, as the kernel of a line must; the printed
+ * eq. Bkernel is the doubly periodic slab's kernel (its limit is 2 exp(-k rho)),
+ * so the paper's formula is read as this integral. nmax = 5, mmax = 12 at
+ * alpha = 1 is the paper's single-precision setting. Nodes, layout and read as
+ * for steps_cyl_build_tail_table; the direct construction runs beside it for
+ * the report (4 doubles, may be NULL): the largest node difference and the
+ * largest node magnitude (envelope units), Ewald build ms, direct build ms. The
+ * Ewald nodes are installed. STEPS_EINVAL for a finite window, FP64 precision,
+ * a sharded context, alpha outside [0.25, 8], nmax < n0 or above 64, mmax
+ * outside [0, 64], or the nx, ny and dR_max bounds above. A checkpoint restores
+ * the table through the direct construction. */
+int steps_cyl_build_tail_table_ewald(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, double dR_max, double alpha,
+                                     int32_t nmax, int32_t mmax, double* report);
+
 /* Copy out the context's table: out = ny x nx x 2 floats (host; may be NULL to
  * read only the sizes), its nx, ny and dR_max (each may be NULL).
  * STEPS_ENOSURROGATE when no table was built. */

@@ -1699,14 +1699,38 @@ int accept_surrogate(steps_cyl_ctx* c, const float* P, double bmed, double bp999
   return STEPS_OK;
 }
 
+// Ewald construction of the infinite-window table: split parameter (1/L), the
+// real-space images |k| <= nmax and the Fourier modes m <= mmax.
+struct EwaldParams {
+  double alpha;
+  int nmax, mmax;
+};
+
+// Device buffers of one table build, freed on every exit path.
+struct TableBuffers {
+  cudaStream_t st;
+  double2 *node = nullptr, *direct = nullptr;
+  float2* f32 = nullptr;
+  ~TableBuffers() {
+    for (void* p : {(void*)node, (void*)direct, (void*)f32})
+      if (p) cudaFreeAsync(p, st);
+  }
+};
+
 // Correction-table tail: node residuals in FP64 on the GPU, stored as an FP32
 // float2 array and read through a texture with bilinear filtering (the
-// cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius.
-int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
+// cloud-in-cell read). dR_max 0 = 2.2 x the largest particle radius. With ew
+// (infinite window only) the nodes come from the Ewald summation, and the
+// direct construction runs beside it for the report: ew_rep = largest node
+// difference, largest node magnitude (both in envelope units), Ewald build ms,
+// direct build ms.
+int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms, const EwaldParams* ew = nullptr,
+                double* ew_rep = nullptr) {
   Range range("steps_cyl.build_table");
   if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
   if (c->p.n0 < 1 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
     return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  if (ew && c->p.n_cut != 0) return fail(STEPS_EINVAL, "the Ewald construction is for the infinite window (n_cut = 0)");
   if (dR_max == 0.0) {
     std::vector<double> hx(c->n), hy(c->n);
     CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
@@ -1716,23 +1740,61 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
     for (int i = 0; i < c->n; ++i) rm = std::max(rm, std::hypot(hx[i], hy[i]));
     dR_max = std::max(2.2 * rm * c->invL, 1.0);
   }
+  const int count = nx * ny;
+  TableBuffers tb{c->st};
+  CK(cudaMallocAsync(&tb.node, sizeof(double2) * count, c->st));
+  CK(cudaMallocAsync(&tb.f32, sizeof(float2) * count, c->st));
+  float t_direct = 0.f, t_ewald = 0.f;
+  CK(cudaEventRecord(c->e0, c->st));
+  tail_table_kernel<<<grid_for(count, 128), 128, 0, c->st>>>(nx, ny, dR_max, c->p.n_cut, c->p.n0, tb.node);
+  CKLAUNCH("tail_table");
+  CK(cudaEventRecord(c->e1, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaEventElapsedTime(&t_direct, c->e0, c->e1));
+  if (ew) {
+    EwaldRule G;
+    std::vector<double> gx, gw;
+    gauss_legendre(8, gx, gw);
+    std::copy(gx.begin(), gx.end(), G.x);
+    std::copy(gw.begin(), gw.end(), G.w);
+    tb.direct = tb.node;
+    tb.node = nullptr;
+    CK(cudaMallocAsync(&tb.node, sizeof(double2) * count, c->st));
+    CK(cudaEventRecord(c->e0, c->st));
+    tail_table_ewald_kernel<<<grid_for(count, 128), 128, 0, c->st>>>(nx, ny, dR_max, c->p.n0, ew->alpha, ew->nmax,
+                                                                     ew->mmax, G, tb.node);
+    CKLAUNCH("tail_table_ewald");
+    CK(cudaEventRecord(c->e1, c->st));
+    std::vector<double2> he(count), hd(count);
+    CK(cudaMemcpyAsync(he.data(), tb.node, sizeof(double2) * count, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(hd.data(), tb.direct, sizeof(double2) * count, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaEventElapsedTime(&t_ewald, c->e0, c->e1));
+    double dmax = 0.0, vmax = 0.0;
+    for (int q = 0; q < count; ++q) {
+      if (!std::isfinite(he[q].x) || !std::isfinite(he[q].y)) return fail(STEPS_ECUDA, "Ewald table node %d is not finite", q);
+      dmax = std::max({dmax, std::fabs(he[q].x - hd[q].x), std::fabs(he[q].y - hd[q].y)});
+      vmax = std::max({vmax, std::fabs(hd[q].x), std::fabs(hd[q].y)});
+    }
+    if (ew_rep) {
+      ew_rep[0] = dmax;
+      ew_rep[1] = vmax;
+      ew_rep[2] = t_ewald;
+      ew_rep[3] = t_direct;
+    }
+  }
+  table_to_float_kernel<<<grid_for(count, 128), 128, 0, c->st>>>(tb.node, count, tb.f32);
+  CKLAUNCH("table_to_float");
   c->tab_ok = false;
   if (c->tab.tex) CK(cudaDestroyTextureObject(c->tab.tex));
   c->tab.tex = 0;
   if (c->tab_arr) CK(cudaFreeArray(c->tab_arr));
   c->tab_arr = nullptr;
-  float2* buf = nullptr;
-  CK(cudaMallocAsync(&buf, sizeof(float2) * (size_t)nx * ny, c->st));
-  CK(cudaEventRecord(c->e0, c->st));
-  tail_table_kernel<<<grid_for(nx * ny, 128), 128, 0, c->st>>>(nx, ny, dR_max, c->p.n_cut, c->p.n0, buf);
-  CKLAUNCH("tail_table");
-  CK(cudaEventRecord(c->e1, c->st));
   const cudaChannelFormatDesc ch = cudaCreateChannelDesc<float2>();
   cudaError_t e = cudaMallocArray(&c->tab_arr, &ch, nx, ny);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DToArrayAsync(c->tab_arr, 0, 0, buf, sizeof(float2) * nx, sizeof(float2) * nx, ny,
+    e = cudaMemcpy2DToArrayAsync(c->tab_arr, 0, 0, tb.f32, sizeof(float2) * nx, sizeof(float2) * nx, ny,
                                  cudaMemcpyDeviceToDevice, c->st);
-  cudaFreeAsync(buf, c->st);
   if (e != cudaSuccess) return fail(STEPS_ECUDA, "table array: %s", cudaGetErrorString(e));
   cudaResourceDesc res;
   std::memset(&res, 0, sizeof res);
@@ -1753,9 +1815,7 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms) {
   c->tab_ny = ny;
   c->tab_dR_max = dR_max;
   CK(cudaStreamSynchronize(c->st));
-  float t = 0.f;
-  CK(cudaEventElapsedTime(&t, c->e0, c->e1));
-  if (ms) *ms = t;
+  if (ms) *ms = ew ? t_ewald : t_direct;
   return STEPS_OK;
 }
 
@@ -2949,6 +3009,28 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* c, int32_t nx, int32_t ny, double 
     report[3] = ms;
   }
   if (!ok) return fail(STEPS_ESURROGATE_REJECTED, "correction table rejected: median %.3g, p99.9 %.3g", med, p999);
+  return STEPS_OK;
+}
+
+int steps_cyl_build_tail_table_ewald(steps_cyl_ctx* c, int32_t nx, int32_t ny, double dR_max, double alpha,
+                                     int32_t nmax, int32_t mmax, double* report) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (c->shard) return refuse_sharded(c, "steps_cyl_build_tail_table_ewald (build before sharding)");
+  if (!is_inf(c)) return fail(STEPS_EINVAL, "the Ewald construction is for the infinite window (n_cut = 0)");
+  if (nx < 2 || nx > 4096 || ny < 2 || ny > 1024) return fail(STEPS_EINVAL, "nx must be in [2, 4096], ny in [2, 1024]");
+  if (!(dR_max >= 0) || !std::isfinite(dR_max)) return fail(STEPS_EINVAL, "dR_max must be finite and >= 0");
+  if (!(alpha >= 0.25 && alpha <= 8.0)) return fail(STEPS_EINVAL, "alpha must be in [0.25, 8] (units 1/L)");
+  if (nmax < c->p.n0 || nmax > 64 || mmax < 0 || mmax > 64)
+    return fail(STEPS_EINVAL, "need n0 <= nmax <= 64 and 0 <= mmax <= 64");
+  if (c->p.precision == STEPS_FP64) return fail(STEPS_EINVAL, "the correction table needs an FP32 precision");
+  DeviceGuard guard(c->dev);
+  const EwaldParams ew{alpha, nmax, mmax};
+  double rep[4] = {0, 0, 0, 0};
+  int rc = build_table(c, nx, ny, dR_max, nullptr, &ew, rep);
+  if (rc) return rc;
+  c->tab_ok = true;
+  if (report) std::copy(rep, rep + 4, report);
   return STEPS_OK;
 }
 

@@ -29,7 +29,7 @@ namespace steps {
 // [ny][nx]. n_cut = 0 is the infinite window: images to |k| <= kKInf exactly
 // and the line ends beyond, against the infinite base.
 
-static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cut, int n0, float2* __restrict__ out) {
+static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cut, int n0, double2* __restrict__ out) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny; q += gridDim.x * blockDim.x) {
     const int i = q % nx, j = q / nx;
     const double dR = dR_max * i / (nx - 1), adz = 0.5 * j / (ny - 1), R2 = dR * dR;
@@ -45,7 +45,7 @@ static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cu
       line_ends_fp64(R2, adz, sr, sz);
       double BR, BZ, ER, EZ;
       tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
-      out[q] = make_float2((float)((sr - BR) / ER), (float)((sz - BZ) / EZ));
+      out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
       continue;
     }
     for (int k = n0 + 1; k <= n_cut + 1; ++k) {
@@ -63,8 +63,100 @@ static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cu
     }
     double BR, BZ, ER, EZ;
     tail_base_fp64(dR, adz, n_cut, n0, BR, BZ, ER, EZ);
-    out[q] = make_float2((float)((sr - BR) / ER), (float)((sz - BZ) / EZ));
+    out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same residuals of the infinite window from the Ewald summation of the
+// line (Sect. 2.3, eqs. cylindricalEwaldSplit, EwaldRealSum, EwaldRecSum and
+// the m = 0 term) instead of the direct sum, in FP64, period 1, split
+// parameter alpha (1/L):
+//   - real space: images |k| <= nmax, each 1/r^3 - alpha^3 E(alpha r) with
+//     E(x) = [erf(x) - (2x/sqrt(pi)) exp(-x^2)] / x^3; the near images
+//     |k| <= n0 are not part of the tail and keep only -alpha^3 E (finite at
+//     r = 0; E from its series below x = 0.25);
+//   - Fourier space: mode k = 2 pi m adds 4 cos(kz) J and 2 k sin(kz) B to the
+//     sums, with J, B = Int_0^{alpha^2} exp(-rho^2 t - k^2/(4t)) (1, 1/t) dt
+//     (the kernel of a line: B -> 2 K0(k rho) as alpha grows; the printed
+//     eq. Bkernel is a slab's), taken in s = ln t with composite Gauss-Legendre;
+//   - m = 0: 2 (1 - exp(-alpha^2 rho^2)) / rho^2.
+struct EwaldRule {
+  double x[8], w[8];  // Gauss-Legendre nodes and weights on [-1, 1]
+};
+
+__device__ __forceinline__ double ewald_E(double x) {
+  const double c = 1.1283791670955126;  // 2 / sqrt(pi)
+  if (x < 0.25) {
+    // c * sum_{n>=1} (-1)^(n+1) 2n x^(2n-2) / (n! (2n+1))
+    const double x2 = x * x;
+    double term = 1.0, fact = 1.0, acc = 0.0;
+    for (int n = 1; n <= 12; ++n) {
+      fact *= (double)n;
+      acc += ((n & 1) ? 2.0 : -2.0) * n * term / (fact * (2.0 * n + 1.0));
+      term *= x2;
+    }
+    return c * acc;
+  }
+  return (erf(x) - c * x * exp(-x * x)) / (x * x * x);
+}
+
+// Int over s = ln t in [ln(k^2/300), ln(alpha^2)] of exp(-rho^2 e^s - k^2/(4 e^s)) (e^s for J, 1 for B)
+__device__ __forceinline__ void ewald_mode(double k, double rho, double alpha, const EwaldRule& G, double& J,
+                                           double& B) {
+  J = 0.0;
+  B = 0.0;
+  const double s_hi = 2.0 * log(alpha), s_lo = log(k * k / 300.0);
+  if (s_lo >= s_hi) return;
+  constexpr int kPanels = 128;
+  const double h = (s_hi - s_lo) / kPanels, half = 0.5 * h;
+  for (int p = 0; p < kPanels; ++p) {
+    const double mid = s_lo + (p + 0.5) * h;
+    double pj = 0.0, pb = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double t = exp(mid + half * G.x[q]);
+      const double g = exp(-rho * rho * t - 0.25 * k * k / t);
+      pj = fma(G.w[q], g * t, pj);
+      pb = fma(G.w[q], g, pb);
+    }
+    J = fma(pj, half, J);
+    B = fma(pb, half, B);
+  }
+}
+
+static __global__ void tail_table_ewald_kernel(int nx, int ny, double dR_max, int n0, double alpha, int nmax,
+                                               int mmax, EwaldRule G, double2* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny; q += gridDim.x * blockDim.x) {
+    const int i = q % nx, j = q / nx;
+    const double dR = dR_max * i / (nx - 1), adz = 0.5 * j / (ny - 1), R2 = dR * dR;
+    const double a3 = alpha * alpha * alpha;
+    double sr = 0.0, sz = 0.0;
+    for (int k = -nmax; k <= nmax; ++k) {
+      const double o = adz + (double)k, r = sqrt(R2 + o * o);
+      double f = -a3 * ewald_E(alpha * r);
+      if (k < -n0 || k > n0) f += 1.0 / (r * r * r);
+      sr += f;
+      sz = fma(o, f, sz);
+    }
+    for (int m = 1; m <= mmax; ++m) {
+      const double kk = 6.283185307179586 * m;
+      double J, B;
+      ewald_mode(kk, dR, alpha, G, J, B);
+      sr = fma(4.0 * cos(kk * adz), J, sr);
+      sz = fma(2.0 * kk * sin(kk * adz), B, sz);
+    }
+    const double y = alpha * alpha * R2;
+    sr += y > 0.0 ? -2.0 * alpha * alpha * expm1(-y) / y : 2.0 * alpha * alpha;
+    double BR, BZ, ER, EZ;
+    tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
+    out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
+  }
+}
+
+static __global__ void table_to_float_kernel(const double2* __restrict__ in, int count, float2* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
+    out[q] = make_float2((float)in[q].x, (float)in[q].y);
 }
 
 // Texture of the residual table and the map from the network-input scaling

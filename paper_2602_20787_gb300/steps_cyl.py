@@ -41,7 +41,8 @@ _EXPORTS = [
     "steps_cyl_last_error", "steps_cyl_pair_accel_noalloc", "steps_cyl_train_cfg_default", "steps_cyl_tail_sums",
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
-    "steps_cyl_build_tail_table", "steps_cyl_get_tail_table", "steps_cyl_check_tail",
+    "steps_cyl_build_tail_table", "steps_cyl_build_tail_table_ewald", "steps_cyl_get_tail_table",
+    "steps_cyl_check_tail",
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
     "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
     "steps_cyl_last_eval", "steps_cyl_shard_mode", "steps_cyl_shard_force", "steps_cyl_shard_finish",
@@ -131,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_set_tail.argtypes = [p, i32]
     L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
     L.steps_cyl_build_tail_table.argtypes = [p, i32, i32, d, d, d, i32, p]
+    L.steps_cyl_build_tail_table_ewald.argtypes = [p, i32, i32, d, d, i32, i32, p]
     L.steps_cyl_get_tail_table.argtypes = [p, p, p, p, p]
     L.steps_cyl_check_tail.argtypes = [p, i32, i32, p]
     L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
@@ -460,6 +462,17 @@ def steps_cyl_build_tail_table(ctx, nx: int = 257, ny: int = 33, dR_max: float =
     rep = np.zeros(4)
     _check(load().steps_cyl_build_tail_table(ctx, int(nx), int(ny), float(dR_max), float(err_median),
                                              float(err_p999), int(check_particles), _ptr(rep)))
+    return rep
+
+
+def steps_cyl_build_tail_table_ewald(ctx, nx: int = 144, ny: int = 128, dR_max: float = 0.0, alpha: float = 1.0,
+                                     nmax: int = 5, mmax: int = 12) -> np.ndarray:
+    """Build the infinite window's table by the Ewald summation of the line;
+    returns (largest node difference to the direct construction, largest node
+    magnitude, Ewald build ms, direct build ms)."""
+    rep = np.zeros(4)
+    _check(load().steps_cyl_build_tail_table_ewald(ctx, int(nx), int(ny), float(dR_max), float(alpha), int(nmax),
+                                                   int(mmax), _ptr(rep)))
     return rep
 
 

@@ -61,6 +61,9 @@ constexpr int kSplineUnroll = STEPS_SPLINE_UNROLL;
 #ifndef STEPS_NCUT_FIXED
 #define STEPS_NCUT_FIXED 1    // compile the windows N_cut = 16 and 64 unrolled beside the general one
 #endif
+#ifndef STEPS_PLAIN_MIN_BLOCKS
+#define STEPS_PLAIN_MIN_BLOCKS 8  // resident CTAs per SM the plain kernels are compiled for (registers)
+#endif
 
 typedef unsigned long long u64;
 

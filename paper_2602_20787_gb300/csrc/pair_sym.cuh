@@ -15,11 +15,14 @@
 // side only (the self pair adds exact zeros); an off-diagonal unit evaluates
 // its 128 x 128 pairs once and adds each to both sides.
 //
-// The j side. Per two j, each lane holds m_i v for its i; a warp-shuffle
-// reduction (the two j exchanged across the half-warps, then a butterfly over
-// 16 lanes) leaves the warp's sums of j0 on lanes 0..15 and of j1 on lanes
-// 16..31, which lanes 0 and 16 write to the warp's row of a shared array. After
-// the tile, thread q adds the four warps' sums of j-slot q in warp order.
+// The j side. In each group of 32 j-slots of a tile, lane l pairs its i with
+// slot (l + s) mod 32 at step s, so every slot meets every lane once in 32
+// steps. A lane keeps the running sum of m_i v for the slot it holds and passes
+// it to lane l - 1 after each step (JRing: one shuffle per component and step);
+// after the group lane l holds the warp's whole sum of slot (l + 31) mod 32 and
+// writes it to the warp's row of a shared array. (STEPS_SYM_RING = 0 keeps all
+// lanes on one slot and reduces each slot over the warp with shuffles instead.)
+// After the tile, thread q adds the four warps' sums of j-slot q in warp order.
 //
 // Accumulation. The i-side sum of a CTA's range (FP32, Kahan-compensated as in
 // the row kernels) and the j-side sum of a unit are converted to 64-bit fixed
@@ -120,6 +123,60 @@ __device__ __forceinline__ void jside_vec(float mi, float dx, float dy, float sr
   w[2] = mi * sz;
 }
 
+#ifndef STEPS_SYM_RING
+#define STEPS_SYM_RING 1  // 1: the j side is carried around the warp (JRing); 0: reduced per two j (jside_pair)
+#endif
+
+// The j-slot that this lane pairs with at step k of a tile. With the ring, in
+// each group of 32 slots lane l takes slot (l + k) mod 32 at step k, so every
+// slot meets every lane once in 32 steps; otherwise all lanes take slot k.
+__device__ __forceinline__ int jslot(int k) {
+#if STEPS_SYM_RING
+  return (k & ~31) | ((k + (int)threadIdx.x) & 31);
+#else
+  return k;
+#endif
+}
+
+// The j side carried around the warp: a lane keeps the running sum of the slot
+// it holds, adds its pair's vector, and takes over the sum of lane l + 1 (the
+// slot it holds at the next step). After the last step of a group no shift is
+// made: lane l then holds the whole warp's sum of slot (l + 31) mod 32, one
+// shuffle per component and step instead of a 32-lane reduction per slot.
+struct JRing {
+  float a[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void take(const float (&w)[3], bool shift) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] += w[c];
+      if (shift) a[c] = __shfl_sync(0xffffffffu, a[c], (threadIdx.x + 1) & 31);
+    }
+  }
+  // k: the group's last step
+  __device__ __forceinline__ void flush(float* row, int k) {
+    float* d = row + 3 * jslot(k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = a[c];
+      a[c] = 0.f;
+    }
+  }
+};
+
+// The j side of the two steps k, k + 1 (k even) into the warp's row.
+__device__ __forceinline__ void jside_two(JRing& ring, const float (&w0)[3], const float (&w1)[3], float* row,
+                                          int k) {
+#if STEPS_SYM_RING
+  const bool last = ((k + 2) & 31) == 0;
+  ring.take(w0, true);
+  ring.take(w1, !last);
+  if (last) ring.flush(row, k + 1);
+#else
+  (void)ring;
+  jside_pair(w0, w1, row, k);
+#endif
+}
+
 // ---- tile functions: all pairs of one i with the kBJ j of a shared tile -------
 // They add m_j v to the i-side Kahan sums and, when sym is set (an
 // off-diagonal unit), write the warp's j-side sums of every j-slot to row.
@@ -129,6 +186,7 @@ template <bool KAHAN>
 __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, const float4* sA, const float4* sB,
                                                bool sym, float* row, int n_cut, float fnc, float& sx, float& sy,
                                                float& sz, float& cx, float& cy, float& cz) {
+  JRing ring;
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -137,8 +195,9 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
       float w[2][3];
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
-        const float4 A = sA[k + jj];
-        const float4 B = sB[k + jj];
+        const int q = jslot(k + jj);
+        const float4 A = sA[q];
+        const float4 B = sB[q];
         float dx, dy, dz, dR2, hh;
         int kw;
         pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
@@ -157,7 +216,7 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
         gz = fmaf(A.w, szz, gz);
         jside_vec(mi, dx, dy, sr, szz, w[jj]);
       }
-      if (sym) jside_pair(w[0], w[1], row, k);
+      if (sym) jside_two(ring, w[0], w[1], row, k);
     }
     acc<KAHAN>(sx, cx, gx);
     acc<KAHAN>(sy, cy, gy);
@@ -165,8 +224,8 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
   }
 }
 
-// One network call of the learned tail for NJ j (slots k .. k + NJ - 1): the
-// i-side group sums and the j-side vectors w.
+// One network call of the learned tail for the NJ steps k .. k + NJ - 1 (slots
+// jslot(k + jj)): the i-side group sums and the j-side vectors w.
 template <int NJ, bool INF>
 __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const float4* sA, const float4* sB, int k,
                                           int self, int n_cut, const SurrW& W, uint32_t* ibuf, const SurrConst& S,
@@ -175,12 +234,14 @@ __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const fl
   int kw[NJ];
   SurrPair P[NJ];
   float u[NJ][3], y[NJ][2];
+  int q[NJ];
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
-    const float4 A = sA[k + jj];
-    const float4 B = sB[k + jj];
+    q[jj] = jslot(k + jj);
+    const float4 A = sA[q[jj]];
+    const float4 B = sB[q[jj]];
     pair_geometry(I, A, B, dx[jj], dy[jj], dz[jj], dR2[jj], hh[jj], kw[jj]);
-    mj[jj] = (k + jj == self) ? 0.0f : A.w;
+    mj[jj] = (q[jj] == self) ? 0.0f : A.w;
     surr_stage_a<INF>(dR2[jj], dz[jj], hh[jj], n_cut, kw[jj], S, P[jj]);
     u[jj][0] = P[jj].u[0];
     u[jj][1] = P[jj].u[1];
@@ -190,7 +251,7 @@ __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const fl
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
     float sr, szz;
-    surr_stage_c<INF>(I, sA[k + jj], sB[k + jj], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr, szz);
+    surr_stage_c<INF>(I, sA[q[jj]], sB[q[jj]], n_cut, kw[jj], S, P[jj], y[jj][0], y[jj][1], sr, szz);
     const float msr = mj[jj] * sr;
     gx = fmaf(dx[jj], msr, gx);
     gy = fmaf(dy[jj], msr, gy);
@@ -212,6 +273,7 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
                                               uint32_t* ibuf, const SurrConst& S, float& sx, float& sy, float& sz,
                                               float& cx, float& cy, float& cz) {
   static_assert(STEPS_SURR_NJ == 1 || STEPS_SURR_NJ == 2, "one or two j per network call");
+  JRing ring;
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -224,7 +286,7 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
         surr_call<1, INF>(I, mi, sA, sB, k, self, n_cut, W, ibuf, S, gx, gy, gz, w);
         surr_call<1, INF>(I, mi, sA, sB, k + 1, self, n_cut, W, ibuf, S, gx, gy, gz, w + 1);
       }
-      if (sym) jside_pair(w[0], w[1], row, k);
+      if (sym) jside_two(ring, w[0], w[1], row, k);
     }
     acc<KAHAN>(sx, cx, gx);
     acc<KAHAN>(sy, cy, gy);
@@ -238,6 +300,7 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
                                                bool sym, float* row, int self, int n_cut, const SurrConst& S,
                                                const TableTail& T, float& sx, float& sy, float& sz, float& cx,
                                                float& cy, float& cz) {
+  JRing ring;
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -246,8 +309,9 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
       float w[2][3];
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
-        const float4 A = sA[k + jj];
-        const float4 B = sB[k + jj];
+        const int q = jslot(k + jj);
+        const float4 A = sA[q];
+        const float4 B = sB[q];
         float dx, dy, dz, dR2, hh;
         int kw;
         pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
@@ -256,14 +320,14 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
         const float2 r = table_read(T, P.u[0], P.u[1]);
         float sr, szz;
         surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
-        const float mj = (k + jj == self) ? 0.0f : A.w;
+        const float mj = (q == self) ? 0.0f : A.w;
         const float msr = mj * sr;
         gx = fmaf(dx, msr, gx);
         gy = fmaf(dy, msr, gy);
         gz = fmaf(mj, szz, gz);
         jside_vec(mi, dx, dy, sr, szz, w[jj]);
       }
-      if (sym) jside_pair(w[0], w[1], row, k);
+      if (sym) jside_two(ring, w[0], w[1], row, k);
     }
     acc<KAHAN>(sx, cx, gx);
     acc<KAHAN>(sy, cy, gy);
@@ -327,7 +391,7 @@ __device__ __forceinline__ void sym_stream_k(const float4* __restrict__ jA, cons
 
 // ---- kernels ---------------------------------------------------------------
 template <bool KAHAN>
-__global__ void __launch_bounds__(kBI, 8)
+__global__ void __launch_bounds__(kBI, STEPS_PLAIN_MIN_BLOCKS)
 pair_sym_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB, long long Ua,
                 long long U, int C, FixAcc F) {
   __shared__ float4 sA[kBJ];

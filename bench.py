@@ -720,6 +720,16 @@ def run_inf(args):
     line["surrogate"] = {"train_ms": rep[5], "check_vs_table_median": rep[2], "check_vs_table_p999": rep[3],
                          "pair_ms": mss, "pair_interactions_per_s": pairs / (mss * 1e-3),
                          "table_speedup_over_surrogate": mss / ms}
+    # the same table built by the Ewald summation of the line (Sect. 2.3), on the
+    # paper's 144 x 128 grid at its single-precision setting, against the direct one
+    sc.steps_cyl_build_tail_table(sim.ctx, 144, 128, dR_max)
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+    a_dir, _ = _timed_forces(sc, torch, sim, 1)
+    rep_e = sc.steps_cyl_build_tail_table_ewald(sim.ctx, 144, 128, dR_max, 1.0, 5, 12)
+    a_ew, mse = _timed_forces(sc, torch, sim, 3)
+    line["ewald_table"] = {"nx": 144, "ny": 128, "alpha": 1.0, "nmax": 5, "mmax": 12, "build_ms": rep_e[2],
+                           "direct_build_ms": rep_e[3], "max_node_difference": rep_e[0], "max_node": rep_e[1],
+                           "pair_ms": mse, "forces_vs_direct_table": _err(a_ew, a_dir)}
     sim.close()
     print(json.dumps(line), flush=True)
     return 0

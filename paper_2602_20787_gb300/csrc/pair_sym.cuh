@@ -181,6 +181,11 @@ __device__ __forceinline__ void jside_two(JRing& ring, const float (&w0)[3], con
 // They add m_j v to the i-side Kahan sums and, when sym is set (an
 // off-diagonal unit), write the warp's j-side sums of every j-slot to row.
 
+#ifndef STEPS_PLAIN_JUNROLL
+#define STEPS_PLAIN_JUNROLL 1  // unroll of the two-j steps of a Kahan group (plain image sum)
+#endif
+constexpr int kPlainJUnroll = STEPS_PLAIN_JUNROLL;
+
 // Plain image sum (pair_fp32.cuh), two j per step.
 template <bool KAHAN>
 __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, const float4* sA, const float4* sB,
@@ -190,7 +195,7 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
     float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll 1
+#pragma unroll(kPlainJUnroll)
     for (int k = k0; k < k0 + STEPS_KAHAN_GROUP; k += 2) {
       float w[2][3];
 #pragma unroll

@@ -65,14 +65,19 @@ def make_surr_cfg(n_cut, n0, dR_max, out_mu=(0.0, 0.0), out_sc=(1.0, 1.0)):
     return c
 
 
+TABLE_CIC, TABLE_TSC = 0, 1
+
+
 class TableCfg(ctypes.Structure):
     _fields_ = [("n_cut", ctypes.c_int32), ("n0", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-                ("dR_max", ctypes.c_double)]
+                ("dR_max", ctypes.c_double), ("read", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
-def make_table_cfg(n_cut, n0, nx, ny, dR_max):
+def make_table_cfg(n_cut, n0, nx, ny, dR_max, read=TABLE_CIC):
+    """Table definition; read = TABLE_CIC (bilinear) or TABLE_TSC (Sect. 2.3)."""
     c = TableCfg()
     c.n_cut, c.n0, c.nx, c.ny, c.dR_max = int(n_cut), int(n0), int(nx), int(ny), float(dR_max)
+    c.read = int(read)
     return c
 
 

@@ -850,9 +850,43 @@ void or_tail_table_build(const or_table_cfg* c, double* tab) {
                        tab + 2 * ((size_t)j * c->nx + i));
 }
 
+/* TSC read: in node units x, the nearest node i = round(x) and d = x - i carry
+ * the triangular-shaped-cloud weights (1/2 - d)^2 / 2, 3/4 - d^2, (1/2 + d)^2 / 2
+ * on nodes i - 1, i, i + 1 (the overlap of a unit-width triangle cloud centred
+ * at x with each node's cell), one factor per axis; a node outside the table
+ * takes the value of the nearest edge node. */
+static void or_tsc_weights(double x, int n, int idx[3], double w[3]) {
+  int i = (int)floor(x + 0.5);
+  double d = x - i;
+  w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+  w[1] = 0.75 - d * d;
+  w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+  for (int k = 0; k < 3; ++k) {
+    int q = i - 1 + k;
+    idx[k] = q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
+  }
+}
+
+static void or_tail_table_read_tsc(const double* tab, const or_table_cfg* c, double fx, double fy, double r[2]) {
+  int ix[3], iy[3];
+  double wx[3], wy[3];
+  or_tsc_weights(fx, c->nx, ix, wx);
+  or_tsc_weights(fy, c->ny, iy, wy);
+  for (int q = 0; q < 2; ++q) {
+    double acc = 0.0;
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) acc += wx[a] * wy[b] * tab[2 * ((size_t)iy[b] * c->nx + ix[a]) + q];
+    r[q] = acc;
+  }
+}
+
 void or_tail_table_read(const double* tab, const or_table_cfg* c, double dR, double adz, double r[2]) {
   double fx = (dR < c->dR_max ? dR : c->dR_max) / c->dR_max * (c->nx - 1);
   double fy = adz / 0.5 * (c->ny - 1);
+  if (c->read == OR_TABLE_TSC) {
+    or_tail_table_read_tsc(tab, c, fx, fy, r);
+    return;
+  }
   int i = (int)floor(fx), j = (int)floor(fy);
   if (i > c->nx - 2) i = c->nx - 2;
   if (j > c->ny - 2) j = c->ny - 2;

@@ -97,10 +97,14 @@ void or_ewald_tail(double dR, double dzw, int32_t n0, double alpha, int32_t nmax
                    double* SZ);
 /* Correction-table tail (the paper's Sect. 2.3 table restated for the windowed
  * sum beyond |k| <= n0): residual of the point-mass tail over the continuum base
- * in envelope units on a uniform (dR, |dz|) grid, read bilinearly. */
+ * in envelope units on a uniform (dR, |dz|) grid, read with cloud-in-cell
+ * (bilinear) or triangular-shaped-cloud weights, the two reads Sect. 2.3 names. */
+#define OR_TABLE_CIC 0
+#define OR_TABLE_TSC 1
 typedef struct {
   int32_t n_cut, n0, nx, ny;   /* n_cut = 0: the infinite window */
   double dR_max;        /* last column; dR beyond it reads the last column */
+  int32_t read, pad;    /* OR_TABLE_CIC or OR_TABLE_TSC */
 } or_table_cfg;
 void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]);
 void or_tail_table_build(const or_table_cfg* c, double* tab); /* tab[ny][nx][2] */

@@ -1218,6 +1218,16 @@ def run_workload(args):
             "roofline": {"bound": "mufu", "mufu_ops_per_pair": mufu_t, "peak_pairs_per_s": peak_t,
                          "achieved_pairs_evaluated_per_s": ev_t["pairs_evaluated"] / (mst * 1e-3),
                          "frac": ev_t["pairs_evaluated"] / (mst * 1e-3) / peak_t, "symmetric": ev_t["symmetric"]}}
+        # the same table read with TSC weights (Sect. 2.3 names CIC and TSC)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
+        sc.steps_cyl_set_table_read(sim.ctx, sc.STEPS_TABLE_READ_TSC)
+        rq = sc.steps_cyl_build_tail_table(sim.ctx, nx, ny)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+        atq, msq = _timed_forces(sc, torch, sim, reps + 1)
+        line["table_tsc"] = {"check_median": rq[0], "check_p999": rq[1], "pair_ms": msq,
+                             "equivalent_pair_images_per_s": pairs * 2 * w.n_cut / (msq * 1e-3),
+                             "error_vs_fp64": _err(atq[idx], a64), "cost_vs_cic": msq / mst}
+        sc.steps_cyl_set_table_read(sim.ctx, sc.STEPS_TABLE_READ_CIC)
         sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
     if w.name.startswith("production") or w.name.startswith("plain_small") or w.name.startswith("lcdm"):
         steps = min(args.steps, w.nsteps) if w.nsteps else args.steps

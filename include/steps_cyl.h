@@ -55,6 +55,9 @@ extern "C" {
 #define STEPS_TAIL_SURROGATE 1  /* images |k| <= n0 direct, far tail from the learned surrogate */
 #define STEPS_TAIL_TABLE 2      /* images |k| <= n0 direct, far tail from the correction table */
 
+#define STEPS_TABLE_READ_CIC 0  /* correction table read with cloud-in-cell (bilinear) weights */
+#define STEPS_TABLE_READ_TSC 1  /* correction table read with triangular-shaped-cloud weights */
+
 #define STEPS_BG_OFF 0       /* no background term */
 #define STEPS_BG_FINITE 1    /* eq. F_horiz: cylinder of radius R_sim and height 2 Ncut L */
 #define STEPS_BG_INFINITE 2  /* eq. F_horiz_infty inside R_sim, line-mass field outside */
@@ -356,13 +359,19 @@ int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
 /* ---- correction-table tail -----------------------------------------------
  * Sect. 2.3, eq. S1R2EwaldCorrectionTable: the paper tabulates the force of the
  * periodic images beyond the nearest on an equally spaced (rho, z) grid and adds
- * it, read with cloud-in-cell interpolation, to the nearest-image force. Here
+ * it, read with cloud-in-cell or triangular-shaped-cloud interpolation, to the
+ * nearest-image force. Here
  * the table holds the images beyond the near range |k| <= n0 of the context's
  * window (eq. ForceCylindrical), for point masses, as the residual of that tail
  * over the continuum base in envelope units (the quantity the surrogate
  * learns), at nodes dR_i = i dR_max / (nx - 1), |dz|_j = j / (2 (ny - 1)) in
  * units of L; dR beyond dR_max reads the last column. It is computed in FP64 on
- * the GPU, stored in FP32 and read with the texture unit's bilinear filter. The
+ * the GPU, stored in FP32 and read with the texture unit's bilinear filter
+ * (CIC, the default), or with TSC weights: in node units x, the nearest node i
+ * and d = x - i weigh nodes i - 1, i, i + 1 by (1/2 - d)^2 / 2, 3/4 - d^2,
+ * (1/2 + d)^2 / 2 per axis (four bilinear fetches), a node beyond the edge
+ * taking the edge value. TSC smooths the table by a quarter of a cell squared
+ * times its curvature, so at the same grid it is less accurate than CIC. The
  * table form (STEPS_TAIL_TABLE) sums the near images exactly, adds
  * base + envelope x table, and corrects tail images inside the softening support
  * exactly, as the surrogate form does. With n_cut = 0 (the infinite window) the
@@ -402,6 +411,14 @@ int steps_cyl_build_tail_table(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, doubl
  * the table through the direct construction. */
 int steps_cyl_build_tail_table_ewald(steps_cyl_ctx* ctx, int32_t nx, int32_t ny, double dR_max, double alpha,
                                      int32_t nmax, int32_t mmax, double* report);
+
+/* Choose the read of the correction table: STEPS_TABLE_READ_CIC (the default)
+ * or STEPS_TABLE_READ_TSC. It applies from the next steps_cyl_build_tail_table
+ * or steps_cyl_build_tail_table_ewald, whose check (finite window) then tests
+ * the table form in that read; a table already built keeps the read it was
+ * built with. A checkpoint records the read of its table. STEPS_EINVAL for any
+ * other value. */
+int steps_cyl_set_table_read(steps_cyl_ctx* ctx, int32_t read);
 
 /* Copy out the context's table: out = ny x nx x 2 floats (host; may be NULL to
  * read only the sizes), its nx, ny and dR_max (each may be NULL).

@@ -299,8 +299,8 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
   }
 }
 
-// Correction-table tail (tail_table.cuh), two j per step.
-template <bool KAHAN, bool INF>
+// Correction-table tail (tail_table.cuh), two j per step; READ: 0 CIC, 1 TSC.
+template <bool KAHAN, bool INF, int READ>
 __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, const float4* sA, const float4* sB,
                                                bool sym, float* row, int self, int n_cut, const SurrConst& S,
                                                const TableTail& T, float& sx, float& sy, float& sz, float& cx,
@@ -322,7 +322,7 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
         pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
         SurrPair P;
         surr_stage_a<INF>(dR2, dz, hh, n_cut, kw, S, P);
-        const float2 r = table_read(T, P.u[0], P.u[1]);
+        const float2 r = table_read<READ>(T, P.u[0], P.u[1]);
         float sr, szz;
         surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
         const float mj = (q == self) ? 0.0f : A.w;
@@ -431,7 +431,7 @@ pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ j
                       });
 }
 
-template <bool KAHAN, bool INF>
+template <bool KAHAN, bool INF, int READ>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_sym_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB,
                       long long Ua, long long U, int C, TableTail T, SurrConst S, FixAcc F) {
@@ -441,8 +441,8 @@ pair_sym_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
   sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int self,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
-                        sym_tile_table<KAHAN, INF>(I, mi, a, bb, sym, row, self, n_cut, S, T, sx, sy, sz, cx, cy,
-                                                   cz);
+                        sym_tile_table<KAHAN, INF, READ>(I, mi, a, bb, sym, row, self, n_cut, S, T, sx, sy, sz,
+                                                         cx, cy, cz);
                       });
 }
 

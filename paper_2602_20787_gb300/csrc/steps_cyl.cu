@@ -278,6 +278,7 @@ struct steps_cyl_ctx {
   TableTail tab{};                 // texture of the residual table
   SurrConst tab_const{};           // mu = 0, sc = 1, the table's dR_max
   int tab_nx = 0, tab_ny = 0;
+  int tab_read_next = STEPS_TABLE_READ_CIC;  // the read of the next table build (tab.tsc: the built one's)
   double tab_dR_max = 0.0;
   bool tab_ok = false;             // an accepted table is loaded
   double tab_bound_med = 1e-5, tab_bound_p999 = 1e-3;
@@ -1018,6 +1019,19 @@ double sym_pairs(const steps_cyl_ctx* c) {
 }
 
 // The symmetric kernel of the form over the units [Ua, Ua + U) into F.
+// The symmetric table kernel in the context's table read (compiled per read, so
+// that the CIC path carries none of the TSC arithmetic).
+template <bool KAHAN, bool INF>
+void launch_sym_table(steps_cyl_ctx* c, bool tsc, int C, int n, int nc, int NB, long long Ua, long long U,
+                      const FixAcc& F) {
+  if (tsc)
+    pair_sym_table_kernel<KAHAN, INF, 1><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
+                                                               c->tab_const, F);
+  else
+    pair_sym_table_kernel<KAHAN, INF, 0><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
+                                                               c->tab_const, F);
+}
+
 int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const FixAcc& F) {
   const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
   const int nc = c->p.n_cut, n = c->n, NB = c->NB;
@@ -1040,17 +1054,15 @@ int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const Fix
     CKLAUNCH("pair_sym_surrogate");
   } else if (form == Form::TABLE) {
     const int C = ctas(c->SYTC);
+    const bool tsc = c->tab.tsc != 0;
     if (is_inf(c) && kahan)
-      pair_sym_table_kernel<true, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->tab, c->tab_const, F);
+      launch_sym_table<true, true>(c, tsc, C, n, 0, NB, Ua, U, F);
     else if (is_inf(c))
-      pair_sym_table_kernel<false, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->tab, c->tab_const,
-                                                               F);
+      launch_sym_table<false, true>(c, tsc, C, n, 0, NB, Ua, U, F);
     else if (kahan)
-      pair_sym_table_kernel<true, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab, c->tab_const,
-                                                               F);
+      launch_sym_table<true, false>(c, tsc, C, n, nc, NB, Ua, U, F);
     else
-      pair_sym_table_kernel<false, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
-                                                                c->tab_const, F);
+      launch_sym_table<false, false>(c, tsc, C, n, nc, NB, Ua, U, F);
     CKLAUNCH("pair_sym_table");
   } else {
     const int C = ctas(c->SYC);
@@ -1809,6 +1821,7 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms, con
   CK(cudaCreateTextureObject(&c->tab.tex, &res, &td, nullptr));
   c->tab.hx = 0.5f * (nx - 1);
   c->tab.hy = 0.5f * (ny - 1);
+  c->tab.tsc = c->tab_read_next == STEPS_TABLE_READ_TSC ? 1 : 0;
   c->tab_const = SurrConst{0.f, 0.f, 1.f, 1.f, (float)(1.0 / dR_max), (float)dR_max, c->p.n0, 0.f, 0.f, 0.f, 0.f};
   surr_const_finish(c->tab_const, c->p.n_cut);
   c->tab_nx = nx;
@@ -2077,7 +2090,7 @@ int allocate_context(steps_cyl_ctx* c) {
   int yocc = 0, ysocc = 0, ytocc = 0;
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&yocc, pair_sym_kernel<true>, kBI, 0));
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ysocc, pair_sym_surr_kernel<true, false>, kBI, 0));
-  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ytocc, pair_sym_table_kernel<true, false>, kBI, 0));
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ytocc, pair_sym_table_kernel<true, false, 0>, kBI, 0));
   c->SYC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(yocc, 1) * STEPS_CTA_MULT);
   c->SYSC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ysocc, 1) * STEPS_CTA_MULT);
   c->SYTC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ytocc, 1) * STEPS_CTA_MULT);
@@ -2650,7 +2663,7 @@ struct CkptHeader {
   double a, t, rho0, bg_dr, bound_med, bound_p999;
   int32_t steps_since_order, steps_since_check, surr_ok, bgK;
   float surr[STEPS_SURR_NPARAM];
-  int32_t tab_ok, tab_nx, tab_ny, pad;  // correction table: rebuilt on resume from its grid
+  int32_t tab_ok, tab_nx, tab_ny, tab_read;  // correction table: rebuilt on resume from its grid and read
   double tab_dR_max, tab_bound_med, tab_bound_p999;
   uint64_t tree_evals;                  // octree: frame counter, fixed frame, radial table (after the header)
   int32_t tree_fixed, rad_nb;
@@ -2683,6 +2696,7 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   hd.bgK = c->bgtab ? c->bgK : 0;
   if (c->surr_ok) std::memcpy(hd.surr, c->surr_params.data(), sizeof hd.surr);
   hd.tab_ok = c->tab_ok ? 1 : 0;
+  hd.tab_read = c->tab.tsc ? STEPS_TABLE_READ_TSC : STEPS_TABLE_READ_CIC;
   hd.tab_nx = c->tab_nx;
   hd.tab_ny = c->tab_ny;
   hd.tab_dR_max = c->tab_dR_max;
@@ -2824,8 +2838,10 @@ int steps_cyl_resume(steps_cyl_ctx** out, const char* path, int32_t device, void
     c->surr_ok = true;
   }
   if (hd.tab_ok) {  // the table is a deterministic function of its grid: rebuilt, not stored
-    if (hd.tab_nx < 2 || hd.tab_nx > 4096 || hd.tab_ny < 2 || hd.tab_ny > 1024 || !(hd.tab_dR_max > 0))
+    if (hd.tab_nx < 2 || hd.tab_nx > 4096 || hd.tab_ny < 2 || hd.tab_ny > 1024 || !(hd.tab_dR_max > 0) ||
+        (hd.tab_read != STEPS_TABLE_READ_CIC && hd.tab_read != STEPS_TABLE_READ_TSC))
       return bail(fail(STEPS_EINVAL, "corrupt checkpoint (table grid)"));
+    c->tab_read_next = hd.tab_read;
     if ((rc = build_table(c, hd.tab_nx, hd.tab_ny, hd.tab_dR_max, nullptr))) return bail(rc);
     c->tab_ok = true;
     c->tab_bound_med = hd.tab_bound_med;
@@ -3031,6 +3047,15 @@ int steps_cyl_build_tail_table_ewald(steps_cyl_ctx* c, int32_t nx, int32_t ny, d
   if (rc) return rc;
   c->tab_ok = true;
   if (report) std::copy(rep, rep + 4, report);
+  return STEPS_OK;
+}
+
+int steps_cyl_set_table_read(steps_cyl_ctx* c, int32_t read) {
+  g_last_error.clear();
+  if (!c) return fail(STEPS_EINVAL, "ctx is NULL");
+  if (read != STEPS_TABLE_READ_CIC && read != STEPS_TABLE_READ_TSC)
+    return fail(STEPS_EINVAL, "read must be STEPS_TABLE_READ_CIC or STEPS_TABLE_READ_TSC");
+  c->tab_read_next = read;
   return STEPS_OK;
 }
 

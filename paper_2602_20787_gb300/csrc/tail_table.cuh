@@ -165,10 +165,37 @@ static __global__ void table_to_float_kernel(const double2* __restrict__ in, int
 struct TableTail {
   cudaTextureObject_t tex;
   float hx, hy;  // (nx - 1) / 2, (ny - 1) / 2
+  int tsc;       // 0: cloud-in-cell (bilinear) read, 1: triangular-shaped cloud
 };
 
+// TSC along one axis, in node units x: the nearest node i and d = x - i weigh
+// nodes i - 1, i, i + 1 by (1/2 - d)^2 / 2, 3/4 - d^2, (1/2 + d)^2 / 2. The first
+// two are one linear fetch between nodes i - 1 and i (weight s at texture
+// coordinate pa), the third a fetch at the centre of node i + 1 (weight wp at
+// pb); the texture's edge clamp gives nodes beyond the table the edge value.
+__device__ __forceinline__ void tsc_axis(float x, float& pa, float& s, float& pb, float& wp) {
+  const float i = rintf(x), d = x - i;
+  const float wm = 0.5f * (0.5f - d) * (0.5f - d), w0 = 0.75f - d * d;
+  wp = 0.5f * (0.5f + d) * (0.5f + d);
+  s = wm + w0;
+  pa = i - 0.5f + __fdividef(w0, s);  // (i - 1) + w0 / s, plus 1/2 to the texel centre
+  pb = i + 1.5f;
+}
+
+// The table at inputs (u0, u1) in [-1, 1]: node coordinates (u + 1) (n - 1) / 2.
+// READ: the read fixed at compile time (0 CIC, 1 TSC), or -1 for T's.
+template <int READ = -1>
 __device__ __forceinline__ float2 table_read(const TableTail& T, float u0, float u1) {
-  return tex2D<float2>(T.tex, fmaf(u0, T.hx, T.hx + 0.5f), fmaf(u1, T.hy, T.hy + 0.5f));
+  const bool tsc = READ < 0 ? T.tsc != 0 : READ == 1;
+  if (!tsc) return tex2D<float2>(T.tex, fmaf(u0, T.hx, T.hx + 0.5f), fmaf(u1, T.hy, T.hy + 0.5f));
+  float ax, sx, bx, px, ay, sy, by, py;
+  tsc_axis(fminf(fmaf(u0, T.hx, T.hx), 2.0f * T.hx), ax, sx, bx, px);
+  tsc_axis(fminf(fmaf(u1, T.hy, T.hy), 2.0f * T.hy), ay, sy, by, py);
+  const float2 f00 = tex2D<float2>(T.tex, ax, ay), f01 = tex2D<float2>(T.tex, ax, by);
+  const float2 f10 = tex2D<float2>(T.tex, bx, ay), f11 = tex2D<float2>(T.tex, bx, by);
+  const float w00 = sx * sy, w01 = sx * py, w10 = px * sy, w11 = px * py;
+  return make_float2(fmaf(w00, f00.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w11 * f11.x))),
+                     fmaf(w00, f00.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w11 * f11.y))));
 }
 
 // All pairs of i with the kBJ j of a (padded) tile with the table tail. S holds

@@ -30,6 +30,7 @@ STEPS_ENOSURROGATE = -6
 
 STEPS_FP64, STEPS_FP32_KAHAN, STEPS_FP32_PLAIN = 0, 1, 2
 STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE, STEPS_TAIL_TABLE = 0, 1, 2
+STEPS_TABLE_READ_CIC, STEPS_TABLE_READ_TSC = 0, 1
 STEPS_BG_OFF, STEPS_BG_FINITE, STEPS_BG_INFINITE, STEPS_BG_SPHERE = 0, 1, 2, 3
 STEPS_TOPO_S1R2, STEPS_TOPO_R3 = 0, 1
 STEPS_FORCE_DIRECT, STEPS_FORCE_OCTREE = 0, 1
@@ -42,7 +43,7 @@ _EXPORTS = [
     "steps_cyl_mlp_loss_grad", "steps_cyl_train_surrogate", "steps_cyl_set_surrogate", "steps_cyl_get_surrogate",
     "steps_cyl_set_tail", "steps_cyl_check_surrogate", "steps_cyl_checkpoint", "steps_cyl_resume",
     "steps_cyl_build_tail_table", "steps_cyl_build_tail_table_ewald", "steps_cyl_get_tail_table",
-    "steps_cyl_check_tail",
+    "steps_cyl_check_tail", "steps_cyl_set_table_read",
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
     "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
     "steps_cyl_last_eval", "steps_cyl_shard_mode", "steps_cyl_shard_force", "steps_cyl_shard_finish",
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
     L.steps_cyl_build_tail_table.argtypes = [p, i32, i32, d, d, d, i32, p]
     L.steps_cyl_build_tail_table_ewald.argtypes = [p, i32, i32, d, d, i32, i32, p]
+    L.steps_cyl_set_table_read.argtypes = [p, i32]
     L.steps_cyl_get_tail_table.argtypes = [p, p, p, p, p]
     L.steps_cyl_check_tail.argtypes = [p, i32, i32, p]
     L.steps_cyl_checkpoint.argtypes = [p, ctypes.c_char_p]
@@ -474,6 +476,11 @@ def steps_cyl_build_tail_table_ewald(ctx, nx: int = 144, ny: int = 128, dR_max: 
     _check(load().steps_cyl_build_tail_table_ewald(ctx, int(nx), int(ny), float(dR_max), float(alpha), int(nmax),
                                                    int(mmax), _ptr(rep)))
     return rep
+
+
+def steps_cyl_set_table_read(ctx, read: int):
+    """STEPS_TABLE_READ_CIC or STEPS_TABLE_READ_TSC for the next table build."""
+    _check(load().steps_cyl_set_table_read(ctx, int(read)))
 
 
 def steps_cyl_get_tail_table(ctx):

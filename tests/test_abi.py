@@ -63,3 +63,19 @@ def test_product_does_not_import_the_oracle():
         if path.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(path).read()
             assert "import oracle" not in src and "from oracle" not in src and "steps_oracle" not in src, path
+
+
+def test_binding_constants_match_the_header():
+    from paper_2602_20787_gb300 import steps_cyl
+    text = open(os.path.join(ROOT, "include", "steps_cyl.h")).read()
+    defs = dict(re.findall(r"^#define (STEPS_\w+) (-?\d+)\b", text, flags=re.M))
+    shared = [k for k in defs if hasattr(steps_cyl, k)]
+    assert "STEPS_TABLE_READ_TSC" in shared and len(shared) > 10
+    for k in shared:
+        assert getattr(steps_cyl, k) == int(defs[k]), k
+
+
+def test_table_read_refuses_without_a_context(lib):
+    from paper_2602_20787_gb300 import steps_cyl as sc
+    lib.steps_cyl_set_table_read.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    assert lib.steps_cyl_set_table_read(None, sc.STEPS_TABLE_READ_TSC) == sc.STEPS_EINVAL

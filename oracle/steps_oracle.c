@@ -828,16 +828,32 @@ void or_tail_base_inf(double dR, double adz, int32_t n0, double* BR, double* BZ)
  * column, plus the exact spline correction of tail images inside the
  * softening support (the table is Newtonian), as for the surrogate.
  * ------------------------------------------------------------------------- */
+/* The frame a table is stored in: the residual over the continuum base in
+ * envelope units for n0 >= 1; for n0 = 0 (the paper's table over the nearest
+ * image alone, D = F_S1xR2 - F_R3(nearest)) the base's near end would reach the
+ * pair itself at |dz| = 1/2, so that table holds the tail sums themselves (no
+ * base, unit envelope). */
+static void or_table_frame(double dR, double adz, int32_t n_cut, int32_t n0, double* BR, double* BZ, double* ER,
+                           double* EZ) {
+  if (n0 == 0) {
+    *BR = *BZ = 0.0;
+    *ER = *EZ = 1.0;
+    return;
+  }
+  if (n_cut == 0)
+    or_tail_base_inf(dR, adz, n0, BR, BZ);
+  else
+    or_tail_base(dR, adz, n_cut, n0, BR, BZ);
+  or_tail_envelope(dR, adz, n0, ER, EZ);
+}
+
 void or_tail_residual(double dR, double adz, int32_t n_cut, int32_t n0, double r[2]) {
   double SR, SZ, BR, BZ, ER, EZ;
-  if (n_cut == 0) { /* infinite window */
+  if (n_cut == 0) /* infinite window */
     or_image_sums_inf(dR, adz, 0.0, n0, &SR, &SZ);
-    or_tail_base_inf(dR, adz, n0, &BR, &BZ);
-  } else {
+  else
     or_tail_sums(dR, adz, 0.0, 1.0, n_cut, n0, &SR, &SZ);
-    or_tail_base(dR, adz, n_cut, n0, &BR, &BZ);
-  }
-  or_tail_envelope(dR, adz, n0, &ER, &EZ);
+  or_table_frame(dR, adz, n_cut, n0, &BR, &BZ, &ER, &EZ);
   r[0] = (SR - BR) / ER;
   r[1] = (SZ - BZ) / EZ;
 }
@@ -901,11 +917,7 @@ void or_tail_table_read(const double* tab, const or_table_cfg* c, double dR, dou
 void or_tail_table(double dR, double dz, double h, const double* tab, const or_table_cfg* c, double* SR,
                    double* SZ) {
   double adz = fabs(dz), BR, BZ, ER, EZ, r[2];
-  if (c->n_cut == 0)
-    or_tail_base_inf(dR, adz, c->n0, &BR, &BZ);
-  else
-    or_tail_base(dR, adz, c->n_cut, c->n0, &BR, &BZ);
-  or_tail_envelope(dR, adz, c->n0, &ER, &EZ);
+  or_table_frame(dR, adz, c->n_cut, c->n0, &BR, &BZ, &ER, &EZ);
   or_tail_table_read(tab, c, dR, adz, r);
   double sr = BR + ER * r[0];
   double sz = BZ + EZ * r[1];

@@ -98,7 +98,9 @@ void or_ewald_tail(double dR, double dzw, int32_t n0, double alpha, int32_t nmax
 /* Correction-table tail (the paper's Sect. 2.3 table restated for the windowed
  * sum beyond |k| <= n0): residual of the point-mass tail over the continuum base
  * in envelope units on a uniform (dR, |dz|) grid, read with cloud-in-cell
- * (bilinear) or triangular-shaped-cloud weights, the two reads Sect. 2.3 names. */
+ * (bilinear) or triangular-shaped-cloud weights, the two reads Sect. 2.3 names.
+ * n0 = 0 is the paper's table over the nearest image alone: it holds the tail
+ * sums themselves (no base, unit envelope). */
 #define OR_TABLE_CIC 0
 #define OR_TABLE_TSC 1
 typedef struct {

@@ -6,7 +6,12 @@ first moment d and second moment d^2 + 1/4 about node i, so the read
 reproduces constants and linear functions exactly and turns x^2 into
 x^2 + 1/4: the smoothing of a unit-width cloud. Nodes beyond the edge take the
 edge value. The TSC table form converges to the exact windowed sum at second
-order, like the bilinear read."""
+order, like the bilinear read.
+
+Also the paper's table over the nearest image alone (n0 = 0), which holds the
+tail sums themselves: its nodes against brute-force image sums, and its
+second-order convergence, far coarser than the residual table's at the same
+grid."""
 import numpy as np
 import pytest
 
@@ -98,3 +103,38 @@ def test_tsc_table_form_converges_to_the_windowed_sum(orc):
     assert errs[-1] < 1e-7
     for a, b in zip(errs, errs[1:]):
         assert 2.5 < a / b < 6.5   # second order: halving the spacing divides the error by ~4
+
+
+def test_nearest_image_table_holds_the_raw_tail(orc):
+    # n0 = 0, the paper's D over the nearest image: no base, unit envelope, so a
+    # node is the point-mass sum of every image but the nearest (brute force)
+    for n_cut in (N_CUT, 0):
+        cfg = oracle.make_table_cfg(n_cut, 0, 9, 5, 2.0)
+        tab = oracle.tail_table_build(cfg)
+        for i, j in [(0, 0), (3, 2), (8, 4), (5, 1)]:
+            dR, adz = 2.0 * i / 8, 0.5 * j / 4
+            kmax = n_cut + 1 if n_cut else 200000
+            ks = np.array([k for k in range(-kmax, kmax + 1) if k != 0 and (n_cut == 0 or abs(adz + k) < n_cut)],
+                          dtype=float)
+            o = adz + ks
+            r3 = (dR * dR + o * o) ** -1.5
+            tol = 1e-12 if n_cut else 1e-9   # the brute-force line is cut at |k| = 2e5
+            assert tab[j, i, 0] == pytest.approx(r3.sum(), rel=tol)
+            assert tab[j, i, 1] == pytest.approx((o * r3).sum(), rel=tol, abs=1e-12)
+
+
+def test_nearest_image_table_converges_at_second_order(orc):
+    w = ics.WORKLOADS["surrogate_n1048576"]
+    d = ics.particle_load(1024, 3, w.M_tot, displaced=True, rho_bar=w.rho_bar)
+    idx = ics.subsample(1024, 48, seed=5)
+    dR_max = 2.2 * np.hypot(d["pos"][:, 0], d["pos"][:, 1]).max()
+    exact = oracle.pair_field(d["pos"], d["m"], d["h"], 1.0, 1.0, N_CUT, idx=idx)
+    errs = []
+    for nx, ny in [(65, 9), (129, 17), (257, 33)]:
+        cfg = oracle.make_table_cfg(N_CUT, 0, nx, ny, dR_max)
+        g = oracle.pair_field_table(d["pos"], d["m"], d["h"], 1.0, 1.0, oracle.tail_table_build(cfg), cfg, idx=idx)
+        errs.append(np.median(np.linalg.norm(g - exact, axis=1) / np.linalg.norm(exact, axis=1)))
+    print("nearest-image table median errors:", errs)
+    assert 1e-5 < errs[-1] < 1e-4   # far coarser than the residual table at the same grid
+    for a, b in zip(errs, errs[1:]):
+        assert 2.5 < a / b < 6.5

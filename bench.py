@@ -731,6 +731,29 @@ def run_inf(args):
                            "direct_build_ms": rep_e[3], "max_node_difference": rep_e[0], "max_node": rep_e[1],
                            "pair_ms": mse, "forces_vs_direct_table": _err(a_ew, a_dir)}
     sim.close()
+    # the paper's table over the nearest image alone (n0 = 0) on its 144 x 128
+    # grid, against the exact line on a small sample, beside the n0 = 4 table
+    idx = ics.subsample(n, 48, seed=12345)
+    bg = oracle.background_field(d["pos"][idx], ics.R_SIM, 0.0, 1.0, w.rho_bar, mode=2)
+    exact = oracle.pair_field_inf(d["pos"], d["m"], d["h"], 1.0, 1.0, idx=idx) + bg
+    cfg0 = sc.Config(n_cut=0, n0=0, precision=sc.STEPS_FP32_KAHAN, tail=sc.STEPS_TAIL_TABLE,
+                     background=sc.STEPS_BG_INFINITE, rho_bar=w.rho_bar, comoving=True, a_start=w.a_start,
+                     t_start=t0, stream=torch.cuda.current_stream().cuda_stream)
+    sim0 = sc.Simulation(cfg0, d["pos"], d["vel"], d["m"], d["h"])
+    paper = {}
+    for name, read in (("cic", sc.STEPS_TABLE_READ_CIC), ("tsc", sc.STEPS_TABLE_READ_TSC)):
+        sc.steps_cyl_set_table_read(sim0.ctx, read)
+        sc.steps_cyl_build_tail_table_ewald(sim0.ctx, 144, 128)
+        a0, ms0 = _timed_forces(sc, torch, sim0, 3)
+        paper[name] = {"pair_ms": ms0, "error_vs_exact_line": _err(a0[idx] * w.a_start ** 3, exact)}
+    sim0.close()
+    line["paper_table_nearest_image"] = {"n0": 0, "nx": 144, "ny": 128, "construction": "Ewald", **paper,
+                                         "sample": "48 i-particles (seed 12345), FP64 oracle's infinite line"}
+    sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+    sc.steps_cyl_build_tail_table_ewald(sim.ctx, 144, 128)
+    a4, _ = _timed_forces(sc, torch, sim, 1)
+    line["paper_table_nearest_image"]["n0_4_table_error_vs_exact_line"] = _err(a4[idx] * w.a_start ** 3, exact)
+    sim.close()
     print(json.dumps(line), flush=True)
     return 0
 

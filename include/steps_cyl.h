@@ -84,7 +84,9 @@ typedef struct {
                      * surrogate trained to infinity may be selected later), an FP32 precision
                      * and STEPS_BG_INFINITE or STEPS_BG_OFF */
   int32_t n0;       /* near range of a modelled tail: images |k| <= n0 summed directly,
-                     * 1 <= n0 < n_cut (1 <= n0 < 512 for the infinite window) */
+                     * 1 <= n0 < n_cut (1 <= n0 < 512 for the infinite window); the
+                     * table tail also takes n0 = 0, the paper's table over the
+                     * nearest image alone (steps_cyl_build_tail_table) */
   int32_t precision;  /* STEPS_FP64 | STEPS_FP32_KAHAN | STEPS_FP32_PLAIN */
   int32_t tail;       /* STEPS_TAIL_FULL | STEPS_TAIL_SURROGATE | STEPS_TAIL_TABLE */
   int32_t background; /* STEPS_BG_OFF | STEPS_BG_FINITE | STEPS_BG_INFINITE */
@@ -377,10 +379,17 @@ int steps_cyl_set_tail(steps_cyl_ctx* ctx, int32_t tail);
  * exactly, as the surrogate form does. With n_cut = 0 (the infinite window) the
  * table holds the whole image line beyond n0, summed exactly to |k| = 512 and
  * by Euler-Maclaurin beyond, over the base of the infinite window; no plain sum
- * exists to check it against, so it is kept without a check. */
+ * exists to check it against, so it is kept without a check.
+ * With n0 = 0 the table is the paper's own, over the nearest image alone
+ * (D = F_S1xR2 - F_R3 of the nearest image): the continuum base would reach the
+ * pair itself at |dz| = 1/2, so the nodes hold the tail sums themselves (no
+ * base, unit envelope). Its interpolation error is far larger than the
+ * residual's (about 1.4e-4 of the force at the median on a 144 x 128 grid,
+ * against 4e-10 with n0 = 4), so the 1e-5 check rejects it at such grids. The
+ * learned tail needs n0 >= 1. */
 
-/* Build the context's table (its n_cut and n0; 1 <= n0 < n_cut, or n0 >= 1 for
- * the infinite window; FP32 precision) and, for a finite window, compare the table form with the plain image sum on
+/* Build the context's table (its n_cut and n0; 0 <= n0 < n_cut, or 0 <= n0 < 512
+ * for the infinite window; FP32 precision) and, for a finite window, compare the table form with the plain image sum on
  * check_particles particles; keep it when median <= err_median and 99.9th
  * percentile <= err_p999 of the relative total-force error. nx in [2, 4096], ny
  * in [2, 1024]; dR_max = 0 picks 2.2 x the largest particle radius / L. report

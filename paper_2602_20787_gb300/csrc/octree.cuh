@@ -423,7 +423,7 @@ __device__ __forceinline__ void tree_eval(const IParticle& I, int me, const floa
       int kw;
       pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
       SurrPair P;
-      surr_stage_a<true>(dR2, dz, hh, 0, kw, S, P);
+      surr_stage_a<true, -1>(dR2, dz, hh, 0, kw, S, P);
       const float2 r = table_read(T, P.u[0], P.u[1]);
       float sr, szz;
       surr_stage_c<true>(I, A, B, 0, kw, S, P, r.x, r.y, sr, szz);

@@ -299,7 +299,8 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
   }
 }
 
-// Correction-table tail (tail_table.cuh), two j per step; READ: 0 CIC, 1 TSC.
+// Correction-table tail (tail_table.cuh), two j per step; READ: the table read
+// (the exact reads belong to the nearest-image table, n0 = 0, stored raw).
 template <bool KAHAN, bool INF, int READ>
 __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, const float4* sA, const float4* sB,
                                                bool sym, float* row, int self, int n_cut, const SurrConst& S,
@@ -321,7 +322,7 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
         int kw;
         pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
         SurrPair P;
-        surr_stage_a<INF>(dR2, dz, hh, n_cut, kw, S, P);
+        surr_stage_a<INF, (READ >= kReadCicExact ? 1 : 0)>(dR2, dz, hh, n_cut, kw, S, P);
         const float2 r = table_read<READ>(T, P.u[0], P.u[1]);
         float sr, szz;
         surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);

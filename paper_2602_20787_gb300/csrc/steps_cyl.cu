@@ -278,7 +278,7 @@ struct steps_cyl_ctx {
   TableTail tab{};                 // texture of the residual table
   SurrConst tab_const{};           // mu = 0, sc = 1, the table's dR_max
   int tab_nx = 0, tab_ny = 0;
-  int tab_read_next = STEPS_TABLE_READ_CIC;  // the read of the next table build (tab.tsc: the built one's)
+  int tab_read_next = STEPS_TABLE_READ_CIC;  // the read of the next table build (tab.read: the built one's)
   double tab_dR_max = 0.0;
   bool tab_ok = false;             // an accepted table is loaded
   double tab_bound_med = 1e-5, tab_bound_p999 = 1e-3;
@@ -370,7 +370,9 @@ int check_params(const steps_cyl_params* p) {
       return fail(STEPS_EINVAL, "the infinite window takes STEPS_BG_INFINITE or STEPS_BG_OFF");
     // the tail sums images |k| <= kKInf one by one and the line ends beyond, so the
     // near range must end inside that range
-    if (p->n0 < 1 || p->n0 >= kKInf) return fail(STEPS_EINVAL, "n0 must be in [1, %d) for the infinite window", kKInf);
+    if (p->n0 < 0 || p->n0 >= kKInf) return fail(STEPS_EINVAL, "n0 must be in [0, %d) for the infinite window", kKInf);
+    if (p->n0 == 0 && p->tail != STEPS_TAIL_TABLE)
+      return fail(STEPS_EINVAL, "n0 = 0 (the table over the nearest image) needs STEPS_TAIL_TABLE");
   }
   if (p->precision < STEPS_FP64 || p->precision > STEPS_FP32_PLAIN) return fail(STEPS_EINVAL, "bad precision");
   if (p->force != STEPS_FORCE_DIRECT && p->force != STEPS_FORCE_OCTREE) return fail(STEPS_EINVAL, "bad force method");
@@ -385,8 +387,11 @@ int check_params(const steps_cyl_params* p) {
   }
   if (p->tail != STEPS_TAIL_FULL && p->tail != STEPS_TAIL_SURROGATE && p->tail != STEPS_TAIL_TABLE)
     return fail(STEPS_EINVAL, "bad tail mode");
-  if (p->tail != STEPS_TAIL_FULL && p->n_cut > 0 && (p->n0 < 1 || p->n0 >= p->n_cut))
-    return fail(STEPS_EINVAL, "n0 must be in [1, n_cut)");
+  if (p->n0 < 0) return fail(STEPS_EINVAL, "n0 must be >= 0");
+  if (p->tail == STEPS_TAIL_SURROGATE && p->n_cut > 0 && (p->n0 < 1 || p->n0 >= p->n_cut))
+    return fail(STEPS_EINVAL, "the learned tail needs n0 in [1, n_cut)");
+  if (p->tail == STEPS_TAIL_TABLE && p->n_cut > 0 && p->n0 >= p->n_cut)
+    return fail(STEPS_EINVAL, "the table tail needs n0 in [0, n_cut)");
   if (p->background < STEPS_BG_OFF || p->background > STEPS_BG_SPHERE) return fail(STEPS_EINVAL, "bad background");
   if (p->comoving) {
     if (!(p->H0 > 0) || !(p->a_start > 0)) return fail(STEPS_EINVAL, "comoving runs need H0 > 0 and a_start > 0");
@@ -1020,16 +1025,27 @@ double sym_pairs(const steps_cyl_ctx* c) {
 
 // The symmetric kernel of the form over the units [Ua, Ua + U) into F.
 // The symmetric table kernel in the context's table read (compiled per read, so
-// that the CIC path carries none of the TSC arithmetic).
+// that the filtered CIC path carries none of the other reads' arithmetic).
 template <bool KAHAN, bool INF>
-void launch_sym_table(steps_cyl_ctx* c, bool tsc, int C, int n, int nc, int NB, long long Ua, long long U,
-                      const FixAcc& F) {
-  if (tsc)
-    pair_sym_table_kernel<KAHAN, INF, 1><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
-                                                               c->tab_const, F);
-  else
-    pair_sym_table_kernel<KAHAN, INF, 0><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->tab,
-                                                               c->tab_const, F);
+void launch_sym_table(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long Ua, long long U, const FixAcc& F) {
+  const TableTail& T = c->tab;
+  switch (T.read) {
+    case kReadTsc:
+      pair_sym_table_kernel<KAHAN, INF, kReadTsc><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                         c->tab_const, F);
+      break;
+    case kReadCicExact:
+      pair_sym_table_kernel<KAHAN, INF, kReadCicExact><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                              c->tab_const, F);
+      break;
+    case kReadTscExact:
+      pair_sym_table_kernel<KAHAN, INF, kReadTscExact><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                              c->tab_const, F);
+      break;
+    default:
+      pair_sym_table_kernel<KAHAN, INF, kReadCic><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                         c->tab_const, F);
+  }
 }
 
 int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const FixAcc& F) {
@@ -1054,15 +1070,14 @@ int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const Fix
     CKLAUNCH("pair_sym_surrogate");
   } else if (form == Form::TABLE) {
     const int C = ctas(c->SYTC);
-    const bool tsc = c->tab.tsc != 0;
     if (is_inf(c) && kahan)
-      launch_sym_table<true, true>(c, tsc, C, n, 0, NB, Ua, U, F);
+      launch_sym_table<true, true>(c, C, n, 0, NB, Ua, U, F);
     else if (is_inf(c))
-      launch_sym_table<false, true>(c, tsc, C, n, 0, NB, Ua, U, F);
+      launch_sym_table<false, true>(c, C, n, 0, NB, Ua, U, F);
     else if (kahan)
-      launch_sym_table<true, false>(c, tsc, C, n, nc, NB, Ua, U, F);
+      launch_sym_table<true, false>(c, C, n, nc, NB, Ua, U, F);
     else
-      launch_sym_table<false, false>(c, tsc, C, n, nc, NB, Ua, U, F);
+      launch_sym_table<false, false>(c, C, n, nc, NB, Ua, U, F);
     CKLAUNCH("pair_sym_table");
   } else {
     const int C = ctas(c->SYC);
@@ -1740,8 +1755,8 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms, con
                 double* ew_rep = nullptr) {
   Range range("steps_cyl.build_table");
   if (is_r3(c)) return fail(STEPS_EINVAL, "the R^3 topology has no image tail to model");
-  if (c->p.n0 < 1 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
-    return fail(STEPS_EINVAL, "the context needs 1 <= n0 < n_cut");
+  if (c->p.n0 < 0 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
+    return fail(STEPS_EINVAL, "the context needs 0 <= n0 < n_cut");
   if (ew && c->p.n_cut != 0) return fail(STEPS_EINVAL, "the Ewald construction is for the infinite window (n_cut = 0)");
   if (dR_max == 0.0) {
     std::vector<double> hx(c->n), hy(c->n);
@@ -1821,7 +1836,8 @@ int build_table(steps_cyl_ctx* c, int nx, int ny, double dR_max, double* ms, con
   CK(cudaCreateTextureObject(&c->tab.tex, &res, &td, nullptr));
   c->tab.hx = 0.5f * (nx - 1);
   c->tab.hy = 0.5f * (ny - 1);
-  c->tab.tsc = c->tab_read_next == STEPS_TABLE_READ_TSC ? 1 : 0;
+  // the nearest-image table (n0 = 0) is read with exact weights (see tail_table.cuh)
+  c->tab.read = (c->tab_read_next == STEPS_TABLE_READ_TSC ? kReadTsc : kReadCic) + (c->p.n0 == 0 ? 2 : 0);
   c->tab_const = SurrConst{0.f, 0.f, 1.f, 1.f, (float)(1.0 / dR_max), (float)dR_max, c->p.n0, 0.f, 0.f, 0.f, 0.f};
   surr_const_finish(c->tab_const, c->p.n_cut);
   c->tab_nx = nx;
@@ -2090,7 +2106,7 @@ int allocate_context(steps_cyl_ctx* c) {
   int yocc = 0, ysocc = 0, ytocc = 0;
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&yocc, pair_sym_kernel<true>, kBI, 0));
   CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ysocc, pair_sym_surr_kernel<true, false>, kBI, 0));
-  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ytocc, pair_sym_table_kernel<true, false, 0>, kBI, 0));
+  CKA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ytocc, pair_sym_table_kernel<true, false, kReadCic>, kBI, 0));
   c->SYC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(yocc, 1) * STEPS_CTA_MULT);
   c->SYSC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ysocc, 1) * STEPS_CTA_MULT);
   c->SYTC = (int)std::min<long long>(c->Usym, (long long)sms * std::max(ytocc, 1) * STEPS_CTA_MULT);
@@ -2696,7 +2712,7 @@ int steps_cyl_checkpoint(steps_cyl_ctx* c, const char* path) {
   hd.bgK = c->bgtab ? c->bgK : 0;
   if (c->surr_ok) std::memcpy(hd.surr, c->surr_params.data(), sizeof hd.surr);
   hd.tab_ok = c->tab_ok ? 1 : 0;
-  hd.tab_read = c->tab.tsc ? STEPS_TABLE_READ_TSC : STEPS_TABLE_READ_CIC;
+  hd.tab_read = (c->tab.read == kReadTsc || c->tab.read == kReadTscExact) ? STEPS_TABLE_READ_TSC : STEPS_TABLE_READ_CIC;
   hd.tab_nx = c->tab_nx;
   hd.tab_ny = c->tab_ny;
   hd.tab_dR_max = c->tab_dR_max;
@@ -2941,6 +2957,8 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* c, const float* params, double err_me
   if (!c || !params) return fail(STEPS_EINVAL, "NULL argument");
   if (c->shard) return refuse_sharded(c, "steps_cyl_set_surrogate (install before sharding)");
   if (!(err_median > 0) || !(err_p999 > 0)) return fail(STEPS_EINVAL, "bounds must be > 0");
+  if (is_r3(c) || c->p.n0 < 1 || (c->p.n_cut > 0 && c->p.n0 >= c->p.n_cut))
+    return fail(STEPS_EINVAL, "the learned tail needs 1 <= n0 < n_cut (S1xR2)");
   DeviceGuard guard(c->dev);
   std::vector<float> P(STEPS_SURR_NPARAM);
   CK(cudaMemcpyAsync(P.data(), params, sizeof(float) * STEPS_SURR_NPARAM, cudaMemcpyDefault, c->st));

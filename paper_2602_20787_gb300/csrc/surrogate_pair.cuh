@@ -400,7 +400,10 @@ struct SurrPair {
 // Stage A: near images |k| <= n0 exactly (the tiered image walk of
 // pair_fp32.cuh without the edge image), the tail base, the envelope and the
 // network inputs. kw: warp-uniform spline bound. INF: the infinite window.
-template <bool INF = false>
+// RAW: the frame of the tail: 0 the base and envelope (the learned tail and
+// the residual tables, n0 >= 1), 1 none (the nearest-image table, n0 = 0, holds
+// the tail sums themselves), -1 chosen at run time from S.n0.
+template <bool INF = false, int RAW = 0>
 __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int n_cut, int kw, const SurrConst& S,
                                              SurrPair& P) {
   (void)n_cut;  // the finite window's far end comes in S.fnh
@@ -414,7 +417,11 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
   // tail base and envelope (|dz|; z part gets sign(dz))
   const float adz = fabsf(dz), A = S.A;
   float br, bz, il1;
-  if (INF) {
+  if (RAW > 0 || (RAW < 0 && S.n0 == 0)) {
+    br = 0.0f;
+    bz = 0.0f;
+    il1 = 1.0f;
+  } else if (INF) {
     tail_base_inf_fp32(dR2, A + adz, A - adz, br, bz, il1);
   } else {
     // far ends: + side (n_cut - 1) + 1/2 + |dz|; - side at n_cut + 1/2 - |dz| when

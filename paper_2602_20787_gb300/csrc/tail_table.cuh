@@ -29,6 +29,16 @@ namespace steps {
 // [ny][nx]. n_cut = 0 is the infinite window: images to |k| <= kKInf exactly
 // and the line ends beyond, against the infinite base.
 
+// A node in the table's frame: for n0 >= 1 the residual of the tail sums over
+// the continuum base (BR, BZ) in envelope units (ER, EZ); for n0 = 0 (the table
+// over the nearest image alone, whose base would reach the pair itself at
+// |dz| = 1/2) the tail sums themselves.
+__device__ __forceinline__ double2 table_node(int n0, double sr, double sz, double BR, double BZ, double ER,
+                                              double EZ) {
+  if (n0 == 0) return make_double2(sr, sz);
+  return make_double2((sr - BR) / ER, (sz - BZ) / EZ);
+}
+
 static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cut, int n0, double2* __restrict__ out) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny; q += gridDim.x * blockDim.x) {
     const int i = q % nx, j = q / nx;
@@ -45,7 +55,7 @@ static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cu
       line_ends_fp64(R2, adz, sr, sz);
       double BR, BZ, ER, EZ;
       tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
-      out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
+      out[q] = table_node(n0, sr, sz, BR, BZ, ER, EZ);
       continue;
     }
     for (int k = n0 + 1; k <= n_cut + 1; ++k) {
@@ -63,7 +73,7 @@ static __global__ void tail_table_kernel(int nx, int ny, double dR_max, int n_cu
     }
     double BR, BZ, ER, EZ;
     tail_base_fp64(dR, adz, n_cut, n0, BR, BZ, ER, EZ);
-    out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
+    out[q] = table_node(n0, sr, sz, BR, BZ, ER, EZ);
   }
 }
 
@@ -150,7 +160,7 @@ static __global__ void tail_table_ewald_kernel(int nx, int ny, double dR_max, in
     sr += y > 0.0 ? -2.0 * alpha * alpha * expm1(-y) / y : 2.0 * alpha * alpha;
     double BR, BZ, ER, EZ;
     tail_base_inf_fp64(dR, adz, n0, BR, BZ, ER, EZ);
-    out[q] = make_double2((sr - BR) / ER, (sz - BZ) / EZ);
+    out[q] = table_node(n0, sr, sz, BR, BZ, ER, EZ);
   }
 }
 
@@ -162,40 +172,77 @@ static __global__ void table_to_float_kernel(const double2* __restrict__ in, int
 // Texture of the residual table and the map from the network-input scaling
 // u = 2 min(dR, dR_max)/dR_max - 1, 4|dz| - 1 to texel coordinates (texel
 // centres at index + 1/2): x = (u0 + 1) (nx - 1)/2 + 1/2.
+// Table reads: cloud-in-cell (bilinear) or triangular-shaped cloud, each either
+// through the texture unit's filter (8-bit fractional weights) or with exact
+// FP32 weights on texel-centre fetches. The residual tables (n0 >= 1) take the
+// filtered reads; the nearest-image table (n0 = 0), whose nodes vary far more
+// between neighbours, takes the exact ones.
+constexpr int kReadCic = 0, kReadTsc = 1, kReadCicExact = 2, kReadTscExact = 3;
+
 struct TableTail {
   cudaTextureObject_t tex;
   float hx, hy;  // (nx - 1) / 2, (ny - 1) / 2
-  int tsc;       // 0: cloud-in-cell (bilinear) read, 1: triangular-shaped cloud
+  int read;      // kReadCic .. kReadTscExact
 };
 
 // TSC along one axis, in node units x: the nearest node i and d = x - i weigh
-// nodes i - 1, i, i + 1 by (1/2 - d)^2 / 2, 3/4 - d^2, (1/2 + d)^2 / 2. The first
-// two are one linear fetch between nodes i - 1 and i (weight s at texture
-// coordinate pa), the third a fetch at the centre of node i + 1 (weight wp at
-// pb); the texture's edge clamp gives nodes beyond the table the edge value.
-__device__ __forceinline__ void tsc_axis(float x, float& pa, float& s, float& pb, float& wp) {
-  const float i = rintf(x), d = x - i;
-  const float wm = 0.5f * (0.5f - d) * (0.5f - d), w0 = 0.75f - d * d;
+// nodes i - 1, i, i + 1 by (1/2 - d)^2 / 2, 3/4 - d^2, (1/2 + d)^2 / 2.
+__device__ __forceinline__ void tsc_weights(float x, float& i, float& wm, float& w0, float& wp) {
+  i = rintf(x);
+  const float d = x - i;
+  wm = 0.5f * (0.5f - d) * (0.5f - d);
+  w0 = 0.75f - d * d;
   wp = 0.5f * (0.5f + d) * (0.5f + d);
-  s = wm + w0;
-  pa = i - 0.5f + __fdividef(w0, s);  // (i - 1) + w0 / s, plus 1/2 to the texel centre
-  pb = i + 1.5f;
+}
+
+// The node (i, j) itself: a fetch at its texel centre (the edge clamp gives
+// nodes beyond the table the edge value).
+__device__ __forceinline__ float2 table_node_at(const TableTail& T, float i, float j) {
+  return tex2D<float2>(T.tex, i + 0.5f, j + 0.5f);
+}
+
+__device__ __forceinline__ void axpy2(float w, const float2& f, float2& acc) {
+  acc.x = fmaf(w, f.x, acc.x);
+  acc.y = fmaf(w, f.y, acc.y);
 }
 
 // The table at inputs (u0, u1) in [-1, 1]: node coordinates (u + 1) (n - 1) / 2.
-// READ: the read fixed at compile time (0 CIC, 1 TSC), or -1 for T's.
+// READ: the read fixed at compile time, or -1 for T's.
 template <int READ = -1>
 __device__ __forceinline__ float2 table_read(const TableTail& T, float u0, float u1) {
-  const bool tsc = READ < 0 ? T.tsc != 0 : READ == 1;
-  if (!tsc) return tex2D<float2>(T.tex, fmaf(u0, T.hx, T.hx + 0.5f), fmaf(u1, T.hy, T.hy + 0.5f));
-  float ax, sx, bx, px, ay, sy, by, py;
-  tsc_axis(fminf(fmaf(u0, T.hx, T.hx), 2.0f * T.hx), ax, sx, bx, px);
-  tsc_axis(fminf(fmaf(u1, T.hy, T.hy), 2.0f * T.hy), ay, sy, by, py);
-  const float2 f00 = tex2D<float2>(T.tex, ax, ay), f01 = tex2D<float2>(T.tex, ax, by);
-  const float2 f10 = tex2D<float2>(T.tex, bx, ay), f11 = tex2D<float2>(T.tex, bx, by);
-  const float w00 = sx * sy, w01 = sx * py, w10 = px * sy, w11 = px * py;
-  return make_float2(fmaf(w00, f00.x, fmaf(w01, f01.x, fmaf(w10, f10.x, w11 * f11.x))),
-                     fmaf(w00, f00.y, fmaf(w01, f01.y, fmaf(w10, f10.y, w11 * f11.y))));
+  const int read = READ < 0 ? T.read : READ;
+  if (read == kReadCic) return tex2D<float2>(T.tex, fmaf(u0, T.hx, T.hx + 0.5f), fmaf(u1, T.hy, T.hy + 0.5f));
+  const float x = fminf(fmaf(u0, T.hx, T.hx), 2.0f * T.hx), y = fminf(fmaf(u1, T.hy, T.hy), 2.0f * T.hy);
+  float2 acc = make_float2(0.0f, 0.0f);
+  if (read == kReadCicExact) {
+    const float i = fminf(floorf(x), 2.0f * T.hx - 1.0f), j = fminf(floorf(y), 2.0f * T.hy - 1.0f);
+    const float a = x - i, b = y - j;
+    axpy2((1.0f - a) * (1.0f - b), table_node_at(T, i, j), acc);
+    axpy2(a * (1.0f - b), table_node_at(T, i + 1.0f, j), acc);
+    axpy2((1.0f - a) * b, table_node_at(T, i, j + 1.0f), acc);
+    axpy2(a * b, table_node_at(T, i + 1.0f, j + 1.0f), acc);
+    return acc;
+  }
+  float ix, wx[3], iy, wy[3];
+  tsc_weights(x, ix, wx[0], wx[1], wx[2]);
+  tsc_weights(y, iy, wy[0], wy[1], wy[2]);
+  if (read == kReadTscExact) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) axpy2(wx[p] * wy[q], table_node_at(T, ix + (p - 1), iy + (q - 1)), acc);
+    return acc;
+  }
+  // filtered TSC: per axis the first two weights are one linear fetch between
+  // nodes i - 1 and i (weight s at i - 1 + w0 / s), the third a fetch at node i + 1
+  const float sx = wx[0] + wx[1], sy = wy[0] + wy[1];
+  const float ax = ix - 0.5f + __fdividef(wx[1], sx), bx = ix + 1.5f;
+  const float ay = iy - 0.5f + __fdividef(wy[1], sy), by = iy + 1.5f;
+  axpy2(sx * sy, tex2D<float2>(T.tex, ax, ay), acc);
+  axpy2(sx * wy[2], tex2D<float2>(T.tex, ax, by), acc);
+  axpy2(wx[2] * sy, tex2D<float2>(T.tex, bx, ay), acc);
+  axpy2(wx[2] * wy[2], tex2D<float2>(T.tex, bx, by), acc);
+  return acc;
 }
 
 // All pairs of i with the kBJ j of a (padded) tile with the table tail. S holds
@@ -216,7 +263,7 @@ __device__ __forceinline__ void pair_tile_table(const IParticle& I, const float4
       int kw;
       pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
       SurrPair P;
-      surr_stage_a<INF>(dR2, dz, hh, n_cut, kw, S, P);
+      surr_stage_a<INF, -1>(dR2, dz, hh, n_cut, kw, S, P);
       const float2 r = table_read(T, P.u[0], P.u[1]);
       float sr, szz;
       surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);

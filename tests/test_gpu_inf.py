@@ -98,7 +98,8 @@ def test_inf_ragged_sizes(sc, n):
 def test_inf_combinations_are_checked(sc, infsim):
     w, d = workload(200, 5)
     bad = [dict(precision=sc.STEPS_FP64), dict(tail=sc.STEPS_TAIL_FULL), dict(background=sc.STEPS_BG_FINITE),
-           dict(n0=0), dict(topology=sc.STEPS_TOPO_R3), dict(n_cut=-1)]
+           dict(n0=-1), dict(n0=512), dict(n0=0, tail=sc.STEPS_TAIL_SURROGATE), dict(topology=sc.STEPS_TOPO_R3),
+           dict(n_cut=-1)]
     for kw in bad:
         with pytest.raises(sc.StepsError) as e:
             sc.Simulation(inf_config(sc, w.rho_bar, **kw), d["pos"], d["vel"], d["m"], d["h"])

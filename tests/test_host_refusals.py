@@ -128,14 +128,22 @@ def init_refused(cfg, what, n=4):
     assert what in str(e.value), str(e.value)
 
 
-@pytest.mark.parametrize("n0", [0, 512, 4000])
+@pytest.mark.parametrize("n0", [-1, 512, 4000])
 def test_infinite_window_near_range(lib, n0):
     cfg = sc.Config(n_cut=0, n0=n0, tail=sc.STEPS_TAIL_TABLE, background=sc.STEPS_BG_INFINITE)
-    init_refused(cfg, "n0 must be in [1, 512)")
+    init_refused(cfg, "n0 must be in [0, 512)")
+
+
+def test_nearest_image_table_only(lib):
+    # n0 = 0 (the table over the nearest image alone) is for the table tail only
+    cfg = sc.Config(n_cut=0, n0=0, tail=sc.STEPS_TAIL_SURROGATE, background=sc.STEPS_BG_INFINITE)
+    init_refused(cfg, "needs STEPS_TAIL_TABLE")
+    init_refused(sc.Config(n_cut=8, n0=0, tail=sc.STEPS_TAIL_SURROGATE), "learned tail needs n0 in [1, n_cut)")
+    init_refused(sc.Config(n_cut=8, n0=-1), "n0 must be >= 0")
 
 
 @pytest.mark.parametrize("kw,what", [(dict(n_cut=4097), "n_cut must be in"), (dict(n_cut=-1), "n_cut must be in"),
-                                     (dict(n_cut=8, n0=8, tail=sc.STEPS_TAIL_TABLE), "n0 must be in [1, n_cut)"),
+                                     (dict(n_cut=8, n0=8, tail=sc.STEPS_TAIL_TABLE), "table tail needs n0 in [0, n_cut)"),
                                      (dict(theta=0.5, force=sc.STEPS_FORCE_OCTREE), "octree needs the infinite"),
                                      (dict(topology=sc.STEPS_TOPO_R3, background=sc.STEPS_BG_FINITE), "R^3 topology")])
 def test_init_parameters(lib, kw, what):

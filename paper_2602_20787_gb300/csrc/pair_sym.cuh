@@ -42,6 +42,32 @@
 namespace steps {
 
 constexpr int kErrFixRange = 32;  // a pair sum left the range of the fixed-point accumulators
+constexpr int kErrIndex = 64;     // (index-checked builds) an index left its buffer
+
+// Index-checked builds (STEPS_DEBUG_INDEX=1) check every computed index of the
+// symmetric kernels' shared and global accesses against its buffer; an index
+// outside is recorded in g_index_err and clamped into the buffer, so that
+// control flow (and every warp-collective call) stays the same. The host folds
+// the record into the device error word (kErrIndex). Release builds compile
+// the checks away.
+#ifndef STEPS_DEBUG_INDEX
+#define STEPS_DEBUG_INDEX 0
+#endif
+#if STEPS_DEBUG_INDEX
+__device__ unsigned int g_index_err;
+#endif
+
+__device__ __forceinline__ long long checked_index(long long v, long long size) {
+#if STEPS_DEBUG_INDEX
+  if (v < 0 || v >= size) {
+    atomicOr(&g_index_err, 1u);
+    return v < 0 ? 0 : size - 1;
+  }
+#else
+  (void)size;
+#endif
+  return v;
+}
 constexpr int kJRow = 3 * kBJ;    // floats of one warp's j-side row: [kBJ][3]
 
 // Fixed-point accumulators (two's complement in unsigned words, unit
@@ -72,7 +98,8 @@ __device__ __forceinline__ void fix_add(const FixAcc& F, int c, int i, double v)
     atomicOr(F.err, kErrFixRange);
     return;
   }
-  atomicAdd(F.acc + fix_index(F, c, i), (unsigned long long)__double2ll_rn(q));
+  const long long size = F.world == 0 ? 3LL * F.n : 3LL * F.world * F.chunk;
+  atomicAdd(F.acc + checked_index(fix_index(F, c, i), size), (unsigned long long)__double2ll_rn(q));
 }
 
 // Offset of row b of the upper triangle (units t = b .. NB - 1 per row).
@@ -108,7 +135,7 @@ __device__ __forceinline__ void jside_pair(const float (&w0)[3], const float (&w
     r[c] = keep;
   }
   if ((lane & 15) == 0) {
-    float* d = row + 3 * (k + (hi ? 1 : 0));
+    float* d = row + 3 * checked_index(k + (hi ? 1 : 0), kBJ);
     d[0] = r[0];
     d[1] = r[1];
     d[2] = r[2];
@@ -132,9 +159,9 @@ __device__ __forceinline__ void jside_vec(float mi, float dx, float dy, float sr
 // slot meets every lane once in 32 steps; otherwise all lanes take slot k.
 __device__ __forceinline__ int jslot(int k) {
 #if STEPS_SYM_RING
-  return (k & ~31) | ((k + (int)threadIdx.x) & 31);
+  return (int)checked_index((k & ~31) | ((k + (int)threadIdx.x) & 31), kBJ);
 #else
-  return k;
+  return (int)checked_index(k, kBJ);
 #endif
 }
 
@@ -355,8 +382,8 @@ __device__ __forceinline__ void sym_stream_k(const float4* __restrict__ jA, cons
   float* row = sJ + (threadIdx.x >> 5) * kJRow;
   long long u = u0;
   while (u < u1) {
-    const int b = tri_row(u, NB);
-    const int t0 = b + (int)(u - tri_off(b, NB));
+    const int b = (int)checked_index(tri_row(u, NB), NB);
+    const int t0 = (int)checked_index(b + (u - tri_off(b, NB)), NB);
     const int t1 = (int)min((long long)NB, (long long)t0 + (u1 - u));
     const int i = b * kBI + threadIdx.x;
     const IParticle I = load_i(jA, jB, min(i, n - 1));

@@ -493,16 +493,27 @@ int read_and_clear_err(steps_cyl_ctx* c, int* out) {
   CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+#if STEPS_DEBUG_INDEX
+  unsigned int ix = 0;
+  CK(cudaMemcpyFromSymbolAsync(&ix, g_index_err, sizeof ix, 0, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (ix) {
+    const unsigned int zero = 0;
+    CK(cudaMemcpyToSymbolAsync(g_index_err, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, c->st));
+    h |= kErrIndex;
+  }
+#endif
   *out = h;
   return STEPS_OK;
 }
 
 int device_error(int e) {
-  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
+  return fail(STEPS_EDEVICE, "device error word 0x%x (%s%s%s%s%s%s%s)", e, (e & kErrNonFinite) ? "non-finite value " : "",
               (e & kErrBgRange) ? "particle beyond background table " : "", (e & kErrZRange) ? "z range " : "",
               (e & kErrTreeRange) ? "particle outside the octree root " : "",
               (e & kErrTreeStack) ? "octree walk stack overflow " : "",
-              (e & kErrFixRange) ? "pair sum beyond the fixed-point range" : "");
+              (e & kErrFixRange) ? "pair sum beyond the fixed-point range " : "",
+              (e & kErrIndex) ? "index outside its buffer (index-checked build)" : "");
 }
 
 // Calls that need every row of the context current refuse a sharded context.

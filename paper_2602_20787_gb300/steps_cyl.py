@@ -100,9 +100,10 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    checked = os.environ.get("STEPS_CYL_INDEX_CHECKED") == "1"   # the index-checked test build
+    path = _build.LIB_CHECKED if checked else _build.LIB
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(checked=checked)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run paper_2602_20787_gb300.build.build()")
     L = ctypes.CDLL(path)

@@ -48,7 +48,7 @@ namespace {
 
 thread_local std::string g_last_error;
 
-// A named host range around one phase of an evaluation or a step, for profilers
+// A named host range over one phase of an evaluation or a step, for profilers
 // that record NVTX ranges; without one attached the calls do nothing.
 struct Range {
   explicit Range(const char* name) { nvtxRangePushA(name); }

@@ -257,12 +257,19 @@ __device__ __forceinline__ void sym_tile_plain(const IParticle& I, float mi, con
 }
 
 // One network call of the learned tail for the NJ steps k .. k + NJ - 1 (slots
-// jslot(k + jj)): the i-side group sums and the j-side vectors w.
-template <int NJ, bool INF>
+// jslot(k + jj)): the i-side group sums and the j-side vectors w. FAR4 (near
+// range n0 = 4): stage A of every pair is first taken as if no lane's pair were
+// inside its softening support (surr_stage_a_far4, no branch), so that the
+// geometry, stage A and the network form one straight run in which the
+// scheduler interleaves the tensor-core chain with the FP32 and MUFU work. A
+// step where some lane's pair is inside its support (kw >= 0, warp-uniform)
+// redoes stage A of that pair with the spline tiers after the network, from
+// the same separation, which gives the tiered call's values bit for bit.
+template <int NJ, bool INF, bool FAR4>
 __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const float4* sA, const float4* sB, int k,
                                           int self, int n_cut, const SurrW& W, uint32_t* ibuf, const SurrConst& S,
                                           float& gx, float& gy, float& gz, float (*w)[3]) {
-  float dx[NJ], dy[NJ], dz[NJ], dR2[NJ], hh[NJ], mj[NJ];
+  float dx[NJ], dy[NJ], mj[NJ];
   int kw[NJ];
   SurrPair P[NJ];
   float u[NJ][3], y[NJ][2];
@@ -272,14 +279,28 @@ __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const fl
     q[jj] = jslot(k + jj);
     const float4 A = sA[q[jj]];
     const float4 B = sB[q[jj]];
-    pair_geometry(I, A, B, dx[jj], dy[jj], dz[jj], dR2[jj], hh[jj], kw[jj]);
+    float dz, dR2, hh;
+    pair_geometry(I, A, B, dx[jj], dy[jj], dz, dR2, hh, kw[jj]);
     mj[jj] = (q[jj] == self) ? 0.0f : A.w;
-    surr_stage_a<INF>(dR2[jj], dz[jj], hh[jj], n_cut, kw[jj], S, P[jj]);
+    if (FAR4)
+      surr_stage_a_far4<INF>(dR2, dz, hh, S, P[jj]);
+    else
+      surr_stage_a<INF>(dR2, dz, hh, n_cut, kw[jj], S, P[jj]);
     u[jj][0] = P[jj].u[0];
     u[jj][1] = P[jj].u[1];
     u[jj][2] = P[jj].u[2];
   }
   mlp_warp<NJ>(W, ibuf, u, y);
+  if (FAR4) {
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      if (kw[jj] >= 0) {
+        float ddx, ddy, dz, dR2, hh;
+        pair_separation(I, sA[q[jj]], sB[q[jj]], ddx, ddy, dz, dR2, hh);
+        surr_stage_a<INF>(dR2, dz, hh, n_cut, kw[jj], S, P[jj]);
+      }
+    }
+  }
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
     float sr, szz;
@@ -298,8 +319,12 @@ __device__ __forceinline__ void surr_call(const IParticle& I, float mi, const fl
 constexpr int kSurrUnroll = STEPS_SURR_UNROLL;
 
 // Learned tail (surrogate_pair.cuh): STEPS_SURR_NJ j per network call, the
-// j side reduced two j at a time.
-template <bool KAHAN, bool INF>
+// j side reduced two j at a time. FAR4: the straight-run calls (near range
+// n0 = 4), which the host takes when every softening support lies within half
+// a period (h_i + h_j < L / 2): only the centre image of a pair can then be
+// softened, and the steps that redo a pair stay rare. Loads with wider
+// supports take the tiered calls throughout.
+template <bool KAHAN, bool INF, bool FAR4>
 __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, const float4* sA, const float4* sB,
                                               bool sym, float* row, int self, int n_cut, const SurrW& W,
                                               uint32_t* ibuf, const SurrConst& S, float& sx, float& sy, float& sz,
@@ -313,10 +338,10 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
     for (int k = k0; k < k0 + STEPS_KAHAN_GROUP; k += 2) {
       float w[2][3];
       if (STEPS_SURR_NJ == 2) {
-        surr_call<2, INF>(I, mi, sA, sB, k, self, n_cut, W, ibuf, S, gx, gy, gz, w);
+        surr_call<2, INF, FAR4>(I, mi, sA, sB, k, self, n_cut, W, ibuf, S, gx, gy, gz, w);
       } else {
-        surr_call<1, INF>(I, mi, sA, sB, k, self, n_cut, W, ibuf, S, gx, gy, gz, w);
-        surr_call<1, INF>(I, mi, sA, sB, k + 1, self, n_cut, W, ibuf, S, gx, gy, gz, w + 1);
+        surr_call<1, INF, FAR4>(I, mi, sA, sB, k, self, n_cut, W, ibuf, S, gx, gy, gz, w);
+        surr_call<1, INF, FAR4>(I, mi, sA, sB, k + 1, self, n_cut, W, ibuf, S, gx, gy, gz, w + 1);
       }
       if (sym) jside_two(ring, w[0], w[1], row, k);
     }
@@ -328,11 +353,17 @@ __device__ __forceinline__ void sym_tile_surr(const IParticle& I, float mi, cons
 
 // Correction-table tail (tail_table.cuh), two j per step; READ: the table read
 // (the exact reads belong to the nearest-image table, n0 = 0, stored raw).
-template <bool KAHAN, bool INF, int READ>
+// FAR4: as for the learned tail, the straight-run stage A of both pairs and
+// their table reads form one run (the fetches are issued as soon as the inputs
+// exist and return while the near images and the base are computed); a pair
+// whose step is softened is redone with the spline tiers after the reads.
+template <bool KAHAN, bool INF, int READ, bool FAR4>
 __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, const float4* sA, const float4* sB,
                                                bool sym, float* row, int self, int n_cut, const SurrConst& S,
                                                const TableTail& T, float& sx, float& sy, float& sz, float& cx,
                                                float& cy, float& cz) {
+  constexpr int RAW = READ >= kReadCicExact ? 1 : 0;
+  static_assert(!(FAR4 && RAW), "the straight run belongs to the residual tables (n0 = 4)");
   JRing ring;
 #pragma unroll 1
   for (int k0 = 0; k0 < kBJ; k0 += STEPS_KAHAN_GROUP) {
@@ -340,25 +371,58 @@ __device__ __forceinline__ void sym_tile_table(const IParticle& I, float mi, con
 #pragma unroll 1
     for (int k = k0; k < k0 + STEPS_KAHAN_GROUP; k += 2) {
       float w[2][3];
+      if (FAR4) {
+        int q[2], kw[2];
+        float dx[2], dy[2];
+        SurrPair P[2];
+        float2 r[2];
 #pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int q = jslot(k + jj);
-        const float4 A = sA[q];
-        const float4 B = sB[q];
-        float dx, dy, dz, dR2, hh;
-        int kw;
-        pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
-        SurrPair P;
-        surr_stage_a<INF, (READ >= kReadCicExact ? 1 : 0)>(dR2, dz, hh, n_cut, kw, S, P);
-        const float2 r = table_read<READ>(T, P.u[0], P.u[1]);
-        float sr, szz;
-        surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
-        const float mj = (q == self) ? 0.0f : A.w;
-        const float msr = mj * sr;
-        gx = fmaf(dx, msr, gx);
-        gy = fmaf(dy, msr, gy);
-        gz = fmaf(mj, szz, gz);
-        jside_vec(mi, dx, dy, sr, szz, w[jj]);
+        for (int jj = 0; jj < 2; ++jj) {
+          q[jj] = jslot(k + jj);
+          float dz, dR2, hh;
+          pair_geometry(I, sA[q[jj]], sB[q[jj]], dx[jj], dy[jj], dz, dR2, hh, kw[jj]);
+          surr_stage_a_far4<INF>(dR2, dz, hh, S, P[jj]);
+          r[jj] = table_read<READ>(T, P[jj].u[0], P[jj].u[1]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const float4 A = sA[q[jj]];
+          const float4 B = sB[q[jj]];
+          if (kw[jj] >= 0) {
+            float ddx, ddy, dz, dR2, hh;
+            pair_separation(I, A, B, ddx, ddy, dz, dR2, hh);
+            surr_stage_a<INF>(dR2, dz, hh, n_cut, kw[jj], S, P[jj]);
+          }
+          float sr, szz;
+          surr_stage_c<INF>(I, A, B, n_cut, kw[jj], S, P[jj], r[jj].x, r[jj].y, sr, szz);
+          const float mj = (q[jj] == self) ? 0.0f : A.w;
+          const float msr = mj * sr;
+          gx = fmaf(dx[jj], msr, gx);
+          gy = fmaf(dy[jj], msr, gy);
+          gz = fmaf(mj, szz, gz);
+          jside_vec(mi, dx[jj], dy[jj], sr, szz, w[jj]);
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int q = jslot(k + jj);
+          const float4 A = sA[q];
+          const float4 B = sB[q];
+          float dx, dy, dz, dR2, hh;
+          int kw;
+          pair_geometry(I, A, B, dx, dy, dz, dR2, hh, kw);
+          SurrPair P;
+          surr_stage_a<INF, RAW>(dR2, dz, hh, n_cut, kw, S, P);
+          const float2 r = table_read<READ>(T, P.u[0], P.u[1]);
+          float sr, szz;
+          surr_stage_c<INF>(I, A, B, n_cut, kw, S, P, r.x, r.y, sr, szz);
+          const float mj = (q == self) ? 0.0f : A.w;
+          const float msr = mj * sr;
+          gx = fmaf(dx, msr, gx);
+          gy = fmaf(dy, msr, gy);
+          gz = fmaf(mj, szz, gz);
+          jside_vec(mi, dx, dy, sr, szz, w[jj]);
+        }
       }
       if (sym) jside_two(ring, w[0], w[1], row, k);
     }
@@ -438,7 +502,7 @@ pair_sym_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, in
                       });
 }
 
-template <bool KAHAN, bool INF>
+template <bool KAHAN, bool INF, bool FAR4 = false>
 __global__ void __launch_bounds__(kBI, STEPS_SURR_MIN_BLOCKS)
 pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB,
                      long long Ua, long long U, int C, const SurrLane* __restrict__ wl, SurrConst S, FixAcc F) {
@@ -454,12 +518,12 @@ pair_sym_surr_kernel(const float4* __restrict__ jA, const float4* __restrict__ j
   sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int self,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
-                        sym_tile_surr<KAHAN, INF>(I, mi, a, bb, sym, row, self, n_cut, W, ibuf, S, sx, sy, sz, cx,
-                                                  cy, cz);
+                        sym_tile_surr<KAHAN, INF, FAR4>(I, mi, a, bb, sym, row, self, n_cut, W, ibuf, S, sx, sy,
+                                                        sz, cx, cy, cz);
                       });
 }
 
-template <bool KAHAN, bool INF, int READ>
+template <bool KAHAN, bool INF, int READ, bool FAR4 = false>
 __global__ void __launch_bounds__(kBI, STEPS_TABLE_MIN_BLOCKS)
 pair_sym_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ jB, int n, int n_cut, int NB,
                       long long Ua, long long U, int C, TableTail T, SurrConst S, FixAcc F) {
@@ -469,7 +533,7 @@ pair_sym_table_kernel(const float4* __restrict__ jA, const float4* __restrict__ 
   sym_stream_k<KAHAN>(jA, jB, n, NB, Ua, U, C, sA, sB, sJ, F,
                       [&](const IParticle& I, float mi, const float4* a, const float4* bb, bool sym, int self,
                           float* row, float& sx, float& sy, float& sz, float& cx, float& cy, float& cz) {
-                        sym_tile_table<KAHAN, INF, READ>(I, mi, a, bb, sym, row, self, n_cut, S, T, sx, sy, sz,
+                        sym_tile_table<KAHAN, INF, READ, FAR4>(I, mi, a, bb, sym, row, self, n_cut, S, T, sx, sy, sz,
                                                          cx, cy, cz);
                       });
 }

@@ -252,6 +252,7 @@ struct steps_cyl_ctx {
   // symmetric (Newton's third law) evaluation into fixed-point accumulators
   unsigned long long* facc = nullptr;  // [3][n]
   double fix_scale = 0.0;              // 2^S
+  double h_max = 0.0;                  // the largest softening (set with fix_scale)
   bool fix_ready = false, fix_ok = false;
   long long Usym = 0;
   int SYC = 0, SYSC = 0, SYTC = 0;     // CTAs of the symmetric plain / surrogate / table kernels
@@ -986,11 +987,13 @@ int fix_scale(steps_cyl_ctx* c) {
   CK(cudaMemcpyAsync(hm.data(), c->m, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(hh.data(), c->h, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  double M = 0.0, hmin = INFINITY;
+  double M = 0.0, hmin = INFINITY, hmax = 0.0;
   for (int k = 0; k < c->n; ++k) {
     M += std::fabs(hm[k]);
     hmin = std::min(hmin, hh[k]);
+    hmax = std::max(hmax, hh[k]);
   }
+  c->h_max = hmax;
   const double q = c->p.L / hmin;
   const double B = M * (q * q + 10.0);
   const int S = (int)std::floor(57.0 - std::log2(B));
@@ -1037,13 +1040,23 @@ double sym_pairs(const steps_cyl_ctx* c) {
 // The symmetric kernel of the form over the units [Ua, Ua + U) into F.
 // The symmetric table kernel in the context's table read (compiled per read, so
 // that the filtered CIC path carries none of the other reads' arithmetic).
+// The straight-run calls of the learned tail and of the residual tables: near
+// range n0 = 4, and every softening support within half a period (h_i + h_j <
+// L / 2), so that only the centre image of a pair can be softened.
+bool straight_run(const steps_cyl_ctx* c) { return c->p.n0 == 4 && 2.0 * c->h_max < 0.5 * c->p.L; }
+
 template <bool KAHAN, bool INF>
 void launch_sym_table(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long Ua, long long U, const FixAcc& F) {
   const TableTail& T = c->tab;
+  const bool far4 = straight_run(c);
   switch (T.read) {
     case kReadTsc:
-      pair_sym_table_kernel<KAHAN, INF, kReadTsc><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
-                                                                         c->tab_const, F);
+      if (far4)
+        pair_sym_table_kernel<KAHAN, INF, kReadTsc, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                               c->tab_const, F);
+      else
+        pair_sym_table_kernel<KAHAN, INF, kReadTsc><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                           c->tab_const, F);
       break;
     case kReadCicExact:
       pair_sym_table_kernel<KAHAN, INF, kReadCicExact><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
@@ -1054,9 +1067,27 @@ void launch_sym_table(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long 
                                                                               c->tab_const, F);
       break;
     default:
-      pair_sym_table_kernel<KAHAN, INF, kReadCic><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
-                                                                         c->tab_const, F);
+      if (far4)
+        pair_sym_table_kernel<KAHAN, INF, kReadCic, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                               c->tab_const, F);
+      else
+        pair_sym_table_kernel<KAHAN, INF, kReadCic><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, T,
+                                                                           c->tab_const, F);
   }
+}
+
+template <bool FAR4>
+void launch_sym_surr(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long Ua, long long U, const FixAcc& F) {
+  const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+  const SurrLane* wl = c->surr_lanes;
+  if (is_inf(c) && kahan)
+    pair_sym_surr_kernel<true, true, FAR4><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, wl, c->surr, F);
+  else if (is_inf(c))
+    pair_sym_surr_kernel<false, true, FAR4><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, wl, c->surr, F);
+  else if (kahan)
+    pair_sym_surr_kernel<true, false, FAR4><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, wl, c->surr, F);
+  else
+    pair_sym_surr_kernel<false, false, FAR4><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, wl, c->surr, F);
 }
 
 int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const FixAcc& F) {
@@ -1067,17 +1098,10 @@ int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const Fix
   };
   if (form == Form::SURROGATE) {
     const int C = ctas(c->SYSC);
-    if (is_inf(c) && kahan)
-      pair_sym_surr_kernel<true, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->surr_lanes, c->surr, F);
-    else if (is_inf(c))
-      pair_sym_surr_kernel<false, true><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, 0, NB, Ua, U, C, c->surr_lanes, c->surr,
-                                                              F);
-    else if (kahan)
-      pair_sym_surr_kernel<true, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->surr_lanes, c->surr,
-                                                              F);
+    if (straight_run(c))
+      launch_sym_surr<true>(c, C, n, nc, NB, Ua, U, F);
     else
-      pair_sym_surr_kernel<false, false><<<C, kBI, 0, c->st>>>(c->jA, c->jB, n, nc, NB, Ua, U, C, c->surr_lanes,
-                                                               c->surr, F);
+      launch_sym_surr<false>(c, C, n, nc, NB, Ua, U, F);
     CKLAUNCH("pair_sym_surrogate");
   } else if (form == Form::TABLE) {
     const int C = ctas(c->SYTC);
@@ -1385,34 +1409,35 @@ uint32_t pack_half2(float lo, float hi) { return half_bits(lo) | (half_bits(hi) 
 
 // Per-lane mma fragments of a parameter vector (layout in include/steps_cyl.h).
 void build_lanes(const float* P, SurrLane lanes[32]) {
-  const float *W1 = P + kOW1, *b1 = P + kOB1, *W2 = P + kOW2, *b2 = P + kOB2, *W3 = P + kOW3, *b3 = P + kOB3;
+  const float *W1 = P + kOW1, *b1 = P + kOB1, *W2 = P + kOW2, *b2 = P + kOB2, *W3 = P + kOW3;
   for (int L = 0; L < 32; ++L) {
     SurrLane& s = lanes[L];
     std::memset(&s, 0, sizeof s);
     const int g = L >> 2, t = L & 3;
     for (int nb = 0; nb < 4; ++nb) {
       const int o = 8 * nb + g;
-      const float w0 = 2 * t < 3 ? W1[o * 3 + 2 * t] : 0.f, w1 = 2 * t + 1 < 3 ? W1[o * 3 + 2 * t + 1] : 0.f;
+      // rows 2t, 2t + 1 of the first layer's [8 x 32] B operand: inputs 0..2,
+      // then the constant-1 input whose weight is the bias, then zeros
+      const float w0 = t == 0 ? W1[o * 3] : (t == 1 ? W1[o * 3 + 2] : 0.f);
+      const float w1 = t == 0 ? W1[o * 3 + 1] : (t == 1 ? b1[o] : 0.f);
       s.w1[nb] = pack_half2(w0, w1);
       // accumulator seeds: columns 2t, 2t + 1 of rows g and g + 8 of n-block nb
-      for (int q = 0; q < 4; ++q) {
-        s.c1[4 * nb + q] = b1[8 * nb + 2 * t + (q & 1)];
-        s.c2[4 * nb + q] = b2[8 * nb + 2 * t + (q & 1)];
-      }
+      for (int q = 0; q < 4; ++q) s.c2[4 * nb + q] = b2[8 * nb + 2 * t + (q & 1)];
       for (int kb = 0; kb < 2; ++kb) {
         const int k = 16 * kb + 2 * t;
-        s.w2[(kb * 4 + nb) * 2] = pack_half2(W2[o * kH + k], W2[o * kH + k + 1]);
-        s.w2[(kb * 4 + nb) * 2 + 1] = pack_half2(W2[o * kH + k + 8], W2[o * kH + k + 9]);
+        s.w2[(nb * 2 + kb) * 2] = pack_half2(W2[o * kH + k], W2[o * kH + k + 1]);
+        s.w2[(nb * 2 + kb) * 2 + 1] = pack_half2(W2[o * kH + k + 8], W2[o * kH + k + 9]);
       }
     }
-    // output column n carries output (n & 1): every lane of a quad then holds
-    // both outputs of the quad's rows, and no lane has to gather them
+    // output column n = g carries output (n & 1); the even m-tile's product
+    // fills columns 0..3 and the odd tile's columns 4..7, so that every lane
+    // of a quad holds both outputs of its own pair
+    uint32_t* w3 = g < 4 ? s.w3e : s.w3o;
     for (int kb = 0; kb < 2; ++kb) {
       const int k = 16 * kb + 2 * t, o = g & 1;
-      s.w3[kb * 2] = pack_half2(W3[o * kH + k], W3[o * kH + k + 1]);
-      s.w3[kb * 2 + 1] = pack_half2(W3[o * kH + k + 8], W3[o * kH + k + 9]);
+      w3[kb * 2] = pack_half2(W3[o * kH + k], W3[o * kH + k + 1]);
+      w3[kb * 2 + 1] = pack_half2(W3[o * kH + k + 8], W3[o * kH + k + 9]);
     }
-    for (int q = 0; q < 4; ++q) s.c3[q] = b3[q & 1];
   }
 }
 
@@ -1422,8 +1447,9 @@ int install_surrogate(steps_cyl_ctx* c, const float* P) {
   if (!c->surr_lanes) CK(cudaMalloc(&c->surr_lanes, sizeof lanes));
   CK(cudaMemcpyAsync(c->surr_lanes, lanes, sizeof lanes, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
-  c->surr.mu0 = P[kNW];
-  c->surr.mu1 = P[kNW + 1];
+  // the output bias b3 enters through the shift: E (sc (y + b3) + mu)
+  c->surr.mu0 = (float)((double)P[kNW] + (double)P[kNW + 2] * (double)P[kOB3]);
+  c->surr.mu1 = (float)((double)P[kNW + 1] + (double)P[kNW + 3] * (double)P[kOB3 + 1]);
   c->surr.sc0 = P[kNW + 2];
   c->surr.sc1 = P[kNW + 3];
   c->surr.dR_max = P[kNW + 4];

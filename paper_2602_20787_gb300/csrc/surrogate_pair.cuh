@@ -11,10 +11,11 @@
 // of both tiles, i.e. its own four pairs. The accumulator fragment of one
 // layer is, after ReLU and packing to f16x2, the A fragment of the next, so
 // activations never leave registers. The three inputs reach the quad through
-// a small per-warp shared buffer, and the output layer's two columns are
-// repeated across all eight, so every lane already holds its own pair's
-// outputs. Weights are B fragments read from shared memory once per call per
-// layer; biases seed the accumulators.
+// a small per-warp shared buffer. The output layer adds the two tiles'
+// products into one accumulator, the even tile's in columns 0..3 and the odd
+// tile's in columns 4..7, each output repeated twice, so every lane already
+// holds its own pair's outputs. Weights are B fragments read from shared memory
+// once per call per layer; the hidden bias seeds the accumulators.
 #pragma once
 #include <cstdint>
 
@@ -23,22 +24,24 @@
 namespace steps {
 
 // Per-lane B fragments and accumulator seeds, prepared on the host from the
-// FP32 weights (W1 as m16n8k8 fragments, W2 and W3 as m16n8k16 fragments). The
-// seeds are the biases laid out as the mma's C operand (c0..c3 of lane (g, t)
-// hold columns 2t, 2t + 1 of rows g and g + 8), so one 128-bit load yields a C
+// FP32 weights (W1 as m16n8k8 fragments, W2 and W3 as m16n8k16 fragments).
+// The first layer's bias rides in the weights: the network's input vector
+// carries a constant 1 as its fourth component, whose weight column is b1. The
+// output bias is folded into the output shift on the host (mu + sc b3). The
+// hidden bias b2 is laid out as the mma's C operand (c0..c3 of lane (g, t) hold
+// columns 2t, 2t + 1 of rows g and g + 8), so one 128-bit load yields a C
 // operand with no register moves.
 struct SurrLane {
-  uint32_t w1[4];   // n-block nb: {W1[8nb+g][2t], W1[8nb+g][2t+1]} (input 2 at t = 1, zero beyond)
-  uint32_t w2[16];  // [kb][nb][2]
-  uint32_t w3[4];   // [kb][2], rows 0, 1 of W3 only
-  float c1[16];     // [nb][4]: b1[8nb+2t], b1[8nb+2t+1], b1[8nb+2t], b1[8nb+2t+1]
-  float c2[16];
-  float c3[4];      // b3[0], b3[1], b3[0], b3[1]
+  uint32_t w1[4];   // n-block nb: {W1[8nb+g][2t], W1[8nb+g][2t+1]}; t = 1: {W1[.][2], b1[8nb+g]}; zero beyond
+  uint32_t w2[16];  // [nb][kb][2]
+  uint32_t w3e[4];  // [kb][2]: output column g of the even m-tile's product (lanes g < 4; zero for g >= 4)
+  uint32_t w3o[4];  // [kb][2]: output column g of the odd m-tile's product (lanes g >= 4; zero for g < 4)
+  float c2[16];     // [nb][4]: b2[8nb+2t], b2[8nb+2t+1], b2[8nb+2t], b2[8nb+2t+1]
 };
-static_assert(sizeof(SurrLane) == 60 * 4, "SurrLane layout");
+static_assert(sizeof(SurrLane) == 44 * 4, "SurrLane layout");
 
 // Lane L's SurrLane lives at wt[L * kSurrStride ...] in shared memory. A row
-// stride of 60 words (28 mod 32) puts the 16-byte loads of a quarter warp (8
+// stride of 44 words (12 mod 32) puts the 16-byte loads of a quarter warp (8
 // lanes) on 32 distinct banks. Each layer's fragments are read once per
 // network call with 128-bit volatile shared loads: kept out of the register
 // file across the j loop, they leave room for resident warps.
@@ -60,7 +63,7 @@ struct SurrW {
     return make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w));
   }
 };
-constexpr int kW1 = 0, kW2 = 4, kW3 = 20, kC1 = 24, kC2 = 40, kC3 = 56;
+constexpr int kW1 = 0, kW2 = 4, kW3E = 20, kW3O = 24, kC2 = 28;
 
 // Stage the 32 lanes' fragments into shared memory (all threads of the block
 // take part; ends with a barrier).
@@ -125,11 +128,11 @@ __device__ __forceinline__ float f32(uint32_t v) { return __uint_as_float(v); }
 // shared memory once per call and the tiles' mma chains are independent work
 // for the scheduler. Must be called by all 32 lanes with uniform control flow.
 // Per-warp exchange buffer of the network inputs: [NJ][slot t][kInStride]
-// words; slot 0 holds the (u0, u1) f16x2 word of each lane, slot 1 the (u2, 0)
-// word, slots 2 and 3 stay zero (columns 4..7 of the A operand). Lane (g, t)
-// reads its A fragment, words 4g .. 4g+3 of slot t, with one 16-byte load; a
-// slot stride of 40 words keeps those loads and the stores free of bank
-// conflicts.
+// words; slot 0 holds the (u0, u1) f16x2 word of each lane, slot 1 the (u2, 1)
+// word (the constant 1 carries the first layer's bias), slots 2 and 3 stay
+// zero (columns 4..7 of the A operand). Lane (g, t) reads its A fragment,
+// words 4g .. 4g+3 of slot t, with one 16-byte load; a slot stride of 40 words
+// keeps those loads and the stores free of bank conflicts.
 constexpr int kInStride = 40;
 constexpr int kInWords = 4 * kInStride;
 
@@ -153,7 +156,7 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
     buf[jj * kInWords + lane] = pack_h2(u[jj][0], u[jj][1]);
-    buf[jj * kInWords + kInStride + lane] = pack_h2(u[jj][2], 0.0f);
+    buf[jj * kInWords + kInStride + lane] = pack_h2(u[jj][2], 1.0f);
   }
   __syncwarp();
 #pragma unroll
@@ -164,18 +167,19 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
     in[jj][2] = v.z;
     in[jj][3] = v.w;
   }
-  // layer 1: [16 pairs x 8 inputs] x [8 x 32] per tile
+  // layer 1: [16 pairs x 8 inputs] x [8 x 32] per tile (input 3 is the
+  // constant 1, so the product already holds the bias)
   uint32_t a2[NT][2][4];
   {
     const uint4 w1 = W.ld4(kW1);
     const uint32_t wv[4] = {w1.x, w1.y, w1.z, w1.w};
-    const float4 cb[4] = {W.ldc(kC1), W.ldc(kC1 + 4), W.ldc(kC1 + 8), W.ldc(kC1 + 12)};
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int tl = 0; tl < NT; ++tl) {
       float d1[4][4];
 #pragma unroll
       for (int nb = 0; nb < 4; ++nb)
-        mma_k8(d1[nb], in[tl >> 1][2 * (tl & 1)], in[tl >> 1][2 * (tl & 1) + 1], wv[nb], cb[nb]);
+        mma_k8(d1[nb], in[tl >> 1][2 * (tl & 1)], in[tl >> 1][2 * (tl & 1) + 1], wv[nb], zero);
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
         a2[tl][kb][0] = relu_pack(d1[2 * kb][0], d1[2 * kb][1]);
@@ -185,54 +189,48 @@ __device__ __forceinline__ void mlp_warp(const SurrW& W, uint32_t* buf, const fl
       }
     }
   }
-  // layer 2: [16 x 32] x [32 x 32] per tile; fragments [kb][nb][2]
+  // layer 2: [16 x 32] x [32 x 32] per tile, one n-block of outputs at a
+  // time over all tiles (its fragments [kb][2] and bias seeds are read once
+  // per call); each n-block's result is packed at once into the next layer's
+  // A fragment: n-block nb fills words 2 (nb & 1), +1 of k-block nb >> 1
   uint32_t a3[NT][2][4];
-  {
-    uint32_t w2[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 v = W.ld4(kW2 + 4 * q);
-      w2[4 * q] = v.x; w2[4 * q + 1] = v.y; w2[4 * q + 2] = v.z; w2[4 * q + 3] = v.w;
-    }
-    const float4 cb[4] = {W.ldc(kC2), W.ldc(kC2 + 4), W.ldc(kC2 + 8), W.ldc(kC2 + 12)};
+  for (int nb = 0; nb < 4; ++nb) {
+    const uint4 w = W.ld4(kW2 + 4 * nb);
+    const float4 cb = W.ldc(kC2 + 4 * nb);
 #pragma unroll
     for (int tl = 0; tl < NT; ++tl) {
-      float d2[4][4];
-#pragma unroll
-      for (int nb = 0; nb < 4; ++nb) {
-        mma_k16(d2[nb], a2[tl][0], w2[2 * nb], w2[2 * nb + 1], cb[nb]);
-        mma_k16_acc(d2[nb], a2[tl][1], w2[2 * (4 + nb)], w2[2 * (4 + nb) + 1]);
-      }
-#pragma unroll
-      for (int kb = 0; kb < 2; ++kb) {
-        a3[tl][kb][0] = relu_pack(d2[2 * kb][0], d2[2 * kb][1]);
-        a3[tl][kb][1] = relu_pack(d2[2 * kb][2], d2[2 * kb][3]);
-        a3[tl][kb][2] = relu_pack(d2[2 * kb + 1][0], d2[2 * kb + 1][1]);
-        a3[tl][kb][3] = relu_pack(d2[2 * kb + 1][2], d2[2 * kb + 1][3]);
-      }
+      float d2[4];
+      mma_k16(d2, a2[tl][0], w.x, w.y, cb);
+      mma_k16_acc(d2, a2[tl][1], w.z, w.w);
+      a3[tl][nb >> 1][2 * (nb & 1)] = relu_pack(d2[0], d2[1]);
+      a3[tl][nb >> 1][2 * (nb & 1) + 1] = relu_pack(d2[2], d2[3]);
     }
   }
-  // layer 3: [16 x 32] x [32 x 8] per tile (columns 0, 1 used)
-  float out[NT][4];
+  // layer 3: per value of j, [16 x 32] x [32 x 8] for the even tile plus the
+  // same for the odd tile into one accumulator: the even tile's weights fill
+  // columns 0..3 and the odd tile's columns 4..7 (output n & 1 in column n),
+  // the other columns' weights being zero. The output bias is in mu.
+  float out[NJ][4];
   {
-    const uint4 w3 = W.ld4(kW3);
-    const float4 c3 = W.ldc(kC3);
+    const uint4 we = W.ld4(kW3E);
+    const uint4 wo = W.ld4(kW3O);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int tl = 0; tl < NT; ++tl) {
-      mma_k16(out[tl], a3[tl][0], w3.x, w3.y, c3);
-      mma_k16_acc(out[tl], a3[tl][1], w3.z, w3.w);
+    for (int jj = 0; jj < NJ; ++jj) {
+      mma_k16(out[jj], a3[2 * jj][0], we.x, we.y, zero);
+      mma_k16_acc(out[jj], a3[2 * jj][1], we.z, we.w);
+      mma_k16_acc(out[jj], a3[2 * jj + 1][0], wo.x, wo.y);
+      mma_k16_acc(out[jj], a3[2 * jj + 1][1], wo.z, wo.w);
     }
   }
-  // output column n carries output (n & 1), so lane (g, t) holds both outputs
-  // of rows g and g+8 of every tile; its own pair is row g + 8 (t & 1) of tile
-  // t >> 1
-  const int mt = t >> 1, hi = t & 1;
+  // lane (g, t) holds columns 2t, 2t + 1 (outputs 0, 1) of rows g and g + 8 of
+  // tile t >> 1; its own pair is row g + 8 (t & 1)
+  const bool hi = (t & 1) != 0;
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
-    const float(&o0)[4] = out[2 * jj];
-    const float(&o1)[4] = out[2 * jj + 1];
-    y[jj][0] = mt == 0 ? (hi ? o0[2] : o0[0]) : (hi ? o1[2] : o1[0]);
-    y[jj][1] = mt == 0 ? (hi ? o0[3] : o0[1]) : (hi ? o1[3] : o1[1]);
+    y[jj][0] = hi ? out[jj][2] : out[jj][0];
+    y[jj][1] = hi ? out[jj][3] : out[jj][1];
   }
 }
 
@@ -389,6 +387,10 @@ __device__ __forceinline__ void near_images_fp32(float dR2, float dz, float hh, 
   sz = (z0 + z1) + dz * cr;
 }
 
+#ifndef STEPS_SURR_N0_FIXED
+#define STEPS_SURR_N0_FIXED 1  // compile the n0 = 4 near range unrolled beside the general one
+#endif
+
 // Per-pair state carried across the network: the image sums are affine in
 // the network outputs, sr = a0 + b0 y0 and sz = a1 + b1 y1 (near images, tail
 // base, envelope, sign(dz) and the output scaling folded in), plus the inputs.
@@ -444,6 +446,50 @@ __device__ __forceinline__ void surr_stage_a(float dR2, float dz, float hh, int 
   P.u[2] = fmaf(fminf(hh, A), S.two_over_A, -1.0f);
 }
 
+// Stage A of a pair that no lane of the warp has inside its softening support
+// (kw < 0), with the near range n0 = 4 fixed: the same arithmetic as
+// surr_stage_a on that path (centre image, then the four image pairs +-k
+// packed, then the tail base, envelope and inputs), written without a branch so
+// that a caller can place it in one straight run with the network.
+template <bool INF = false>
+__device__ __forceinline__ void surr_stage_a_far4(float dR2, float dz, float hh, const SurrConst& S, SurrPair& P) {
+  const float adz = fabsf(dz), A = S.A;
+  const float dR = dR2 * rsq(fmaxf(dR2, 1e-30f));
+  P.u[0] = fmaf(fminf(dR, S.dR_max), S.two_inv_dR_max, -1.0f);
+  P.u[1] = fmaf(adz, 4.0f, -1.0f);
+  P.u[2] = fmaf(fminf(hh, A), S.two_over_A, -1.0f);
+  // near images |k| <= 4, all Newtonian
+  const u64 DR2 = pk(dR2, dR2);
+  const u64 STEP = pk(1.0f, -1.0f);
+  u64 O = pk(dz, dz);
+  u64 SR = pk(0.0f, 0.0f), SZ = pk(0.0f, 0.0f);
+  const float ri = rsq(fmaf(dz, dz, dR2));
+  const float cr = ri * ri * ri;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) newton_pair(O, STEP, DR2, SR, SZ);
+  float s0, s1, z0, z1;
+  upk(SR, s0, s1);
+  upk(SZ, z0, z1);
+  const float sr = (s0 + s1) + cr;
+  const float sz = (z0 + z1) + dz * cr;
+  // tail base and envelope, as in surr_stage_a
+  float br, bz, il1;
+  if (INF) {
+    tail_base_inf_fp32(dR2, A + adz, A - adz, br, bz, il1);
+  } else {
+    const float hb = (adz > 0.0f ? S.fnh + 1.0f : S.fnh) - adz;
+    tail_base_fp32(dR2, A + adz, A - adz, S.fnh + adz, hb, br, bz, il1);
+  }
+  const float e = il1 * il1;
+  const float er = e * e * e;
+  const float sg = dz > 0.0f ? 1.0f : (dz < 0.0f ? -1.0f : 0.0f);
+  const float ez = sg * (e * e * il1);
+  P.a0 = fmaf(er, S.mu0, sr + br);
+  P.b0 = er * S.sc0;
+  P.a1 = fmaf(ez, S.mu1, fmaf(sg, bz, sz));
+  P.b1 = ez * S.sc1;
+}
+
 // Stage C: tail = base + envelope x network output, plus the exact spline
 // correction of tail images inside some lane's softening support.
 // The separation is recomputed from the tile (same arithmetic, same values)
@@ -496,9 +542,6 @@ __device__ __forceinline__ void surr_stage_c(const IParticle& I, const float4& A
   }
 }
 
-#ifndef STEPS_SURR_N0_FIXED
-#define STEPS_SURR_N0_FIXED 1  // compile the n0 = 4 near range unrolled beside the general one
-#endif
 #ifndef STEPS_SURR_NJ
 #define STEPS_SURR_NJ 2  // values of j per network call (independent mma chains per warp)
 #endif

@@ -322,6 +322,7 @@ struct steps_cyl_ctx {
   double last_images = 0.0;
   double last_pairs = 0.0;   // pairs the last pair kernel evaluated
   bool last_sym = false;     // ... with the symmetric kernels
+  bool last_straight = false;  // ... taking the straight run of the modelled tails
   bool timed = false;
 };
 
@@ -1092,6 +1093,9 @@ void launch_sym_surr(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long U
 
 int launch_sym(steps_cyl_ctx* c, Form form, long long Ua, long long U, const FixAcc& F) {
   const bool kahan = c->p.precision == STEPS_FP32_KAHAN;
+  c->last_straight = (form == Form::SURROGATE || (form == Form::TABLE && (c->tab.read == kReadCic ||
+                                                                          c->tab.read == kReadTsc))) &&
+                     straight_run(c);
   const int nc = c->p.n_cut, n = c->n, NB = c->NB;
   auto ctas = [&](int full) {  // the CTA count of the whole triangle, scaled to a share of it
     return (int)std::max<long long>(1, std::min<long long>(U, (long long)full * U / std::max<long long>(c->Usym, 1)));
@@ -2678,7 +2682,7 @@ int steps_cyl_last_eval(steps_cyl_ctx* c, double out[4]) {
   out[0] = c->last_images;
   out[1] = c->last_pairs;
   out[2] = ms;
-  out[3] = c->last_sym ? 1.0 : 0.0;
+  out[3] = c->last_sym ? (c->last_straight ? 2.0 : 1.0) : 0.0;
   return STEPS_OK;
 }
 

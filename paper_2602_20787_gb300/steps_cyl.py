@@ -294,11 +294,12 @@ def steps_cyl_last_timing(ctx):
 
 def steps_cyl_last_eval(ctx) -> dict:
     """The last direct force evaluation: pair-images delivered, pairs the
-    kernel evaluated, its device ms, and whether it was a symmetric kernel."""
+    kernel evaluated, its device ms, whether it was a symmetric kernel, and
+    whether that kernel took the modelled tails' straight run."""
     out = np.zeros(4)
     _check(load().steps_cyl_last_eval(ctx, _ptr(out)))
     return {"pair_images": float(out[0]), "pairs_evaluated": float(out[1]), "pair_ms": float(out[2]),
-            "symmetric": bool(out[3])}
+            "symmetric": bool(out[3]), "straight_run": out[3] == 2.0}
 
 
 def steps_cyl_free(ctx):

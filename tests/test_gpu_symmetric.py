@@ -6,6 +6,9 @@ accumulators.
 - Every FP32 direct form (plain Kahan and plain sums, correction table, learned
   tail, infinite window) against the row kernels, which evaluate each ordered
   pair (two emulated shards), and against the FP64 oracle.
+- The modelled tails' straight-run kernels (near range n0 = 4, every h_i + h_j
+  below L / 2, softened steps redone with the spline tiers) against the row
+  kernels and the oracle's surrogate form.
 - Newton's third law to the rounding of the FP32 partial sums.
 - A softening so small that the fixed-point unit would be too coarse falls back
   to the row kernels."""
@@ -101,6 +104,60 @@ def test_modelled_tails_match_row_kernels(env):
     ref += oracle.background_field(d["pos"][idx], ics.R_SIM, 0.0, 1.0, w.rho_bar, mode=2)
     med, _, mx = stats(a[idx], ref)
     assert med <= 1e-5 and mx <= 1e-3, (med, mx)
+
+
+def test_straight_run_matches_row_kernels_and_oracle(env):
+    # The production softening law (h_i + h_j <= 0.16 L) takes the straight-run
+    # kernels of both modelled tails. Pairs inside their softening support exist
+    # in this load, so the redo of softened steps runs as well. The row kernels
+    # take the tiered calls throughout.
+    torch, sc, shard = env
+    w = ics.WORKLOADS["production_n65536"]
+    n = 2600
+    d = ics.particle_load(n, 65, w.M_tot, displaced=True, rho_bar=w.rho_bar, eps_law="ratio8")
+    assert 2.0 * d["h"].max() < 0.5
+    pos = d["pos"]
+    dR = np.hypot(pos[:, None, 0] - pos[None, :, 0], pos[:, None, 1] - pos[None, :, 1])
+    np.fill_diagonal(dR, np.inf)
+    softened = np.nonzero((dR < d["h"][:, None] + d["h"][None, :]).any(1))[0]
+    assert softened.size >= 20, softened.size
+    cfg = sc.Config(n_cut=w.n_cut, n0=w.n0, precision=sc.STEPS_FP32_KAHAN, rho_bar=w.rho_bar, reorder_every=-1)
+    seeded = {}
+
+    def surrogate(sim):
+        seeded["net"] = seeded_surrogate(sc, sim.ctx, 44, w.n_cut, w.n0)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+
+    def table(sim):
+        sc.steps_cyl_build_tail_table(sim.ctx, 129, 17)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+
+    for setup in (surrogate, table):
+        sim = sc.Simulation(cfg, d["pos"], d["vel"], d["m"], d["h"])
+        setup(sim)
+        a = sim.forces()
+        ev = sc.steps_cyl_last_eval(sim.ctx)
+        assert ev["symmetric"] and ev["straight_run"], ev
+        sim.close()
+        r = rel_err(a, row_forces(sc, shard, cfg, d, setup))
+        assert np.median(r) <= 1e-6 and r.max() <= 1e-4, (setup.__name__, np.median(r), r.max())
+        if setup is surrogate:
+            w16, scfg = seeded["net"]
+            idx = np.union1d(ics.subsample(n, 60, seed=5), softened[:40])
+            ref = oracle.pair_field_surrogate(d["pos"], d["m"], d["h"], 1.0, 1.0, w16, scfg, idx=idx)
+            ref += oracle.background_field(d["pos"][idx], ics.R_SIM, w.n_cut * 1.0, 1.0, w.rho_bar, mode=1)
+            med, _, mx = stats(a[idx], ref)
+            assert med <= 2e-6 and mx <= 1e-4, (med, mx)
+    # the literal softening law of the learned-tail workloads keeps the tiered calls
+    wl = ics.WORKLOADS["surrogate_n65536"]
+    dl = ics.particle_load(n, 66, wl.M_tot, displaced=True, rho_bar=wl.rho_bar)
+    assert 2.0 * dl["h"].max() >= 0.5
+    sim = sc.Simulation(cfg, dl["pos"], dl["vel"], dl["m"], dl["h"])
+    surrogate(sim)
+    sim.forces()
+    ev = sc.steps_cyl_last_eval(sim.ctx)
+    assert ev["symmetric"] and not ev["straight_run"], ev
+    sim.close()
 
 
 def test_newton_third_law(env):

@@ -3,7 +3,8 @@ computed index of their shared and global accesses checked against its buffer,
 an index outside recorded and clamped, the record folded into the device error
 word). compute-sanitizer is not available here, so this build stands in for
 it: every symmetric form (plain Kahan and plain sums, learned tail, correction
-table with each read, nearest-image table, infinite window, the symmetric
+table with each read, the straight-run instances of both modelled tails on the
+production softening law, nearest-image table, infinite window, the symmetric
 sharded step of two emulated ranks) runs on ragged sizes, and each call must
 return without STEPS_EDEVICE and give the release build's forces.
 
@@ -49,6 +50,24 @@ for n in (2, 129, 1000, 2500):
         sc.steps_cyl_build_tail_table(sim.ctx, 65, 9, err_median=1.0, err_p999=1.0, check_particles=64)
         sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
         forms["table_" + name] = sim.forces()
+    sim.close()
+    # the production softening law (every h_i + h_j < L / 2): the straight-run
+    # instances of the learned tail and the residual tables
+    dp = ics.particle_load(n, 200 + n, w.M_tot, displaced=True, rho_bar=w.rho_bar, eps_law="ratio8")
+    sim = sc.Simulation(sc.Config(**base), dp["pos"], dp["vel"], dp["m"], dp["h"])
+    seeded_surrogate(sc, sim.ctx, 42, w.n_cut, w.n0)
+    sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_SURROGATE)
+    forms["surrogate_straight"] = sim.forces()
+    ev = sc.steps_cyl_last_eval(sim.ctx)
+    assert ev["straight_run"] or (n < 3 and not ev["symmetric"]), ev
+    for name, read in (("cic", sc.STEPS_TABLE_READ_CIC), ("tsc", sc.STEPS_TABLE_READ_TSC)):
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_FULL)
+        sc.steps_cyl_set_table_read(sim.ctx, read)
+        sc.steps_cyl_build_tail_table(sim.ctx, 65, 9, err_median=1.0, err_p999=1.0, check_particles=64)
+        sc.steps_cyl_set_tail(sim.ctx, sc.STEPS_TAIL_TABLE)
+        forms["table_straight_" + name] = sim.forces()
+        ev = sc.steps_cyl_last_eval(sim.ctx)
+        assert ev["straight_run"] or (n < 3 and not ev["symmetric"]), ev
     sim.close()
     near = dict(base, n0=0)
     sim = sc.Simulation(sc.Config(**near), d["pos"], d["vel"], d["m"], d["h"])

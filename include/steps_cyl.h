@@ -353,6 +353,29 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* ctx, const float* params, double err_
  * STEPS_ENOSURROGATE when none is loaded. */
 int steps_cyl_get_surrogate(steps_cyl_ctx* ctx, float* params);
 
+/* The network's tensor-core operands exactly as the surrogate kernels stage them
+ * in shared memory, for checking the fragment layout on a host without a GPU
+ * (no context, no CUDA call). The paper has no counterpart: the network is this
+ * project's. params: STEPS_SURR_NPARAM floats (host) in the layout above.
+ * lanes (host, 32 x STEPS_SURR_LANE_WORDS words, caller-owned) receives lane
+ * L = 4g + t's record at lanes[L * STEPS_SURR_LANE_WORDS]:
+ *   words 0-3   the first layer's B operand of mma.m16n8k8 (f16x2), n-block nb:
+ *               rows 2t, 2t + 1 of column 8 nb + g of the 8 x 32 matrix whose
+ *               rows are the weights of u0, u1, u2, then b1 (the input vector
+ *               carries a constant 1 as its fourth component), then zeros;
+ *   words 4-19  the hidden layer's B operands of mma.m16n8k16 (f16x2), [nb][kb]
+ *               {rows 16 kb + 2t, +1 | 16 kb + 2t + 8, +9} of column 8 nb + g;
+ *   words 20-23 the output layer's B operands for the even m-tile, [kb]: column
+ *               g carries output g & 1 for g < 4, zero for g >= 4;
+ *   words 24-27 the same for the odd m-tile (columns g >= 4);
+ *   words 28-43 the hidden bias b2 as FP32 C operands, [nb]: columns 8 nb + 2t,
+ *               8 nb + 2t + 1 for rows g and g + 8.
+ * shift (host, 2 floats) receives the output shift mu + sc b3 the kernels add,
+ * so that the tail is B1 + E (y sc + shift) with y the network without b3.
+ * STEPS_EINVAL for a NULL pointer. */
+#define STEPS_SURR_LANE_WORDS 44
+int steps_cyl_surrogate_lanes(const float* params, uint32_t* lanes, float* shift);
+
 /* Select the tail form: STEPS_TAIL_FULL, STEPS_TAIL_SURROGATE or
  * STEPS_TAIL_TABLE (a modelled tail requires an accepted network / table and an
  * FP32 precision; the infinite window refuses STEPS_TAIL_FULL). As with

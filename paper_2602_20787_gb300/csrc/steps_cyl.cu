@@ -1445,15 +1445,23 @@ void build_lanes(const float* P, SurrLane lanes[32]) {
   }
 }
 
+// The output shift the kernels add: mu + sc b3, so that b3 enters the tail as
+// E (sc (y + b3) + mu) with the network's last layer run without its bias.
+void surr_shift(const float* P, float shift[2]) {
+  shift[0] = (float)((double)P[kNW] + (double)P[kNW + 2] * (double)P[kOB3]);
+  shift[1] = (float)((double)P[kNW + 1] + (double)P[kNW + 3] * (double)P[kOB3 + 1]);
+}
+
 int install_surrogate(steps_cyl_ctx* c, const float* P) {
   SurrLane lanes[32];
   build_lanes(P, lanes);
   if (!c->surr_lanes) CK(cudaMalloc(&c->surr_lanes, sizeof lanes));
   CK(cudaMemcpyAsync(c->surr_lanes, lanes, sizeof lanes, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
-  // the output bias b3 enters through the shift: E (sc (y + b3) + mu)
-  c->surr.mu0 = (float)((double)P[kNW] + (double)P[kNW + 2] * (double)P[kOB3]);
-  c->surr.mu1 = (float)((double)P[kNW + 1] + (double)P[kNW + 3] * (double)P[kOB3 + 1]);
+  float shift[2];
+  surr_shift(P, shift);
+  c->surr.mu0 = shift[0];
+  c->surr.mu1 = shift[1];
   c->surr.sc0 = P[kNW + 2];
   c->surr.sc1 = P[kNW + 3];
   c->surr.dR_max = P[kNW + 4];
@@ -3019,6 +3027,17 @@ int steps_cyl_set_surrogate(steps_cyl_ctx* c, const float* params, double err_me
     c->p.tail = STEPS_TAIL_FULL;
     return fail(STEPS_ESURROGATE_REJECTED, "surrogate rejected: median %.3g, p99.9 %.3g", med, p999);
   }
+  return STEPS_OK;
+}
+
+int steps_cyl_surrogate_lanes(const float* params, uint32_t* lanes, float* shift) {
+  g_last_error.clear();
+  if (!params || !lanes || !shift) return fail(STEPS_EINVAL, "NULL argument");
+  static_assert(sizeof(SurrLane) == 4 * STEPS_SURR_LANE_WORDS, "lane record size");
+  SurrLane rec[32];
+  build_lanes(params, rec);
+  std::memcpy(lanes, rec, sizeof rec);
+  surr_shift(params, shift);
   return STEPS_OK;
 }
 

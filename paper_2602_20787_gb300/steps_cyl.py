@@ -47,10 +47,12 @@ _EXPORTS = [
     "steps_cyl_tree_frame", "steps_cyl_tree_frame_r3", "steps_cyl_tree_stats", "steps_cyl_tree_calibrate",
     "steps_cyl_tree_set_radial", "steps_cyl_shard", "steps_cyl_shard_drift", "steps_cyl_shard_kick",
     "steps_cyl_last_eval", "steps_cyl_shard_mode", "steps_cyl_shard_force", "steps_cyl_shard_finish",
+    "steps_cyl_surrogate_lanes",
 ]
 
 STEPS_SURR_NW = 1250
 STEPS_SURR_NPARAM = 1255
+STEPS_SURR_LANE_WORDS = 44
 
 # size limit of the allocation-free entry point (include/steps_cyl.h)
 STEPS_NOALLOC_MAX_N = 65536
@@ -131,6 +133,7 @@ def load(build_if_missing: bool = True):
     L.steps_cyl_train_surrogate.argtypes = [p, ctypes.POINTER(TrainCfg), p]
     L.steps_cyl_set_surrogate.argtypes = [p, p, d, d, p]
     L.steps_cyl_get_surrogate.argtypes = [p, p]
+    L.steps_cyl_surrogate_lanes.argtypes = [p, p, p]
     L.steps_cyl_set_tail.argtypes = [p, i32]
     L.steps_cyl_check_surrogate.argtypes = [p, i32, p]
     L.steps_cyl_build_tail_table.argtypes = [p, i32, i32, d, d, d, i32, p]
@@ -447,6 +450,18 @@ def steps_cyl_get_surrogate(ctx) -> np.ndarray:
     out = np.zeros(STEPS_SURR_NPARAM, dtype=np.float32)
     _check(load().steps_cyl_get_surrogate(ctx, _ptr(out)))
     return out
+
+
+def steps_cyl_surrogate_lanes(params):
+    """The network's per-lane tensor-core operands as the kernels stage them
+    (host only): (lanes uint32 [32][STEPS_SURR_LANE_WORDS], shift float32 [2])."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (STEPS_SURR_NPARAM,):
+        raise StepsError(STEPS_EINVAL, f"params must hold {STEPS_SURR_NPARAM} floats")
+    lanes = np.zeros((32, STEPS_SURR_LANE_WORDS), dtype=np.uint32)
+    shift = np.zeros(2, dtype=np.float32)
+    _check(load().steps_cyl_surrogate_lanes(_ptr(p), _ptr(lanes), _ptr(shift)))
+    return lanes, shift
 
 
 def steps_cyl_set_tail(ctx, tail: int):

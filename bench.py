@@ -246,7 +246,7 @@ def run_reference(args, rank, world):
 
 
 def measured_peaks():
-    """The measured peaks of the GB300s (MEASURED_PEAKS.json), or None."""
+    """The measured copy-bandwidth and bf16 GEMM peaks of the GB300 (MEASURED_PEAKS.json), or None."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as fh:

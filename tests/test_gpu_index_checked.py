@@ -1,8 +1,8 @@
 """The symmetric kernels in the index-checked build (STEPS_DEBUG_INDEX=1: every
 computed index of their shared and global accesses checked against its buffer,
 an index outside recorded and clamped, the record folded into the device error
-word). compute-sanitizer is not available here, so this build stands in for
-it: every symmetric form (plain Kahan and plain sums, learned tail, correction
+word). Where compute-sanitizer cannot run, the index-checked library stands in
+for it: every symmetric form (plain Kahan and plain sums, learned tail, correction
 table with each read, the straight-run instances of both modelled tails on the
 production softening law, nearest-image table, infinite window, the symmetric
 sharded step of two emulated ranks) runs on ragged sizes, and each call must

@@ -180,8 +180,9 @@ int steps_cyl_last_timing(steps_cyl_ctx* ctx, double* pair_images, double* pair_
  * out[0] = pair-images delivered (as steps_cyl_last_timing), out[1] = pairs the
  * pair kernel evaluated, out[2] = its device time in ms, out[3] = 1 when it was
  * a symmetric kernel, 2 when that symmetric kernel was a modelled tail's
- * straight-run form (learned tail or residual table with near range n0 = 4 and
- * every h_i + h_j below L / 2; same values as the tiered form). The FP32 direct forms of an S1xR2 context whose rows are
+ * straight-run form (learned tail or residual table of a finite window with
+ * near range n0 = 4 and every h_i + h_j below L / 2; same values as the tiered
+ * form). The FP32 direct forms of an S1xR2 context whose rows are
  * not shared with other ranks evaluate each unordered pair of particles once
  * and add it to both (Newton's third law; the window of eq. ForceCylindrical is
  * symmetric in i and j), so out[1] is n (n - 1) / 2 plus the pairs inside each

@@ -1041,10 +1041,13 @@ double sym_pairs(const steps_cyl_ctx* c) {
 // The symmetric kernel of the form over the units [Ua, Ua + U) into F.
 // The symmetric table kernel in the context's table read (compiled per read, so
 // that the filtered CIC path carries none of the other reads' arithmetic).
-// The straight-run calls of the learned tail and of the residual tables: near
-// range n0 = 4, and every softening support within half a period (h_i + h_j <
-// L / 2), so that only the centre image of a pair can be softened.
-bool straight_run(const steps_cyl_ctx* c) { return c->p.n0 == 4 && 2.0 * c->h_max < 0.5 * c->p.L; }
+// The straight-run calls of the learned tail and of the residual tables: a
+// finite window, near range n0 = 4, and every softening support within half a
+// period (h_i + h_j < L / 2), so that only the centre image of a pair can be
+// softened. (The infinite window keeps the tiered calls.)
+bool straight_run(const steps_cyl_ctx* c) {
+  return !is_inf(c) && c->p.n0 == 4 && 2.0 * c->h_max < 0.5 * c->p.L;
+}
 
 template <bool KAHAN, bool INF>
 void launch_sym_table(steps_cyl_ctx* c, int C, int n, int nc, int NB, long long Ua, long long U, const FixAcc& F) {
